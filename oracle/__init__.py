@@ -1,0 +1,300 @@
+"""CPU oracle for the EDFFS decoder and hybrid GA (arXiv 1903.10741).
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference leg may import this package.  The product
+(``paper_1903_10741_gb300``) never does.  The arithmetic lives in ``ffs_oracle.c``
+(plain single-threaded C); this module compiles it with gcc and marshals arguments.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ffs_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "libffs_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ST_FREE, ST_EXEC, ST_DONE = 0, 1, 2
+ORDER_TOPO, ORDER_STAGE, ORDER_GIVEN = 0, 1, 2
+MACH_GENE, MACH_EARLIEST = 0, 1
+
+_i32p = C.POINTER(C.c_int32)
+
+
+class _Inst(C.Structure):
+    _fields_ = [("N", C.c_int32), ("g", C.c_int32), ("Qmax", C.c_int32), ("WT", C.c_int32),
+                ("RS", C.c_int32), ("o", _i32p), ("p", _i32p), ("q", _i32p), ("R", _i32p),
+                ("D", _i32p), ("status", _i32p), ("S0", _i32p), ("M0", _i32p)]
+
+
+class _Eval(C.Structure):
+    _fields_ = [("obj", C.c_int64), ("tard", C.c_int64), ("cmax", C.c_int32),
+                ("err", C.c_int32), ("probes", C.c_int64), ("span", C.c_int64)]
+
+
+class _GAParams(C.Structure):
+    _fields_ = [("P", C.c_int32), ("I", C.c_int32), ("tour_k", C.c_int32),
+                ("pc_num", C.c_int32), ("pc_den", C.c_int32), ("pm_num", C.c_int32),
+                ("pm_den", C.c_int32), ("order_mode", C.c_int32), ("mach_mode", C.c_int32),
+                ("migrate_every", C.c_int32), ("instance_id", C.c_int32), ("pad", C.c_int32),
+                ("seed", C.c_uint64)]
+
+
+class _GAState(C.Structure):
+    _fields_ = [("Y", C.c_void_p), ("X", C.c_void_p), ("obj", C.c_void_p), ("fit", C.c_void_p),
+                ("bY", C.c_void_p), ("bX", C.c_void_p), ("bobj", C.c_void_p), ("bfit", C.c_void_p),
+                ("emax", C.c_int64), ("gen", C.c_int32), ("K", C.c_int32)]
+
+
+def build(force: bool = False) -> str:
+    """Compile ffs_oracle.c into a shared library (gcc, -O2, no tuning flags)."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            return _LIB
+        os.makedirs(_LIB_DIR, exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-Wall",
+                               "-Wno-unused-function", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        L.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+        L.orc_draw.restype = C.c_uint32
+        L.orc_draw.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]
+        L.orc_classify.argtypes = [C.c_int32, C.c_int32, _i32p, _i32p, C.c_int32, _i32p]
+        L.orc_gene_count.restype = C.c_int32
+        L.orc_gene_count.argtypes = [C.POINTER(_Inst)]
+        L.orc_gene_map.argtypes = [C.POINTER(_Inst), _i32p, _i32p]
+        L.orc_decode.restype = C.c_int32
+        L.orc_decode.argtypes = [C.POINTER(_Inst), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, _i32p, _i32p, C.POINTER(_Eval)]
+        L.orc_objective.restype = C.c_int64
+        L.orc_objective.argtypes = [C.c_int32, _i32p, _i32p, C.c_int32, C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int32)]
+        L.orc_correct.argtypes = [C.c_int32, C.c_void_p]
+        L.orc_crossover.argtypes = [C.c_int32] + [C.c_void_p] * 4 + [C.c_int32, C.c_int32] + [C.c_void_p] * 4
+        L.orc_mutate.argtypes = [C.c_int32, _i32p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]
+        L.orc_ga_init.restype = C.c_int32
+        L.orc_ga_init.argtypes = [C.POINTER(_Inst), C.POINTER(_GAParams), C.POINTER(_GAState)]
+        L.orc_ga_step.restype = C.c_int32
+        L.orc_ga_step.argtypes = [C.POINTER(_Inst), C.POINTER(_GAParams), C.POINTER(_GAState)]
+        _lib = L
+    return _lib
+
+
+def _p32(a: np.ndarray):
+    return a.ctypes.data_as(_i32p)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+# ------------------------------------------------------------------ Philox
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def draw(seed: int, purpose: int, instance: int, gen: int, slot: int, d: int) -> int:
+    return int(lib().orc_draw(seed, purpose, instance, gen, slot, d))
+
+
+# ------------------------------------------------------------------ instance
+
+class Instance:
+    """An EDFFS instance at a rescheduling point, with the committed plan of frozen ops."""
+
+    def __init__(self, problem):
+        self.o = np.ascontiguousarray(problem.o, dtype=np.int32)
+        self.p = np.ascontiguousarray(problem.p, dtype=np.int32)
+        self.q = np.ascontiguousarray(problem.q, dtype=np.int32)
+        self.R = np.ascontiguousarray(problem.R, dtype=np.int32)
+        self.D = np.ascontiguousarray(problem.D, dtype=np.int32)
+        self.Qmax = int(problem.Qmax)
+        self.WT = int(problem.WT)
+        self.RS = 0
+        N, g = self.p.shape
+        self.status = np.zeros((N, g), dtype=np.int32)
+        self.S0 = np.zeros((N, g), dtype=np.int32)
+        self.M0 = np.zeros((N, g), dtype=np.int32)
+
+    @property
+    def N(self):
+        return int(self.p.shape[0])
+
+    @property
+    def g(self):
+        return int(self.p.shape[1])
+
+    def _c(self) -> _Inst:
+        for name in ("p", "status", "S0", "M0"):
+            setattr(self, name, np.ascontiguousarray(getattr(self, name), dtype=np.int32))
+        s = _Inst(self.N, self.g, self.Qmax, self.WT, self.RS, _p32(self.o), _p32(self.p),
+                  _p32(self.q), _p32(self.R), _p32(self.D), _p32(self.status), _p32(self.S0),
+                  _p32(self.M0))
+        return s
+
+    @property
+    def K(self) -> int:
+        c = self._c()
+        return int(lib().orc_gene_count(C.byref(c)))
+
+    def gene_map(self):
+        K = self.K
+        gj = np.zeros(max(K, 1), dtype=np.int32)
+        gs = np.zeros(max(K, 1), dtype=np.int32)
+        c = self._c()
+        lib().orc_gene_map(C.byref(c), _p32(gj), _p32(gs))
+        return gj[:K], gs[:K]
+
+    def gene_machines(self) -> np.ndarray:
+        _, gs = self.gene_map()
+        return self.o[gs]
+
+    def decode(self, y, x=None, order_mode=ORDER_STAGE, mach_mode=MACH_EARLIEST, given=None):
+        y = np.ascontiguousarray(y, dtype=np.int16)
+        K = self.K
+        x = np.zeros(K, dtype=np.int8) if x is None else np.ascontiguousarray(x, dtype=np.int8)
+        gv = None if given is None else np.ascontiguousarray(given, dtype=np.int32)
+        S = np.zeros((self.N, self.g), dtype=np.int32)
+        M = np.zeros((self.N, self.g), dtype=np.int32)
+        ev = _Eval()
+        c = self._c()
+        rc = lib().orc_decode(C.byref(c), order_mode, mach_mode, _ptr(y), _ptr(x), _ptr(gv),
+                              _p32(S), _p32(M), C.byref(ev))
+        if rc != 0:
+            raise ValueError(f"oracle decode rejected the chromosome (code {rc})")
+        return dict(S=S, M=M, obj=int(ev.obj), tard=int(ev.tard), cmax=int(ev.cmax),
+                    probes=int(ev.probes), span=int(ev.span))
+
+    def commit(self, S, M):
+        """Make (S, M) the plan being executed."""
+        self.S0 = np.ascontiguousarray(S, dtype=np.int32).copy()
+        self.M0 = np.ascontiguousarray(M, dtype=np.int32).copy()
+
+    def reschedule(self, arrivals, t_now: int):
+        """Freeze at t_now using the committed plan (Alg. 1), append the new jobs."""
+        if t_now < self.RS:
+            raise ValueError("t_now must not precede the previous rescheduling point")
+        st = np.zeros_like(self.status)
+        lib().orc_classify(self.N, self.g, _p32(self.p), _p32(self.S0), int(t_now), _p32(st))
+        n = arrivals.n
+        g = self.g
+        self.status = np.concatenate([st, np.zeros((n, g), np.int32)])
+        self.S0 = np.concatenate([self.S0, np.zeros((n, g), np.int32)])
+        self.M0 = np.concatenate([self.M0, np.zeros((n, g), np.int32)])
+        self.p = np.concatenate([self.p, arrivals.p.astype(np.int32)])
+        self.R = np.concatenate([self.R, arrivals.R.astype(np.int32)])
+        self.D = np.concatenate([self.D, arrivals.D.astype(np.int32)])
+        self.RS = int(t_now)
+
+
+def objective(C_j, D, WT):
+    C_j = np.ascontiguousarray(C_j, dtype=np.int32)
+    D = np.ascontiguousarray(D, dtype=np.int32)
+    t = C.c_int64()
+    cm = C.c_int32()
+    obj = lib().orc_objective(len(C_j), _p32(C_j), _p32(D), int(WT), C.byref(t), C.byref(cm))
+    return int(obj), int(t.value), int(cm.value)
+
+
+def correct(y):
+    y = np.ascontiguousarray(y, dtype=np.int16).copy()
+    lib().orc_correct(len(y), _ptr(y))
+    return y
+
+
+def crossover(ya, xa, yb, xb, cx, cy):
+    K = len(ya)
+    ya, yb = (np.ascontiguousarray(v, dtype=np.int16) for v in (ya, yb))
+    xa, xb = (np.ascontiguousarray(v, dtype=np.int8) for v in (xa, xb))
+    y0, y1 = np.zeros(K, np.int16), np.zeros(K, np.int16)
+    x0, x1 = np.zeros(K, np.int8), np.zeros(K, np.int8)
+    lib().orc_crossover(K, _ptr(ya), _ptr(xa), _ptr(yb), _ptr(xb), int(cx), int(cy),
+                        _ptr(y0), _ptr(x0), _ptr(y1), _ptr(x1))
+    return y0, x0, y1, x1
+
+
+def mutate(y, x, gene_o, xr, a, b):
+    y = np.ascontiguousarray(y, dtype=np.int16).copy()
+    x = np.ascontiguousarray(x, dtype=np.int8).copy()
+    go = np.ascontiguousarray(gene_o, dtype=np.int32)
+    xr = np.ascontiguousarray(xr, dtype=np.uint32)
+    lib().orc_mutate(len(y), _p32(go), _ptr(y), _ptr(x), _ptr(xr), int(a), int(b))
+    return y, x
+
+
+# ------------------------------------------------------------------ GA
+
+class GA:
+    """The hybrid GA run on the CPU, one generation at a time."""
+
+    def __init__(self, inst: Instance, P: int, island: int = 64, tour_k: int = 2,
+                 pc=(4, 5), pm=(1, 10), order_mode=ORDER_STAGE, mach_mode=MACH_EARLIEST,
+                 migrate_every: int = 10, seed: int = 1, instance_id: int = 0):
+        self.inst = inst
+        island = min(island, P)
+        self.par = _GAParams(P, island, tour_k, pc[0], pc[1], pm[0], pm[1], order_mode,
+                             mach_mode, migrate_every, instance_id, 0, seed)
+        K = inst.K
+        self.K = K
+        nisl = P // island
+        self.Y = np.zeros((P, max(K, 1)), np.int16)
+        self.X = np.zeros((P, max(K, 1)), np.int8)
+        self.obj = np.zeros(P, np.int64)
+        self.fit = np.zeros(P, np.int64)
+        self.bY = np.zeros((nisl, max(K, 1)), np.int16)
+        self.bX = np.zeros((nisl, max(K, 1)), np.int8)
+        self.bobj = np.zeros(nisl, np.int64)
+        self.bfit = np.zeros(nisl, np.int64)
+        self.st = _GAState(self.Y.ctypes.data, self.X.ctypes.data, self.obj.ctypes.data,
+                           self.fit.ctypes.data, self.bY.ctypes.data, self.bX.ctypes.data,
+                           self.bobj.ctypes.data, self.bfit.ctypes.data, 0, 0, K)
+        self._inst_c = None
+
+    def _ic(self):
+        self._inst_c = self.inst._c()
+        return self._inst_c
+
+    def init(self):
+        rc = lib().orc_ga_init(C.byref(self._ic()), C.byref(self.par), C.byref(self.st))
+        if rc:
+            raise RuntimeError(f"oracle GA init failed ({rc})")
+        return self
+
+    def step(self, n: int = 1):
+        for _ in range(n):
+            rc = lib().orc_ga_step(C.byref(self._ic()), C.byref(self.par), C.byref(self.st))
+            if rc:
+                raise RuntimeError(f"oracle GA step failed ({rc})")
+        return self
+
+    @property
+    def gen(self):
+        return int(self.st.gen)
+
+    @property
+    def emax(self):
+        return int(self.st.emax)
+
+    def best(self):
+        """Best-ever individual over all islands (largest fitness, lowest island)."""
+        i = int(np.argmax(self.bfit))
+        return self.bY[i, :self.K].copy(), self.bX[i, :self.K].copy(), int(self.bobj[i])

@@ -1,0 +1,417 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU)."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import MACH_EARLIEST, MACH_GENE, ORDER_GIVEN, ORDER_STAGE, ORDER_TOPO
+from paper_1903_10741_gb300 import workloads as wl
+from schedule_checks import check_greedy_earliest, check_invariants, stage_order
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ Philox
+
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces the published known-answer vectors (Salmon et al. 2011)."""
+    n = 0
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(t, 16) for t in line.split()]
+            out = oracle.philox4x32_10(v[0:4], v[4:6])
+            assert list(out) == v[6:10]
+            n += 1
+    assert n == 3
+
+
+def test_draw_counter_map():
+    """A draw is word d%4 of the block at counter (d/4, slot, gen, purpose<<24|instance)."""
+    seed = 0x1234_5678_9ABC_DEF0
+    for d in range(9):
+        blk = oracle.philox4x32_10([d >> 2, 7, 3, (4 << 24) | 5], [seed & 0xFFFFFFFF, seed >> 32])
+        assert oracle.draw(seed, 4, 5, 3, 7, d) == int(blk[d & 3])
+
+
+# ------------------------------------------------------------------ worked example
+
+def _worked_example():
+    ex = json.load(open(os.path.join(GOLDEN, "worked_example.json")))
+    n0, g = ex["n_original"], ex["g"]
+    pst = np.array(ex["p_per_stage"])
+    prob = wl.Problem(o=ex["o"], p=np.tile(pst, (n0, 1)), q=np.full(sum(ex["o"]), ex["q"]),
+                      R=ex["R"][:n0], D=np.full(n0, 10**6), Qmax=ex["Qmax"], WT=ex["WT"])
+    inst = oracle.Instance(prob)
+    inst.commit(np.array(ex["S_original"]), np.array(ex["M_original"]))
+    n1 = len(ex["R"]) - n0
+    inst.reschedule(wl.Arrivals(p=np.tile(pst, (n1, 1)), R=ex["R"][n0:], D=[10**6] * n1), ex["RS"])
+    return ex, inst
+
+
+def test_worked_example_classification():
+    """Alg. 1 first branch on Table 4 at RS = 7: r = 11 frozen ops, K = 13 genes, the
+    executing ops are exactly the Z = 0 cells and the completed ones the Z = C cells."""
+    ex, inst = _worked_example()
+    Z = ex["Z_printed"]
+    assert inst.K == ex["K"] == 8 * 3 - ex["r"]
+    for j in range(8):
+        for s in range(3):
+            want = {"C": oracle.ST_DONE, 0: oracle.ST_EXEC}.get(Z[j][s], oracle.ST_FREE)
+            assert inst.status[j, s] == want, (j, s)
+    # the -1 cells of X and Y are exactly the frozen ops
+    X, Y = np.array(ex["X"]), np.array(ex["Y"])
+    assert np.array_equal(X < 0, inst.status != oracle.ST_FREE)
+    assert np.array_equal(Y < 0, inst.status != oracle.ST_FREE)
+    # the free Y values are a permutation of 1..K (Eq. 11)
+    assert sorted(Y[Y > 0].tolist()) == list(range(1, ex["K"] + 1))
+
+
+def _example_genes(ex, inst):
+    gj, gs = inst.gene_map()
+    Y, X, Z = np.array(ex["Y"]), np.array(ex["X"]), ex["Z_printed"]
+    given = sorted(range(len(gj)), key=lambda k: Z[gj[k]][gs[k]])
+    return Y[gj, gs], X[gj, gs], given, gj, gs
+
+
+def test_worked_example_decode_printed_order():
+    """Alg. 2 on the printed Z: job 7 at stage 0 is delayed to 13.91, the completion of
+    job 5 at stage 2 on machine 4 (Sec. 4.3 narrative), and C_max = 20.42 (Fig. 8)."""
+    ex, inst = _worked_example()
+    y, x, given, gj, gs = _example_genes(ex, inst)
+    r = inst.decode(y, x, ORDER_GIVEN, MACH_GENE, given=given)
+    S, M = r["S"], r["M"]
+    assert S[7, 0] == ex["expect_job7_stage0_start"]
+    d = ex["expect_delay_until_end_of"]
+    assert d["global_machine"] == 2 * d["stage"] + M[d["job"], d["stage"]]
+    assert S[d["job"], d["stage"]] + inst.p[d["job"], d["stage"]] == S[7, 0]
+    assert r["cmax"] == ex["expect_cmax"]
+    check_invariants(inst, S, M, obj=r["obj"], tard=r["tard"], cmax=r["cmax"])
+    check_greedy_earliest(inst, given, S, M, any_machine=False)
+    # Without the power limit job 7 would have started when machine 0 freed (7.80).
+    assert S[7, 0] > 780
+
+
+def test_worked_example_topological_reading():
+    """The topological reading of Alg. 1 (largest y among ready job heads) gives the same
+    C_max as the printed Z on this example."""
+    ex, inst = _worked_example()
+    y, x, given, gj, gs = _example_genes(ex, inst)
+    r = inst.decode(y, x, ORDER_TOPO, MACH_GENE)
+    assert r["cmax"] == ex["expect_cmax"]
+    # Kahn order respects both pairwise rules of Alg. 1 wherever they do not conflict:
+    # within a job stages ascend; a ready head with larger y always goes first.
+    check_invariants(inst, r["S"], r["M"], obj=r["obj"], tard=r["tard"], cmax=r["cmax"])
+
+
+# ------------------------------------------------------------------ objective
+
+@pytest.mark.parametrize("wt,tard,cmax,obj", [
+    (0.01, 35.23, 40.54, 40.89), (0.1, 23.43, 40.78, 43.12), (0.4, 19.04, 41.14, 48.76),
+    (0.7, 18.61, 41.23, 54.26), (1, 18.29, 41.44, 59.73), (4, 17.83, 42.15, 113.46),
+    (7, 17.69, 42.18, 166.00), (10, 17.57, 42.12, 217.86), (100, 17.58, 42.39, 1800.43)])
+def test_objective_table11(wt, tard, cmax, obj):
+    """Eq. (1): objective = WT * total tardiness + C_max on rows of Table 11: the weight
+    multiplies the tardiness and the makespan is added unweighted.  Times are on a 1/100
+    grid and WT on a 1/100 grid, so obj_int = (100 WT) * (100 T) + 100 C_max * 100."""
+    scale = 100
+    # job 0 carries the whole tardiness; job 1 sets the makespan and is never late
+    C_j = np.array([int(round(tard * scale)), int(round(cmax * scale))], np.int32)
+    D = np.array([0, 10**8], np.int32)
+    wt_i = int(round(wt * 100))
+    o, t, cm = oracle.objective(C_j, D, wt_i)
+    assert t == C_j[0] and cm == C_j[1]
+    got = (o - cm) / (100 * scale) + cm / scale
+    # the table prints 100-run averages rounded to 0.01: T carries +-0.005 * WT
+    assert abs(got - obj) <= 0.005 * wt + 0.0051
+
+
+# ------------------------------------------------------------------ invariants
+
+def _random_problem(seed, N=8, g=3, o=(1, 3), p_hi=20, q=(1, 10), pct=55, release_hi=0):
+    rng = np.random.default_rng(seed)
+    return wl.random_instance(rng, N, g, o[0], o[1], p_hi, q[0], q[1], pct, release_hi=release_hi)
+
+
+@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("mode", [(ORDER_STAGE, MACH_EARLIEST), (ORDER_TOPO, MACH_GENE),
+                                  (ORDER_STAGE, MACH_GENE), (ORDER_TOPO, MACH_EARLIEST)])
+def test_decode_invariants_and_greedy(seed, mode):
+    """Every decoded schedule satisfies Eq. (2)-(10) and each op sits at its earliest
+    feasible slot given the ops before it (brute force over integer starts)."""
+    prob = _random_problem(seed, release_hi=30 if seed % 2 else 0)
+    inst = oracle.Instance(prob)
+    rng = np.random.default_rng(100 + seed)
+    Y, X = wl.random_chromosomes(rng, 4, inst.K, inst.gene_machines())
+    for y, x in zip(Y, X):
+        r = inst.decode(y, x, *mode)
+        check_invariants(inst, r["S"], r["M"], obj=r["obj"], tard=r["tard"], cmax=r["cmax"])
+        if mode[0] == ORDER_STAGE:
+            order = stage_order(inst, y)
+            check_greedy_earliest(inst, order, r["S"], r["M"], any_machine=mode[1] == MACH_EARLIEST)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_reschedule_chain_invariants(seed):
+    """Freeze at RS, append arrivals, decode again: frozen ops keep their plan, executing
+    ops keep their machine busy and draw power until they end, and no new op starts
+    before RS (Eq. 10)."""
+    rng = np.random.default_rng(seed)
+    prob = wl.random_instance(rng, 10, 4, 1, 3, 30, 5, 30, 50)
+    inst = oracle.Instance(prob)
+    r = inst.decode(np.arange(inst.K, 0, -1), None, ORDER_STAGE, MACH_EARLIEST)
+    for ev in range(3):
+        inst.commit(r["S"], r["M"])
+        t_now = int(r["cmax"] * (2 + ev) // 6)
+        inst.reschedule(wl.random_arrivals(rng, 3, inst.g, t_now, 30), t_now)
+        assert (inst.status[inst.N - 3:] == oracle.ST_FREE).all()
+        Y, X = wl.random_chromosomes(rng, 3, inst.K, inst.gene_machines())
+        for y in Y:
+            r = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST)
+            check_invariants(inst, r["S"], r["M"], obj=r["obj"], tard=r["tard"], cmax=r["cmax"])
+            check_greedy_earliest(inst, stage_order(inst, y), r["S"], r["M"], any_machine=True)
+
+
+def test_classify_boundaries():
+    """Alg. 1: S+P <= RS completed, S < RS < S+P executing, S >= RS free (half-open
+    operation intervals, Eq. 9)."""
+    p = np.array([[5, 5, 5]], np.int32)
+    inst = oracle.Instance(wl.Problem(o=[1, 1, 1], p=p, q=[1, 1, 1], R=[0], D=[0], Qmax=3))
+    inst.commit(np.array([[0, 5, 10]]), np.zeros((1, 3)))
+    inst.reschedule(wl.Arrivals(p=np.zeros((0, 3)), R=[], D=[]), 5)
+    assert inst.status.tolist() == [[oracle.ST_DONE, oracle.ST_FREE, oracle.ST_FREE]]
+    inst.commit(np.array([[0, 5, 10]]), np.zeros((1, 3)))
+    inst.reschedule(wl.Arrivals(p=np.zeros((0, 3)), R=[], D=[]), 6)
+    assert inst.status.tolist() == [[oracle.ST_DONE, oracle.ST_EXEC, oracle.ST_FREE]]
+
+
+# ------------------------------------------------------------------ closed forms
+
+def test_single_machine_closed_form():
+    """g = 1, o = 1, power not binding: ops run back to back in y-descending order, so
+    C_j is the prefix sum of p in that order and C_max = sum p."""
+    rng = np.random.default_rng(3)
+    N = 9
+    p = rng.integers(1, 30, size=(N, 1))
+    D = rng.integers(10, 150, size=N)
+    inst = oracle.Instance(wl.Problem(o=[1], p=p, q=[4], R=np.zeros(N), D=D, Qmax=10))
+    y = rng.permutation(N) + 1
+    r = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST)
+    seq = np.argsort(-y)
+    Cj = np.empty(N, np.int64)
+    Cj[seq] = np.cumsum(p[seq, 0])
+    assert r["cmax"] == p.sum()
+    assert r["tard"] == int(np.maximum(Cj - D, 0).sum())
+    assert r["obj"] == 100 * r["tard"] + r["cmax"]
+
+
+def test_power_serialises_everything():
+    """If Qmax equals every machine's power, only one op can run at any instant; with all
+    releases 0 the stage-by-stage decode leaves no idle time: C_max = sum of all p."""
+    rng = np.random.default_rng(5)
+    N, g = 7, 3
+    p = rng.integers(1, 15, size=(N, g))
+    inst = oracle.Instance(wl.Problem(o=[2, 3, 2], p=p, q=np.full(7, 6), R=np.zeros(N),
+                                      D=np.zeros(N), Qmax=6))
+    for seed in range(5):
+        y = np.random.default_rng(seed).permutation(inst.K) + 1
+        r = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST)
+        assert r["cmax"] == p.sum()
+
+
+def test_permutation_flow_shop_recursion():
+    """One machine per stage and power never binding: with y giving every stage the same
+    job sequence, C_max follows the textbook permutation flow shop recursion
+    C[k][s] = max(C[k-1][s], C[k][s-1]) + p."""
+    rng = np.random.default_rng(11)
+    N, g = 8, 4
+    p = rng.integers(1, 25, size=(N, g))
+    inst = oracle.Instance(wl.Problem(o=[1] * g, p=p, q=np.ones(g), R=np.zeros(N),
+                                      D=np.zeros(N), Qmax=g))
+    seq = rng.permutation(N)
+    rank = np.empty(N, np.int64)
+    rank[seq] = np.arange(N)
+    # y: larger for earlier jobs, identical job order at every stage
+    gj, gs = inst.gene_map()
+    y = (N - rank[gj]) * g - gs  # unique, same job order in each stage
+    y = np.argsort(np.argsort(y)) + 1
+    r = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST)
+    Cm = np.zeros((N + 1, g + 1), np.int64)
+    for k, j in enumerate(seq, start=1):
+        for s in range(1, g + 1):
+            Cm[k, s] = max(Cm[k - 1, s], Cm[k, s - 1]) + p[j, s - 1]
+    assert r["cmax"] == Cm[N, g]
+
+
+def test_parallel_list_scheduling_closed_form():
+    """One stage, o identical machines, power never binding: each op goes to the machine
+    that frees first (lowest index on ties), i.e. classic list scheduling."""
+    rng = np.random.default_rng(2)
+    N, o = 12, 3
+    p = rng.integers(1, 40, size=(N, 1))
+    inst = oracle.Instance(wl.Problem(o=[o], p=p, q=[1, 2, 3], R=np.zeros(N), D=np.zeros(N), Qmax=6))
+    y = rng.permutation(N) + 1
+    r = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST)
+    free = [0] * o
+    for j in np.argsort(-y):
+        m = min(range(o), key=lambda i: (free[i], i))
+        assert r["S"][j, 0] == free[m] and r["M"][j, 0] == m
+        free[m] += int(p[j, 0])
+
+
+# ------------------------------------------------------------------ brute force
+
+def _all_stage_orders(inst):
+    """Every chromosome that yields a distinct per-stage order (y up to stage-wise rank)."""
+    gj, gs = inst.gene_map()
+    K = len(gj)
+    stages = sorted(set(gs.tolist()))
+    per = [[k for k in range(K) if gs[k] == s] for s in stages]
+    for combo in itertools.product(*[itertools.permutations(v) for v in per]):
+        y = np.zeros(K, np.int64)
+        val = K
+        for seq in combo:
+            for k in seq:
+                y[k] = val
+                val -= 1
+        yield y
+
+
+def test_bruteforce_small_space_and_ga_reaches_it():
+    """N = 4, g = 2: enumerate all (4!)^2 per-stage orders; the GA's best is never below
+    the brute-force minimum and reaches it on this tiny space."""
+    rng = np.random.default_rng(21)
+    prob = wl.random_instance(rng, 4, 2, 2, 2, 20, 3, 9, 50)
+    inst = oracle.Instance(prob)
+    best = None
+    for y in _all_stage_orders(inst):
+        r = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST)
+        check_invariants(inst, r["S"], r["M"], obj=r["obj"])
+        best = r["obj"] if best is None else min(best, r["obj"])
+    ga = oracle.GA(inst, P=32, island=16, seed=3).init()
+    ga.step(60)
+    assert ga.bobj.min() >= best
+    assert ga.bobj.min() == best
+
+
+# ------------------------------------------------------------------ GA operators
+
+FIG11_A_X = [[-1, 1, 0], [-1, -1, 1], [1, 0, 1]]
+FIG11_A_Y = [[-1, 6, 1], [-1, -1, 5], [4, 3, 2]]
+FIG11_B_X = [[-1, 0, 0], [-1, -1, 0], [1, 1, 1]]
+FIG11_B_Y = [[-1, 3, 6], [-1, -1, 1], [4, 2, 5]]
+
+
+def _free(mat):
+    a = np.array(mat)
+    return a[a >= 0]
+
+
+def _unfree(vals, like):
+    a = np.array(like).copy()
+    a[a >= 0] = vals
+    return a.tolist()
+
+
+def test_crossover_fig11():
+    """Fig. 11: X cut after 2 free genes, Y cut after 1; child0 = head(A)+tail(B),
+    child1 = head(B)+tail(A); the later duplicate takes the missing value."""
+    y0, x0, y1, x1 = oracle.crossover(_free(FIG11_A_Y), _free(FIG11_A_X), _free(FIG11_B_Y),
+                                      _free(FIG11_B_X), cx=2, cy=1)
+    assert _unfree(x0, FIG11_A_X) == [[-1, 1, 0], [-1, -1, 0], [1, 1, 1]]
+    assert _unfree(y0, FIG11_A_Y) == [[-1, 6, 3], [-1, -1, 1], [4, 2, 5]]
+    assert _unfree(x1, FIG11_A_X) == [[-1, 0, 0], [-1, -1, 1], [1, 0, 1]]
+    assert _unfree(y1, FIG11_A_Y) == [[-1, 3, 1], [-1, -1, 5], [4, 6, 2]]
+
+
+def test_correction_several_duplicates():
+    """Duplicates, in scan order, take the missing values in ascending order."""
+    y = np.array([5, 2, 5, 1, 2, 5], np.int16)  # missing 3, 4, 6; dups at 2, 4, 5
+    assert oracle.correct(y).tolist() == [5, 2, 3, 1, 4, 6]
+
+
+def test_mutation_fig12():
+    """Fig. 12 with two machines per stage: every free x flips; y swaps the first and last
+    free genes (6 <-> 2)."""
+    x = _free(FIG11_A_X)
+    y = _free(FIG11_A_Y)
+    go = np.full(len(y), 2)
+    ym, xm = oracle.mutate(y, x, go, np.zeros(len(y), np.uint32), 0, len(y) - 1)
+    assert _unfree(xm, FIG11_A_X) == [[-1, 0, 1], [-1, -1, 0], [0, 1, 0]]
+    assert _unfree(ym, FIG11_A_Y) == [[-1, 2, 1], [-1, -1, 5], [4, 3, 6]]
+
+
+def test_mutation_never_keeps_machine():
+    """Each redraw lands on one of the other o-1 machines, all reachable."""
+    go = np.full(4, 5)
+    x = np.array([0, 2, 4, 3], np.int8)
+    seen = set()
+    for r in range(4):
+        _, xm = oracle.mutate(np.arange(1, 5), x, go, np.full(4, r, np.uint32), 0, 1)
+        assert (xm != x).all()
+        seen.add(tuple(xm.tolist()))
+    assert len(seen) == 4
+
+
+# ------------------------------------------------------------------ GA properties
+
+def test_ga_population_stays_valid_and_elitist():
+    """Every generation keeps each Y a permutation of 1..K, the best-ever objective never
+    rises, and each island holds its best-ever individual."""
+    prob = wl.static_small(1)
+    inst = oracle.Instance(prob)
+    ga = oracle.GA(inst, P=64, island=16, seed=7, migrate_every=5).init()
+    K = inst.K
+    prev = ga.bobj.copy()
+    for _ in range(30):
+        ga.step()
+        for row in ga.Y[:, :K]:
+            assert sorted(row.tolist()) == list(range(1, K + 1))
+        assert (ga.bobj <= prev).all()
+        prev = ga.bobj.copy()
+        for isl in range(4):
+            assert ga.obj[isl * 16:(isl + 1) * 16].min() <= ga.bobj[isl]
+        assert ((ga.fit == np.maximum(ga.emax - ga.obj, 0))).all()
+
+
+def test_ga_emax_rule():
+    """E_max = 10^a with the smallest a >= 1 such that every initial objective is below it
+    (Sec. 5)."""
+    inst = oracle.Instance(wl.static_small(1))
+    ga = oracle.GA(inst, P=64, seed=1).init()
+    mx = int(ga.obj.max())
+    assert ga.emax > mx and (ga.emax // 10 <= mx or ga.emax == 10)
+    assert str(ga.emax).strip("0") == "1"
+
+
+def test_ga_resume_is_bit_exact():
+    """The stream is counter based: 20 generations equal 10 + 10 from a copied state."""
+    inst = oracle.Instance(wl.static_small(2))
+    a = oracle.GA(inst, P=64, island=32, seed=9).init()
+    a.step(20)
+    b = oracle.GA(inst, P=64, island=32, seed=9).init()
+    b.step(10)
+    c = oracle.GA(inst, P=64, island=32, seed=9)
+    for name in ("Y", "X", "obj", "fit", "bY", "bX", "bobj", "bfit"):
+        getattr(c, name)[...] = getattr(b, name)
+    c.st.emax, c.st.gen = b.st.emax, b.st.gen
+    c.step(10)
+    for name in ("Y", "obj", "bY", "bobj"):
+        assert np.array_equal(getattr(a, name), getattr(c, name))
+
+
+def test_ga_paper_mode_runs():
+    """Paper mode (Kahn order, machine genes, local 5-neighbourhood selection) keeps X in
+    range and improves on the initial population."""
+    inst = oracle.Instance(wl.static_small(1))
+    ga = oracle.GA(inst, P=64, island=16, tour_k=0, order_mode=ORDER_TOPO, mach_mode=MACH_GENE,
+                   pc=(9, 10), seed=4).init()
+    first = int(ga.bobj.min())
+    ga.step(40)
+    gm = inst.gene_machines()
+    assert (ga.X[:, :inst.K] < gm[None, :]).all() and (ga.X >= 0).all()
+    assert int(ga.bobj.min()) <= first
