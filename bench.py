@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Throughput of exact chromosome decodes in the GPU hybrid GA on the dynamic rescheduling
+workload (predictive-reactive complete rescheduling, Sec. 4.1 of arXiv 1903.10741).
+
+One step = one whole rescheduling job: 50 initial jobs, 5 stages of U{2..4} identical
+machines, int32 processing times U{1..99}, powers U{5..30}, peak 55 % of the all-on
+power; the GA (population 1024 in islands of 64, tournament 2, crossover 0.8, mutation
+0.1, ring migration every 10) runs 500 generations on the initial problem and again after
+each of three events at t = 100, 250, 400 that freeze the executed plan and add 10 jobs.
+Every generation decodes the whole population exactly; the metric counts those decodes.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the single-threaded CPU
+oracle on a bounded sample of the same job.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1903_10741_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "exact chromosome decodes/sec"
+UNIT = "decodes/s"
+P, ISLAND, TOUR_K, PC, PM, MIGRATE, SEED = 1024, 64, 2, (4, 5), (1, 10), 10, 1
+WORKLOAD = ("dynamic rescheduling, plain GA: 50 initial jobs, 5 stages x U{2..4} identical machines, "
+            "p U{1..99}, q U{5..30} kW, peak 55% of all-on power; events at t=100,250,400 adding 10 jobs "
+            "(due = arrival + U[1.2,2.0] x work); complete reschedule at each event; population 1024 "
+            "(16 islands of 64), tournament 2, pc 0.8, pm 0.1, migration every 10; 500 generations per solve")
+# Algorithmic work of one exact decode on this job: per-instant power checks (Eq. 7) over
+# every machine of the op's stage plus profile updates (Eq. 8), averaged by the oracle over
+# its own GA trajectory of this job (python -m oracle.work_per_decode --generations 500
+# --every 50: 53232 / 62226 / 68630 / 75374 for the four solves, mean 64865).
+SLOTS_PER_DECODE = 64865.5
+# INT32 issue ceiling: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (lane-ops/s).
+ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev), "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        smax.append(float(parts[2]))
+                        power.append(float(parts[3]))
+                    except ValueError:
+                        continue
+                    for nm, v in zip(names, parts[5:9]):
+                        if v.lower() == "active":
+                            reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------------------------- helpers
+def aggregate(dist, decodes: float, seconds: float, device=None):
+    """Whole-job throughput over ranks: all ranks' decodes / the slowest rank's time."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return decodes, seconds
+    import torch
+    t = torch.tensor([decodes, seconds], dtype=torch.float64, device=device)
+    tot = t.clone()
+    dist.all_reduce(tot[0:1], op=dist.ReduceOp.SUM)
+    dist.all_reduce(tot[1:2], op=dist.ReduceOp.MAX)
+    return float(tot[0]), float(tot[1])
+
+
+def input_bytes(dyn) -> int:
+    pr = dyn.problem
+    b = sum(np.asarray(a, np.int32).nbytes for a in (pr.o, pr.p, pr.q, pr.R, pr.D))
+    for _, arr in dyn.events:
+        b += sum(np.asarray(a, np.int32).nbytes for a in (arr.p, arr.R, arr.D))
+    return b
+
+
+def run_job(ffs, inst, dyn, generations: int, stream, profile: bool, out_stats: dict):
+    """Initial solve + one solve per event on `inst`; returns exact decodes performed."""
+    decodes = 0
+    d2h = 0
+    for solve in range(len(dyn.events) + 1):
+        pop = ffs.Population(inst, P=P, island=ISLAND, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE,
+                             seed=SEED, instance_id=solve, stream=stream)
+        if profile:
+            pop.set_profiling(True)
+        res = pop.run(generations)
+        if profile:
+            ms, n = pop.profile()
+            out_stats["kernel_ms"] = out_stats.get("kernel_ms", 0.0) + ms
+            out_stats["kernel_launches"] = out_stats.get("kernel_launches", 0) + n
+        out_stats.setdefault("best_obj", []).append(res["obj"])
+        d2h += res["S"].nbytes + res["M"].nbytes + 20
+        decodes += P * (generations + 1) + 1
+        pop.close()
+        if solve < len(dyn.events):
+            t_now, arr = dyn.events[solve]
+            inst.reschedule(arr, t_now)
+    out_stats["d2h"] = d2h
+    return decodes
+
+
+def slots_per_decode() -> float:
+    return SLOTS_PER_DECODE
+
+
+# ----------------------------------------------------------------------------- ours
+def bench_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1903_10741_gb300 import ffs
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    ffs.lib()
+    stream = torch.cuda.current_stream(dev)
+    dyn = wl.dynamic_medium(1)
+    G = args.generations
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        run_job(ffs, ffs.Instance(dyn.problem), dyn, G, stream, False, {})
+    insts = [ffs.Instance(dyn.problem) for _ in range(args.steps)]  # inputs resident before timing
+    for inst in insts:
+        inst.decode(torch.ones((1, inst.K), dtype=torch.int16, device=dev) *
+                    torch.arange(1, inst.K + 1, dtype=torch.int16, device=dev))  # upload tables
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ffs.kernel_launches()
+    stats, total_ms, decodes = {}, 0.0, 0
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        decodes += run_job(ffs, insts[k], dyn, G, stream, True, stats)
+        e.record(stream)
+        e.synchronize()
+        total_ms += s.elapsed_time(e)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = ffs.kernel_launches() - launches0
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    tot_decodes, max_s = aggregate(dist if world > 1 else None, float(decodes), total_ms / 1e3, dev)
+
+    # end to end through the public API: host arrays in, host schedules out, per step
+    e2e_s, e2e_dec, e2e_stats = 0.0, 0, {}
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        inst = ffs.Instance(dyn.problem)
+        e2e_dec += run_job(ffs, inst, dyn, G, stream, False, e2e_stats)
+        torch.cuda.synchronize()
+        e2e_s += time.perf_counter() - t0
+        inst.close()
+    e2e_tot, e2e_max = aggregate(dist if world > 1 else None, float(e2e_dec), e2e_s, dev)
+
+    avg_launch_s = stats["kernel_ms"] / stats["kernel_launches"] / 1e3
+    achieved = slots_per_decode() * P / avg_launch_s / 1e12
+    line = {
+        "metric": METRIC, "value": tot_decodes / max_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "generations_per_solve": G, "solves_per_step": len(dyn.events) + 1,
+                   "decodes_per_step": decodes // args.steps, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "wall_s": t_wall, "best_objectives_last_step": stats["best_obj"][-(len(dyn.events) + 1):]},
+        "e2e": {"value": e2e_tot / e2e_max, "unit": UNIT, "h2d_bytes_per_step": input_bytes(dyn),
+                "d2h_bytes_per_step": e2e_stats["d2h"]},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "fused selection/crossover/mutation/decode generation kernel",
+                     "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS,
+                     "traffic": None, "avg_launch_us": avg_launch_s * 1e6,
+                     "work_per_launch": f"{slots_per_decode():.0f} slot checks/decode x {P} decodes"},
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle
+def _oracle_ga(dyn):
+    import oracle
+    inst = oracle.Instance(dyn.problem)
+    return oracle.GA(inst, P=P, island=ISLAND, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE,
+                     seed=SEED, instance_id=0).init()
+
+
+def cpu_baseline(seconds: float) -> dict:
+    """The oracle GA, single-threaded, on the initial solve of the same job for about
+    `seconds` of CPU time."""
+    dyn = wl.dynamic_medium(1)
+    t0 = time.perf_counter()
+    ga = _oracle_ga(dyn)
+    gens = 0
+    while time.perf_counter() - t0 < seconds:
+        ga.step()
+        gens += 1
+    dt = time.perf_counter() - t0
+    dec = P * (gens + 1)
+    return {"value": dec / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle GA on the initial solve (population {P}): init + {gens} generations, "
+                      f"{dec} exact decodes in {dt:.1f} s"}
+
+
+def bench_reference(args):
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    dyn = wl.dynamic_medium(1)
+    ga = _oracle_ga(dyn)
+    for _ in range(args.warmup):
+        ga.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ga.step(args.ref_generations)
+    dt = time.perf_counter() - t0
+    dec = P * args.ref_generations * args.steps
+    v = dec / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"{args.ref_generations} oracle GA generations per step "
+                                                   "on the initial solve"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} x {args.ref_generations} generations x {P} decodes"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--generations", type=int, default=500, help="GA generations per solve")
+    ap.add_argument("--ref-generations", type=int, default=2, help="oracle generations per reference step")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

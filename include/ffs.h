@@ -1,0 +1,223 @@
+/*
+ * ffs.h -- C ABI of the GB300 EDFFS library: decoding of priority chromosomes into
+ * energy-efficient flexible-flow-shop schedules and the priority-based hybrid parallel GA
+ * with predictive-reactive complete rescheduling, after Luo, Fujimura & El Baz,
+ * "GPU based Parallel Genetic Algorithm for Solving an Energy Efficient Dynamic Flexible
+ * Flow Shop Scheduling Problem" (arXiv 1903.10741).
+ *
+ * Conventions
+ *   - Every function returns FFS_OK (0) or a negative FFS_E_* code; ffs_strerror() names it.
+ *   - Times, processing times and powers are int32 >= 0; objectives are int64.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory of
+ *     the current device.  Inputs are copied at the call; the caller keeps ownership of
+ *     every array it passes.  Opaque handles are owned by the library until destroyed.
+ *   - A handle must not be used by two threads at once.
+ *   - Stream arguments are cudaStream_t values passed as void* (NULL = legacy stream).
+ *   - Matrices are row-major: op (j, s) of job j at stage s sits at index j * g + s.
+ *   - Machines are numbered per stage (0 .. o_s - 1); "global" machine numbers are
+ *     stage-major (stage 0's machines first).
+ *   - Genes are the free operations at the current rescheduling point, numbered job-major
+ *     then by stage (the row-major order of the X/Y matrices of Eq. (10)-(11) with their
+ *     -1 cells removed).  K is their count.
+ *
+ * Size limits (checked, FFS_E_ARG beyond them): jobs and genes <= 32767, stages and
+ * machines per stage <= 127, total machines <= 32767, processing time <= 32767, peak
+ * power <= 65535.
+ */
+#ifndef FFS_H
+#define FFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes */
+#define FFS_OK            0
+#define FFS_E_ARG        -1   /* invalid argument or size limit exceeded                 */
+#define FFS_E_INFEASIBLE -2   /* some machine's power exceeds the peak, or a stage has no machine */
+#define FFS_E_NOMEM      -3   /* device or host allocation failed                        */
+#define FFS_E_CUDA       -4   /* a CUDA call failed                                      */
+#define FFS_E_TIMEOUT    -5   /* a bounded device-side wait ran out                      */
+#define FFS_E_ADMISSION  -6   /* the service cannot admit the request                    */
+#define FFS_E_STATE      -7   /* call not valid in the handle's current state            */
+#define FFS_E_DEVICE     -8   /* a kernel reported an internal error (bad chromosome, overflow) */
+
+/* ---- decoding modes (Sec. 4.3) */
+#define FFS_ORDER_TOPO      0  /* Alg. 1: largest y among the next free op of every job   */
+#define FFS_ORDER_STAGE     1  /* stage by stage, y descending within a stage            */
+#define FFS_MACH_GENE       0  /* machine of op (j, s) is x_js, Eq. (10)                 */
+#define FFS_MACH_EARLIEST   1  /* machine with the earliest power-feasible start          */
+
+typedef struct ffs_instance ffs_instance;      /* opaque: problem + rescheduling state    */
+typedef struct ga_population ga_population;    /* opaque: device-resident GA state        */
+
+/* An EDFFS instance, Table 2 of the paper.  All arrays are host memory. */
+typedef struct {
+    int32_t n_jobs;                      /* n                                           */
+    int32_t n_stages;                    /* g                                           */
+    const int32_t *machines_per_stage;   /* [g]  o_s >= 1, identical parallel machines  */
+    const int32_t *proc;                 /* [n][g] P_js (the same on every machine of s) */
+    const int32_t *power;                /* [sum o_s] Q of each machine, stage-major     */
+    const int32_t *release;              /* [n]  R_j                                    */
+    const int32_t *due;                  /* [n]  D_j                                    */
+    int32_t peak_power;                  /* Q_max, Eq. (7)                              */
+    int32_t wt;                          /* WT, Eq. (1)                                 */
+} ffs_problem;
+
+/* New jobs J' arriving at a rescheduling point (Sec. 4.1).  Host arrays. */
+typedef struct {
+    int32_t job_count;                   /* n'                                          */
+    const int32_t *proc;                 /* [n'][g]                                     */
+    const int32_t *release;              /* [n']                                        */
+    const int32_t *due;                  /* [n']                                        */
+} ffs_arrivals;
+
+/* GA settings (Sec. 4.2, 4.4). */
+typedef struct {
+    int32_t pop;            /* population size P, even, a multiple of `island`         */
+    int32_t island;         /* island size (individuals per island), even              */
+    int32_t tournament_k;   /* tournament size within the island; 0 = best of the 5-cell
+                               neighbourhood on the sqrt(P) x sqrt(P) torus (P square)   */
+    int32_t pc_num, pc_den; /* crossover probability per pair                          */
+    int32_t pm_num, pm_den; /* mutation probability per individual                     */
+    int32_t order_mode;     /* FFS_ORDER_*                                             */
+    int32_t machine_mode;   /* FFS_MACH_*                                              */
+    int32_t migrate_every;  /* ring migration period in generations; 0 = none          */
+    int32_t instance_id;    /* 24-bit id mixed into every random stream                */
+    uint64_t seed;          /* Philox4x32-10 key                                       */
+    void *cuda_stream;      /* stream for every launch of this population              */
+} ga_params;
+
+/* Best schedule returned by ga_run. */
+typedef struct {
+    int64_t objective;        /* WT * sum_j T_j + C_max, Eq. (1)                      */
+    int64_t total_tardiness;  /* sum_j T_j, Eq. (2)                                   */
+    int32_t makespan;         /* C_max, Eq. (3)                                       */
+    int32_t n_ops;            /* n_jobs * n_stages of the current instance            */
+    int32_t *start;           /* host [n][g] S_js, or NULL; caller-allocated          */
+    int32_t *machine;         /* host [n][g] M_js (stage-local), or NULL              */
+} ffs_result;
+
+/* Sizes of an instance at its current rescheduling point. */
+typedef struct {
+    int32_t n_jobs, n_stages, n_machines, n_genes;  /* N, g, sum o_s, K              */
+    int32_t rs;                                     /* current rescheduling point     */
+    int32_t horizon;        /* length of the power profile past RS that bounds any schedule */
+    int32_t peak_power, wt;
+} ffs_info;
+
+/* ---------------------------------------------------------------- instances */
+
+/* Creates an instance from the problem statement of Sec. 3.2 (Table 2), with RS = 0 and
+ * every operation free.  Copies all inputs.  FFS_E_INFEASIBLE if some machine's power
+ * exceeds peak_power (no schedule can satisfy Eq. 7) or some stage has no machine. */
+int ffs_instance_create(const ffs_problem *problem, ffs_instance **out);
+
+/* Frees an instance and its device tables.  NULL is accepted. */
+int ffs_instance_destroy(ffs_instance *inst);
+
+/* Sizes of the instance at its current rescheduling point. */
+int ffs_instance_info(const ffs_instance *inst, ffs_info *info);
+
+/* Gene numbering: host arrays [K] receive the job and the stage of every free op. */
+int ffs_instance_genes(const ffs_instance *inst, int32_t *gene_job, int32_t *gene_stage);
+
+/* Per-op status at the current rescheduling point: host [n][g], 0 free, 1 being executed,
+ * 2 completed (Alg. 1, first branch). */
+int ffs_instance_status(const ffs_instance *inst, int32_t *status);
+
+/* Makes (start, machine) -- host [n][g], stage-local machines -- the plan being executed.
+ * Frozen ops must keep their committed values.  ga_run commits its best schedule itself. */
+int ffs_commit(ffs_instance *inst, const int32_t *start, const int32_t *machine);
+
+/* Predictive-reactive complete rescheduling (Sec. 4.1, Alg. 1): at t_now, every op of the
+ * committed plan with S + P <= t_now is completed, S < t_now < S + P is being executed
+ * (keeps its machine and power until it ends), S >= t_now is free again; the arriving
+ * jobs are appended with all stages free; genes are renumbered.  t_now must not precede
+ * the previous rescheduling point (FFS_E_ARG); a plan must have been committed unless
+ * every op is still free at t_now (FFS_E_STATE). */
+int ffs_reschedule(ffs_instance *inst, const ffs_arrivals *arrivals, int32_t t_now);
+
+/* ---------------------------------------------------------------- decoding */
+
+/* Decodes `count` chromosomes (Sec. 4.3, Alg. 1-2) and writes their objectives.
+ *   y    device [count][K] int16, each row a permutation of 1..K (larger = higher priority)
+ *   x    device [count][K] int8 stage-local machines (FFS_MACH_GENE), or NULL
+ *   obj  device [count] int64 Eq. (1);  tard device [count] int64 or NULL;
+ *   cmax device [count] int32 or NULL.
+ * Asynchronous on `stream`; FFS_E_DEVICE is reported by a later synchronising call if a
+ * row was not a permutation.  The kernel uses a device scratch buffer owned by the instance
+ * for chromosomes whose schedule outgrows shared memory. */
+int ffs_decode(ffs_instance *inst, int32_t order_mode, int32_t machine_mode,
+               const int16_t *y, const int8_t *x, int32_t count,
+               int64_t *obj, int64_t *tard, int32_t *cmax, void *stream);
+
+/* As ffs_decode, and also writes every schedule: start, machine device [count][n][g]
+ * (frozen ops carry their committed values). */
+int ffs_decode_schedule(ffs_instance *inst, int32_t order_mode, int32_t machine_mode,
+                        const int16_t *y, const int8_t *x, int32_t count,
+                        int64_t *obj, int32_t *start, int32_t *machine, void *stream);
+
+/* Synchronises `stream` and returns FFS_E_DEVICE if a decode since the last check met a
+ * malformed chromosome, FFS_OK otherwise (and clears the flag). */
+int ffs_decode_check(ffs_instance *inst, void *stream);
+
+/* ---------------------------------------------------------------- GA */
+
+/* Allocates the device-resident population for the instance's current genes and runs
+ * generation 0: random X (uniform machine) and Y (Fisher-Yates permutation) drawn from
+ * Philox4x32-10, decoding, E_max = 10^a above every initial objective (Sec. 5), fitness
+ * (Eq. 13) and the best-ever individual of every island. */
+int ga_population_create(ffs_instance *inst, const ga_params *params, ga_population **out);
+
+/* Frees a population.  NULL is accepted. */
+int ga_population_destroy(ga_population *pop);
+
+/* Runs `generations` generations (Sec. 4.4: selection, paired crossover with correction,
+ * mutation, decoding, elitist replacement per island, ring migration every
+ * migrate_every), continuing the generation counter, so two calls equal one longer call.
+ * Writes the best-ever schedule into *best (if not NULL) and commits it to the instance.
+ * Synchronises the population's stream. */
+int ga_run(ga_population *pop, int32_t generations, ffs_result *best);
+
+/* Copies the population state to host arrays (any may be NULL): Y [P][K], X [P][K],
+ * objective and fitness [P], island best-ever bY [P/island][K], bX, bobj, bfit
+ * [P/island], E_max and the generation counter. */
+int ga_population_read(ga_population *pop, int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit,
+                       int16_t *bY, int8_t *bX, int64_t *bobj, int64_t *bfit,
+                       int64_t *emax, int32_t *generation);
+
+/* Serialises the full GA state.  With buf == NULL, stores the required size in *len. */
+int ga_checkpoint(ga_population *pop, void *buf, size_t *len);
+
+/* Restores a state written by ga_checkpoint for the same instance and parameters.
+ * FFS_E_ARG if the buffer does not match or holds a chromosome that is not a permutation
+ * of 1..K with machines in range; FFS_E_STATE if the instance was rescheduled since the
+ * population was created. */
+int ga_restore(ga_population *pop, const void *buf, size_t len);
+
+/* Switches ga_run between replaying the captured generation graph (enable = 0, default)
+ * and launching each generation's kernels directly with a CUDA event pair on the
+ * population's stream around the fused selection/crossover/mutation/decode kernel, whose
+ * durations are summed.  Results are identical in both modes.  Resets the sums. */
+int ga_set_profiling(ga_population *pop, int32_t enable);
+
+/* Summed duration (milliseconds) and launch count of the fused generation kernel measured
+ * since profiling was enabled. */
+int ga_profile_read(ga_population *pop, double *kernel_ms, int64_t *launches);
+
+/* Number of kernels this library has launched in the process so far (graph replays count
+ * each kernel node).  For benchmark accounting. */
+int ffs_kernel_launches(uint64_t *count);
+
+/* Human-readable name of a status code. */
+const char *ffs_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFS_H */

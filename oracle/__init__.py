@@ -36,7 +36,8 @@ class _Inst(C.Structure):
 
 class _Eval(C.Structure):
     _fields_ = [("obj", C.c_int64), ("tard", C.c_int64), ("cmax", C.c_int32),
-                ("err", C.c_int32), ("probes", C.c_int64), ("span", C.c_int64)]
+                ("err", C.c_int32), ("probes", C.c_int64), ("span", C.c_int64),
+                ("slots", C.c_int64)]
 
 
 class _GAParams(C.Structure):
@@ -182,7 +183,7 @@ class Instance:
         if rc != 0:
             raise ValueError(f"oracle decode rejected the chromosome (code {rc})")
         return dict(S=S, M=M, obj=int(ev.obj), tard=int(ev.tard), cmax=int(ev.cmax),
-                    probes=int(ev.probes), span=int(ev.span))
+                    probes=int(ev.probes), span=int(ev.span), slots=int(ev.slots))
 
     def commit(self, S, M):
         """Make (S, M) the plan being executed."""

@@ -105,6 +105,9 @@ typedef struct {
     int32_t err;      /* 0 ok, <0 invalid input                        */
     int64_t probes;   /* time slots examined by the Eq. (7) checks     */
     int64_t span;     /* sum over ops of (start - t0 + p) on the chosen machine */
+    int64_t slots;    /* algorithmic work: for every op, sum over the machines tried of
+                         (earliest feasible start - earliest availability + p), plus p for
+                         the profile update: the instants an exact Eq. (7) check must read */
 } orc_eval;
 
 /* Alg. 1, first branch: classify every op of the executed plan at RS.
@@ -318,6 +321,7 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
                 if (bad < 0) break;
                 t = bad + 1;                             /* delayed past the violation */
             }
+            ev->slots += (int64_t)(t - t0) + pj;
             if (best_m < 0 || t < best_t) { best_t = t; best_m = m; best_t0 = t0; }
         }
         int32_t mg = moff[s] + best_m;
@@ -328,6 +332,7 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
         S_out[j * g + s] = best_t;
         M_out[j * g + s] = best_m;
         ev->span += (int64_t)(best_t - best_t0) + pj;
+        ev->slots += pj;
         placed[k] = 1;
     }
 

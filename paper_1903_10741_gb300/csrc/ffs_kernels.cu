@@ -1,0 +1,561 @@
+// ffs_kernels.cu -- EDFFS decode and GA kernels for sm_103a.
+//
+// Mapping: one warp per chromosome.  A CTA stages the instance tables (processing
+// times, powers, releases, due dates, gene map, initial power profile) into shared memory
+// with a single bulk copy; each warp then keeps its chromosome, per-job completion times,
+// per-machine free times and the power headroom profile of its schedule in its own slice
+// of shared memory.  The decoder's inner step scans 32 time slots per ballot.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <climits>
+#include <map>
+#include <mutex>
+
+#include "ffs_device.cuh"
+#include "ffs_kernels.cuh"
+
+namespace edffs {
+
+namespace {
+
+struct WarpPtrs {
+    uint16_t *h;
+    int32_t *C, *mfree;
+    int16_t *inv, *y;
+    int8_t *x;
+    uint32_t *bits;
+};
+
+__device__ __forceinline__ WarpPtrs warp_ptrs(char *tab, int blob_bytes, const Tabs &T, int Hcap,
+                                              bool ga, bool gprof, uint16_t *gscratch, int warp) {
+    const WarpLayout L = warp_layout(T.N, T.M, T.K, gprof ? 0 : Hcap, ga);
+    char *ws = tab + ((blob_bytes + 127) & ~127) + warp * L.bytes;
+    WarpPtrs w;
+    w.h = gprof ? gscratch + (size_t)(blockIdx.x * kWarpsPerBlock + warp) * (size_t)Hcap
+                : reinterpret_cast<uint16_t *>(ws + L.off_h);
+    w.C = reinterpret_cast<int32_t *>(ws + L.off_C);
+    w.mfree = reinterpret_cast<int32_t *>(ws + L.off_mfree);
+    w.inv = reinterpret_cast<int16_t *>(ws + L.off_inv);
+    w.y = reinterpret_cast<int16_t *>(ws + L.off_y);
+    w.x = reinterpret_cast<int8_t *>(ws + L.off_x);
+    w.bits = reinterpret_cast<uint32_t *>(ws + L.off_bits);
+    return w;
+}
+
+// Better individual: larger fitness, ties to the lower population index.
+__device__ __forceinline__ bool fitter(long long f, int i, long long bf, int bi) {
+    return f > bf || (f == bf && i < bi);
+}
+
+__device__ __forceinline__ void warp_best(long long &bf, int &bi) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const long long of = __shfl_xor_sync(kFull, bf, off);
+        const int oi = __shfl_xor_sync(kFull, bi, off);
+        if (fitter(of, oi, bf, bi)) {
+            bf = of;
+            bi = oi;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- decode kernel
+template <int ORDER, int MACH, bool GPROF>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_decode(DecodeArgs a) {
+    extern __shared__ __align__(128) char smem[];
+    char *tab = smem + 128;
+    if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
+    const Tabs T = tabs_view(tab);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, false, GPROF, a.gscratch, warp);
+    const int buf = a.gdev ? ((a.gdev->gen + 1) & 1) : 0;
+    const int n = a.list ? *a.list_count : a.count;
+    const int K = T.K, NG = T.N * T.g;
+    for (int c = blockIdx.x * kWarpsPerBlock + warp; c < n; c += gridDim.x * kWarpsPerBlock) {
+        const int idx = a.list ? a.list[c] : c;
+        const int16_t *yg = a.Y[buf] + (size_t)idx * K;
+        for (int k = lane; k < K; k += 32) w.y[k] = yg[k];
+        if (MACH == kMachGene) {
+            const int8_t *xg = a.X[buf] + (size_t)idx * K;
+            for (int k = lane; k < K; k += 32) w.x[k] = xg[k];
+        }
+        int32_t *S = a.S ? a.S + (size_t)idx * NG : nullptr;
+        int32_t *Mo = a.S ? a.Mo + (size_t)idx * NG : nullptr;
+        if (S) {
+            for (int i = lane; i < NG; i += 32)
+                if (a.status[i] != kStFree) {
+                    S[i] = a.S0[i];
+                    Mo[i] = a.M0[i];
+                }
+        }
+        __syncwarp();
+        const DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x, S, Mo, lane);
+        if (lane == 0) {
+            if (r.status == 1) {
+                if (GPROF) atomicOr(a.err, kErrOverflow);
+                else a.over_list[atomicAdd(a.over_count, 1)] = idx;
+            } else if (r.status == 2) {
+                atomicOr(a.err, kErrBadChromosome);
+                a.obj[buf][idx] = -1;
+            } else {
+                const long long o = (long long)T.WT * r.tard + r.cmax;
+                a.obj[buf][idx] = o;
+                if (a.tard) a.tard[idx] = r.tard;
+                if (a.cmax) a.cmax[idx] = r.cmax;
+                if (a.gdev) {
+                    const long long f = a.gdev->emax - o;
+                    a.fit[buf][idx] = f > 0 ? f : 0;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- GA: generation 0
+template <int ORDER, int MACH>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_init(GenArgs a) {
+    extern __shared__ __align__(128) char smem[];
+    char *tab = smem + 128;
+    if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
+    const Tabs T = tabs_view(tab);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, true, false, nullptr, warp);
+    const int K = T.K;
+    for (int i = blockIdx.x * kWarpsPerBlock + warp; i < a.P; i += gridDim.x * kWarpsPerBlock) {
+        // Fisher-Yates: step d swaps position K-1-d with a uniform position <= K-1-d.
+        int16_t *target = w.inv;
+        for (int d = lane; d < K - 1; d += 32) {
+            const uint32_t u = draw(a.seed, kPInitY, a.instance_id, 0, (uint32_t)i, (uint32_t)d);
+            target[d] = (int16_t)below(u, (uint32_t)(K - d));
+        }
+        for (int k = lane; k < K; k += 32) w.y[k] = (int16_t)(k + 1);
+        __syncwarp();
+        if (lane == 0) {
+            for (int d = 0; d < K - 1; ++d) {
+                const int pa = K - 1 - d, pb = target[d];
+                const int16_t t = w.y[pa];
+                w.y[pa] = w.y[pb];
+                w.y[pb] = t;
+            }
+        }
+        __syncwarp();
+        int16_t *yo = a.Y[0] + (size_t)i * K;
+        for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
+        if (MACH == kMachGene) {
+            int8_t *xo = a.X[0] + (size_t)i * K;
+            for (int k = lane; k < K; k += 32) {
+                const uint32_t u = draw(a.seed, kPInitX, a.instance_id, 0, (uint32_t)i, (uint32_t)k);
+                w.x[k] = (int8_t)below(u, (uint32_t)T.o[T.gstg[k]]);
+                xo[k] = w.x[k];
+            }
+        }
+        __syncwarp();
+        const DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x,
+                                                     nullptr, nullptr, lane);
+        if (lane == 0) {
+            if (r.status == 1) a.over_list[atomicAdd(&a.dev->nover, 1)] = i;
+            else if (r.status == 2) atomicOr(a.err, kErrBadChromosome);
+            else a.obj[0][i] = (long long)T.WT * r.tard + r.cmax;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- GA: one generation
+// Selection -> paired crossover + correction -> mutation -> decode, one child per warp.
+// Each warp recomputes both parents of its pair from the counter-based stream, so the
+// children of a pair are built independently by two warps.
+template <int ORDER, int MACH>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a) {
+    extern __shared__ __align__(128) char smem[];
+    char *tab = smem + 128;
+    if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
+    const Tabs T = tabs_view(tab);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, true, false, nullptr, warp);
+    const int K = T.K, I = a.I;
+    const int cur = a.dev->gen & 1, nx = cur ^ 1;
+    const uint32_t gen = (uint32_t)a.dev->gen + 1;
+    const long long emax = a.dev->emax;
+    const int16_t *Yc = a.Y[cur];
+    const int8_t *Xc = a.X[cur];
+    const int64_t *fc = a.fit[cur];
+
+    for (int i = blockIdx.x * kWarpsPerBlock + warp; i < a.P; i += gridDim.x * kWarpsPerBlock) {
+        const int pp = i >> 1;
+        int parent[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int slot = 2 * pp + t;
+            long long bf = LLONG_MIN;
+            int bi = INT_MAX;
+            if (a.tour_k > 0) {
+                if (lane < a.tour_k) {
+                    const int lo = (slot / I) * I;
+                    bi = lo + (int)below(draw(a.seed, kPSelect, a.instance_id, gen, (uint32_t)slot, (uint32_t)lane),
+                                         (uint32_t)I);
+                    bf = fc[bi];
+                }
+            } else if (lane < 5) {  // the cell and its N, S, W, E neighbours on the torus
+                const int sd = a.side, r = slot / sd, cc = slot % sd;
+                const int rr = lane == 1 ? (r + sd - 1) % sd : lane == 2 ? (r + 1) % sd : r;
+                const int c2 = lane == 3 ? (cc + sd - 1) % sd : lane == 4 ? (cc + 1) % sd : cc;
+                bi = rr * sd + c2;
+                bf = fc[bi];
+            }
+            warp_best(bf, bi);
+            parent[t] = bi;
+        }
+        const uint4 rc = stream_block(a.seed, kPCross, a.instance_id, gen, (uint32_t)pp, 0);
+        const bool cross = K >= 2 && (uint64_t)rc.x < a.pc_thr;
+        const int first = (i & 1) ? parent[1] : parent[0];
+        const int second = (i & 1) ? parent[0] : parent[1];
+        const int16_t *yf = Yc + (size_t)first * K, *yb = Yc + (size_t)second * K;
+        if (!cross) {
+            for (int k = lane; k < K; k += 32) w.y[k] = yf[k];
+            if (MACH == kMachGene)
+                for (int k = lane; k < K; k += 32) w.x[k] = Xc[(size_t)first * K + k];
+        } else {
+            const int cx = 1 + (int)below(rc.y, (uint32_t)(K - 1));
+            const int cy = 1 + (int)below(rc.z, (uint32_t)(K - 1));
+            const int nw = (K + 32) / 32;  // bitmap words covering values 0..K
+            for (int q = lane; q < nw; q += 32) w.bits[q] = 0;
+            __syncwarp();
+            for (int k = lane; k < cy; k += 32) {
+                const int v = yf[k];
+                w.y[k] = (int16_t)v;
+                atomicOr(&w.bits[v >> 5], 1u << (v & 31));
+            }
+            __syncwarp();
+            for (int k = cy + lane; k < K; k += 32) {  // tail values already in the head: duplicates
+                const int v = yb[k];
+                const bool dup = (w.bits[v >> 5] >> (v & 31)) & 1u;
+                w.y[k] = dup ? (int16_t)0 : (int16_t)v;
+            }
+            __syncwarp();
+            for (int k = cy + lane; k < K; k += 32) {
+                const int v = w.y[k];
+                if (v) atomicOr(&w.bits[v >> 5], 1u << (v & 31));
+            }
+            __syncwarp();
+            // Missing values, ascending, into `miss`.
+            int16_t *miss = w.inv;
+            int base = 0;
+            for (int q0 = 0; q0 < nw; q0 += 32) {
+                const int q = q0 + lane;
+                unsigned m = 0;
+                if (q < nw) {
+                    m = ~w.bits[q];
+                    if (q == 0) m &= ~1u;
+                    const int hi = K - q * 32;  // highest valid bit
+                    if (hi < 31) m &= hi >= 0 ? ((2u << hi) - 1u) : 0u;
+                }
+                const int cnt = __popc(m);
+                int incl = cnt;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int v = __shfl_up_sync(kFull, incl, off);
+                    if (lane >= off) incl += v;
+                }
+                int o = base + incl - cnt;
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    miss[o++] = (int16_t)(q * 32 + b);
+                }
+                base += __shfl_sync(kFull, incl, 31);
+            }
+            __syncwarp();
+            int rank = 0;
+            for (int k0 = cy; k0 < K; k0 += 32) {  // the r-th duplicate takes the r-th missing value
+                const int k = k0 + lane;
+                const bool dup = k < K && w.y[k] == 0;
+                const unsigned bm = __ballot_sync(kFull, dup);
+                if (dup) w.y[k] = miss[rank + __popc(bm & ((1u << lane) - 1u))];
+                rank += __popc(bm);
+            }
+            if (MACH == kMachGene)
+                for (int k = lane; k < K; k += 32)
+                    w.x[k] = k < cx ? Xc[(size_t)first * K + k] : Xc[(size_t)second * K + k];
+        }
+        __syncwarp();
+        const uint4 rm = stream_block(a.seed, kPMutate, a.instance_id, gen, (uint32_t)i, 0);
+        if ((uint64_t)rm.x < a.pm_thr) {
+            if (K >= 2 && lane == 0) {
+                const int ma = (int)below(rm.y, (uint32_t)K);
+                int mb = (int)below(rm.z, (uint32_t)(K - 1));
+                mb += mb >= ma;
+                const int16_t t = w.y[ma];
+                w.y[ma] = w.y[mb];
+                w.y[mb] = t;
+            }
+            if (MACH == kMachGene) {
+                for (int k = lane; k < K; k += 32) {
+                    const int o = T.o[T.gstg[k]];
+                    if (o >= 2) {
+                        const uint32_t u = draw(a.seed, kPMutate, a.instance_id, gen, (uint32_t)i, (uint32_t)(3 + k));
+                        const int r = (int)below(u, (uint32_t)(o - 1));
+                        w.x[k] = (int8_t)(r + (r >= w.x[k]));
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        int16_t *yo = a.Y[nx] + (size_t)i * K;
+        for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
+        if (MACH == kMachGene) {
+            int8_t *xo = a.X[nx] + (size_t)i * K;
+            for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
+        }
+        const DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x,
+                                                     nullptr, nullptr, lane);
+        if (lane == 0) {
+            if (r.status == 1) {
+                a.over_list[atomicAdd(&a.dev->nover, 1)] = i;
+            } else if (r.status == 2) {
+                atomicOr(a.err, kErrBadChromosome);
+            } else {
+                const long long o = (long long)T.WT * r.tard + r.cmax;
+                a.obj[nx][i] = o;
+                a.fit[nx][i] = emax - o > 0 ? emax - o : 0;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- GA: island bookkeeping
+constexpr int kReplThreads = 256;
+
+// Block-wide best (largest fitness, lowest index) and worst (smallest fitness, lowest index).
+__device__ void island_extremes(const int64_t *fit, int lo, int n, int &best, int &worst) {
+    __shared__ long long sbf[kReplThreads / 32], swf[kReplThreads / 32];
+    __shared__ int sbi[kReplThreads / 32], swi[kReplThreads / 32];
+    long long bf = LLONG_MIN, wf = LLONG_MAX;
+    int bi = INT_MAX, wi = INT_MAX;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const long long f = fit[lo + t];
+        if (fitter(f, lo + t, bf, bi)) { bf = f; bi = lo + t; }
+        if (f < wf || (f == wf && lo + t < wi)) { wf = f; wi = lo + t; }
+    }
+    warp_best(bf, bi);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const long long of = __shfl_xor_sync(kFull, wf, off);
+        const int oi = __shfl_xor_sync(kFull, wi, off);
+        if (of < wf || (of == wf && oi < wi)) { wf = of; wi = oi; }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sbf[warp] = bf; sbi[warp] = bi; swf[warp] = wf; swi[warp] = wi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            if (fitter(sbf[q], sbi[q], sbf[0], sbi[0])) { sbf[0] = sbf[q]; sbi[0] = sbi[q]; }
+            if (swf[q] < swf[0] || (swf[q] == swf[0] && swi[q] < swi[0])) { swf[0] = swf[q]; swi[0] = swi[q]; }
+        }
+    }
+    __syncthreads();
+    best = sbi[0];
+    worst = swi[0];
+    __syncthreads();
+}
+
+__device__ void copy_ind(int16_t *yd, int8_t *xd, const int16_t *ys, const int8_t *xs, int K) {
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        yd[k] = ys[k];
+        xd[k] = xs[k];
+    }
+}
+
+// E_max = 10^a, the smallest a >= 1 above every initial objective (Sec. 5); fitness Eq. (13).
+__global__ void k_emax(ReplArgs a) {
+    __shared__ long long smax[32];
+    long long mx = 0;
+    for (int i = threadIdx.x; i < a.P; i += blockDim.x) mx = max(mx, (long long)a.obj[0][i]);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, off));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) mx = max(mx, smax[q]);
+        long long e = 10;
+        while (e <= mx) e *= 10;
+        a.dev->emax = e;
+        smax[0] = e;
+    }
+    __syncthreads();
+    const long long e = smax[0];
+    for (int i = threadIdx.x; i < a.P; i += blockDim.x) {
+        const long long f = e - a.obj[0][i];
+        a.fit[0][i] = f > 0 ? f : 0;
+    }
+}
+
+// Elitist replacement (one CTA per island): the best-ever individual of the island is
+// updated from the children and overwrites the worst child.  At migration generations
+// the island's best and worst after replacement are recorded for the ring exchange.
+__global__ void __launch_bounds__(kReplThreads) k_replace(ReplArgs a) {
+    const int isl = blockIdx.x, lo = isl * a.I, K = a.K;
+    const int buf = a.init ? 0 : ((a.dev->gen + 1) & 1);
+    const int gen = a.dev->gen + 1;
+    int16_t *Y = a.Y[buf];
+    int8_t *X = a.X[buf];
+    int64_t *obj = a.obj[buf], *fit = a.fit[buf];
+    int best, worst;
+    island_extremes(fit, lo, a.I, best, worst);
+    const bool improve = a.init || fit[best] > a.bfit[isl];
+    __syncthreads();  // every thread has read bfit before thread 0 may overwrite it
+    if (improve) {
+        copy_ind(a.bY + (size_t)isl * K, a.bX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K);
+        if (threadIdx.x == 0) {
+            a.bobj[isl] = obj[best];
+            a.bfit[isl] = fit[best];
+        }
+    }
+    __syncthreads();
+    if (a.init) return;
+    copy_ind(Y + (size_t)worst * K, X + (size_t)worst * K, a.bY + (size_t)isl * K, a.bX + (size_t)isl * K, K);
+    if (threadIdx.x == 0) {
+        obj[worst] = a.bobj[isl];
+        fit[worst] = a.bfit[isl];
+    }
+    __syncthreads();
+    const int nisl = a.P / a.I;
+    if (a.migrate_every > 0 && gen % a.migrate_every == 0 && nisl > 1) {
+        island_extremes(fit, lo, a.I, best, worst);
+        copy_ind(a.mY + (size_t)isl * K, a.mX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K);
+        if (threadIdx.x == 0) {
+            a.mobj[isl] = obj[best];
+            a.mfit[isl] = fit[best];
+            a.mw[isl] = worst;
+        }
+    }
+}
+
+// Single-ring migration: island i's worst <- island (i-1)'s best, from the snapshot.
+__global__ void __launch_bounds__(kReplThreads) k_migrate(ReplArgs a) {
+    const int nisl = a.P / a.I, gen = a.dev->gen + 1;
+    if (!(a.migrate_every > 0 && gen % a.migrate_every == 0 && nisl > 1)) return;
+    const int isl = blockIdx.x, K = a.K, buf = (a.dev->gen + 1) & 1;
+    const int src = (isl + nisl - 1) % nisl, w = a.mw[isl];
+    copy_ind(a.Y[buf] + (size_t)w * K, a.X[buf] + (size_t)w * K, a.mY + (size_t)src * K, a.mX + (size_t)src * K, K);
+    if (threadIdx.x == 0) {
+        a.obj[buf][w] = a.mobj[src];
+        a.fit[buf][w] = a.mfit[src];
+    }
+}
+
+__global__ void k_advance(GADev *dev) {
+    dev->gen += 1;
+    dev->nover = 0;
+}
+
+// Raises a kernel's dynamic shared memory limit once per (kernel, size); later calls,
+// including those made while a stream is being captured, find it already set.
+std::mutex g_attr_mu;
+std::map<const void *, int> g_attr_smem;
+
+template <typename KernelT>
+cudaError_t prepare(KernelT kernel, int smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(g_attr_mu);
+    int &have = g_attr_smem[reinterpret_cast<const void *>(kernel)];
+    if (have >= smem) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) have = smem;
+    return e;
+}
+
+}  // namespace
+
+int cta_smem_bytes(const TabHeader &h, int Hcap, bool ga, bool global_profile) {
+    const WarpLayout L = warp_layout(h.N, h.M, h.K, global_profile ? 0 : Hcap, ga);
+    return 128 + ((h.bytes + 127) & ~127) + kWarpsPerBlock * L.bytes;
+}
+
+// Runs the body with O_/M_ bound to the (order, mach) pair of the enclosing scope.
+#define FFS_DISPATCH(...)                                                                        \
+    do {                                                                                         \
+        if (order == kOrderStage && mach == kMachEarliest) {                                     \
+            constexpr int O_ = kOrderStage, M_ = kMachEarliest;                                  \
+            __VA_ARGS__;                                                                         \
+        } else if (order == kOrderStage && mach == kMachGene) {                                  \
+            constexpr int O_ = kOrderStage, M_ = kMachGene;                                      \
+            __VA_ARGS__;                                                                         \
+        } else if (order == kOrderTopo && mach == kMachEarliest) {                               \
+            constexpr int O_ = kOrderTopo, M_ = kMachEarliest;                                   \
+            __VA_ARGS__;                                                                         \
+        } else {                                                                                 \
+            constexpr int O_ = kOrderTopo, M_ = kMachGene;                                       \
+            __VA_ARGS__;                                                                         \
+        }                                                                                        \
+    } while (0)
+
+cudaError_t launch_decode(int order, int mach, bool global_profile, const DecodeArgs &a,
+                          const TabHeader &h, int grid, cudaStream_t st) {
+    const int smem = cta_smem_bytes(h, a.Hcap, false, global_profile);
+    cudaError_t e = cudaSuccess;
+    FFS_DISPATCH({
+        if (global_profile) {
+            e = prepare(k_decode<O_, M_, true>, smem);
+            if (e == cudaSuccess) k_decode<O_, M_, true><<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
+        } else {
+            e = prepare(k_decode<O_, M_, false>, smem);
+            if (e == cudaSuccess) k_decode<O_, M_, false><<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
+        }
+    });
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_ga_init(int order, int mach, const GenArgs &a, const TabHeader &h, int grid,
+                           cudaStream_t st) {
+    const int smem = cta_smem_bytes(h, a.Hcap, true, false);
+    cudaError_t e = cudaSuccess;
+    FFS_DISPATCH({
+        e = prepare(k_ga_init<O_, M_>, smem);
+        if (e == cudaSuccess) k_ga_init<O_, M_><<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
+    });
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_ga_generation(int order, int mach, const GenArgs &a, const TabHeader &h,
+                                 int grid, cudaStream_t st) {
+    const int smem = cta_smem_bytes(h, a.Hcap, true, false);
+    cudaError_t e = cudaSuccess;
+    FFS_DISPATCH({
+        e = prepare(k_ga_generation<O_, M_>, smem);
+        if (e == cudaSuccess) k_ga_generation<O_, M_><<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
+    });
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t prepare_ga_generation(int order, int mach, const TabHeader &h, int Hcap) {
+    const int smem = cta_smem_bytes(h, Hcap, true, false);
+    cudaError_t e = cudaSuccess;
+    FFS_DISPATCH({ e = prepare(k_ga_generation<O_, M_>, smem); });
+    return e;
+}
+
+cudaError_t launch_emax(const ReplArgs &a, cudaStream_t st) {
+    k_emax<<<1, 1024, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_replace(const ReplArgs &a, cudaStream_t st) {
+    k_replace<<<a.P / a.I, kReplThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_migrate(const ReplArgs &a, cudaStream_t st) {
+    k_migrate<<<a.P / a.I, kReplThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(GADev *dev, cudaStream_t st) {
+    k_advance<<<1, 1, 0, st>>>(dev);
+    return cudaGetLastError();
+}
+
+}  // namespace edffs

@@ -1,0 +1,890 @@
+// ffs_runtime.cu -- host runtime behind the C ABI of include/ffs.h.
+//
+// An ffs_instance keeps the problem (Table 2), the committed plan and the classification
+// of every operation at the current rescheduling point (Alg. 1), and mirrors them on the
+// device as one table blob.  A ga_population keeps the GA state on the device; one
+// generation is five kernels (fused selection/crossover/mutation/decode, overflow
+// fallback decode, elitist replacement, migration, counter advance) captured once in a
+// CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ffs.h"
+#include "ffs_kernels.cuh"
+#include "ffs_layout.h"
+
+using namespace edffs;
+
+namespace {
+
+std::atomic<unsigned long long> g_launches{0};  // kernels issued by this library
+
+constexpr int kSmemBudget = 112 * 1024;  // per CTA: two CTAs of four warps per SM
+constexpr int kMinSmemSlots = 256;       // below this the shared-memory profile is not worth it
+constexpr int kMaxN = 32767, kMaxG = 127, kMaxO = 127, kMaxM = 32767, kMaxP = 32767, kMaxQ = 65535;
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+}
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+}  // namespace
+
+struct ffs_instance {
+    int N = 0, g = 0, M = 0, Qmax = 0, WT = 0, RS = 0;
+    std::vector<int32_t> o, moff, p, q, R, D;   // problem
+    std::vector<int32_t> status, S0, M0;       // plan and classification, [N*g]
+    bool has_plan = false;
+    bool dev_dirty = true;  // host tables or plan changed since the last upload
+    int K = 0, Hfull = 0;
+    std::vector<int32_t> gjob, gstg;
+    TabHeader hdr{};
+    std::vector<char> blob;
+    int version = 0;
+    // device mirrors
+    char *d_blob = nullptr;
+    size_t d_blob_cap = 0;
+    int32_t *d_S0 = nullptr, *d_M0 = nullptr, *d_status = nullptr;
+    size_t d_plan_cap = 0;
+    uint16_t *d_scratch = nullptr;  // global power profiles for the fallback decode
+    size_t d_scratch_cap = 0;
+    int32_t *d_over = nullptr;
+    size_t d_over_cap = 0;
+    int32_t *d_over_count = nullptr, *d_err = nullptr;
+
+    ~ffs_instance() {
+        dfree(d_blob);
+        dfree(d_S0);
+        dfree(d_M0);
+        dfree(d_status);
+        dfree(d_scratch);
+        dfree(d_over);
+        dfree(d_over_count);
+        dfree(d_err);
+    }
+};
+
+struct ga_population {
+    ffs_instance *inst = nullptr;
+    int version = 0;
+    ga_params par{};
+    cudaStream_t st = nullptr;
+    int P = 0, I = 0, K = 0, nisl = 0, side = 0;
+    int Hcap = 0, grid_gen = 0, grid_fb = 0;
+    TabHeader hdr{};
+    char *d_blob = nullptr;  // private copy of the instance tables at creation
+    int16_t *Y[2] = {nullptr, nullptr};
+    int8_t *X[2] = {nullptr, nullptr};
+    int64_t *obj[2] = {nullptr, nullptr}, *fit[2] = {nullptr, nullptr};
+    int16_t *bY = nullptr, *mY = nullptr;
+    int8_t *bX = nullptr, *mX = nullptr;
+    int64_t *bobj = nullptr, *bfit = nullptr, *mobj = nullptr, *mfit = nullptr;
+    int32_t *mw = nullptr, *over = nullptr, *err = nullptr;
+    GADev *dev = nullptr;
+    uint16_t *scratch = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool profiling = false;                 // eager launches with timed generation kernels
+    std::vector<cudaEvent_t> ev;            // event pairs, reused across ga_run calls
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0;
+
+    ~ga_population() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (graph) cudaGraphExecDestroy(graph);
+        dfree(d_blob);
+        for (int b = 0; b < 2; ++b) {
+            dfree(Y[b]);
+            dfree(X[b]);
+            dfree(obj[b]);
+            dfree(fit[b]);
+        }
+        dfree(bY); dfree(bX); dfree(bobj); dfree(bfit);
+        dfree(mY); dfree(mX); dfree(mobj); dfree(mfit); dfree(mw);
+        dfree(over); dfree(err); dfree(dev); dfree(scratch);
+    }
+};
+
+namespace {
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? FFS_OK : FFS_E_CUDA; }
+
+#define FFS_TRY(expr)                 \
+    do {                              \
+        const int rc_ = (expr);       \
+        if (rc_ != FFS_OK) return rc_; \
+    } while (0)
+#define FFS_CUDA(expr) FFS_TRY(cuda_rc(expr))
+
+// Rebuilds the gene map, the profile bound and the table blob, and uploads them.
+int rebuild(ffs_instance *in) {
+    const int N = in->N, g = in->g, M = in->M, RS = in->RS;
+    in->gjob.clear();
+    in->gstg.clear();
+    std::vector<int16_t> gfirst(N, -1);
+    std::vector<int8_t> gcnt(N, 0);
+    std::vector<int32_t> C0(N, 0), mfree0(M, RS);
+    long long base = RS, work = 0, exec_end = RS;
+    for (int j = 0; j < N; ++j) {
+        base = std::max<long long>(base, in->R[j]);
+        for (int s = 0; s < g; ++s) {
+            const int k = j * g + s;
+            if (in->status[k] == kStFree) {
+                if (gfirst[j] < 0) gfirst[j] = (int16_t)in->gjob.size();
+                gcnt[j]++;
+                in->gjob.push_back(j);
+                in->gstg.push_back(s);
+                work += in->p[k];
+            } else {
+                const int end = in->S0[k] + in->p[k];
+                C0[j] = end;  // frozen ops form a prefix of the job's stages
+                if (in->status[k] == kStExec) {
+                    const int mg = in->moff[s] + in->M0[k];
+                    mfree0[mg] = std::max(mfree0[mg], end);
+                    exec_end = std::max<long long>(exec_end, end);
+                }
+            }
+        }
+    }
+    base = std::max(base, exec_end);
+    const long long H = ((base - RS + work + 1) + 7) / 8 * 8;
+    if (H > INT32_MAX / 2 || (long long)RS + H > INT32_MAX) return FFS_E_ARG;
+    in->K = (int)in->gjob.size();
+    if (in->K > kMaxN) return FFS_E_ARG;
+    in->Hfull = (int)H;
+    const int E0 = (int)(exec_end - RS);
+    std::vector<uint16_t> h0(E0, (uint16_t)in->Qmax);
+    for (int j = 0; j < N; ++j)
+        for (int s = 0; s < g; ++s) {
+            const int k = j * g + s;
+            if (in->status[k] != kStExec) continue;
+            const int q = in->q[in->moff[s] + in->M0[k]];
+            for (int t = RS; t < in->S0[k] + in->p[k]; ++t) h0[t - RS] = (uint16_t)(h0[t - RS] - q);
+        }
+
+    TabHeader h{};
+    h.N = N; h.g = g; h.M = M; h.K = in->K;
+    h.RS = RS; h.Qmax = in->Qmax; h.WT = in->WT; h.H = in->Hfull; h.E0 = E0; h.maxo = 0;
+    for (int s = 0; s < g; ++s) h.maxo = std::max(h.maxo, in->o[s]);
+    int off = align16((int)sizeof(TabHeader));
+    auto take = [&](int32_t &field, int bytes) {
+        field = off;
+        off += align16(bytes);
+    };
+    take(h.off_o, 4 * g);
+    take(h.off_moff, 4 * (g + 1));
+    take(h.off_q, 4 * M);
+    take(h.off_p, 2 * N * g);
+    take(h.off_R, 4 * N);
+    take(h.off_D, 4 * N);
+    take(h.off_C0, 4 * N);
+    take(h.off_mfree0, 4 * M);
+    take(h.off_gjob, 2 * in->K);
+    take(h.off_gstg, in->K);
+    take(h.off_gfirst, 2 * N);
+    take(h.off_gcnt, N);
+    take(h.off_h0, 2 * E0);
+    h.bytes = off;
+    in->hdr = h;
+    in->blob.assign(off, 0);
+    char *b = in->blob.data();
+    std::memcpy(b, &h, sizeof(h));
+    std::memcpy(b + h.off_o, in->o.data(), 4 * g);
+    std::memcpy(b + h.off_moff, in->moff.data(), 4 * (g + 1));
+    std::memcpy(b + h.off_q, in->q.data(), 4 * M);
+    int16_t *pp = reinterpret_cast<int16_t *>(b + h.off_p);
+    for (int i = 0; i < N * g; ++i) pp[i] = (int16_t)in->p[i];
+    std::memcpy(b + h.off_R, in->R.data(), 4 * N);
+    std::memcpy(b + h.off_D, in->D.data(), 4 * N);
+    std::memcpy(b + h.off_C0, C0.data(), 4 * N);
+    std::memcpy(b + h.off_mfree0, mfree0.data(), 4 * M);
+    int16_t *gj = reinterpret_cast<int16_t *>(b + h.off_gjob);
+    int8_t *gs = reinterpret_cast<int8_t *>(b + h.off_gstg);
+    for (int k = 0; k < in->K; ++k) {
+        gj[k] = (int16_t)in->gjob[k];
+        gs[k] = (int8_t)in->gstg[k];
+    }
+    std::memcpy(b + h.off_gfirst, gfirst.data(), 2 * N);
+    std::memcpy(b + h.off_gcnt, gcnt.data(), N);
+    if (E0) std::memcpy(b + h.off_h0, h0.data(), 2 * E0);
+
+    in->dev_dirty = true;
+    in->version++;
+    return FFS_OK;
+}
+
+// Uploads the tables and the committed plan if the host copy changed since the last upload.
+int sync_device(ffs_instance *in) {
+    if (!in->dev_dirty) return FFS_OK;
+    const int off = in->hdr.bytes;
+    if ((size_t)off > in->d_blob_cap) {
+        dfree(in->d_blob);
+        FFS_CUDA(dalloc(&in->d_blob, (size_t)off));
+        in->d_blob_cap = off;
+    }
+    FFS_CUDA(cudaMemcpy(in->d_blob, in->blob.data(), off, cudaMemcpyHostToDevice));
+    const size_t NG = (size_t)in->N * in->g;
+    if (NG > in->d_plan_cap) {
+        dfree(in->d_S0);
+        dfree(in->d_M0);
+        dfree(in->d_status);
+        FFS_CUDA(dalloc(&in->d_S0, NG));
+        FFS_CUDA(dalloc(&in->d_M0, NG));
+        FFS_CUDA(dalloc(&in->d_status, NG));
+        in->d_plan_cap = NG;
+    }
+    FFS_CUDA(cudaMemcpy(in->d_S0, in->S0.data(), 4 * NG, cudaMemcpyHostToDevice));
+    FFS_CUDA(cudaMemcpy(in->d_M0, in->M0.data(), 4 * NG, cudaMemcpyHostToDevice));
+    FFS_CUDA(cudaMemcpy(in->d_status, in->status.data(), 4 * NG, cudaMemcpyHostToDevice));
+    if (!in->d_over_count) {
+        FFS_CUDA(dalloc(&in->d_over_count, 1));
+        FFS_CUDA(dalloc(&in->d_err, 1));
+        FFS_CUDA(cudaMemset(in->d_err, 0, 4));
+    }
+    in->dev_dirty = false;
+    return FFS_OK;
+}
+
+// Profile slots per warp that fit the shared-memory budget (0 if too few to be useful).
+int smem_slots(const TabHeader &h, bool ga) {
+    const int fixed = cta_smem_bytes(h, 0, ga, true);
+    const int per_warp = (kSmemBudget - fixed) / kWarpsPerBlock;
+    int slots = per_warp / 2 / 8 * 8;
+    if (slots < kMinSmemSlots) return 0;
+    return std::min(slots, h.H);
+}
+
+int ensure_scratch(uint16_t **p, size_t *cap, size_t elems) {
+    if (elems > *cap) {
+        dfree(*p);
+        FFS_CUDA(dalloc(p, elems));
+        *cap = elems;
+    }
+    return FFS_OK;
+}
+
+int check_modes(int32_t order_mode, int32_t machine_mode) {
+    if ((order_mode != FFS_ORDER_TOPO && order_mode != FFS_ORDER_STAGE) ||
+        (machine_mode != FFS_MACH_GENE && machine_mode != FFS_MACH_EARLIEST))
+        return FFS_E_ARG;
+    return FFS_OK;
+}
+
+int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y, const int8_t *x,
+                int32_t count, int64_t *obj, int64_t *tard, int32_t *cmax, int32_t *S, int32_t *Mo,
+                cudaStream_t st) {
+    FFS_TRY(check_modes(order, mach));
+    if (count < 0 || (count > 0 && (!y || !obj)) || (mach == FFS_MACH_GENE && count > 0 && !x)) return FFS_E_ARG;
+    if (count == 0) return FFS_OK;
+    FFS_TRY(sync_device(in));
+    const TabHeader &h = in->hdr;
+    DecodeArgs a{};
+    a.blob = in->d_blob;
+    a.blob_bytes = h.bytes;
+    a.Y[0] = a.Y[1] = y;
+    a.X[0] = a.X[1] = x;
+    a.count = count;
+    a.obj[0] = a.obj[1] = obj;
+    a.tard = tard;
+    a.cmax = cmax;
+    a.S = S;
+    a.Mo = Mo;
+    a.S0 = in->d_S0;
+    a.M0 = in->d_M0;
+    a.status = in->d_status;
+    a.err = in->d_err;
+    const int slots = smem_slots(h, false);
+    const int sms = num_sms();
+    if (slots > 0) {
+        if ((size_t)count > in->d_over_cap) {
+            dfree(in->d_over);
+            FFS_CUDA(dalloc(&in->d_over, (size_t)count));
+            in->d_over_cap = count;
+        }
+        FFS_CUDA(cudaMemsetAsync(in->d_over_count, 0, 4, st));
+        a.Hcap = slots;
+        a.over_list = in->d_over;
+        a.over_count = in->d_over_count;
+        const int per_sm = std::max(1, (228 * 1024) / (cta_smem_bytes(h, slots, false, false) + 1024));
+        const int grid = std::max(1, std::min((count + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * per_sm));
+        FFS_CUDA(launch_decode(order, mach, false, a, h, grid, st));
+        g_launches += 1;
+        if (slots >= h.H) return FFS_OK;  // the profile bound fits: nothing can overflow
+        a.list = in->d_over;
+        a.list_count = in->d_over_count;
+    }
+    // Global-memory profiles: the whole bound per warp.
+    const int grid = std::max(1, std::min((count + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * 2));
+    FFS_TRY(ensure_scratch(&in->d_scratch, &in->d_scratch_cap, (size_t)grid * kWarpsPerBlock * h.H));
+    a.gscratch = in->d_scratch;
+    a.Hcap = h.H;
+    g_launches += 1;
+    return cuda_rc(launch_decode(order, mach, true, a, h, grid, st));
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char *ffs_strerror(int code) {
+    switch (code) {
+        case FFS_OK: return "ok";
+        case FFS_E_ARG: return "invalid argument";
+        case FFS_E_INFEASIBLE: return "infeasible instance (machine power above the peak, or an empty stage)";
+        case FFS_E_NOMEM: return "out of memory";
+        case FFS_E_CUDA: return "CUDA error";
+        case FFS_E_TIMEOUT: return "device wait timed out";
+        case FFS_E_ADMISSION: return "request not admitted";
+        case FFS_E_STATE: return "call not valid in the current state";
+        case FFS_E_DEVICE: return "kernel reported an error";
+        default: return "unknown status";
+    }
+}
+
+int ffs_instance_create(const ffs_problem *pr, ffs_instance **out) {
+    if (!pr || !out) return FFS_E_ARG;
+    *out = nullptr;
+    const int N = pr->n_jobs, g = pr->n_stages;
+    if (N < 1 || N > kMaxN || g < 1 || g > kMaxG || !pr->machines_per_stage || !pr->proc || !pr->power ||
+        !pr->release || !pr->due || pr->peak_power < 0 || pr->peak_power > kMaxQ || pr->wt < 0)
+        return FFS_E_ARG;
+    int M = 0;
+    for (int s = 0; s < g; ++s) {
+        const int o = pr->machines_per_stage[s];
+        if (o < 1) return FFS_E_INFEASIBLE;
+        if (o > kMaxO) return FFS_E_ARG;
+        M += o;
+    }
+    if (M > kMaxM) return FFS_E_ARG;
+    for (int i = 0; i < N * g; ++i)
+        if (pr->proc[i] < 0 || pr->proc[i] > kMaxP) return FFS_E_ARG;
+    for (int m = 0; m < M; ++m) {
+        if (pr->power[m] < 0) return FFS_E_ARG;
+        if (pr->power[m] > pr->peak_power) return FFS_E_INFEASIBLE;
+    }
+    for (int j = 0; j < N; ++j)
+        if (pr->release[j] < 0) return FFS_E_ARG;
+    ffs_instance *in = new (std::nothrow) ffs_instance();
+    if (!in) return FFS_E_NOMEM;
+    in->N = N; in->g = g; in->M = M; in->Qmax = pr->peak_power; in->WT = pr->wt; in->RS = 0;
+    in->o.assign(pr->machines_per_stage, pr->machines_per_stage + g);
+    in->moff.assign(g + 1, 0);
+    for (int s = 0; s < g; ++s) in->moff[s + 1] = in->moff[s] + in->o[s];
+    in->p.assign(pr->proc, pr->proc + N * g);
+    in->q.assign(pr->power, pr->power + M);
+    in->R.assign(pr->release, pr->release + N);
+    in->D.assign(pr->due, pr->due + N);
+    in->status.assign(N * g, kStFree);
+    in->S0.assign(N * g, 0);
+    in->M0.assign(N * g, 0);
+    const int rc = rebuild(in);
+    if (rc != FFS_OK) {
+        delete in;
+        return rc;
+    }
+    *out = in;
+    return FFS_OK;
+}
+
+int ffs_instance_destroy(ffs_instance *in) {
+    delete in;
+    return FFS_OK;
+}
+
+int ffs_instance_info(const ffs_instance *in, ffs_info *info) {
+    if (!in || !info) return FFS_E_ARG;
+    info->n_jobs = in->N;
+    info->n_stages = in->g;
+    info->n_machines = in->M;
+    info->n_genes = in->K;
+    info->rs = in->RS;
+    info->horizon = in->Hfull;
+    info->peak_power = in->Qmax;
+    info->wt = in->WT;
+    return FFS_OK;
+}
+
+int ffs_instance_genes(const ffs_instance *in, int32_t *gene_job, int32_t *gene_stage) {
+    if (!in || (in->K > 0 && (!gene_job || !gene_stage))) return FFS_E_ARG;
+    for (int k = 0; k < in->K; ++k) {
+        gene_job[k] = in->gjob[k];
+        gene_stage[k] = in->gstg[k];
+    }
+    return FFS_OK;
+}
+
+int ffs_instance_status(const ffs_instance *in, int32_t *status) {
+    if (!in || !status) return FFS_E_ARG;
+    std::memcpy(status, in->status.data(), sizeof(int32_t) * in->status.size());
+    return FFS_OK;
+}
+
+int ffs_commit(ffs_instance *in, const int32_t *start, const int32_t *machine) {
+    if (!in || !start || !machine) return FFS_E_ARG;
+    const int NG = in->N * in->g;
+    for (int i = 0; i < NG; ++i) {
+        const int s = i % in->g;
+        if (machine[i] < 0 || machine[i] >= in->o[s] || start[i] < 0) return FFS_E_ARG;
+        if (in->status[i] != kStFree && (start[i] != in->S0[i] || machine[i] != in->M0[i])) return FFS_E_ARG;
+        if (in->status[i] == kStFree && start[i] < in->RS) return FFS_E_ARG;
+    }
+    std::memcpy(in->S0.data(), start, 4 * (size_t)NG);
+    std::memcpy(in->M0.data(), machine, 4 * (size_t)NG);
+    in->has_plan = true;
+    in->dev_dirty = true;
+    return FFS_OK;
+}
+
+int ffs_reschedule(ffs_instance *in, const ffs_arrivals *arr, int32_t t_now) {
+    if (!in || t_now < in->RS) return FFS_E_ARG;
+    const int n1 = arr ? arr->job_count : 0;
+    if (n1 < 0 || in->N + n1 > kMaxN || (n1 > 0 && (!arr->proc || !arr->release || !arr->due))) return FFS_E_ARG;
+    for (int i = 0; i < n1 * in->g; ++i)
+        if (arr->proc[i] < 0 || arr->proc[i] > kMaxP) return FFS_E_ARG;
+    for (int j = 0; j < n1; ++j)
+        if (arr->release[j] < 0) return FFS_E_ARG;
+    if (!in->has_plan && t_now != in->RS) return FFS_E_STATE;
+    const int g = in->g;
+    if (in->has_plan) {
+        // Alg. 1: S + P <= RS completed, S < RS < S + P being executed, otherwise free.
+        for (int i = 0; i < in->N * g; ++i) {
+            const int st = in->S0[i], en = in->S0[i] + in->p[i];
+            in->status[i] = en <= t_now ? kStDone : st < t_now ? kStExec : kStFree;
+        }
+    }
+    for (int j = 0; j < n1; ++j) {
+        for (int s = 0; s < g; ++s) {
+            in->p.push_back(arr->proc[j * g + s]);
+            in->status.push_back(kStFree);
+            in->S0.push_back(0);
+            in->M0.push_back(0);
+        }
+        in->R.push_back(arr->release[j]);
+        in->D.push_back(arr->due[j]);
+    }
+    in->N += n1;
+    in->RS = t_now;
+    in->has_plan = false;
+    return rebuild(in);
+}
+
+int ffs_decode(ffs_instance *in, int32_t order_mode, int32_t machine_mode, const int16_t *y,
+               const int8_t *x, int32_t count, int64_t *obj, int64_t *tard, int32_t *cmax, void *stream) {
+    if (!in) return FFS_E_ARG;
+    return decode_impl(in, order_mode, machine_mode, y, x, count, obj, tard, cmax, nullptr, nullptr,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int ffs_decode_schedule(ffs_instance *in, int32_t order_mode, int32_t machine_mode, const int16_t *y,
+                        const int8_t *x, int32_t count, int64_t *obj, int32_t *start, int32_t *machine,
+                        void *stream) {
+    if (!in || (count > 0 && (!start || !machine))) return FFS_E_ARG;
+    return decode_impl(in, order_mode, machine_mode, y, x, count, obj, nullptr, nullptr, start, machine,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int ffs_decode_check(ffs_instance *in, void *stream) {
+    if (!in) return FFS_E_ARG;
+    FFS_TRY(sync_device(in));
+    FFS_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int32_t e = 0;
+    FFS_CUDA(cudaMemcpy(&e, in->d_err, 4, cudaMemcpyDeviceToHost));
+    FFS_CUDA(cudaMemset(in->d_err, 0, 4));
+    if (e & kErrTimeout) return FFS_E_TIMEOUT;
+    return e ? FFS_E_DEVICE : FFS_OK;
+}
+
+// ---------------------------------------------------------------- GA
+
+static int ga_replace_args(ga_population *pp, ReplArgs *r, int init) {
+    *r = ReplArgs{};
+    for (int b = 0; b < 2; ++b) {
+        r->Y[b] = pp->Y[b];
+        r->X[b] = pp->X[b];
+        r->obj[b] = pp->obj[b];
+        r->fit[b] = pp->fit[b];
+    }
+    r->bY = pp->bY; r->bX = pp->bX; r->bobj = pp->bobj; r->bfit = pp->bfit;
+    r->mY = pp->mY; r->mX = pp->mX; r->mobj = pp->mobj; r->mfit = pp->mfit; r->mw = pp->mw;
+    r->dev = pp->dev;
+    r->P = pp->P; r->I = pp->I; r->K = pp->K;
+    r->migrate_every = pp->par.migrate_every;
+    r->init = init;
+    return FFS_OK;
+}
+
+static void ga_gen_args(ga_population *pp, GenArgs *a) {
+    *a = GenArgs{};
+    a->blob = pp->d_blob;
+    a->blob_bytes = pp->hdr.bytes;
+    a->Hcap = pp->Hcap;
+    for (int b = 0; b < 2; ++b) {
+        a->Y[b] = pp->Y[b];
+        a->X[b] = pp->X[b];
+        a->obj[b] = pp->obj[b];
+        a->fit[b] = pp->fit[b];
+    }
+    a->dev = pp->dev;
+    a->P = pp->P;
+    a->I = pp->I;
+    a->tour_k = pp->par.tournament_k;
+    a->side = pp->side;
+    a->pc_thr = ((uint64_t)(uint32_t)pp->par.pc_num << 32) / (uint64_t)(uint32_t)pp->par.pc_den;
+    a->pm_thr = ((uint64_t)(uint32_t)pp->par.pm_num << 32) / (uint64_t)(uint32_t)pp->par.pm_den;
+    a->instance_id = (uint32_t)pp->par.instance_id & 0xFFFFFFu;
+    a->seed = pp->par.seed;
+    a->over_list = pp->over;
+    a->err = pp->err;
+}
+
+static void ga_fallback_args(ga_population *pp, DecodeArgs *d, bool ga_mode) {
+    *d = DecodeArgs{};
+    d->blob = pp->d_blob;
+    d->blob_bytes = pp->hdr.bytes;
+    d->Hcap = pp->hdr.H;
+    for (int b = 0; b < 2; ++b) {
+        d->Y[b] = pp->Y[b];
+        d->X[b] = pp->X[b];
+        d->obj[b] = pp->obj[b];
+        d->fit[b] = pp->fit[b];
+    }
+    d->list = pp->over;
+    d->list_count = &pp->dev->nover;
+    d->gdev = ga_mode ? pp->dev : nullptr;
+    d->gscratch = pp->scratch;
+    d->err = pp->err;
+}
+
+// One generation: fused operators + decode, fallback decode, replacement, migration, advance.
+// With timing events, the fused kernel is bracketed by ev0/ev1 on the population's stream.
+static int ga_enqueue_generation(ga_population *pp, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
+    const int order = pp->par.order_mode, mach = pp->par.machine_mode;
+    GenArgs a;
+    ga_gen_args(pp, &a);
+    if (ev0) FFS_CUDA(cudaEventRecord(ev0, pp->st));
+    FFS_CUDA(launch_ga_generation(order, mach, a, pp->hdr, pp->grid_gen, pp->st));
+    if (ev1) FFS_CUDA(cudaEventRecord(ev1, pp->st));
+    DecodeArgs d;
+    ga_fallback_args(pp, &d, true);
+    FFS_CUDA(launch_decode(order, mach, true, d, pp->hdr, pp->grid_fb, pp->st));
+    ReplArgs r;
+    ga_replace_args(pp, &r, 0);
+    FFS_CUDA(launch_replace(r, pp->st));
+    FFS_CUDA(launch_migrate(r, pp->st));
+    FFS_CUDA(launch_advance(pp->dev, pp->st));
+    return FFS_OK;
+}
+
+int ga_population_create(ffs_instance *in, const ga_params *par, ga_population **out) {
+    if (!in || !par || !out) return FFS_E_ARG;
+    *out = nullptr;
+    FFS_TRY(check_modes(par->order_mode, par->machine_mode));
+    const int P = par->pop, I = par->island;
+    if (P < 2 || P % 2 || I < 2 || I % 2 || P % I || par->tournament_k < 0 || par->tournament_k > 32 ||
+        par->pc_den <= 0 || par->pm_den <= 0 || par->pc_num < 0 || par->pm_num < 0 ||
+        par->pc_num > par->pc_den || par->pm_num > par->pm_den || par->migrate_every < 0)
+        return FFS_E_ARG;
+    int side = 0;
+    if (par->tournament_k == 0) {
+        while (side * side < P) ++side;
+        if (side * side != P) return FFS_E_ARG;
+    }
+    if (in->K < 1) return FFS_E_STATE;
+    ga_population *pp = new (std::nothrow) ga_population();
+    if (!pp) return FFS_E_NOMEM;
+    auto fail = [&](int rc) {
+        delete pp;
+        return rc;
+    };
+    pp->inst = in;
+    pp->version = in->version;
+    pp->par = *par;
+    pp->st = static_cast<cudaStream_t>(par->cuda_stream);
+    pp->P = P;
+    pp->I = I;
+    pp->K = in->K;
+    pp->nisl = P / I;
+    pp->side = side;
+    pp->hdr = in->hdr;
+    const size_t PK = (size_t)P * pp->K, NK = (size_t)pp->nisl * pp->K;
+    bool ok = dalloc(&pp->d_blob, (size_t)in->hdr.bytes) == cudaSuccess;
+    for (int b = 0; b < 2 && ok; ++b)
+        ok = dalloc(&pp->Y[b], PK) == cudaSuccess && dalloc(&pp->X[b], PK) == cudaSuccess &&
+             dalloc(&pp->obj[b], P) == cudaSuccess && dalloc(&pp->fit[b], P) == cudaSuccess;
+    ok = ok && dalloc(&pp->bY, NK) == cudaSuccess && dalloc(&pp->bX, NK) == cudaSuccess &&
+         dalloc(&pp->bobj, pp->nisl) == cudaSuccess && dalloc(&pp->bfit, pp->nisl) == cudaSuccess &&
+         dalloc(&pp->mY, NK) == cudaSuccess && dalloc(&pp->mX, NK) == cudaSuccess &&
+         dalloc(&pp->mobj, pp->nisl) == cudaSuccess && dalloc(&pp->mfit, pp->nisl) == cudaSuccess &&
+         dalloc(&pp->mw, pp->nisl) == cudaSuccess && dalloc(&pp->over, P) == cudaSuccess &&
+         dalloc(&pp->err, 1) == cudaSuccess && dalloc(&pp->dev, 1) == cudaSuccess;
+    if (!ok) return fail(FFS_E_NOMEM);
+    pp->Hcap = smem_slots(pp->hdr, true);
+    pp->grid_gen = std::max(1, std::min((P + kWarpsPerBlock - 1) / kWarpsPerBlock,
+                                        num_sms() * std::max(1, (228 * 1024) / (cta_smem_bytes(pp->hdr, pp->Hcap, true, false) + 1024))));
+    pp->grid_fb = std::max(1, std::min((P + kWarpsPerBlock - 1) / kWarpsPerBlock, num_sms() * 2));
+    if (dalloc(&pp->scratch, (size_t)pp->grid_fb * kWarpsPerBlock * pp->hdr.H) != cudaSuccess) return fail(FFS_E_NOMEM);
+    cudaStream_t st = pp->st;
+    int rc = FFS_OK;
+    auto step = [&](cudaError_t e) {
+        if (rc == FFS_OK && e != cudaSuccess) rc = FFS_E_CUDA;
+    };
+    step(cudaMemcpyAsync(pp->d_blob, in->blob.data(), in->hdr.bytes, cudaMemcpyHostToDevice, st));
+    for (int b = 0; b < 2; ++b) step(cudaMemsetAsync(pp->X[b], 0, PK, st));
+    step(cudaMemsetAsync(pp->err, 0, 4, st));
+    step(cudaMemsetAsync(pp->dev, 0, sizeof(GADev), st));
+    GenArgs a;
+    ga_gen_args(pp, &a);
+    step(launch_ga_init(par->order_mode, par->machine_mode, a, pp->hdr, pp->grid_gen, st));
+    DecodeArgs d;
+    ga_fallback_args(pp, &d, false);
+    step(launch_decode(par->order_mode, par->machine_mode, true, d, pp->hdr, pp->grid_fb, st));
+    ReplArgs r;
+    ga_replace_args(pp, &r, 1);
+    step(launch_emax(r, st));
+    step(launch_replace(r, st));
+    step(cudaMemsetAsync(&pp->dev->nover, 0, 4, st));
+    if (rc != FFS_OK) return fail(rc);
+    g_launches += 4;
+    // Capture one generation once; ga_run replays it.
+    if (prepare_ga_generation(par->order_mode, par->machine_mode, pp->hdr, pp->Hcap) != cudaSuccess)
+        return fail(FFS_E_CUDA);
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(FFS_E_CUDA);
+    const int erc = ga_enqueue_generation(pp);
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (erc != FFS_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(FFS_E_CUDA);
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&pp->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(FFS_E_CUDA);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(FFS_E_CUDA);
+    int32_t e = 0;
+    if (cudaMemcpy(&e, pp->err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(FFS_E_CUDA);
+    if (e) return fail(e & kErrTimeout ? FFS_E_TIMEOUT : FFS_E_DEVICE);
+    *out = pp;
+    return FFS_OK;
+}
+
+int ga_population_destroy(ga_population *pp) {
+    delete pp;
+    return FFS_OK;
+}
+
+int ga_population_read(ga_population *pp, int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit, int16_t *bY,
+                       int8_t *bX, int64_t *bobj, int64_t *bfit, int64_t *emax, int32_t *generation) {
+    if (!pp) return FFS_E_ARG;
+    FFS_CUDA(cudaStreamSynchronize(pp->st));
+    GADev dv;
+    FFS_CUDA(cudaMemcpy(&dv, pp->dev, sizeof(dv), cudaMemcpyDeviceToHost));
+    const int b = dv.gen & 1;
+    const size_t PK = (size_t)pp->P * pp->K, NK = (size_t)pp->nisl * pp->K;
+    if (Y) FFS_CUDA(cudaMemcpy(Y, pp->Y[b], 2 * PK, cudaMemcpyDeviceToHost));
+    if (X) FFS_CUDA(cudaMemcpy(X, pp->X[b], PK, cudaMemcpyDeviceToHost));
+    if (obj) FFS_CUDA(cudaMemcpy(obj, pp->obj[b], 8 * (size_t)pp->P, cudaMemcpyDeviceToHost));
+    if (fit) FFS_CUDA(cudaMemcpy(fit, pp->fit[b], 8 * (size_t)pp->P, cudaMemcpyDeviceToHost));
+    if (bY) FFS_CUDA(cudaMemcpy(bY, pp->bY, 2 * NK, cudaMemcpyDeviceToHost));
+    if (bX) FFS_CUDA(cudaMemcpy(bX, pp->bX, NK, cudaMemcpyDeviceToHost));
+    if (bobj) FFS_CUDA(cudaMemcpy(bobj, pp->bobj, 8 * (size_t)pp->nisl, cudaMemcpyDeviceToHost));
+    if (bfit) FFS_CUDA(cudaMemcpy(bfit, pp->bfit, 8 * (size_t)pp->nisl, cudaMemcpyDeviceToHost));
+    if (emax) *emax = dv.emax;
+    if (generation) *generation = dv.gen;
+    return FFS_OK;
+}
+
+int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
+    if (!pp || generations < 0) return FFS_E_ARG;
+    ffs_instance *in = pp->inst;
+    if (pp->version != in->version) return FFS_E_STATE;
+    if (!pp->profiling) {
+        for (int i = 0; i < generations; ++i) FFS_CUDA(cudaGraphLaunch(pp->graph, pp->st));
+        g_launches += 5ull * (unsigned long long)generations;
+        FFS_CUDA(cudaStreamSynchronize(pp->st));
+    } else {
+        while ((int)pp->ev.size() < 2 * generations) {
+            cudaEvent_t e;
+            FFS_CUDA(cudaEventCreate(&e));
+            pp->ev.push_back(e);
+        }
+        for (int i = 0; i < generations; ++i) FFS_TRY(ga_enqueue_generation(pp, pp->ev[2 * i], pp->ev[2 * i + 1]));
+        g_launches += 5ull * (unsigned long long)generations;
+        FFS_CUDA(cudaStreamSynchronize(pp->st));
+        for (int i = 0; i < generations; ++i) {
+            float ms = 0.f;
+            FFS_CUDA(cudaEventElapsedTime(&ms, pp->ev[2 * i], pp->ev[2 * i + 1]));
+            pp->prof_ms += ms;
+        }
+        pp->prof_launches += generations;
+    }
+    int32_t e = 0;
+    FFS_CUDA(cudaMemcpy(&e, pp->err, 4, cudaMemcpyDeviceToHost));
+    if (e) return e & kErrTimeout ? FFS_E_TIMEOUT : FFS_E_DEVICE;
+    // best-ever island: largest fitness, lowest island index
+    std::vector<int64_t> bfit(pp->nisl);
+    FFS_CUDA(cudaMemcpy(bfit.data(), pp->bfit, 8 * (size_t)pp->nisl, cudaMemcpyDeviceToHost));
+    int bi = 0;
+    for (int i = 1; i < pp->nisl; ++i)
+        if (bfit[i] > bfit[bi]) bi = i;
+    const size_t NG = (size_t)in->N * in->g;
+    int64_t *d_obj = nullptr, *d_tard = nullptr;
+    int32_t *d_cm = nullptr, *d_S = nullptr, *d_M = nullptr;
+    int rc = FFS_OK;
+    if (dalloc(&d_obj, 1) != cudaSuccess || dalloc(&d_tard, 1) != cudaSuccess || dalloc(&d_cm, 1) != cudaSuccess ||
+        dalloc(&d_S, NG) != cudaSuccess || dalloc(&d_M, NG) != cudaSuccess)
+        rc = FFS_E_NOMEM;
+    if (rc == FFS_OK)
+        rc = decode_impl(in, pp->par.order_mode, pp->par.machine_mode, pp->bY + (size_t)bi * pp->K,
+                         pp->bX + (size_t)bi * pp->K, 1, d_obj, d_tard, d_cm, d_S, d_M, pp->st);
+    std::vector<int32_t> S(NG), M(NG);
+    int64_t o = 0, t = 0;
+    int32_t cm = 0;
+    if (rc == FFS_OK) rc = ffs_decode_check(in, pp->st);
+    if (rc == FFS_OK)
+        rc = cuda_rc(cudaMemcpy(S.data(), d_S, 4 * NG, cudaMemcpyDeviceToHost)) |
+             cuda_rc(cudaMemcpy(M.data(), d_M, 4 * NG, cudaMemcpyDeviceToHost)) |
+             cuda_rc(cudaMemcpy(&o, d_obj, 8, cudaMemcpyDeviceToHost)) |
+             cuda_rc(cudaMemcpy(&t, d_tard, 8, cudaMemcpyDeviceToHost)) |
+             cuda_rc(cudaMemcpy(&cm, d_cm, 4, cudaMemcpyDeviceToHost));
+    dfree(d_obj); dfree(d_tard); dfree(d_cm); dfree(d_S); dfree(d_M);
+    if (rc != FFS_OK) return rc < 0 ? rc : FFS_E_CUDA;
+    FFS_TRY(ffs_commit(in, S.data(), M.data()));
+    if (best) {
+        best->objective = o;
+        best->total_tardiness = t;
+        best->makespan = cm;
+        best->n_ops = (int32_t)NG;
+        if (best->start) std::memcpy(best->start, S.data(), 4 * NG);
+        if (best->machine) std::memcpy(best->machine, M.data(), 4 * NG);
+    }
+    return FFS_OK;
+}
+
+int ga_set_profiling(ga_population *pp, int32_t enable) {
+    if (!pp) return FFS_E_ARG;
+    pp->profiling = enable != 0;
+    pp->prof_ms = 0.0;
+    pp->prof_launches = 0;
+    return FFS_OK;
+}
+
+int ga_profile_read(ga_population *pp, double *kernel_ms, int64_t *launches) {
+    if (!pp || !kernel_ms || !launches) return FFS_E_ARG;
+    *kernel_ms = pp->prof_ms;
+    *launches = pp->prof_launches;
+    return FFS_OK;
+}
+
+int ffs_kernel_launches(uint64_t *count) {
+    if (!count) return FFS_E_ARG;
+    *count = g_launches.load();
+    return FFS_OK;
+}
+
+struct CkptHeader {
+    uint32_t magic, version;
+    int32_t P, K, nisl, gen;
+    int64_t emax;
+};
+
+int ga_checkpoint(ga_population *pp, void *buf, size_t *len) {
+    if (!pp || !len) return FFS_E_ARG;
+    const size_t PK = (size_t)pp->P * pp->K, NK = (size_t)pp->nisl * pp->K;
+    const size_t need = sizeof(CkptHeader) + 3 * PK + 16 * (size_t)pp->P + 3 * NK + 16 * (size_t)pp->nisl;
+    if (!buf) {
+        *len = need;
+        return FFS_OK;
+    }
+    if (*len < need) return FFS_E_ARG;
+    char *b = static_cast<char *>(buf);
+    CkptHeader h{0x47534646u, 1u, pp->P, pp->K, pp->nisl, 0, 0};
+    char *p = b + sizeof(h);
+    int16_t *Y = reinterpret_cast<int16_t *>(p); p += 2 * PK;
+    int8_t *X = reinterpret_cast<int8_t *>(p); p += PK;
+    int64_t *obj = reinterpret_cast<int64_t *>(p); p += 8 * (size_t)pp->P;
+    int64_t *fit = reinterpret_cast<int64_t *>(p); p += 8 * (size_t)pp->P;
+    int16_t *bY = reinterpret_cast<int16_t *>(p); p += 2 * NK;
+    int8_t *bX = reinterpret_cast<int8_t *>(p); p += NK;
+    int64_t *bobj = reinterpret_cast<int64_t *>(p); p += 8 * (size_t)pp->nisl;
+    int64_t *bfit = reinterpret_cast<int64_t *>(p);
+    FFS_TRY(ga_population_read(pp, Y, X, obj, fit, bY, bX, bobj, bfit, &h.emax, &h.gen));
+    std::memcpy(b, &h, sizeof(h));
+    *len = need;
+    return FFS_OK;
+}
+
+int ga_restore(ga_population *pp, const void *buf, size_t len) {
+    if (!pp || !buf || len < sizeof(CkptHeader)) return FFS_E_ARG;
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    const size_t PK = (size_t)pp->P * pp->K, NK = (size_t)pp->nisl * pp->K;
+    const size_t need = sizeof(CkptHeader) + 3 * PK + 16 * (size_t)pp->P + 3 * NK + 16 * (size_t)pp->nisl;
+    if (h.magic != 0x47534646u || h.version != 1u || h.P != pp->P || h.K != pp->K || h.nisl != pp->nisl ||
+        len < need || h.gen < 0)
+        return FFS_E_ARG;
+    const char *p = static_cast<const char *>(buf) + sizeof(h);
+    const int b = h.gen & 1;
+    {   // every chromosome must be a permutation of 1..K with machines in range
+        const int K = pp->K;
+        const int16_t *Y = reinterpret_cast<const int16_t *>(p);
+        const int8_t *X = reinterpret_cast<const int8_t *>(p + 2 * PK);
+        const char *q2 = p + 3 * PK + 16 * (size_t)pp->P;
+        const int16_t *bY = reinterpret_cast<const int16_t *>(q2);
+        const int8_t *bX = reinterpret_cast<const int8_t *>(q2 + 2 * NK);
+        std::vector<char> seen(K + 1);
+        auto valid = [&](const int16_t *y, const int8_t *x) {
+            std::fill(seen.begin(), seen.end(), 0);
+            for (int k = 0; k < K; ++k) {
+                if (y[k] < 1 || y[k] > K || seen[y[k]]) return false;
+                seen[y[k]] = 1;
+                if (x[k] < 0 || x[k] >= pp->inst->o[pp->inst->gstg[k]]) return false;
+            }
+            return true;
+        };
+        if (pp->version != pp->inst->version) return FFS_E_STATE;
+        for (int i = 0; i < pp->P; ++i)
+            if (!valid(Y + (size_t)i * K, X + (size_t)i * K)) return FFS_E_ARG;
+        for (int i = 0; i < pp->nisl; ++i)
+            if (!valid(bY + (size_t)i * K, bX + (size_t)i * K)) return FFS_E_ARG;
+    }
+    FFS_CUDA(cudaStreamSynchronize(pp->st));
+    FFS_CUDA(cudaMemcpy(pp->Y[b], p, 2 * PK, cudaMemcpyHostToDevice)); p += 2 * PK;
+    FFS_CUDA(cudaMemcpy(pp->X[b], p, PK, cudaMemcpyHostToDevice)); p += PK;
+    FFS_CUDA(cudaMemcpy(pp->obj[b], p, 8 * (size_t)pp->P, cudaMemcpyHostToDevice)); p += 8 * (size_t)pp->P;
+    FFS_CUDA(cudaMemcpy(pp->fit[b], p, 8 * (size_t)pp->P, cudaMemcpyHostToDevice)); p += 8 * (size_t)pp->P;
+    FFS_CUDA(cudaMemcpy(pp->bY, p, 2 * NK, cudaMemcpyHostToDevice)); p += 2 * NK;
+    FFS_CUDA(cudaMemcpy(pp->bX, p, NK, cudaMemcpyHostToDevice)); p += NK;
+    FFS_CUDA(cudaMemcpy(pp->bobj, p, 8 * (size_t)pp->nisl, cudaMemcpyHostToDevice)); p += 8 * (size_t)pp->nisl;
+    FFS_CUDA(cudaMemcpy(pp->bfit, p, 8 * (size_t)pp->nisl, cudaMemcpyHostToDevice));
+    GADev dv{};
+    dv.gen = h.gen;
+    dv.emax = h.emax;
+    FFS_CUDA(cudaMemcpy(pp->dev, &dv, sizeof(dv), cudaMemcpyHostToDevice));
+    return FFS_OK;
+}
+
+}  // extern "C"

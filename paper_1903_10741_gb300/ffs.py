@@ -1,0 +1,300 @@
+"""Python binding of the C ABI in ``include/ffs.h`` (ctypes, argument marshalling only).
+
+Every computation runs in ``libffs.so``'s CUDA kernels.  Device buffers are torch CUDA
+tensors (PyTorch supplies device memory and streams); host results are numpy arrays.
+There is no CPU fallback: if the library cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+FFS_OK = 0
+ORDER_TOPO, ORDER_STAGE = 0, 1
+MACH_GENE, MACH_EARLIEST = 0, 1
+ST_FREE, ST_EXEC, ST_DONE = 0, 1, 2
+
+_i32p = C.POINTER(C.c_int32)
+_lib = None
+
+
+class FFSError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = lib().ffs_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})")
+
+
+class Problem_c(C.Structure):
+    _fields_ = [("n_jobs", C.c_int32), ("n_stages", C.c_int32), ("machines_per_stage", _i32p),
+                ("proc", _i32p), ("power", _i32p), ("release", _i32p), ("due", _i32p),
+                ("peak_power", C.c_int32), ("wt", C.c_int32)]
+
+
+class Arrivals_c(C.Structure):
+    _fields_ = [("job_count", C.c_int32), ("proc", _i32p), ("release", _i32p), ("due", _i32p)]
+
+
+class GAParams_c(C.Structure):
+    _fields_ = [("pop", C.c_int32), ("island", C.c_int32), ("tournament_k", C.c_int32),
+                ("pc_num", C.c_int32), ("pc_den", C.c_int32), ("pm_num", C.c_int32),
+                ("pm_den", C.c_int32), ("order_mode", C.c_int32), ("machine_mode", C.c_int32),
+                ("migrate_every", C.c_int32), ("instance_id", C.c_int32), ("seed", C.c_uint64),
+                ("cuda_stream", C.c_void_p)]
+
+
+class Result_c(C.Structure):
+    _fields_ = [("objective", C.c_int64), ("total_tardiness", C.c_int64), ("makespan", C.c_int32),
+                ("n_ops", C.c_int32), ("start", _i32p), ("machine", _i32p)]
+
+
+class Info_c(C.Structure):
+    _fields_ = [("n_jobs", C.c_int32), ("n_stages", C.c_int32), ("n_machines", C.c_int32),
+                ("n_genes", C.c_int32), ("rs", C.c_int32), ("horizon", C.c_int32),
+                ("peak_power", C.c_int32), ("wt", C.c_int32)]
+
+
+_SIGS = {
+    "ffs_strerror": (C.c_char_p, [C.c_int]),
+    "ffs_instance_create": (C.c_int, [C.POINTER(Problem_c), C.POINTER(C.c_void_p)]),
+    "ffs_instance_destroy": (C.c_int, [C.c_void_p]),
+    "ffs_instance_info": (C.c_int, [C.c_void_p, C.POINTER(Info_c)]),
+    "ffs_instance_genes": (C.c_int, [C.c_void_p, _i32p, _i32p]),
+    "ffs_instance_status": (C.c_int, [C.c_void_p, _i32p]),
+    "ffs_commit": (C.c_int, [C.c_void_p, _i32p, _i32p]),
+    "ffs_reschedule": (C.c_int, [C.c_void_p, C.POINTER(Arrivals_c), C.c_int32]),
+    "ffs_decode": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ffs_decode_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                      C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ffs_decode_check": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ga_population_create": (C.c_int, [C.c_void_p, C.POINTER(GAParams_c), C.POINTER(C.c_void_p)]),
+    "ga_population_destroy": (C.c_int, [C.c_void_p]),
+    "ga_run": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Result_c)]),
+    "ga_population_read": (C.c_int, [C.c_void_p] + [C.c_void_p] * 10),
+    "ga_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "ga_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "ffs_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
+    "ga_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ga_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+}
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libffs in this process so far."""
+    n = C.c_uint64(0)
+    _check(lib().ffs_kernel_launches(C.byref(n)), "ffs_kernel_launches")
+    return int(n.value)
+
+
+def header_functions():
+    """Names of the functions declared in include/ffs.h."""
+    with open(os.path.join(_build.INCLUDE, "ffs.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^(?:int|const char \*)\s*(\w+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    """Loads libffs.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != FFS_OK:
+        raise FFSError(rc, what)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_i32p)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _dptr(t):
+    return None if t is None else t.data_ptr()
+
+
+class Instance:
+    """An EDFFS instance held by the library (``ffs_instance``)."""
+
+    def __init__(self, problem):
+        self._keep = [_i32(problem.o), _i32(problem.p), _i32(problem.q), _i32(problem.R), _i32(problem.D)]
+        o, p, q, R, D = self._keep
+        pr = Problem_c(int(p.shape[0]), int(o.shape[0]), _p(o), _p(p), _p(q), _p(R), _p(D),
+                       int(problem.Qmax), int(problem.WT))
+        h = C.c_void_p()
+        _check(lib().ffs_instance_create(C.byref(pr), C.byref(h)), "ffs_instance_create")
+        self._h = h
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().ffs_instance_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        i = Info_c()
+        _check(lib().ffs_instance_info(self._h, C.byref(i)), "ffs_instance_info")
+        return {n: getattr(i, n) for n, _ in Info_c._fields_}
+
+    @property
+    def K(self) -> int:
+        return self.info()["n_genes"]
+
+    def genes(self):
+        K = self.K
+        gj = np.zeros(max(K, 1), np.int32)
+        gs = np.zeros(max(K, 1), np.int32)
+        _check(lib().ffs_instance_genes(self._h, _p(gj), _p(gs)), "ffs_instance_genes")
+        return gj[:K], gs[:K]
+
+    def status(self) -> np.ndarray:
+        inf = self.info()
+        st = np.zeros((inf["n_jobs"], inf["n_stages"]), np.int32)
+        _check(lib().ffs_instance_status(self._h, _p(st)), "ffs_instance_status")
+        return st
+
+    def commit(self, S, M):
+        S, M = _i32(S), _i32(M)
+        _check(lib().ffs_commit(self._h, _p(S), _p(M)), "ffs_commit")
+
+    def reschedule(self, arrivals, t_now: int):
+        p, R, D = _i32(arrivals.p), _i32(arrivals.R), _i32(arrivals.D)
+        a = Arrivals_c(int(p.shape[0]), _p(p), _p(R), _p(D))
+        _check(lib().ffs_reschedule(self._h, C.byref(a), int(t_now)), "ffs_reschedule")
+
+    def decode(self, y, x=None, order_mode=ORDER_STAGE, mach_mode=MACH_EARLIEST, stream=None,
+               schedule=False, check=True):
+        """Decodes device chromosomes ``y`` (int16 [count, K]) and ``x`` (int8, machine genes).
+        Returns device tensors: obj (int64), tard, cmax, and with ``schedule`` S, M [count, N, g]."""
+        import torch
+        count = int(y.shape[0]) if y.dim() == 2 else 1
+        dev = y.device
+        obj = torch.empty(count, dtype=torch.int64, device=dev)
+        st = _stream_ptr(stream)
+        out = {"obj": obj}
+        if schedule:
+            inf = self.info()
+            S = torch.empty((count, inf["n_jobs"], inf["n_stages"]), dtype=torch.int32, device=dev)
+            M = torch.empty_like(S)
+            _check(lib().ffs_decode_schedule(self._h, order_mode, mach_mode, _dptr(y), _dptr(x), count,
+                                             _dptr(obj), _dptr(S), _dptr(M), st), "ffs_decode_schedule")
+            out.update(S=S, M=M)
+        else:
+            tard = torch.empty(count, dtype=torch.int64, device=dev)
+            cmax = torch.empty(count, dtype=torch.int32, device=dev)
+            _check(lib().ffs_decode(self._h, order_mode, mach_mode, _dptr(y), _dptr(x), count,
+                                    _dptr(obj), _dptr(tard), _dptr(cmax), st), "ffs_decode")
+            out.update(tard=tard, cmax=cmax)
+        if check:
+            _check(lib().ffs_decode_check(self._h, st), "ffs_decode")
+        return out
+
+
+class Population:
+    """A device-resident GA population (``ga_population``)."""
+
+    def __init__(self, inst: Instance, P: int, island: int = 64, tour_k: int = 2, pc=(4, 5),
+                 pm=(1, 10), order_mode=ORDER_STAGE, mach_mode=MACH_EARLIEST, migrate_every: int = 10,
+                 seed: int = 1, instance_id: int = 0, stream=None):
+        self.inst = inst
+        island = min(island, P)
+        self.P, self.island = P, island
+        self.nisl = P // island
+        self.mach_mode = mach_mode
+        par = GAParams_c(P, island, tour_k, pc[0], pc[1], pm[0], pm[1], order_mode, mach_mode,
+                         migrate_every, instance_id, seed, _stream_ptr(stream))
+        h = C.c_void_p()
+        _check(lib().ga_population_create(inst.handle, C.byref(par), C.byref(h)), "ga_population_create")
+        self._h = h
+        self.K = inst.K
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().ga_population_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, generations: int, want_schedule: bool = True) -> dict:
+        inf = self.inst.info()
+        S = np.zeros((inf["n_jobs"], inf["n_stages"]), np.int32)
+        M = np.zeros_like(S)
+        r = Result_c(0, 0, 0, 0, _p(S) if want_schedule else None, _p(M) if want_schedule else None)
+        _check(lib().ga_run(self._h, int(generations), C.byref(r)), "ga_run")
+        out = dict(obj=int(r.objective), tard=int(r.total_tardiness), cmax=int(r.makespan))
+        if want_schedule:
+            out.update(S=S, M=M)
+        return out
+
+    def read(self) -> dict:
+        P, K, n = self.P, self.K, self.nisl
+        d = dict(Y=np.zeros((P, K), np.int16), X=np.zeros((P, K), np.int8), obj=np.zeros(P, np.int64),
+                 fit=np.zeros(P, np.int64), bY=np.zeros((n, K), np.int16), bX=np.zeros((n, K), np.int8),
+                 bobj=np.zeros(n, np.int64), bfit=np.zeros(n, np.int64))
+        emax = C.c_int64()
+        gen = C.c_int32()
+        _check(lib().ga_population_read(self._h, *[d[k].ctypes.data for k in
+                                                   ("Y", "X", "obj", "fit", "bY", "bX", "bobj", "bfit")],
+                                        C.addressof(emax), C.addressof(gen)), "ga_population_read")
+        d["emax"] = int(emax.value)
+        d["gen"] = int(gen.value)
+        return d
+
+    def set_profiling(self, enable: bool):
+        _check(lib().ga_set_profiling(self._h, 1 if enable else 0), "ga_set_profiling")
+
+    def profile(self):
+        """(summed milliseconds, launches) of the fused generation kernel while profiling."""
+        ms = C.c_double()
+        n = C.c_int64()
+        _check(lib().ga_profile_read(self._h, C.byref(ms), C.byref(n)), "ga_profile_read")
+        return float(ms.value), int(n.value)
+
+    def checkpoint(self) -> bytes:
+        n = C.c_size_t(0)
+        _check(lib().ga_checkpoint(self._h, None, C.byref(n)), "ga_checkpoint")
+        buf = (C.c_char * n.value)()
+        _check(lib().ga_checkpoint(self._h, buf, C.byref(n)), "ga_checkpoint")
+        return bytes(buf)
+
+    def restore(self, data: bytes):
+        buf = C.create_string_buffer(data, len(data))
+        _check(lib().ga_restore(self._h, buf, len(data)), "ga_restore")

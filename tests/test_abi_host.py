@@ -1,0 +1,104 @@
+"""The C ABI on the host (no GPU): the library loads, exports what include/ffs.h
+declares, validates its inputs, and its rescheduling freeze and gene numbering agree with
+the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_10741_gb300 import ffs
+from paper_1903_10741_gb300 import workloads as wl
+
+
+def test_library_exports_every_declared_function():
+    L = ffs.lib()
+    names = ffs.header_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_strerror_names_every_code():
+    for code in range(0, -9, -1):
+        assert ffs.lib().ffs_strerror(code).decode() != "unknown status"
+
+
+def test_create_rejects_infeasible_and_bad_input():
+    prob = wl.static_small(1)
+    bad = wl.Problem(o=prob.o, p=prob.p, q=prob.q, R=prob.R, D=prob.D, Qmax=int(prob.q.max()) - 1)
+    with pytest.raises(ffs.FFSError) as e:
+        ffs.Instance(bad)
+    assert e.value.code == -2
+    empty_stage = wl.Problem(o=[2, 0, 2], p=prob.p, q=prob.q[:4], R=prob.R, D=prob.D, Qmax=prob.Qmax)
+    with pytest.raises(ffs.FFSError) as e:
+        ffs.Instance(empty_stage)
+    assert e.value.code == -2
+    neg = wl.Problem(o=prob.o, p=-prob.p, q=prob.q, R=prob.R, D=prob.D, Qmax=prob.Qmax)
+    with pytest.raises(ffs.FFSError) as e:
+        ffs.Instance(neg)
+    assert e.value.code == -1
+
+
+def _pair(problem):
+    return ffs.Instance(problem), oracle.Instance(problem)
+
+
+def test_fresh_instance_all_free():
+    lib_i, orc_i = _pair(wl.static_small(1))
+    inf = lib_i.info()
+    assert inf["n_genes"] == orc_i.K == 30 and inf["rs"] == 0
+    gj, gs = lib_i.genes()
+    ogj, ogs = orc_i.gene_map()
+    assert np.array_equal(gj, ogj) and np.array_equal(gs, ogs)
+    assert (lib_i.status() == 0).all()
+    # the profile bound covers running every op back to back
+    assert inf["horizon"] >= int(orc_i.p.sum()) + 1
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_reschedule_chain_matches_oracle(seed):
+    """Alg. 1 freeze + arrival append on the library's host side equals the oracle's."""
+    dyn = wl.dynamic_medium(seed + 1)
+    lib_i, orc_i = _pair(dyn.problem)
+    rng = np.random.default_rng(seed)
+    for t_now, arr in dyn.events:
+        y = rng.permutation(orc_i.K) + 1
+        r = orc_i.decode(y, None, oracle.ORDER_STAGE, oracle.MACH_EARLIEST)
+        orc_i.commit(r["S"], r["M"])
+        lib_i.commit(r["S"], r["M"])
+        orc_i.reschedule(arr, t_now)
+        lib_i.reschedule(arr, t_now)
+        assert np.array_equal(lib_i.status(), orc_i.status)
+        gj, gs = lib_i.genes()
+        ogj, ogs = orc_i.gene_map()
+        assert np.array_equal(gj, ogj) and np.array_equal(gs, ogs)
+        inf = lib_i.info()
+        assert inf["rs"] == t_now and inf["n_jobs"] == orc_i.N and inf["n_genes"] == orc_i.K
+
+
+def test_reschedule_rules():
+    lib_i = ffs.Instance(wl.static_small(1))
+    arr = wl.Arrivals(p=np.ones((1, 3)), R=[5], D=[50])
+    with pytest.raises(ffs.FFSError) as e:  # no plan committed and time moved on
+        lib_i.reschedule(arr, 5)
+    assert e.value.code == -7
+    lib_i.reschedule(arr, 0)                # nothing has run yet: append only
+    assert lib_i.info()["n_jobs"] == 11
+    orc_i = oracle.Instance(wl.static_small(1))
+    orc_i.reschedule(arr, 0)
+    r = orc_i.decode(np.arange(orc_i.K, 0, -1), None, oracle.ORDER_STAGE, oracle.MACH_EARLIEST)
+    lib_i.commit(r["S"], r["M"])
+    lib_i.reschedule(wl.Arrivals(p=np.ones((0, 3)), R=[], D=[]), 10)
+    with pytest.raises(ffs.FFSError) as e:  # time cannot go backwards
+        lib_i.reschedule(arr, 9)
+    assert e.value.code in (-1, -7)
+
+
+def test_commit_validation():
+    lib_i = ffs.Instance(wl.static_small(1))
+    S = np.zeros((10, 3), np.int32)
+    M = np.zeros((10, 3), np.int32)
+    M[0, 1] = 3  # stage 1 has 3 machines: 0..2
+    with pytest.raises(ffs.FFSError):
+        lib_i.commit(S, M)
+    M[0, 1] = 2
+    lib_i.commit(S, M)
