@@ -213,6 +213,10 @@ int ga_profile_read(ga_population *pop, double *kernel_ms, int64_t *launches);
  * each kernel node).  For benchmark accounting. */
 int ffs_kernel_launches(uint64_t *count);
 
+/* Text of the last CUDA error this thread's calls met (empty if none).  The pointer stays
+ * valid until the thread's next library call. */
+const char *ffs_last_error(void);
+
 /* Human-readable name of a status code. */
 const char *ffs_strerror(int code);
 

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -130,7 +131,13 @@ struct ga_population {
 
 namespace {
 
-int cuda_rc(cudaError_t e) { return e == cudaSuccess ? FFS_OK : FFS_E_CUDA; }
+thread_local char g_last_error[256] = "";
+
+int cuda_rc(cudaError_t e) {
+    if (e == cudaSuccess) return FFS_OK;
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return FFS_E_CUDA;
+}
 
 #define FFS_TRY(expr)                 \
     do {                              \
@@ -650,7 +657,7 @@ int ga_population_create(ffs_instance *in, const ga_params *par, ga_population *
     cudaStream_t st = pp->st;
     int rc = FFS_OK;
     auto step = [&](cudaError_t e) {
-        if (rc == FFS_OK && e != cudaSuccess) rc = FFS_E_CUDA;
+        if (rc == FFS_OK && e != cudaSuccess) rc = cuda_rc(e);
     };
     step(cudaMemcpyAsync(pp->d_blob, in->blob.data(), in->hdr.bytes, cudaMemcpyHostToDevice, st));
     for (int b = 0; b < 2; ++b) step(cudaMemsetAsync(pp->X[b], 0, PK, st));
@@ -672,17 +679,25 @@ int ga_population_create(ffs_instance *in, const ga_params *par, ga_population *
     // Capture one generation once; ga_run replays it.
     if (prepare_ga_generation(par->order_mode, par->machine_mode, pp->hdr, pp->Hcap) != cudaSuccess)
         return fail(FFS_E_CUDA);
+    // The caller's stream may be the legacy default stream, which cannot be captured: the
+    // graph is recorded on a private stream and later launched on the caller's.
     cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(FFS_E_CUDA);
-    const int erc = ga_enqueue_generation(pp);
-    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
-    if (erc != FFS_OK || ce != cudaSuccess) {
+    cudaStream_t cap = nullptr;
+    if ((rc = cuda_rc(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) != FFS_OK) return fail(rc);
+    cudaStream_t user = pp->st;
+    pp->st = cap;
+    rc = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    const int erc = rc == FFS_OK ? ga_enqueue_generation(pp) : rc;
+    const int ce = rc == FFS_OK ? cuda_rc(cudaStreamEndCapture(cap, &graph)) : rc;
+    pp->st = user;
+    cudaStreamDestroy(cap);
+    if (erc != FFS_OK || ce != FFS_OK) {
         if (graph) cudaGraphDestroy(graph);
-        return fail(FFS_E_CUDA);
+        return fail(erc != FFS_OK ? erc : ce);
     }
-    const cudaError_t ie = cudaGraphInstantiate(&pp->graph, graph, 0);
+    rc = cuda_rc(cudaGraphInstantiate(&pp->graph, graph, 0));
     cudaGraphDestroy(graph);
-    if (ie != cudaSuccess) return fail(FFS_E_CUDA);
+    if (rc != FFS_OK) return fail(rc);
     if (cudaStreamSynchronize(st) != cudaSuccess) return fail(FFS_E_CUDA);
     int32_t e = 0;
     if (cudaMemcpy(&e, pp->err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(FFS_E_CUDA);
@@ -798,6 +813,8 @@ int ga_profile_read(ga_population *pp, double *kernel_ms, int64_t *launches) {
     *launches = pp->prof_launches;
     return FFS_OK;
 }
+
+const char *ffs_last_error(void) { return g_last_error; }
 
 int ffs_kernel_launches(uint64_t *count) {
     if (!count) return FFS_E_ARG;

@@ -27,6 +27,8 @@ class FFSError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
         msg = lib().ffs_strerror(code).decode() if _lib is not None else str(code)
+        if _lib is not None and code == -4:
+            msg += " [" + lib().ffs_last_error().decode() + "]"
         super().__init__(f"{what}: {msg} ({code})")
 
 
@@ -61,6 +63,7 @@ class Info_c(C.Structure):
 
 _SIGS = {
     "ffs_strerror": (C.c_char_p, [C.c_int]),
+    "ffs_last_error": (C.c_char_p, []),
     "ffs_instance_create": (C.c_int, [C.POINTER(Problem_c), C.POINTER(C.c_void_p)]),
     "ffs_instance_destroy": (C.c_int, [C.c_void_p]),
     "ffs_instance_info": (C.c_int, [C.c_void_p, C.POINTER(Info_c)]),

@@ -95,9 +95,9 @@ def test_worked_example_on_gpu():
     compare(lib_i, orc_i, Y, X, ffs.ORDER_TOPO, ffs.MACH_GENE)
     torch = _torch()
     out = lib_i.decode(torch.from_numpy(Y).cuda(), torch.from_numpy(X).cuda(), ffs.ORDER_TOPO,
-                       ffs.MACH_GENE, schedule=True)
-    assert int(out["S"][0, 7, 0]) == ex["expect_job7_stage0_start"]
-    assert int(out["S"].max() + 300) >= ex["expect_cmax"]
+                       ffs.MACH_GENE)
+    # Fig. 8: C_max = 20.42 (the topological reading reaches the printed Z's makespan)
+    assert int(out["cmax"][0]) == ex["expect_cmax"]
 
 
 @pytest.mark.parametrize("case", ["one_gene", "single_machine", "serialised", "tiny_peak_tall_p"])
@@ -124,7 +124,7 @@ def test_all_frozen_but_one():
     """Only one free op remains after the freeze: K = 1."""
     prob = wl.Problem(o=[1, 1], p=[[5, 5], [5, 5]], q=[1, 1], R=[0, 0], D=[0, 0], Qmax=2)
     lib_i, orc_i = ffs.Instance(prob), oracle.Instance(prob)
-    S = np.array([[0, 5], [5, 10]])
+    S = np.array([[0, 5], [5, 12]])  # job 1 stage 1 starts after RS = 11: the only free op
     M = np.zeros((2, 2), int)
     for inst in (lib_i, orc_i):
         inst.commit(S, M)
