@@ -184,7 +184,7 @@ def bench_ours(args):
 
     # warm-up (untimed)
     for _ in range(args.warmup):
-        run_job(ffs, ffs.Instance(dyn.problem), dyn, G, stream, False, {})
+        run_job(ffs, ffs.Instance(dyn.problem), dyn, G, stream, args.eager, {})
     insts = [ffs.Instance(dyn.problem) for _ in range(args.steps)]  # inputs resident before timing
     for inst in insts:
         inst.decode(torch.ones((1, inst.K), dtype=torch.int16, device=dev) *
@@ -220,7 +220,7 @@ def bench_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         inst = ffs.Instance(dyn.problem)
-        e2e_dec += run_job(ffs, inst, dyn, G, stream, False, e2e_stats)
+        e2e_dec += run_job(ffs, inst, dyn, G, stream, args.eager, e2e_stats)
         torch.cuda.synchronize()
         e2e_s += time.perf_counter() - t0
         inst.close()
@@ -316,6 +316,9 @@ def main():
     ap.add_argument("--ref-generations", type=int, default=2, help="oracle generations per reference step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch every generation directly instead of replaying its CUDA graph "
+                         "(for profilers that cannot follow graph launches)")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)

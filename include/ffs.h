@@ -20,9 +20,10 @@
  *     then by stage (the row-major order of the X/Y matrices of Eq. (10)-(11) with their
  *     -1 cells removed).  K is their count.
  *
- * Size limits (checked, FFS_E_ARG beyond them): jobs and genes <= 32767, stages and
- * machines per stage <= 127, total machines <= 32767, processing time <= 32767, peak
- * power <= 65535.
+ * Size limits (checked, FFS_E_ARG beyond them): jobs and genes <= 32767, stages <= 127,
+ * machines per stage <= 31, total machines <= 32767, processing time <= 32767, peak
+ * power <= 32767, and the schedule horizon past the rescheduling point (the latest
+ * release or executing end plus the total free processing time) below 2^26.
  */
 #ifndef FFS_H
 #define FFS_H

@@ -100,27 +100,68 @@ struct DecodeOut {
     int status;      // 0 ok, 1 profile outgrew Hcap, 2 malformed chromosome
 };
 
+// 4-bit mask of slots b .. b+3 that fall in [lo, hi).
+__device__ __forceinline__ unsigned range4(int b, int lo, int hi) {
+    const int l = min(max(lo - b, 0), 4), h = min(max(hi - b, 0), 4);
+    return ((1u << h) - 1u) & ~((1u << l) - 1u);
+}
+
+// Expands bits 0/1 of m to the low/high halfword of a 32-bit word.
+__device__ __forceinline__ uint32_t halves(unsigned m) {
+    return (m & 1u) * 0xFFFFu + (m & 2u) * 0x7FFF8000u;
+}
+
 // Earliest start r >= t0 (slots past RS) such that headroom h[r .. r+p) >= q everywhere.
-// Slots at or beyond the high-water mark hw were never touched and hold the full peak.
-// Returns `limit` as soon as the answer cannot be below it.  One 32-slot window per step:
-// a ballot finds the last violating slot and the candidate jumps past it.
+// Slots at or beyond the high-water mark hw were never touched and hold the full peak, so
+// only [r, min(r+p, hw)) needs checking.  Each lane reads 4 consecutive slots with one
+// 64-bit load (128 slots per step) and compares both halfwords of a word at once: with
+// headroom and q below 2^15, (h | 0x8000) - q keeps bit 15 set exactly when h >= q, and no
+// borrow crosses into the next halfword.  A ballot finds the last violating slot and the
+// candidate jumps past it.  Returns `limit` as soon as the answer cannot be below it.
+// Loads stay below hw <= Hcap, Hcap a multiple of 4.
 __device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0, int p, unsigned q,
                                               int limit, int lane) {
-    int run = t0, c = t0;
+    const uint32_t q2 = q * 0x10001u;
+    int run = t0, c = t0 & ~3;
     for (;;) {
         if (run >= limit) return limit;
-        const int end = run + p;
-        if (c >= end || c >= hw) return run;
-        const int pos = c + lane;
-        const bool bad = pos < end && pos < hw && h[pos] < q;
-        const unsigned bm = __ballot_sync(kFull, bad);
+        const int end = min(run + p, hw);
+        if (c >= end) return run;
+        const int b = c + 4 * lane;
+        unsigned badm = 0;  // bit i: slot b + i violates
+        if (b < end) {
+            const uint2 w = *reinterpret_cast<const uint2 *>(h + b);
+            const uint32_t dx = (w.x | 0x80008000u) - q2, dy = (w.y | 0x80008000u) - q2;
+            const unsigned good = ((dx >> 15) & 1u) | ((dx >> 30) & 2u) | ((dy >> 13) & 4u) | ((dy >> 28) & 8u);
+            badm = ~good & range4(b, run, end);
+        }
+        const unsigned bm = __ballot_sync(kFull, badm != 0);
         if (bm == 0) {
-            c += 32;
+            c += 128;
         } else {
-            run = c + 32 - __clz(bm);  // one past the last violating slot
-            c = run;
+            const int l = 31 - __clz(bm);
+            const unsigned lm = __shfl_sync(kFull, badm, l);
+            run = c + 4 * l + (31 - __clz(lm)) + 1;  // one past the last violating slot
+            c = run & ~3;
         }
     }
+}
+
+// Draws q on [t, e) and extends the touched region to e (untouched slots read as Qmax).
+// Slots in [t, e) hold at least q, so the halfword subtraction never borrows.
+__device__ __forceinline__ void commit_power(uint16_t *h, int &hw, int t, int e, unsigned q,
+                                             unsigned Qmax, int lane) {
+    const uint32_t q2 = q * 0x10001u, Q2 = Qmax * 0x10001u;
+    for (int b = (min(t, hw) & ~3) + 4 * lane; b < e; b += 128) {
+        const unsigned keep = range4(b, 0, hw), sub = range4(b, t, e);
+        uint2 w = make_uint2(0u, 0u);
+        if (keep) w = *reinterpret_cast<const uint2 *>(h + b);
+        const uint32_t kx = halves(keep), ky = halves(keep >> 2);
+        w.x = ((w.x & kx) | (Q2 & ~kx)) - (q2 & halves(sub));
+        w.y = ((w.y & ky) | (Q2 & ~ky)) - (q2 & halves(sub >> 2));
+        *reinterpret_cast<uint2 *>(h + b) = w;
+    }
+    hw = max(hw, e);
 }
 
 // Decodes one chromosome with the whole warp (Sec. 4.3, Alg. 1-2).  State lives in the
@@ -165,22 +206,41 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
 
     // Assigns gene k (Alg. 2); returns false if the profile would outgrow Hcap.
     auto place = [&](int k) -> bool {
-        const int j = T.gjob[k], s = T.gstg[k];
-        const int p = T.p[j * g + s];
-        const int est = max(RS, max(T.R[j], C[j])) - RS;
-        const int mo = T.moff[s];
-        int best_t = INT_MAX, best_m = 0;
+        const uint2 gr = T.grec[k];
+        const int j = (int)(gr.x & 0xFFFFu), s = (int)((gr.x >> 16) & 0xFFu), os = (int)(gr.x >> 24);
+        const int p = (int)(gr.y & 0xFFFFu), mo = (int)(gr.y >> 16);
+        const int cj = C[j], rj = T.R[j];
+        int mf = INT_MAX;   // lane m < o_s: end of the last op on machine m of stage s
+        unsigned ql = 0;    // ... and its power
+        if (lane < os) {
+            mf = mfree[mo + lane];
+            ql = (unsigned)T.q[mo + lane];
+        }
+        const int est = max(RS, max(rj, cj)) - RS;
+        int best_t, best_m;
         if (MACH == kMachGene) {
             best_m = x[k];
-            best_t = earliest_start(h, hw, max(est, mfree[mo + best_m] - RS), p, (unsigned)T.q[mo + best_m],
-                                    INT_MAX, lane);
+            const int t0 = max(est, __shfl_sync(kFull, mf, best_m) - RS);
+            best_t = earliest_start(h, hw, t0, p, __shfl_sync(kFull, ql, best_m), INT_MAX, lane);
         } else {
-            const int os = T.o[s];
-            for (int m = 0; m < os; ++m) {
-                const int t0 = max(est, mfree[mo + m] - RS);
-                if (t0 >= best_t) continue;  // cannot beat (or tie below) the best so far
-                const int t = earliest_start(h, hw, t0, p, (unsigned)T.q[mo + m], best_t, lane);
-                if (t < best_t) {
+            // Lexicographic minimum of (start, machine): the machine that frees first is
+            // scanned first; another is scanned only if it could still start earlier.
+            // Keys pack (t0, machine) so one warp reduction finds the minimum.
+            const int t0 = lane < os ? max(est, mf - RS) : INT_MAX;
+            const unsigned key = lane < os ? ((unsigned)t0 << 5) | (unsigned)lane : 0xFFFFFFFFu;
+            const unsigned kmin = __reduce_min_sync(kFull, key);
+            const int bmi = (int)(kmin & 31u), bt = (int)(kmin >> 5);
+            best_m = bmi;
+            best_t = earliest_start(h, hw, bt, p, __shfl_sync(kFull, ql, bmi), INT_MAX, lane);
+            unsigned cand = __ballot_sync(kFull, lane < os && lane != bmi && t0 <= best_t);
+            while (cand) {
+                const int m = __ffs(cand) - 1;
+                cand &= cand - 1;
+                const int tm = __shfl_sync(kFull, t0, m);
+                const int lim = best_t + (m < best_m ? 1 : 0);
+                if (tm >= lim) continue;
+                const int t = earliest_start(h, hw, tm, p, __shfl_sync(kFull, ql, m), lim, lane);
+                if (t < lim) {
                     best_t = t;
                     best_m = m;
                 }
@@ -188,15 +248,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
         }
         const int e = best_t + p;
         if (e > Hcap) return false;
-        const unsigned qq = (unsigned)T.q[mo + best_m];
-        const int lo = min(best_t, hw);
-        for (int pos = lo + lane; pos < e; pos += 32) {
-            unsigned v = pos < hw ? h[pos] : Qmax;
-            if (pos >= best_t) v -= qq;
-            h[pos] = (uint16_t)v;
-        }
-        hw = max(hw, e);
-        __syncwarp();
+        commit_power(h, hw, best_t, e, __shfl_sync(kFull, ql, best_m), Qmax, lane);
         if (lane == 0) {
             mfree[mo + best_m] = e + RS;
             C[j] = e + RS;
@@ -224,26 +276,12 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
         }
     } else {
         for (int n = 0; n < K; ++n) {
-            int besty = 0, bestj = -1;
+            unsigned kmax = 0;  // (y << 15 | job) of the best ready job head
             for (int j = lane; j < N; j += 32) {
                 const int k = nxt[j];
-                if (k >= 0 && k < T.gfirst[j] + T.gcnt[j]) {
-                    const int v = y[k];
-                    if (v > besty) {
-                        besty = v;
-                        bestj = j;
-                    }
-                }
+                if (k >= 0 && k < T.gfirst[j] + T.gcnt[j]) kmax = max(kmax, ((unsigned)y[k] << 15) | (unsigned)j);
             }
-#pragma unroll
-            for (int off = 16; off; off >>= 1) {
-                const int oy = __shfl_xor_sync(kFull, besty, off);
-                const int oj = __shfl_xor_sync(kFull, bestj, off);
-                if (oy > besty) {
-                    besty = oy;
-                    bestj = oj;
-                }
-            }
+            const int bestj = (int)(__reduce_max_sync(kFull, kmax) & 0x7FFFu);
             const int k = nxt[bestj];
             __syncwarp();
             if (lane == 0) nxt[bestj] = (int16_t)(k + 1);

@@ -3,6 +3,11 @@
 // stage them into shared memory with one bulk copy).  Internal to the library.
 #pragma once
 #include <stdint.h>
+#ifndef __CUDACC__
+struct uint2 { unsigned int x, y; };
+#else
+#include <vector_types.h>
+#endif
 
 #ifdef __CUDACC__
 #define FFS_HD __host__ __device__ __forceinline__
@@ -23,7 +28,7 @@ struct TabHeader {
     int32_t off_o, off_moff, off_q, off_p;
     int32_t off_R, off_D, off_C0, off_mfree0;
     int32_t off_gjob, off_gstg, off_gfirst, off_gcnt;
-    int32_t off_h0, pad1, pad2, pad3;
+    int32_t off_h0, off_grec, pad2, pad3;
 };
 static_assert(sizeof(TabHeader) == 112, "header layout");
 
@@ -36,6 +41,8 @@ struct Tabs {
     const int16_t *p, *gjob, *gfirst;
     const int8_t *gstg, *gcnt;
     const uint16_t *h0;
+    // Per gene, packed: x = job | stage << 16 | o_stage << 24, y = p | first machine << 16.
+    const uint2 *grec;
 };
 
 FFS_HD Tabs tabs_view(const char *base) {
@@ -56,11 +63,13 @@ FFS_HD Tabs tabs_view(const char *base) {
     t.gfirst = reinterpret_cast<const int16_t *>(base + h->off_gfirst);
     t.gcnt = reinterpret_cast<const int8_t *>(base + h->off_gcnt);
     t.h0 = reinterpret_cast<const uint16_t *>(base + h->off_h0);
+    t.grec = reinterpret_cast<const uint2 *>(base + h->off_grec);
     return t;
 }
 
 // Per-warp decode workspace in shared memory.
-//   h     uint16 [Hcap]   power headroom Qmax - Q_t for t = RS + i (Eq. 7-8)
+//   h     uint16 [Hcap]   power headroom Qmax - Q_t for t = RS + i (Eq. 7-8); Hcap is a
+//                         multiple of 8 and the slice is read and written 4 slots at a time
 //   C     int32  [N]      completion of each job's last assigned stage
 //   mfree int32  [M]      end of the last op assigned to each machine
 //   inv   int16  [K + N]  gene by priority rank (stage order) / next gene per job (Alg. 1)

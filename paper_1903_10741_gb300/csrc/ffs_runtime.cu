@@ -28,7 +28,7 @@ std::atomic<unsigned long long> g_launches{0};  // kernels issued by this librar
 
 constexpr int kSmemBudget = 112 * 1024;  // per CTA: two CTAs of four warps per SM
 constexpr int kMinSmemSlots = 256;       // below this the shared-memory profile is not worth it
-constexpr int kMaxN = 32767, kMaxG = 127, kMaxO = 127, kMaxM = 32767, kMaxP = 32767, kMaxQ = 65535;
+constexpr int kMaxN = 32767, kMaxG = 127, kMaxO = 31, kMaxM = 32767, kMaxP = 32767, kMaxQ = 32767;
 
 int num_sms() {
     static int n = 0;
@@ -178,7 +178,8 @@ int rebuild(ffs_instance *in) {
     }
     base = std::max(base, exec_end);
     const long long H = ((base - RS + work + 1) + 7) / 8 * 8;
-    if (H > INT32_MAX / 2 || (long long)RS + H > INT32_MAX) return FFS_E_ARG;
+    // start times are packed with a 5-bit machine index into 32-bit keys
+    if (H >= (1ll << 26) || (long long)RS + H > INT32_MAX) return FFS_E_ARG;
     in->K = (int)in->gjob.size();
     if (in->K > kMaxN) return FFS_E_ARG;
     in->Hfull = (int)H;
@@ -214,6 +215,7 @@ int rebuild(ffs_instance *in) {
     take(h.off_gfirst, 2 * N);
     take(h.off_gcnt, N);
     take(h.off_h0, 2 * E0);
+    take(h.off_grec, 8 * in->K);
     h.bytes = off;
     in->hdr = h;
     in->blob.assign(off, 0);
@@ -237,6 +239,12 @@ int rebuild(ffs_instance *in) {
     std::memcpy(b + h.off_gfirst, gfirst.data(), 2 * N);
     std::memcpy(b + h.off_gcnt, gcnt.data(), N);
     if (E0) std::memcpy(b + h.off_h0, h0.data(), 2 * E0);
+    uint32_t *gr = reinterpret_cast<uint32_t *>(b + h.off_grec);
+    for (int k = 0; k < in->K; ++k) {
+        const int j = in->gjob[k], s = in->gstg[k];
+        gr[2 * k] = (uint32_t)j | ((uint32_t)s << 16) | ((uint32_t)in->o[s] << 24);
+        gr[2 * k + 1] = (uint32_t)in->p[j * g + s] | ((uint32_t)in->moff[s] << 16);
+    }
 
     in->dev_dirty = true;
     in->version++;
