@@ -118,23 +118,20 @@ __device__ __forceinline__ uint32_t halves(unsigned m) {
 // headroom and q below 2^15, (h | 0x8000) - q keeps bit 15 set exactly when h >= q, and no
 // borrow crosses into the next halfword.  A ballot finds the last violating slot and the
 // candidate jumps past it.  Returns `limit` as soon as the answer cannot be below it.
-// Loads stay below hw <= Hcap, Hcap a multiple of 4.
-__device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0, int p, unsigned q,
+// Loads stay below hw <= Hcap (Hcap a multiple of 4); lanes past the window read slot 0.
+__device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0, int p, uint32_t q2,
                                               int limit, int lane) {
-    const uint32_t q2 = q * 0x10001u;
-    int run = t0, c = t0 & ~3;
-    for (;;) {
-        if (run >= limit) return limit;
-        const int end = min(run + p, hw);
-        if (c >= end) return run;
+    int run = t0;
+    if (run >= limit) return limit;
+    int end = min(run + p, hw);
+    int c = run & ~3;
+    while (c < end) {
         const int b = c + 4 * lane;
-        unsigned badm = 0;  // bit i: slot b + i violates
-        if (b < end) {
-            const uint2 w = *reinterpret_cast<const uint2 *>(h + b);
-            const uint32_t dx = (w.x | 0x80008000u) - q2, dy = (w.y | 0x80008000u) - q2;
-            const unsigned good = ((dx >> 15) & 1u) | ((dx >> 30) & 2u) | ((dy >> 13) & 4u) | ((dy >> 28) & 8u);
-            badm = ~good & range4(b, run, end);
-        }
+        const bool in = b < end;
+        const uint2 w = *reinterpret_cast<const uint2 *>(h + (in ? b : 0));
+        const uint32_t dx = (w.x | 0x80008000u) - q2, dy = (w.y | 0x80008000u) - q2;
+        const unsigned good = ((dx >> 15) & 1u) | ((dx >> 30) & 2u) | ((dy >> 13) & 4u) | ((dy >> 28) & 8u);
+        const unsigned badm = in ? (~good & range4(b, run, end)) : 0u;  // bit i: slot b + i violates
         const unsigned bm = __ballot_sync(kFull, badm != 0);
         if (bm == 0) {
             c += 128;
@@ -142,16 +139,18 @@ __device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0,
             const int l = 31 - __clz(bm);
             const unsigned lm = __shfl_sync(kFull, badm, l);
             run = c + 4 * l + (31 - __clz(lm)) + 1;  // one past the last violating slot
+            if (run >= limit) return limit;
+            end = min(run + p, hw);
             c = run & ~3;
         }
     }
+    return run;
 }
 
 // Draws q on [t, e) and extends the touched region to e (untouched slots read as Qmax).
 // Slots in [t, e) hold at least q, so the halfword subtraction never borrows.
-__device__ __forceinline__ void commit_power(uint16_t *h, int &hw, int t, int e, unsigned q,
-                                             unsigned Qmax, int lane) {
-    const uint32_t q2 = q * 0x10001u, Q2 = Qmax * 0x10001u;
+__device__ __forceinline__ void commit_power(uint16_t *h, int &hw, int t, int e, uint32_t q2,
+                                             uint32_t Q2, int lane) {
     for (int b = (min(t, hw) & ~3) + 4 * lane; b < e; b += 128) {
         const unsigned keep = range4(b, 0, hw), sub = range4(b, t, e);
         uint2 w = make_uint2(0u, 0u);
@@ -164,19 +163,46 @@ __device__ __forceinline__ void commit_power(uint16_t *h, int &hw, int t, int e,
     hw = max(hw, e);
 }
 
+// Machine choice for one op among the lanes m < os of a stage, each holding its machine's
+// availability t0 (slots past RS; INT_MAX elsewhere) and power q2.  Returns the
+// lexicographic minimum of (earliest power-feasible start, machine): the machine that
+// frees first is scanned first, another only if it could still start earlier.
+__device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int t0, uint32_t q2, int os,
+                                                 int p, int lane, int &best_t, int &best_m) {
+    const unsigned key = lane < os ? ((unsigned)t0 << 5) | (unsigned)lane : 0xFFFFFFFFu;
+    const unsigned kmin = __reduce_min_sync(kFull, key);
+    best_m = (int)(kmin & 31u);
+    best_t = earliest_start(h, hw, (int)(kmin >> 5), p, __shfl_sync(kFull, q2, best_m), INT_MAX, lane);
+    unsigned cand = __ballot_sync(kFull, lane < os && lane != best_m && t0 < best_t + (lane < best_m));
+    while (cand) {
+        const int m = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const int tm = __shfl_sync(kFull, t0, m);
+        const int lim = best_t + (m < best_m ? 1 : 0);
+        if (tm >= lim) continue;
+        const int t = earliest_start(h, hw, tm, p, __shfl_sync(kFull, q2, m), lim, lane);
+        if (t < lim) {
+            best_t = t;
+            best_m = m;
+        }
+    }
+}
+
 // Decodes one chromosome with the whole warp (Sec. 4.3, Alg. 1-2).  State lives in the
-// caller's workspace: h [Hcap] headroom, C [N], mfree [M], inv [K+N], y [K], x [K].
+// caller's workspace: h [Hcap] headroom, C [N], mfree [M], inv [2K+N], y [K], x [K].
 // Schedule output (S_out/M_out, [N*g]) is written for free ops only when non-null.
+//
+// C[j] starts at the end of the job's frozen prefix, raised to R_j when the job still
+// has free ops, so every op becomes available at max(RS, C[j]).
 template <int ORDER, int MACH>
 __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *C, int32_t *mfree,
                                  int16_t *inv, const int16_t *y, const int8_t *x, int32_t *S_out,
                                  int32_t *M_out, int lane) {
-    const int N = T.N, K = T.K, M = T.M, g = T.g, RS = T.RS;
-    const unsigned Qmax = (unsigned)T.Qmax;
+    const int N = T.N, K = T.K, g = T.g, RS = T.RS;
+    const uint32_t Q2 = (uint32_t)T.Qmax * 0x10001u;
 
     if (T.E0 > Hcap) return {0, 0, 1};  // executing ops alone outgrow the profile slice
-    for (int j = lane; j < N; j += 32) C[j] = T.C0[j];
-    for (int m = lane; m < M; m += 32) mfree[m] = T.mfree0[m];
+    for (int j = lane; j < N; j += 32) C[j] = T.gcnt[j] > 0 ? max(T.C0[j], T.R[j]) : T.C0[j];
     for (int i = lane; i < T.E0; i += 32) h[i] = T.h0[i];
     int hw = T.E0;
 
@@ -198,83 +224,75 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
         if (inv[i] < 0) bad = true;
     if (__any_sync(kFull, bad)) return {0, 0, 2};
 
-    int16_t *nxt = inv + K;  // Alg. 1 reading: next free gene of each job
-    if (ORDER == kOrderTopo) {
-        for (int j = lane; j < N; j += 32) nxt[j] = T.gfirst[j];
-        __syncwarp();
-    }
-
-    // Assigns gene k (Alg. 2); returns false if the profile would outgrow Hcap.
-    auto place = [&](int k) -> bool {
-        const uint2 gr = T.grec[k];
-        const int j = (int)(gr.x & 0xFFFFu), s = (int)((gr.x >> 16) & 0xFFu), os = (int)(gr.x >> 24);
-        const int p = (int)(gr.y & 0xFFFFu), mo = (int)(gr.y >> 16);
-        const int cj = C[j], rj = T.R[j];
-        int mf = INT_MAX;   // lane m < o_s: end of the last op on machine m of stage s
-        unsigned ql = 0;    // ... and its power
-        if (lane < os) {
-            mf = mfree[mo + lane];
-            ql = (unsigned)T.q[mo + lane];
-        }
-        const int est = max(RS, max(rj, cj)) - RS;
-        int best_t, best_m;
-        if (MACH == kMachGene) {
-            best_m = x[k];
-            const int t0 = max(est, __shfl_sync(kFull, mf, best_m) - RS);
-            best_t = earliest_start(h, hw, t0, p, __shfl_sync(kFull, ql, best_m), INT_MAX, lane);
-        } else {
-            // Lexicographic minimum of (start, machine): the machine that frees first is
-            // scanned first; another is scanned only if it could still start earlier.
-            // Keys pack (t0, machine) so one warp reduction finds the minimum.
-            const int t0 = lane < os ? max(est, mf - RS) : INT_MAX;
-            const unsigned key = lane < os ? ((unsigned)t0 << 5) | (unsigned)lane : 0xFFFFFFFFu;
-            const unsigned kmin = __reduce_min_sync(kFull, key);
-            const int bmi = (int)(kmin & 31u), bt = (int)(kmin >> 5);
-            best_m = bmi;
-            best_t = earliest_start(h, hw, bt, p, __shfl_sync(kFull, ql, bmi), INT_MAX, lane);
-            unsigned cand = __ballot_sync(kFull, lane < os && lane != bmi && t0 <= best_t);
-            while (cand) {
-                const int m = __ffs(cand) - 1;
-                cand &= cand - 1;
-                const int tm = __shfl_sync(kFull, t0, m);
-                const int lim = best_t + (m < best_m ? 1 : 0);
-                if (tm >= lim) continue;
-                const int t = earliest_start(h, hw, tm, p, __shfl_sync(kFull, ql, m), lim, lane);
-                if (t < lim) {
-                    best_t = t;
-                    best_m = m;
-                }
-            }
-        }
-        const int e = best_t + p;
-        if (e > Hcap) return false;
-        commit_power(h, hw, best_t, e, __shfl_sync(kFull, ql, best_m), Qmax, lane);
-        if (lane == 0) {
-            mfree[mo + best_m] = e + RS;
-            C[j] = e + RS;
-            if (S_out) {
-                S_out[j * g + s] = best_t + RS;
-                M_out[j * g + s] = best_m;
-            }
-        }
-        __syncwarp();
-        return true;
-    };
-
     if (ORDER == kOrderStage) {
+        // Z: stage by stage, y descending.  Each stage's genes, in priority order, go to
+        // order[soff[s] ..) by a ballot-compaction pass over inv.
+        int16_t *order = inv + K;
         for (int s = 0; s < g; ++s) {
+            int pos = T.soff[s];
             for (int base = 0; base < K; base += 32) {
                 const int i = base + lane;
                 const int k = i < K ? inv[i] : -1;
-                unsigned mask = __ballot_sync(kFull, k >= 0 && T.gstg[k] == s);
-                while (mask) {
-                    const int l = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    if (!place(__shfl_sync(kFull, k, l))) return {0, 0, 1};
+                const bool sel = k >= 0 && T.gstg[k] == s;
+                const unsigned mask = __ballot_sync(kFull, sel);
+                if (sel) order[pos + __popc(mask & ((1u << lane) - 1u))] = (int16_t)k;
+                pos += __popc(mask);
+            }
+        }
+        __syncwarp();
+        // Place the ops; the stage's machines live in lanes (availability, power).
+        for (int s = 0; s < g; ++s) {
+            const int lo = T.soff[s], hi = T.soff[s + 1];
+            if (lo == hi) continue;
+            const int mo = T.moff[s], os = T.o[s];
+            int mf = INT_MAX;  // lane m < os: end of the last op on machine m, past RS
+            uint32_t q2 = 0;
+            if (lane < os) {
+                mf = T.mfree0[mo + lane] - RS;
+                q2 = (uint32_t)T.q[mo + lane] * 0x10001u;
+            }
+            // software pipeline: the next op's record and job completion are loaded early
+            // (within a stage every job appears once, so C of the next job is final)
+            int k = order[lo];
+            uint2 gr = T.grec[k];
+            int cj = C[gr.x & 0xFFFFu];
+            for (int n = lo; n < hi; ++n) {
+                const int kn = order[min(n + 1, hi - 1)];
+                const uint2 grn = T.grec[kn];
+                const int cjn = C[grn.x & 0xFFFFu];
+                const int j = (int)(gr.x & 0xFFFFu), p = (int)(gr.y & 0xFFFFu);
+                const int est = max(cj - RS, 0);
+                int best_t, best_m;
+                if (MACH == kMachGene) {
+                    best_m = x[k];
+                    best_t = earliest_start(h, hw, max(est, __shfl_sync(kFull, mf, best_m)), p,
+                                            __shfl_sync(kFull, q2, best_m), INT_MAX, lane);
+                } else {
+                    earliest_machine(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m);
                 }
+                const int e = best_t + p;
+                if (e > Hcap) return {0, 0, 1};
+                commit_power(h, hw, best_t, e, __shfl_sync(kFull, q2, best_m), Q2, lane);
+                if (lane == best_m) mf = e;
+                if (lane == 0) {
+                    C[j] = e + RS;
+                    if (S_out) {
+                        S_out[j * g + s] = best_t + RS;
+                        M_out[j * g + s] = best_m;
+                    }
+                }
+                __syncwarp();
+                k = kn;
+                gr = grn;
+                cj = cjn;
             }
         }
     } else {
+        // Alg. 1 read as a topological order: the ready job head with the largest y.
+        int16_t *nxt = inv + K;
+        for (int j = lane; j < N; j += 32) nxt[j] = T.gfirst[j];
+        for (int m = lane; m < T.M; m += 32) mfree[m] = T.mfree0[m];
+        __syncwarp();
         for (int n = 0; n < K; ++n) {
             unsigned kmax = 0;  // (y << 15 | job) of the best ready job head
             for (int j = lane; j < N; j += 32) {
@@ -283,10 +301,38 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             }
             const int bestj = (int)(__reduce_max_sync(kFull, kmax) & 0x7FFFu);
             const int k = nxt[bestj];
+            const uint2 gr = T.grec[k];
+            const int j = (int)(gr.x & 0xFFFFu), s = (int)((gr.x >> 16) & 0xFFu), os = (int)(gr.x >> 24);
+            const int p = (int)(gr.y & 0xFFFFu), mo = (int)(gr.y >> 16);
+            int mf = INT_MAX;
+            uint32_t q2 = 0;
+            if (lane < os) {
+                mf = mfree[mo + lane] - RS;
+                q2 = (uint32_t)T.q[mo + lane] * 0x10001u;
+            }
+            const int est = max(C[j] - RS, 0);
+            int best_t, best_m;
+            if (MACH == kMachGene) {
+                best_m = x[k];
+                best_t = earliest_start(h, hw, max(est, __shfl_sync(kFull, mf, best_m)), p,
+                                        __shfl_sync(kFull, q2, best_m), INT_MAX, lane);
+            } else {
+                earliest_machine(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m);
+            }
+            const int e = best_t + p;
+            if (e > Hcap) return {0, 0, 1};
+            commit_power(h, hw, best_t, e, __shfl_sync(kFull, q2, best_m), Q2, lane);
             __syncwarp();
-            if (lane == 0) nxt[bestj] = (int16_t)(k + 1);
+            if (lane == 0) {
+                nxt[bestj] = (int16_t)(k + 1);
+                mfree[mo + best_m] = e + RS;
+                C[j] = e + RS;
+                if (S_out) {
+                    S_out[j * g + s] = best_t + RS;
+                    M_out[j * g + s] = best_m;
+                }
+            }
             __syncwarp();
-            if (!place(k)) return {0, 0, 1};
         }
     }
 

@@ -163,6 +163,105 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_init(GenArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- GA: island bookkeeping
+// Best (largest fitness, lowest index) and worst (smallest fitness, lowest index) of
+// fit[lo .. lo+n) with one warp; reads bypass L1 because other SMs wrote the values.
+__device__ __forceinline__ void warp_extremes(const int64_t *fit, int lo, int n, int lane, int &best, int &worst) {
+    long long bf = LLONG_MIN, wf = LLONG_MAX;
+    int bi = INT_MAX, wi = INT_MAX;
+    for (int t = lane; t < n; t += 32) {
+        const long long f = __ldcg(fit + lo + t);
+        if (fitter(f, lo + t, bf, bi)) { bf = f; bi = lo + t; }
+        if (f < wf || (f == wf && lo + t < wi)) { wf = f; wi = lo + t; }
+    }
+    warp_best(bf, bi);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const long long of = __shfl_xor_sync(kFull, wf, off);
+        const int oi = __shfl_xor_sync(kFull, wi, off);
+        if (of < wf || (of == wf && oi < wi)) { wf = of; wi = oi; }
+    }
+    best = bi;
+    worst = wi;
+}
+
+__device__ __forceinline__ void warp_copy_ind(int16_t *yd, int8_t *xd, const int16_t *ys, const int8_t *xs, int K,
+                                              int lane) {
+    for (int k = lane; k < K; k += 32) {
+        yd[k] = __ldcg(ys + k);
+        xd[k] = __ldcg(xs + k);
+    }
+}
+
+// Called by every warp after writing its child.  The last warp to finish an island does
+// the elitist replacement (Sec. 4.4: the island's best-ever individual overwrites its
+// worst child) and, at migration generations, records the island's best and worst; the
+// last island to finish performs the single-ring migration (island i's worst <- island
+// i-1's best, from those records) and advances the generation counter.  Completion is
+// counted with atomics after a device-wide fence; nothing waits.
+template <typename Args>
+__device__ void island_finish(const Args &a, int isl, int nx, int gen, int lane) {
+    __threadfence();
+    int ticket = 0;
+    if (lane == 0) ticket = atomicAdd(a.isl_done + isl, 1);
+    ticket = __shfl_sync(kFull, ticket, 0);
+    if (ticket != a.I - 1) return;
+    __threadfence();
+    const int K = a.K, I = a.I, lo = isl * I;
+    int16_t *Y = a.Y[nx];
+    int8_t *X = a.X[nx];
+    int64_t *obj = a.obj[nx], *fit = a.fit[nx];
+    int best, worst;
+    warp_extremes(fit, lo, I, lane, best, worst);
+    const long long fb = __ldcg(fit + best);
+    if (fb > a.bfit[isl]) {
+        warp_copy_ind(a.bY + (size_t)isl * K, a.bX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K, lane);
+        if (lane == 0) {
+            a.bobj[isl] = __ldcg(obj + best);
+            a.bfit[isl] = fb;
+        }
+    }
+    __syncwarp();
+    warp_copy_ind(Y + (size_t)worst * K, X + (size_t)worst * K, a.bY + (size_t)isl * K, a.bX + (size_t)isl * K, K, lane);
+    if (lane == 0) {
+        obj[worst] = a.bobj[isl];
+        fit[worst] = a.bfit[isl];
+        a.isl_done[isl] = 0;
+    }
+    __syncwarp();
+    const bool migrate = a.migrate_every > 0 && gen % a.migrate_every == 0 && a.nisl > 1;
+    if (migrate) {
+        warp_extremes(fit, lo, I, lane, best, worst);
+        warp_copy_ind(a.mY + (size_t)isl * K, a.mX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K, lane);
+        if (lane == 0) {
+            a.mobj[isl] = __ldcg(obj + best);
+            a.mfit[isl] = __ldcg(fit + best);
+            a.mw[isl] = worst;
+        }
+    }
+    __threadfence();
+    if (lane == 0) ticket = atomicAdd(&a.dev->islands_done, 1);
+    ticket = __shfl_sync(kFull, ticket, 0);
+    if (ticket != a.nisl - 1) return;
+    __threadfence();
+    if (migrate) {
+        for (int d = 0; d < a.nisl; ++d) {
+            const int src = (d + a.nisl - 1) % a.nisl, w = __ldcg(a.mw + d);
+            warp_copy_ind(Y + (size_t)w * K, X + (size_t)w * K, a.mY + (size_t)src * K, a.mX + (size_t)src * K, K, lane);
+            if (lane == 0) {
+                obj[w] = __ldcg(a.mobj + src);
+                fit[w] = __ldcg(a.mfit + src);
+            }
+        }
+    }
+    if (lane == 0) {
+        a.dev->islands_done = 0;
+        a.dev->nover = 0;
+        __threadfence();
+        a.dev->gen = gen;
+    }
+}
+
 // ---------------------------------------------------------------- GA: one generation
 // Selection -> paired crossover + correction -> mutation -> decode, one child per warp.
 // Each warp recomputes both parents of its pair from the counter-based stream, so the
@@ -309,24 +408,25 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
             int8_t *xo = a.X[nx] + (size_t)i * K;
             for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
         }
-        const DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x,
-                                                     nullptr, nullptr, lane);
+        DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
+        if (r.status == 1) {  // the schedule outgrew the shared slice: redo it in global memory
+            uint16_t *hg = a.gscratch + (size_t)(blockIdx.x * kWarpsPerBlock + warp) * (size_t)a.H;
+            r = decode_warp<ORDER, MACH>(T, hg, a.H, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
+        }
         if (lane == 0) {
-            if (r.status == 1) {
-                a.over_list[atomicAdd(&a.dev->nover, 1)] = i;
-            } else if (r.status == 2) {
-                atomicOr(a.err, kErrBadChromosome);
+            if (r.status != 0) {
+                atomicOr(a.err, r.status == 2 ? kErrBadChromosome : kErrOverflow);
             } else {
                 const long long o = (long long)T.WT * r.tard + r.cmax;
                 a.obj[nx][i] = o;
                 a.fit[nx][i] = emax - o > 0 ? emax - o : 0;
             }
         }
-        __syncwarp();
+        island_finish(a, i / I, nx, (int)gen, lane);
     }
 }
 
-// ---------------------------------------------------------------- GA: island bookkeeping
+// ---------------------------------------------------------------- GA: generation 0 bookkeeping
 constexpr int kReplThreads = 256;
 
 // Block-wide best (largest fitness, lowest index) and worst (smallest fitness, lowest index).
@@ -393,63 +493,16 @@ __global__ void k_emax(ReplArgs a) {
     }
 }
 
-// Elitist replacement (one CTA per island): the best-ever individual of the island is
-// updated from the children and overwrites the worst child.  At migration generations
-// the island's best and worst after replacement are recorded for the ring exchange.
-__global__ void __launch_bounds__(kReplThreads) k_replace(ReplArgs a) {
+// Generation 0: the best initial individual of every island becomes its best-ever.
+__global__ void __launch_bounds__(kReplThreads) k_init_best(ReplArgs a) {
     const int isl = blockIdx.x, lo = isl * a.I, K = a.K;
-    const int buf = a.init ? 0 : ((a.dev->gen + 1) & 1);
-    const int gen = a.dev->gen + 1;
-    int16_t *Y = a.Y[buf];
-    int8_t *X = a.X[buf];
-    int64_t *obj = a.obj[buf], *fit = a.fit[buf];
     int best, worst;
-    island_extremes(fit, lo, a.I, best, worst);
-    const bool improve = a.init || fit[best] > a.bfit[isl];
-    __syncthreads();  // every thread has read bfit before thread 0 may overwrite it
-    if (improve) {
-        copy_ind(a.bY + (size_t)isl * K, a.bX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K);
-        if (threadIdx.x == 0) {
-            a.bobj[isl] = obj[best];
-            a.bfit[isl] = fit[best];
-        }
-    }
-    __syncthreads();
-    if (a.init) return;
-    copy_ind(Y + (size_t)worst * K, X + (size_t)worst * K, a.bY + (size_t)isl * K, a.bX + (size_t)isl * K, K);
+    island_extremes(a.fit[0], lo, a.I, best, worst);
+    copy_ind(a.bY + (size_t)isl * K, a.bX + (size_t)isl * K, a.Y[0] + (size_t)best * K, a.X[0] + (size_t)best * K, K);
     if (threadIdx.x == 0) {
-        obj[worst] = a.bobj[isl];
-        fit[worst] = a.bfit[isl];
+        a.bobj[isl] = a.obj[0][best];
+        a.bfit[isl] = a.fit[0][best];
     }
-    __syncthreads();
-    const int nisl = a.P / a.I;
-    if (a.migrate_every > 0 && gen % a.migrate_every == 0 && nisl > 1) {
-        island_extremes(fit, lo, a.I, best, worst);
-        copy_ind(a.mY + (size_t)isl * K, a.mX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K);
-        if (threadIdx.x == 0) {
-            a.mobj[isl] = obj[best];
-            a.mfit[isl] = fit[best];
-            a.mw[isl] = worst;
-        }
-    }
-}
-
-// Single-ring migration: island i's worst <- island (i-1)'s best, from the snapshot.
-__global__ void __launch_bounds__(kReplThreads) k_migrate(ReplArgs a) {
-    const int nisl = a.P / a.I, gen = a.dev->gen + 1;
-    if (!(a.migrate_every > 0 && gen % a.migrate_every == 0 && nisl > 1)) return;
-    const int isl = blockIdx.x, K = a.K, buf = (a.dev->gen + 1) & 1;
-    const int src = (isl + nisl - 1) % nisl, w = a.mw[isl];
-    copy_ind(a.Y[buf] + (size_t)w * K, a.X[buf] + (size_t)w * K, a.mY + (size_t)src * K, a.mX + (size_t)src * K, K);
-    if (threadIdx.x == 0) {
-        a.obj[buf][w] = a.mobj[src];
-        a.fit[buf][w] = a.mfit[src];
-    }
-}
-
-__global__ void k_advance(GADev *dev) {
-    dev->gen += 1;
-    dev->nover = 0;
 }
 
 // Raises a kernel's dynamic shared memory limit once per (kernel, size); later calls,
@@ -544,17 +597,7 @@ cudaError_t launch_emax(const ReplArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_replace(const ReplArgs &a, cudaStream_t st) {
-    k_replace<<<a.P / a.I, kReplThreads, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_migrate(const ReplArgs &a, cudaStream_t st) {
-    k_migrate<<<a.P / a.I, kReplThreads, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_advance(GADev *dev, cudaStream_t st) {
-    k_advance<<<1, 1, 0, st>>>(dev);
+    k_init_best<<<a.P / a.I, kReplThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -37,18 +37,30 @@ struct DecodeArgs {
 struct GenArgs {
     const char *blob;
     int blob_bytes;
-    int Hcap;
+    int Hcap;                   // shared-memory profile slots per warp
+    int H;                      // full profile bound: slots per warp of gscratch
+    uint16_t *gscratch;         // global profiles for children that outgrow Hcap
     int16_t *Y[2];
     int8_t *X[2];
     int64_t *obj[2];
     int64_t *fit[2];
     GADev *dev;
-    int P, I, tour_k, side;     // side: torus side for 5-neighbourhood selection
+    int P, I, K, tour_k, side;  // side: torus side for 5-neighbourhood selection
     uint64_t pc_thr, pm_thr;    // floor(p * 2^32)
     uint32_t instance_id;
     uint64_t seed;
     int32_t *over_list;
     int32_t *err;
+    // island bookkeeping, done by the last warp to finish each island
+    int32_t *isl_done;          // [n_isl] children finished this generation
+    int nisl, migrate_every;
+    int16_t *bY;                // best-ever individual per island
+    int8_t *bX;
+    int64_t *bobj, *bfit;
+    int16_t *mY;                // migrants (island bests after replacement)
+    int8_t *mX;
+    int64_t *mobj, *mfit;
+    int32_t *mw;                // worst slot of each island at migration time
 };
 
 struct ReplArgs {
@@ -80,7 +92,5 @@ cudaError_t launch_ga_generation(int order, int mach, const GenArgs &a, const Ta
 cudaError_t prepare_ga_generation(int order, int mach, const TabHeader &h, int Hcap);
 cudaError_t launch_emax(const ReplArgs &a, cudaStream_t st);
 cudaError_t launch_replace(const ReplArgs &a, cudaStream_t st);
-cudaError_t launch_migrate(const ReplArgs &a, cudaStream_t st);
-cudaError_t launch_advance(GADev *dev, cudaStream_t st);
 
 }  // namespace edffs

@@ -28,7 +28,7 @@ struct TabHeader {
     int32_t off_o, off_moff, off_q, off_p;
     int32_t off_R, off_D, off_C0, off_mfree0;
     int32_t off_gjob, off_gstg, off_gfirst, off_gcnt;
-    int32_t off_h0, off_grec, pad2, pad3;
+    int32_t off_h0, off_grec, off_soff, pad3;
 };
 static_assert(sizeof(TabHeader) == 112, "header layout");
 
@@ -43,6 +43,7 @@ struct Tabs {
     const uint16_t *h0;
     // Per gene, packed: x = job | stage << 16 | o_stage << 24, y = p | first machine << 16.
     const uint2 *grec;
+    const int32_t *soff;  // [g+1] first gene index of each stage in the stage-major order
 };
 
 FFS_HD Tabs tabs_view(const char *base) {
@@ -64,6 +65,7 @@ FFS_HD Tabs tabs_view(const char *base) {
     t.gcnt = reinterpret_cast<const int8_t *>(base + h->off_gcnt);
     t.h0 = reinterpret_cast<const uint16_t *>(base + h->off_h0);
     t.grec = reinterpret_cast<const uint2 *>(base + h->off_grec);
+    t.soff = reinterpret_cast<const int32_t *>(base + h->off_soff);
     return t;
 }
 
@@ -72,7 +74,8 @@ FFS_HD Tabs tabs_view(const char *base) {
 //                         multiple of 8 and the slice is read and written 4 slots at a time
 //   C     int32  [N]      completion of each job's last assigned stage
 //   mfree int32  [M]      end of the last op assigned to each machine
-//   inv   int16  [K + N]  gene by priority rank (stage order) / next gene per job (Alg. 1)
+//   inv   int16  [2K + N] gene by priority rank, then the stage-by-stage order (or the
+//                         next gene of every job for Alg. 1)
 //   y     int16  [K], x int8 [K]   the chromosome being decoded
 //   bits  uint32 [K/32+1] value bitmap for the crossover correction (GA kernels only)
 struct WarpLayout {
@@ -85,7 +88,7 @@ FFS_HD WarpLayout warp_layout(int N, int M, int K, int Hcap, bool ga) {
     L.off_h = o;     o += align16(Hcap * 2);
     L.off_C = o;     o += align16(N * 4);
     L.off_mfree = o; o += align16(M * 4);
-    L.off_inv = o;   o += align16((K + N) * 2);
+    L.off_inv = o;   o += align16((2 * K + N) * 2);
     L.off_y = o;     o += align16(K * 2);
     L.off_x = o;     o += align16(K);
     L.off_bits = o;  o += ga ? align16(((K + 32) / 32) * 4) : 0;
@@ -98,7 +101,7 @@ struct GADev {
     int32_t gen;     // generations completed; population lives in buffer gen & 1
     int32_t nover;   // children whose profile outgrew shared memory this generation
     int32_t err;     // sticky error bits (1 bad chromosome, 2 profile overflow, 4 wait timeout)
-    int32_t pad;
+    int32_t islands_done;  // islands whose replacement finished this generation
     int64_t emax;    // E_max of Eq. (13)
 };
 

@@ -104,7 +104,7 @@ struct ga_population {
     int16_t *bY = nullptr, *mY = nullptr;
     int8_t *bX = nullptr, *mX = nullptr;
     int64_t *bobj = nullptr, *bfit = nullptr, *mobj = nullptr, *mfit = nullptr;
-    int32_t *mw = nullptr, *over = nullptr, *err = nullptr;
+    int32_t *mw = nullptr, *over = nullptr, *err = nullptr, *isl_done = nullptr;
     GADev *dev = nullptr;
     uint16_t *scratch = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -125,7 +125,7 @@ struct ga_population {
         }
         dfree(bY); dfree(bX); dfree(bobj); dfree(bfit);
         dfree(mY); dfree(mX); dfree(mobj); dfree(mfit); dfree(mw);
-        dfree(over); dfree(err); dfree(dev); dfree(scratch);
+        dfree(over); dfree(err); dfree(dev); dfree(scratch); dfree(isl_done);
     }
 };
 
@@ -216,6 +216,7 @@ int rebuild(ffs_instance *in) {
     take(h.off_gcnt, N);
     take(h.off_h0, 2 * E0);
     take(h.off_grec, 8 * in->K);
+    take(h.off_soff, 4 * (g + 1));
     h.bytes = off;
     in->hdr = h;
     in->blob.assign(off, 0);
@@ -239,6 +240,9 @@ int rebuild(ffs_instance *in) {
     std::memcpy(b + h.off_gfirst, gfirst.data(), 2 * N);
     std::memcpy(b + h.off_gcnt, gcnt.data(), N);
     if (E0) std::memcpy(b + h.off_h0, h0.data(), 2 * E0);
+    int32_t *soff = reinterpret_cast<int32_t *>(b + h.off_soff);
+    for (int k = 0; k < in->K; ++k) soff[in->gstg[k] + 1]++;
+    for (int s = 0; s < g; ++s) soff[s + 1] += soff[s];
     uint32_t *gr = reinterpret_cast<uint32_t *>(b + h.off_grec);
     for (int k = 0; k < in->K; ++k) {
         const int j = in->gjob[k], s = in->gstg[k];
@@ -566,6 +570,14 @@ static void ga_gen_args(ga_population *pp, GenArgs *a) {
     a->dev = pp->dev;
     a->P = pp->P;
     a->I = pp->I;
+    a->K = pp->K;
+    a->H = pp->hdr.H;
+    a->gscratch = pp->scratch;
+    a->isl_done = pp->isl_done;
+    a->nisl = pp->nisl;
+    a->migrate_every = pp->par.migrate_every;
+    a->bY = pp->bY; a->bX = pp->bX; a->bobj = pp->bobj; a->bfit = pp->bfit;
+    a->mY = pp->mY; a->mX = pp->mX; a->mobj = pp->mobj; a->mfit = pp->mfit; a->mw = pp->mw;
     a->tour_k = pp->par.tournament_k;
     a->side = pp->side;
     a->pc_thr = ((uint64_t)(uint32_t)pp->par.pc_num << 32) / (uint64_t)(uint32_t)pp->par.pc_den;
@@ -594,23 +606,15 @@ static void ga_fallback_args(ga_population *pp, DecodeArgs *d, bool ga_mode) {
     d->err = pp->err;
 }
 
-// One generation: fused operators + decode, fallback decode, replacement, migration, advance.
-// With timing events, the fused kernel is bracketed by ev0/ev1 on the population's stream.
+// One generation is one kernel: selection, crossover, mutation and decoding per child,
+// then (by the last warps to finish) elitist replacement, migration and the counter.
+// With timing events, the kernel is bracketed by ev0/ev1 on the population's stream.
 static int ga_enqueue_generation(ga_population *pp, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
-    const int order = pp->par.order_mode, mach = pp->par.machine_mode;
     GenArgs a;
     ga_gen_args(pp, &a);
     if (ev0) FFS_CUDA(cudaEventRecord(ev0, pp->st));
-    FFS_CUDA(launch_ga_generation(order, mach, a, pp->hdr, pp->grid_gen, pp->st));
+    FFS_CUDA(launch_ga_generation(pp->par.order_mode, pp->par.machine_mode, a, pp->hdr, pp->grid_gen, pp->st));
     if (ev1) FFS_CUDA(cudaEventRecord(ev1, pp->st));
-    DecodeArgs d;
-    ga_fallback_args(pp, &d, true);
-    FFS_CUDA(launch_decode(order, mach, true, d, pp->hdr, pp->grid_fb, pp->st));
-    ReplArgs r;
-    ga_replace_args(pp, &r, 0);
-    FFS_CUDA(launch_replace(r, pp->st));
-    FFS_CUDA(launch_migrate(r, pp->st));
-    FFS_CUDA(launch_advance(pp->dev, pp->st));
     return FFS_OK;
 }
 
@@ -655,13 +659,15 @@ int ga_population_create(ffs_instance *in, const ga_params *par, ga_population *
          dalloc(&pp->mY, NK) == cudaSuccess && dalloc(&pp->mX, NK) == cudaSuccess &&
          dalloc(&pp->mobj, pp->nisl) == cudaSuccess && dalloc(&pp->mfit, pp->nisl) == cudaSuccess &&
          dalloc(&pp->mw, pp->nisl) == cudaSuccess && dalloc(&pp->over, P) == cudaSuccess &&
-         dalloc(&pp->err, 1) == cudaSuccess && dalloc(&pp->dev, 1) == cudaSuccess;
+         dalloc(&pp->err, 1) == cudaSuccess && dalloc(&pp->dev, 1) == cudaSuccess &&
+         dalloc(&pp->isl_done, pp->nisl) == cudaSuccess;
     if (!ok) return fail(FFS_E_NOMEM);
     pp->Hcap = smem_slots(pp->hdr, true);
     pp->grid_gen = std::max(1, std::min((P + kWarpsPerBlock - 1) / kWarpsPerBlock,
                                         num_sms() * std::max(1, (228 * 1024) / (cta_smem_bytes(pp->hdr, pp->Hcap, true, false) + 1024))));
     pp->grid_fb = std::max(1, std::min((P + kWarpsPerBlock - 1) / kWarpsPerBlock, num_sms() * 2));
-    if (dalloc(&pp->scratch, (size_t)pp->grid_fb * kWarpsPerBlock * pp->hdr.H) != cudaSuccess) return fail(FFS_E_NOMEM);
+    if (dalloc(&pp->scratch, (size_t)std::max(pp->grid_fb, pp->grid_gen) * kWarpsPerBlock * pp->hdr.H) != cudaSuccess)
+        return fail(FFS_E_NOMEM);
     cudaStream_t st = pp->st;
     int rc = FFS_OK;
     auto step = [&](cudaError_t e) {
@@ -671,6 +677,7 @@ int ga_population_create(ffs_instance *in, const ga_params *par, ga_population *
     for (int b = 0; b < 2; ++b) step(cudaMemsetAsync(pp->X[b], 0, PK, st));
     step(cudaMemsetAsync(pp->err, 0, 4, st));
     step(cudaMemsetAsync(pp->dev, 0, sizeof(GADev), st));
+    step(cudaMemsetAsync(pp->isl_done, 0, 4 * (size_t)pp->nisl, st));
     GenArgs a;
     ga_gen_args(pp, &a);
     step(launch_ga_init(par->order_mode, par->machine_mode, a, pp->hdr, pp->grid_gen, st));
@@ -683,7 +690,7 @@ int ga_population_create(ffs_instance *in, const ga_params *par, ga_population *
     step(launch_replace(r, st));
     step(cudaMemsetAsync(&pp->dev->nover, 0, 4, st));
     if (rc != FFS_OK) return fail(rc);
-    g_launches += 4;
+    g_launches += 4;  // init, fallback decode, E_max, island bests
     // Capture one generation once; ga_run replays it.
     if (prepare_ga_generation(par->order_mode, par->machine_mode, pp->hdr, pp->Hcap) != cudaSuccess)
         return fail(FFS_E_CUDA);
@@ -746,7 +753,7 @@ int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
     if (pp->version != in->version) return FFS_E_STATE;
     if (!pp->profiling) {
         for (int i = 0; i < generations; ++i) FFS_CUDA(cudaGraphLaunch(pp->graph, pp->st));
-        g_launches += 5ull * (unsigned long long)generations;
+        g_launches += (unsigned long long)generations;
         FFS_CUDA(cudaStreamSynchronize(pp->st));
     } else {
         while ((int)pp->ev.size() < 2 * generations) {
@@ -755,7 +762,7 @@ int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
             pp->ev.push_back(e);
         }
         for (int i = 0; i < generations; ++i) FFS_TRY(ga_enqueue_generation(pp, pp->ev[2 * i], pp->ev[2 * i + 1]));
-        g_launches += 5ull * (unsigned long long)generations;
+        g_launches += (unsigned long long)generations;
         FFS_CUDA(cudaStreamSynchronize(pp->st));
         for (int i = 0; i < generations; ++i) {
             float ms = 0.f;
