@@ -45,6 +45,10 @@ WORKLOAD = ("dynamic rescheduling, plain GA: 50 initial jobs, 5 stages x U{2..4}
 # its own GA trajectory of this job (python -m oracle.work_per_decode --generations 500
 # --every 50: 53232 / 62226 / 68630 / 75374 for the four solves, mean 64865).
 SLOTS_PER_DECODE = 64865.5
+# DRAM bytes (read + write) of one generation-kernel launch from the ncu capture of the
+# current kernel (dram__bytes_read.sum + dram__bytes_write.sum, initial solve); None once
+# the kernel changes until it is captured again.
+TRAFFIC_BYTES = 418816
 # INT32 issue ceiling: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (lane-ops/s).
 ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
@@ -257,7 +261,7 @@ def bench_ours(args):
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "fused selection/crossover/mutation/decode generation kernel",
                      "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS,
-                     "traffic": None, "avg_launch_us": avg_launch_s * 1e6,
+                     "traffic": TRAFFIC_BYTES, "avg_launch_us": avg_launch_s * 1e6,
                      "timing": f"CUDA events around each of {prof['kernel_launches']} launches in a profiled pass of "
                                f"{args.steps} jobs",
                      "work_per_launch": f"{slots_per_decode():.0f} slot checks/decode x {P} decodes"},
