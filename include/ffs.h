@@ -162,6 +162,26 @@ int ffs_decode_schedule(ffs_instance *inst, int32_t order_mode, int32_t machine_
                         const int16_t *y, const int8_t *x, int32_t count,
                         int64_t *obj, int32_t *start, int32_t *machine, void *stream);
 
+/* Allocation-free variant of ffs_decode, for callers that cannot allocate device memory:
+ * code that runs while a CUDA stream is being captured (cudaMalloc is not permitted
+ * there), hosts that fix the process's device memory at start-up, and real-time loops
+ * that must not wait on the allocator.  The paper has no counterpart; it is a deployment
+ * aid.  Arguments and results are those of ffs_decode.  It allocates nothing: its scratch
+ * (error word, instance tables, per-warp power profiles) is one 16 MiB device array
+ * inside the library, reserved on every GPU that loads it until the process exits.
+ *   - Limits: instance tables up to 1 MiB, and 4 warps' profiles (4 * 2 bytes per slot of
+ *     ffs_info.horizon) within the remaining ~15 MiB; beyond them it returns FFS_E_ARG
+ *     and ffs_last_error() explains.  ffs_decode has no such limit.
+ *   - The first call on each device looks up the array's device address; make that
+ *     first call before any stream capture begins.
+ *   - Every call shares the one array: calls whose work overlaps on the GPU (other
+ *     streams, other threads) race and must be serialised by the caller.
+ *   - Synchronous: returns after `stream` has finished, with FFS_E_DEVICE if a row was
+ *     not a permutation of 1..K. */
+int ffs_decode_noalloc(ffs_instance *inst, int32_t order_mode, int32_t machine_mode,
+                       const int16_t *y, const int8_t *x, int32_t count,
+                       int64_t *obj, int64_t *tard, int32_t *cmax, void *stream);
+
 /* Synchronises `stream` and returns FFS_E_DEVICE if a decode since the last check met a
  * malformed chromosome, FFS_OK otherwise (and clears the flag). */
 int ffs_decode_check(ffs_instance *inst, void *stream);

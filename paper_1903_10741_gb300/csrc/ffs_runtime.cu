@@ -13,6 +13,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -920,3 +921,99 @@ int ga_restore(ga_population *pp, const void *buf, size_t len) {
 }
 
 }  // extern "C"
+
+// ====================================================================== allocation-free decode
+//
+// Some callers cannot allocate device memory: code running inside a CUDA stream capture,
+// where cudaMalloc is not permitted; hosts that hand the library a fixed memory budget and
+// forbid growth after start-up; and real-time loops that must not block on the
+// allocator.  ffs_decode_noalloc serves them.  It runs the global-profile decode kernel
+// with every piece of scratch it needs placed in one file-scope device array, so it
+// allocates nothing.
+//
+// The array is kNoAllocBytes, reserved on every GPU that loads the library until the
+// process exits.  Its layout is: [0, 256) the kernel's error word; [256, 256 + 1 MiB)
+// the instance tables; the rest per-warp power profiles.
+namespace {
+
+constexpr size_t kNoAllocBytes = 16u << 20;
+constexpr size_t kNoAllocTableOff = 256, kNoAllocTableCap = 1u << 20;
+constexpr size_t kNoAllocProfileOff = kNoAllocTableOff + kNoAllocTableCap;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {};  // device address of the array, per device
+
+// Looks up the array's device address for the current device once.  In host code the
+// array's name is only a host-side stand-in, so the kernel must get this address.
+int noalloc_scratch(void **out) {
+    int dev = 0;
+    FFS_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return FFS_E_ARG;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        FFS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return FFS_OK;
+}
+
+}  // namespace
+
+extern "C" int ffs_decode_noalloc(ffs_instance *in, int32_t order_mode, int32_t machine_mode,
+                                  const int16_t *y, const int8_t *x, int32_t count, int64_t *obj,
+                                  int64_t *tard, int32_t *cmax, void *stream) {
+    if (!in) return FFS_E_ARG;
+    FFS_TRY(check_modes(order_mode, machine_mode));
+    if (count < 0 || (count > 0 && (!y || !obj)) || (machine_mode == FFS_MACH_GENE && count > 0 && !x))
+        return FFS_E_ARG;
+    if (count == 0) return FFS_OK;
+    const TabHeader &h = in->hdr;
+    const size_t per_cta = (size_t)kWarpsPerBlock * (size_t)h.H * sizeof(uint16_t);
+    const size_t profile_bytes = kNoAllocBytes - kNoAllocProfileOff;
+    if ((size_t)h.bytes > kNoAllocTableCap || per_cta > profile_bytes) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "ffs_decode_noalloc: instance needs %d table bytes (limit %zu) and %zu profile bytes per "
+                      "4 warps (limit %zu); use ffs_decode",
+                      h.bytes, kNoAllocTableCap, per_cta, profile_bytes);
+        return FFS_E_ARG;
+    }
+    void *base = nullptr;
+    FFS_TRY(noalloc_scratch(&base));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *b = static_cast<char *>(base);
+    int32_t *err = reinterpret_cast<int32_t *>(b);
+    char *blob = b + kNoAllocTableOff;
+    uint16_t *prof = reinterpret_cast<uint16_t *>(b + kNoAllocProfileOff);
+    // The array keeps the previous call's contents: the error word must start at zero.
+    // The tables are rewritten and every profile slice is initialised by the kernel.
+    FFS_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+    FFS_CUDA(cudaMemcpyAsync(blob, in->blob.data(), (size_t)h.bytes, cudaMemcpyHostToDevice, st));
+    const int fit = (int)std::min<size_t>(profile_bytes / per_cta, (size_t)INT32_MAX);
+    const int grid = std::max(1, std::min({(count + kWarpsPerBlock - 1) / kWarpsPerBlock, num_sms() * 4, fit}));
+    DecodeArgs a{};
+    a.blob = blob;
+    a.blob_bytes = h.bytes;
+    a.Hcap = h.H;
+    a.Y[0] = a.Y[1] = y;
+    a.X[0] = a.X[1] = x;
+    a.count = count;
+    a.obj[0] = a.obj[1] = obj;
+    a.tard = tard;
+    a.cmax = cmax;
+    a.gscratch = prof;
+    a.err = err;
+    FFS_CUDA(launch_decode(order_mode, machine_mode, true, a, h, grid, st));
+    g_launches += 1;
+    // The host copy of the tables must outlive the copy, and the error word is read here:
+    // the call returns after the stream has finished its work.
+    FFS_CUDA(cudaStreamSynchronize(st));
+    int32_t e = 0;
+    FFS_CUDA(cudaMemcpy(&e, err, sizeof(e), cudaMemcpyDeviceToHost));
+    if (e & kErrTimeout) return FFS_E_TIMEOUT;
+    return e ? FFS_E_DEVICE : FFS_OK;
+}

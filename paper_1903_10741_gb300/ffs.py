@@ -76,6 +76,8 @@ _SIGS = {
     "ffs_decode_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                       C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ffs_decode_check": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ffs_decode_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ga_population_create": (C.c_int, [C.c_void_p, C.POINTER(GAParams_c), C.POINTER(C.c_void_p)]),
     "ga_population_destroy": (C.c_int, [C.c_void_p]),
     "ga_run": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Result_c)]),
@@ -225,6 +227,21 @@ class Instance:
         if check:
             _check(lib().ffs_decode_check(self._h, st), "ffs_decode")
         return out
+
+    def decode_noalloc(self, y, x=None, order_mode=ORDER_STAGE, mach_mode=MACH_EARLIEST, stream=None):
+        """Decodes like ``decode`` through ``ffs_decode_noalloc``: the library uses only its
+        fixed internal device scratch, never allocating, for callers that cannot allocate
+        (for instance while a CUDA graph is being captured).  The output tensors are
+        allocated here, by the caller's side.  Synchronous."""
+        import torch
+        count = int(y.shape[0]) if y.dim() == 2 else 1
+        obj = torch.empty(count, dtype=torch.int64, device=y.device)
+        tard = torch.empty(count, dtype=torch.int64, device=y.device)
+        cmax = torch.empty(count, dtype=torch.int32, device=y.device)
+        _check(lib().ffs_decode_noalloc(self._h, order_mode, mach_mode, _dptr(y), _dptr(x), count,
+                                        _dptr(obj), _dptr(tard), _dptr(cmax), _stream_ptr(stream)),
+               "ffs_decode_noalloc")
+        return {"obj": obj, "tard": tard, "cmax": cmax}
 
 
 class Population:
