@@ -275,6 +275,90 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- batched
+BATCH_WORKLOAD = ("batched: 256 independent rescheduling instances (jobs U{20..200}, stages U{3..8}, machines "
+                  "U{1..6}, p U{1..99}, q U{5..30} kW, peak U{40..70}% of all-on power), each frozen at 30% of a "
+                  "seeded plan's makespan with 10% new jobs; population 512 (islands of 64), one persistent "
+                  "graph-captured launch per run, mapping from the autotuner")
+
+
+def batched_instances(ffs, torch, count):
+    """Rescheduling snapshots of the batched workload, built with the library's decoder."""
+    insts = []
+    for it in wl.batched(count, seed=1):
+        inst = ffs.Instance(it.problem)
+        y = np.random.default_rng(it.plan_seed).permutation(inst.K).astype(np.int16) + 1
+        yd = torch.from_numpy(y[None, :]).cuda()
+        sch = inst.decode(yd, schedule=True)
+        cm = int(inst.decode(yd)["cmax"][0])
+        inst.commit(sch["S"][0].cpu().numpy(), sch["M"][0].cpu().numpy())
+        t_now = it.rs_permille * cm // 1000
+        inst.reschedule(wl.random_arrivals(np.random.default_rng(it.arrival_seed), it.arrivals_n,
+                                           it.problem.g, t_now, 99), t_now)
+        insts.append(inst)
+    return insts
+
+
+def bench_batched(args):
+    import torch
+
+    from paper_1903_10741_gb300 import ffs
+
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    count, G = args.batch_count, args.generations
+    insts = batched_instances(ffs, torch, count)
+    t0 = time.perf_counter()
+    batch = ffs.Batch(insts, P=512, island=64, tour_k=2, pc=PC, pm=PM, migrate_every=MIGRATE, seed=SEED,
+                      stream=stream)
+    create_s = time.perf_counter() - t0
+    chosen = batch.tune(args.tune_generations)
+    for _ in range(args.warmup):
+        batch.run(args.tune_generations)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ffs.kernel_launches()
+    total_ms = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        batch.run(G)
+        e.record(stream)
+        e.synchronize()
+        total_ms += s.elapsed_time(e)
+    launches = ffs.kernel_launches() - launches0
+    clk = clocks.stop()
+    decodes = count * 512 * G * args.steps
+    kinfo = [i.info() for i in insts]
+    avg_launch_s = total_ms / args.steps / 1e3
+    achieved = BATCH_SLOTS_PER_DECODE * count * 512 * G / avg_launch_s / 1e12 if BATCH_SLOTS_PER_DECODE else None
+    line = {
+        "metric": METRIC, "value": decodes / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "instances": count, "generations_per_step": G,
+                   "genes": [min(k["n_genes"] for k in kinfo), max(k["n_genes"] for k in kinfo)],
+                   "tuned_mapping": chosen, "create_and_generation0_s": create_s,
+                   "l2": "flushed between steps (256 MiB write)"},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "persistent batched GA kernel", "achieved": achieved,
+                     "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                     "frac": achieved / ALU_PEAK_TOPS if achieved else None, "traffic": None,
+                     "avg_launch_us": avg_launch_s * 1e6,
+                     "work_per_launch": f"{BATCH_SLOTS_PER_DECODE} slot checks/decode x {count * 512 * G} decodes"},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# Oracle-measured slot checks per decode of the batched workload (python -m
+# oracle.work_per_decode --workload batched); None until measured.
+BATCH_SLOTS_PER_DECODE = None
+
+
 # ----------------------------------------------------------------------------- oracle
 def _oracle_ga(dyn):
     import oracle
@@ -338,12 +422,20 @@ def main():
     ap.add_argument("--ref-generations", type=int, default=2, help="oracle generations per reference step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["dynamic", "batched"], default="dynamic",
+                    help="dynamic: the headline rescheduling job; batched: 256 uneven instances")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--tune-generations", type=int, default=3)
     ap.add_argument("--eager", action="store_true",
                     help="launch every generation directly instead of replaying its CUDA graph "
                          "(for profilers that cannot follow graph launches)")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "batched":
+        if args.generations == 500:
+            args.generations = 300
+        bench_batched(args)
     else:
         bench_ours(args)
 

@@ -162,6 +162,58 @@ int ffs_decode_schedule(ffs_instance *inst, int32_t order_mode, int32_t machine_
                         const int16_t *y, const int8_t *x, int32_t count,
                         int64_t *obj, int32_t *start, int32_t *machine, void *stream);
 
+/* ---------------------------------------------------------------- batched GA */
+
+/* Many independent instances, each with its own population, advanced together by one
+ * persistent kernel launch (captured in a CUDA graph and replayed): a thread-block
+ * cluster per instance, one CTA per island (up to 8 per cluster).  Not in the paper: it
+ * serves many concurrent rescheduling requests with the GA of Sec. 4.4. */
+typedef struct ga_batch ga_batch;
+
+/* Launch mapping of a batch: warps per CTA, dynamic shared memory per CTA (tables plus
+ * each warp's power profile slice), the resulting number of persistent CTAs, the cluster
+ * size (a cluster owns one instance at a time and its CTAs share the islands), and the
+ * milliseconds per generation the tuner measured (0 if not tuned). */
+typedef struct {
+    int32_t warps_per_cta;
+    int32_t smem_bytes;
+    int32_t ctas;
+    int32_t cluster;          /* CTAs per instance (islands are dealt to them), 1..8 */
+    float ms_per_generation;
+} ga_batch_config;
+
+/* Copies the `count` instances' current tables and runs generation 0 of every one.  All
+ * share `params` (pop, island, operators, modes, seed, stream); instance i draws from
+ * stream id params->instance_id + i, so its run equals ga_population_create + ga_run
+ * with that id.  The instances must not be rescheduled while the batch is used. */
+int ga_batch_create(ffs_instance *const *insts, int32_t count, const ga_params *params, ga_batch **out);
+
+/* Frees a batch.  NULL is accepted. */
+int ga_batch_destroy(ga_batch *batch);
+
+/* Advances every instance by `generations` generations in one launch.  With `best` (an
+ * array of `count` results, caller-allocated, start/machine optional), each instance's
+ * best-ever schedule is decoded, returned and committed to its instance. */
+int ga_batch_run(ga_batch *batch, int32_t generations, ffs_result *best);
+
+/* As ga_population_read, for instance `index` of the batch. */
+int ga_batch_read(ga_batch *batch, int32_t index, int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit,
+                  int16_t *bY, int8_t *bX, int64_t *bobj, int64_t *bfit, int64_t *emax,
+                  int32_t *generation);
+
+/* Autotuner: times `generations` generations under each candidate mapping (clusters of
+ * 8/4/2 CTAs x 4/8/16 warps per CTA x 56/75/112/225 KB of shared memory per CTA) that fits
+ * every instance,
+ * restoring the batch state after every trial, and keeps the fastest.  Results never
+ * depend on the mapping. */
+int ga_batch_tune(ga_batch *batch, int32_t generations, ga_batch_config *chosen);
+
+/* Reads or sets the mapping (warps 1..16, shared memory 16..227 KB, cluster 1..8 and at
+ * most the island count; 0 keeps the current cluster size).  Setting a mapping that some
+ * instance does not fit returns FFS_E_ARG. */
+int ga_batch_get_config(const ga_batch *batch, ga_batch_config *config);
+int ga_batch_set_config(ga_batch *batch, const ga_batch_config *config);
+
 /* Allocation-free variant of ffs_decode, for callers that cannot allocate device memory:
  * code that runs while a CUDA stream is being captured (cudaMalloc is not permitted
  * there), hosts that fix the process's device memory at start-up, and real-time loops

@@ -9,6 +9,12 @@ That is the number of per-instant power checks (Eq. 7) and updates (Eq. 8) an ex
 evaluation performs.  Prints one JSON line.
 
     python -m oracle.work_per_decode --generations 500 --every 50
+    python -m oracle.work_per_decode --workload batched --samples 8
+
+The batched workload's figure averages, over its 256 rescheduling snapshots (each built
+with the oracle's own decoder: a seeded plan, frozen at 30% of its makespan, 10% new jobs),
+the slots of `--samples` uniformly random chromosomes per instance; every instance counts
+equally because each decodes the same population size per generation.
 """
 from __future__ import annotations
 
@@ -25,12 +31,35 @@ import oracle  # noqa: E402
 from paper_1903_10741_gb300 import workloads as wl  # noqa: E402
 
 
+def batched(samples: int):
+    per_inst = []
+    for it in wl.batched(256, seed=1):
+        inst = oracle.Instance(it.problem)
+        y = np.random.default_rng(it.plan_seed).permutation(inst.K).astype(np.int16) + 1
+        r = inst.decode(y)
+        inst.commit(r["S"], r["M"])
+        t_now = it.rs_permille * r["cmax"] // 1000
+        inst.reschedule(wl.random_arrivals(np.random.default_rng(it.arrival_seed), it.arrivals_n,
+                                           it.problem.g, t_now, 99), t_now)
+        rng = np.random.default_rng(0)
+        s = [inst.decode(rng.permutation(inst.K) + 1)["slots"] for _ in range(samples)]
+        per_inst.append(float(np.mean(s)))
+    print(json.dumps(dict(workload="batched(256, seed=1)", samples=samples,
+                          slots_per_decode=float(np.mean(per_inst)),
+                          min=min(per_inst), max=max(per_inst))))
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", choices=["dynamic", "batched"], default="dynamic")
+    ap.add_argument("--samples", type=int, default=8)
     ap.add_argument("--generations", type=int, default=500)
     ap.add_argument("--every", type=int, default=50)
     ap.add_argument("--pop", type=int, default=1024)
     a = ap.parse_args()
+    if a.workload == "batched":
+        batched(a.samples)
+        return
     dyn = wl.dynamic_medium(1)
     inst = oracle.Instance(dyn.problem)
     per_solve = []

@@ -189,14 +189,16 @@ __device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int 
 }
 
 // Decodes one chromosome with the whole warp (Sec. 4.3, Alg. 1-2).  State lives in the
-// caller's workspace: h [Hcap] headroom, C [N], mfree [M], inv [2K+N], y [K], x [K].
-// Schedule output (S_out/M_out, [N*g]) is written for free ops only when non-null.
+// caller's workspace: h [Hcap] headroom, C [N], mfree [M], inv [K+N], y [K], x [K].  In
+// stage order the priority list overwrites y once its inverse is built, so y must be a
+// scratch copy.  Schedule output (S_out/M_out, [N*g]) is written for free ops only when
+// non-null.
 //
 // C[j] starts at the end of the job's frozen prefix, raised to R_j when the job still
 // has free ops, so every op becomes available at max(RS, C[j]).
 template <int ORDER, int MACH>
 __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *C, int32_t *mfree,
-                                 int16_t *inv, const int16_t *y, const int8_t *x, int32_t *S_out,
+                                 int16_t *inv, int16_t *y, const int8_t *x, int32_t *S_out,
                                  int32_t *M_out, int lane) {
     const int N = T.N, K = T.K, g = T.g, RS = T.RS;
     const uint32_t Q2 = (uint32_t)T.Qmax * 0x10001u;
@@ -226,8 +228,9 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
 
     if (ORDER == kOrderStage) {
         // Z: stage by stage, y descending.  Each stage's genes, in priority order, go to
-        // order[soff[s] ..) by a ballot-compaction pass over inv.
-        int16_t *order = inv + K;
+        // order[soff[s] ..) by a ballot-compaction pass over inv; y is no longer needed.
+        int16_t *order = y;
+        __syncwarp();
         for (int s = 0; s < g; ++s) {
             int pos = T.soff[s];
             for (int base = 0; base < K; base += 32) {

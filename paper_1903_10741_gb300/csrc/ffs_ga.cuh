@@ -1,0 +1,304 @@
+// ffs_ga.cuh -- GA building blocks shared by the per-generation kernel and the batched
+// persistent kernel: warp workspace views, child construction (Sec. 4.4: selection,
+// neighbouring paired crossover with correction, mutation), generation-0 initialisation
+// (Sec. 4.3) and warp-level elitist replacement and ring migration.
+#pragma once
+#include <stdint.h>
+
+#include <climits>
+
+#include "ffs_device.cuh"
+
+namespace edffs {
+
+struct WarpPtrs {
+    uint16_t *h;
+    int32_t *C, *mfree;
+    int16_t *inv, *y;
+    int8_t *x;
+    uint32_t *bits;
+};
+
+// Views of one warp's slice `ws` laid out by warp_layout(..., Hcap, ga); with a global
+// profile (`hg` non-null) the profile lives there instead.
+__device__ __forceinline__ WarpPtrs warp_view(char *ws, const WarpLayout &L, uint16_t *hg) {
+    WarpPtrs w;
+    w.h = hg ? hg : reinterpret_cast<uint16_t *>(ws + L.off_h);
+    w.C = reinterpret_cast<int32_t *>(ws + L.off_C);
+    w.mfree = reinterpret_cast<int32_t *>(ws + L.off_mfree);
+    w.inv = reinterpret_cast<int16_t *>(ws + L.off_inv);
+    w.y = reinterpret_cast<int16_t *>(ws + L.off_y);
+    w.x = reinterpret_cast<int8_t *>(ws + L.off_x);
+    w.bits = reinterpret_cast<uint32_t *>(ws + L.off_bits);
+    return w;
+}
+
+// Better individual: larger fitness, ties to the lower population index.
+__device__ __forceinline__ bool fitter(long long f, int i, long long bf, int bi) {
+    return f > bf || (f == bf && i < bi);
+}
+
+__device__ __forceinline__ void warp_best(long long &bf, int &bi) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const long long of = __shfl_xor_sync(kFull, bf, off);
+        const int oi = __shfl_xor_sync(kFull, bi, off);
+        if (fitter(of, oi, bf, bi)) {
+            bf = of;
+            bi = oi;
+        }
+    }
+}
+
+
+// Parent population and operator settings of one generation.
+struct GASrc {
+    const int16_t *Yc;   // [P][K] parents
+    const int8_t *Xc;
+    const int64_t *fc;   // [P] parents' fitness
+    int P, I, K, tour_k, side;
+    uint64_t pc_thr, pm_thr, seed;
+    uint32_t iid;        // 24-bit instance id of the stream
+};
+
+// Builds child i of generation `gen` into the warp's w.y / w.x: both parents of its pair
+// are selected from the counter-based stream, so the two children of a pair can be built
+// by different warps.
+template <int MACH>
+__device__ __forceinline__ void make_child(const Tabs &T, const WarpPtrs &w, const GASrc &s, int i, uint32_t gen,
+                                           int lane) {
+    const int K = s.K, I = s.I;
+    const int pp = i >> 1;
+    int parent[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int slot = 2 * pp + t;
+        long long bf = LLONG_MIN;
+        int bi = INT_MAX;
+        if (s.tour_k > 0) {
+            if (lane < s.tour_k) {
+                const int lo = (slot / I) * I;
+                bi = lo + (int)below(draw(s.seed, kPSelect, s.iid, gen, (uint32_t)slot, (uint32_t)lane),
+                                     (uint32_t)I);
+                bf = s.fc[bi];
+            }
+        } else if (lane < 5) {  // the cell and its N, S, W, E neighbours on the torus
+            const int sd = s.side, r = slot / sd, cc = slot % sd;
+            const int rr = lane == 1 ? (r + sd - 1) % sd : lane == 2 ? (r + 1) % sd : r;
+            const int c2 = lane == 3 ? (cc + sd - 1) % sd : lane == 4 ? (cc + 1) % sd : cc;
+            bi = rr * sd + c2;
+            bf = s.fc[bi];
+        }
+        warp_best(bf, bi);
+        parent[t] = bi;
+    }
+    const uint4 rc = stream_block(s.seed, kPCross, s.iid, gen, (uint32_t)pp, 0);
+    const bool cross = K >= 2 && (uint64_t)rc.x < s.pc_thr;
+    const int first = (i & 1) ? parent[1] : parent[0];
+    const int second = (i & 1) ? parent[0] : parent[1];
+    const int16_t *yf = s.Yc + (size_t)first * K, *yb = s.Yc + (size_t)second * K;
+    if (!cross) {
+        for (int k = lane; k < K; k += 32) w.y[k] = yf[k];
+        if (MACH == kMachGene)
+            for (int k = lane; k < K; k += 32) w.x[k] = s.Xc[(size_t)first * K + k];
+    } else {
+        const int cx = 1 + (int)below(rc.y, (uint32_t)(K - 1));
+        const int cy = 1 + (int)below(rc.z, (uint32_t)(K - 1));
+        const int nw = (K + 32) / 32;  // bitmap words covering values 0..K
+        for (int q = lane; q < nw; q += 32) w.bits[q] = 0;
+        __syncwarp();
+        for (int k = lane; k < cy; k += 32) {
+            const int v = yf[k];
+            w.y[k] = (int16_t)v;
+            atomicOr(&w.bits[v >> 5], 1u << (v & 31));
+        }
+        __syncwarp();
+        for (int k = cy + lane; k < K; k += 32) {  // tail values already in the head: duplicates
+            const int v = yb[k];
+            const bool dup = (w.bits[v >> 5] >> (v & 31)) & 1u;
+            w.y[k] = dup ? (int16_t)0 : (int16_t)v;
+        }
+        __syncwarp();
+        for (int k = cy + lane; k < K; k += 32) {
+            const int v = w.y[k];
+            if (v) atomicOr(&w.bits[v >> 5], 1u << (v & 31));
+        }
+        __syncwarp();
+        // Missing values, ascending, into `miss`.
+        int16_t *miss = w.inv;
+        int base = 0;
+        for (int q0 = 0; q0 < nw; q0 += 32) {
+            const int q = q0 + lane;
+            unsigned m = 0;
+            if (q < nw) {
+                m = ~w.bits[q];
+                if (q == 0) m &= ~1u;
+                const int hi = K - q * 32;  // highest valid bit
+                if (hi < 31) m &= hi >= 0 ? ((2u << hi) - 1u) : 0u;
+            }
+            const int cnt = __popc(m);
+            int incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int v = __shfl_up_sync(kFull, incl, off);
+                if (lane >= off) incl += v;
+            }
+            int o = base + incl - cnt;
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                miss[o++] = (int16_t)(q * 32 + b);
+            }
+            base += __shfl_sync(kFull, incl, 31);
+        }
+        __syncwarp();
+        int rank = 0;
+        for (int k0 = cy; k0 < K; k0 += 32) {  // the r-th duplicate takes the r-th missing value
+            const int k = k0 + lane;
+            const bool dup = k < K && w.y[k] == 0;
+            const unsigned bm = __ballot_sync(kFull, dup);
+            if (dup) w.y[k] = miss[rank + __popc(bm & ((1u << lane) - 1u))];
+            rank += __popc(bm);
+        }
+        if (MACH == kMachGene)
+            for (int k = lane; k < K; k += 32)
+                w.x[k] = k < cx ? s.Xc[(size_t)first * K + k] : s.Xc[(size_t)second * K + k];
+    }
+    __syncwarp();
+    const uint4 rm = stream_block(s.seed, kPMutate, s.iid, gen, (uint32_t)i, 0);
+    if ((uint64_t)rm.x < s.pm_thr) {
+        if (K >= 2 && lane == 0) {
+            const int ma = (int)below(rm.y, (uint32_t)K);
+            int mb = (int)below(rm.z, (uint32_t)(K - 1));
+            mb += mb >= ma;
+            const int16_t t = w.y[ma];
+            w.y[ma] = w.y[mb];
+            w.y[mb] = t;
+        }
+        if (MACH == kMachGene) {
+            for (int k = lane; k < K; k += 32) {
+                const int o = T.o[T.gstg[k]];
+                if (o >= 2) {
+                    const uint32_t u = draw(s.seed, kPMutate, s.iid, gen, (uint32_t)i, (uint32_t)(3 + k));
+                    const int r = (int)below(u, (uint32_t)(o - 1));
+                    w.x[k] = (int8_t)(r + (r >= w.x[k]));
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Generation 0 of individual i (Sec. 4.3): Y a Fisher-Yates permutation of 1..K, X uniform
+// machines, into w.y / w.x.
+template <int MACH>
+__device__ __forceinline__ void make_initial(const Tabs &T, const WarpPtrs &w, uint64_t seed, uint32_t iid, int i,
+                                             int lane) {
+    const int K = T.K;
+    // Fisher-Yates: step d swaps position K-1-d with a uniform position <= K-1-d.
+    int16_t *target = w.inv;
+    for (int d = lane; d < K - 1; d += 32) {
+        const uint32_t u = draw(seed, kPInitY, iid, 0, (uint32_t)i, (uint32_t)d);
+        target[d] = (int16_t)below(u, (uint32_t)(K - d));
+    }
+    for (int k = lane; k < K; k += 32) w.y[k] = (int16_t)(k + 1);
+    __syncwarp();
+    if (lane == 0) {
+        for (int d = 0; d < K - 1; ++d) {
+            const int pa = K - 1 - d, pb = target[d];
+            const int16_t t = w.y[pa];
+            w.y[pa] = w.y[pb];
+            w.y[pb] = t;
+        }
+    }
+    __syncwarp();
+    if (MACH == kMachGene) {
+        for (int k = lane; k < K; k += 32) {
+            const uint32_t u = draw(seed, kPInitX, iid, 0, (uint32_t)i, (uint32_t)k);
+            w.x[k] = (int8_t)below(u, (uint32_t)T.o[T.gstg[k]]);
+        }
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------- GA: island bookkeeping
+// Best (largest fitness, lowest index) and worst (smallest fitness, lowest index) of
+// fit[lo .. lo+n) with one warp; reads bypass L1 because other SMs wrote the values.
+__device__ __forceinline__ void warp_extremes(const int64_t *fit, int lo, int n, int lane, int &best, int &worst) {
+    long long bf = LLONG_MIN, wf = LLONG_MAX;
+    int bi = INT_MAX, wi = INT_MAX;
+    for (int t = lane; t < n; t += 32) {
+        const long long f = __ldcg(fit + lo + t);
+        if (fitter(f, lo + t, bf, bi)) { bf = f; bi = lo + t; }
+        if (f < wf || (f == wf && lo + t < wi)) { wf = f; wi = lo + t; }
+    }
+    warp_best(bf, bi);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const long long of = __shfl_xor_sync(kFull, wf, off);
+        const int oi = __shfl_xor_sync(kFull, wi, off);
+        if (of < wf || (of == wf && oi < wi)) { wf = of; wi = oi; }
+    }
+    best = bi;
+    worst = wi;
+}
+
+__device__ __forceinline__ void warp_copy_ind(int16_t *yd, int8_t *xd, const int16_t *ys, const int8_t *xs, int K,
+                                              int lane) {
+    for (int k = lane; k < K; k += 32) {
+        yd[k] = __ldcg(ys + k);
+        xd[k] = __ldcg(xs + k);
+    }
+}
+
+// Elitist replacement of island `isl` by one warp (Sec. 4.4): the best-ever individual is
+// updated if a child is strictly fitter, then overwrites the worst child.  With `migrate`,
+// the island's best and worst after replacement are recorded for the ring exchange.
+__device__ __forceinline__ void island_replace(int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit, int16_t *bY,
+                                               int8_t *bX, int64_t *bobj, int64_t *bfit, int isl, int I, int K,
+                                               bool migrate, int16_t *mY, int8_t *mX, int64_t *mobj, int64_t *mfit,
+                                               int32_t *mw, int lane) {
+    const int lo = isl * I;
+    int best, worst;
+    warp_extremes(fit, lo, I, lane, best, worst);
+    const long long fb = __ldcg(fit + best);
+    if (fb > bfit[isl]) {
+        warp_copy_ind(bY + (size_t)isl * K, bX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K, lane);
+        if (lane == 0) {
+            bobj[isl] = __ldcg(obj + best);
+            bfit[isl] = fb;
+        }
+    }
+    __syncwarp();
+    warp_copy_ind(Y + (size_t)worst * K, X + (size_t)worst * K, bY + (size_t)isl * K, bX + (size_t)isl * K, K, lane);
+    if (lane == 0) {
+        obj[worst] = bobj[isl];
+        fit[worst] = bfit[isl];
+    }
+    __syncwarp();
+    if (migrate) {
+        warp_extremes(fit, lo, I, lane, best, worst);
+        warp_copy_ind(mY + (size_t)isl * K, mX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K, lane);
+        if (lane == 0) {
+            mobj[isl] = __ldcg(obj + best);
+            mfit[isl] = __ldcg(fit + best);
+            mw[isl] = worst;
+        }
+    }
+}
+
+// Single-ring migration by one warp: island d's recorded worst <- island d-1's migrant.
+__device__ __forceinline__ void ring_migrate(int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit, const int16_t *mY,
+                                             const int8_t *mX, const int64_t *mobj, const int64_t *mfit,
+                                             const int32_t *mw, int nisl, int K, int lane) {
+    for (int d = 0; d < nisl; ++d) {
+        const int src = (d + nisl - 1) % nisl, wslot = __ldcg(mw + d);
+        warp_copy_ind(Y + (size_t)wslot * K, X + (size_t)wslot * K, mY + (size_t)src * K, mX + (size_t)src * K, K, lane);
+        if (lane == 0) {
+            obj[wslot] = __ldcg(mobj + src);
+            fit[wslot] = __ldcg(mfit + src);
+        }
+    }
+}
+
+}  // namespace edffs

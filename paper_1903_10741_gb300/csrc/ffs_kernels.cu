@@ -13,51 +13,19 @@
 #include <mutex>
 
 #include "ffs_device.cuh"
+#include "ffs_ga.cuh"
 #include "ffs_kernels.cuh"
 
 namespace edffs {
 
 namespace {
 
-struct WarpPtrs {
-    uint16_t *h;
-    int32_t *C, *mfree;
-    int16_t *inv, *y;
-    int8_t *x;
-    uint32_t *bits;
-};
-
+// Views of warp `warp`'s slice after the staged tables.
 __device__ __forceinline__ WarpPtrs warp_ptrs(char *tab, int blob_bytes, const Tabs &T, int Hcap,
                                               bool ga, bool gprof, uint16_t *gscratch, int warp) {
     const WarpLayout L = warp_layout(T.N, T.M, T.K, gprof ? 0 : Hcap, ga);
     char *ws = tab + ((blob_bytes + 127) & ~127) + warp * L.bytes;
-    WarpPtrs w;
-    w.h = gprof ? gscratch + (size_t)(blockIdx.x * kWarpsPerBlock + warp) * (size_t)Hcap
-                : reinterpret_cast<uint16_t *>(ws + L.off_h);
-    w.C = reinterpret_cast<int32_t *>(ws + L.off_C);
-    w.mfree = reinterpret_cast<int32_t *>(ws + L.off_mfree);
-    w.inv = reinterpret_cast<int16_t *>(ws + L.off_inv);
-    w.y = reinterpret_cast<int16_t *>(ws + L.off_y);
-    w.x = reinterpret_cast<int8_t *>(ws + L.off_x);
-    w.bits = reinterpret_cast<uint32_t *>(ws + L.off_bits);
-    return w;
-}
-
-// Better individual: larger fitness, ties to the lower population index.
-__device__ __forceinline__ bool fitter(long long f, int i, long long bf, int bi) {
-    return f > bf || (f == bf && i < bi);
-}
-
-__device__ __forceinline__ void warp_best(long long &bf, int &bi) {
-#pragma unroll
-    for (int off = 16; off; off >>= 1) {
-        const long long of = __shfl_xor_sync(kFull, bf, off);
-        const int oi = __shfl_xor_sync(kFull, bi, off);
-        if (fitter(of, oi, bf, bi)) {
-            bf = of;
-            bi = oi;
-        }
-    }
+    return warp_view(ws, L, gprof ? gscratch + (size_t)(blockIdx.x * kWarpsPerBlock + warp) * (size_t)Hcap : nullptr);
 }
 
 // ---------------------------------------------------------------- decode kernel
@@ -124,34 +92,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_init(GenArgs a) {
     const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, true, false, nullptr, warp);
     const int K = T.K;
     for (int i = blockIdx.x * kWarpsPerBlock + warp; i < a.P; i += gridDim.x * kWarpsPerBlock) {
-        // Fisher-Yates: step d swaps position K-1-d with a uniform position <= K-1-d.
-        int16_t *target = w.inv;
-        for (int d = lane; d < K - 1; d += 32) {
-            const uint32_t u = draw(a.seed, kPInitY, a.instance_id, 0, (uint32_t)i, (uint32_t)d);
-            target[d] = (int16_t)below(u, (uint32_t)(K - d));
-        }
-        for (int k = lane; k < K; k += 32) w.y[k] = (int16_t)(k + 1);
-        __syncwarp();
-        if (lane == 0) {
-            for (int d = 0; d < K - 1; ++d) {
-                const int pa = K - 1 - d, pb = target[d];
-                const int16_t t = w.y[pa];
-                w.y[pa] = w.y[pb];
-                w.y[pb] = t;
-            }
-        }
-        __syncwarp();
+        make_initial<MACH>(T, w, a.seed, a.instance_id, i, lane);
         int16_t *yo = a.Y[0] + (size_t)i * K;
         for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
         if (MACH == kMachGene) {
             int8_t *xo = a.X[0] + (size_t)i * K;
-            for (int k = lane; k < K; k += 32) {
-                const uint32_t u = draw(a.seed, kPInitX, a.instance_id, 0, (uint32_t)i, (uint32_t)k);
-                w.x[k] = (int8_t)below(u, (uint32_t)T.o[T.gstg[k]]);
-                xo[k] = w.x[k];
-            }
+            for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
         }
-        __syncwarp();
         const DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x,
                                                      nullptr, nullptr, lane);
         if (lane == 0) {
@@ -160,36 +107,6 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_init(GenArgs a) {
             else a.obj[0][i] = (long long)T.WT * r.tard + r.cmax;
         }
         __syncwarp();
-    }
-}
-
-// ---------------------------------------------------------------- GA: island bookkeeping
-// Best (largest fitness, lowest index) and worst (smallest fitness, lowest index) of
-// fit[lo .. lo+n) with one warp; reads bypass L1 because other SMs wrote the values.
-__device__ __forceinline__ void warp_extremes(const int64_t *fit, int lo, int n, int lane, int &best, int &worst) {
-    long long bf = LLONG_MIN, wf = LLONG_MAX;
-    int bi = INT_MAX, wi = INT_MAX;
-    for (int t = lane; t < n; t += 32) {
-        const long long f = __ldcg(fit + lo + t);
-        if (fitter(f, lo + t, bf, bi)) { bf = f; bi = lo + t; }
-        if (f < wf || (f == wf && lo + t < wi)) { wf = f; wi = lo + t; }
-    }
-    warp_best(bf, bi);
-#pragma unroll
-    for (int off = 16; off; off >>= 1) {
-        const long long of = __shfl_xor_sync(kFull, wf, off);
-        const int oi = __shfl_xor_sync(kFull, wi, off);
-        if (of < wf || (of == wf && oi < wi)) { wf = of; wi = oi; }
-    }
-    best = bi;
-    worst = wi;
-}
-
-__device__ __forceinline__ void warp_copy_ind(int16_t *yd, int8_t *xd, const int16_t *ys, const int8_t *xs, int K,
-                                              int lane) {
-    for (int k = lane; k < K; k += 32) {
-        yd[k] = __ldcg(ys + k);
-        xd[k] = __ldcg(xs + k);
     }
 }
 
@@ -207,53 +124,20 @@ __device__ void island_finish(const Args &a, int isl, int nx, int gen, int lane)
     ticket = __shfl_sync(kFull, ticket, 0);
     if (ticket != a.I - 1) return;
     __threadfence();
-    const int K = a.K, I = a.I, lo = isl * I;
+    const int K = a.K;
     int16_t *Y = a.Y[nx];
     int8_t *X = a.X[nx];
     int64_t *obj = a.obj[nx], *fit = a.fit[nx];
-    int best, worst;
-    warp_extremes(fit, lo, I, lane, best, worst);
-    const long long fb = __ldcg(fit + best);
-    if (fb > a.bfit[isl]) {
-        warp_copy_ind(a.bY + (size_t)isl * K, a.bX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K, lane);
-        if (lane == 0) {
-            a.bobj[isl] = __ldcg(obj + best);
-            a.bfit[isl] = fb;
-        }
-    }
-    __syncwarp();
-    warp_copy_ind(Y + (size_t)worst * K, X + (size_t)worst * K, a.bY + (size_t)isl * K, a.bX + (size_t)isl * K, K, lane);
-    if (lane == 0) {
-        obj[worst] = a.bobj[isl];
-        fit[worst] = a.bfit[isl];
-        a.isl_done[isl] = 0;
-    }
-    __syncwarp();
     const bool migrate = a.migrate_every > 0 && gen % a.migrate_every == 0 && a.nisl > 1;
-    if (migrate) {
-        warp_extremes(fit, lo, I, lane, best, worst);
-        warp_copy_ind(a.mY + (size_t)isl * K, a.mX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K, lane);
-        if (lane == 0) {
-            a.mobj[isl] = __ldcg(obj + best);
-            a.mfit[isl] = __ldcg(fit + best);
-            a.mw[isl] = worst;
-        }
-    }
+    island_replace(Y, X, obj, fit, a.bY, a.bX, a.bobj, a.bfit, isl, a.I, K, migrate, a.mY, a.mX, a.mobj, a.mfit,
+                   a.mw, lane);
+    if (lane == 0) a.isl_done[isl] = 0;
     __threadfence();
     if (lane == 0) ticket = atomicAdd(&a.dev->islands_done, 1);
     ticket = __shfl_sync(kFull, ticket, 0);
     if (ticket != a.nisl - 1) return;
     __threadfence();
-    if (migrate) {
-        for (int d = 0; d < a.nisl; ++d) {
-            const int src = (d + a.nisl - 1) % a.nisl, w = __ldcg(a.mw + d);
-            warp_copy_ind(Y + (size_t)w * K, X + (size_t)w * K, a.mY + (size_t)src * K, a.mX + (size_t)src * K, K, lane);
-            if (lane == 0) {
-                obj[w] = __ldcg(a.mobj + src);
-                fit[w] = __ldcg(a.mfit + src);
-            }
-        }
-    }
+    if (migrate) ring_migrate(Y, X, obj, fit, a.mY, a.mX, a.mobj, a.mfit, a.mw, a.nisl, K, lane);
     if (lane == 0) {
         a.dev->islands_done = 0;
         a.dev->nover = 0;
@@ -278,130 +162,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
     const int cur = a.dev->gen & 1, nx = cur ^ 1;
     const uint32_t gen = (uint32_t)a.dev->gen + 1;
     const long long emax = a.dev->emax;
-    const int16_t *Yc = a.Y[cur];
-    const int8_t *Xc = a.X[cur];
-    const int64_t *fc = a.fit[cur];
+    const GASrc src{a.Y[cur], a.X[cur], a.fit[cur], a.P, a.I, K, a.tour_k, a.side, a.pc_thr, a.pm_thr, a.seed,
+                    a.instance_id};
 
     for (int i = blockIdx.x * kWarpsPerBlock + warp; i < a.P; i += gridDim.x * kWarpsPerBlock) {
-        const int pp = i >> 1;
-        int parent[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int slot = 2 * pp + t;
-            long long bf = LLONG_MIN;
-            int bi = INT_MAX;
-            if (a.tour_k > 0) {
-                if (lane < a.tour_k) {
-                    const int lo = (slot / I) * I;
-                    bi = lo + (int)below(draw(a.seed, kPSelect, a.instance_id, gen, (uint32_t)slot, (uint32_t)lane),
-                                         (uint32_t)I);
-                    bf = fc[bi];
-                }
-            } else if (lane < 5) {  // the cell and its N, S, W, E neighbours on the torus
-                const int sd = a.side, r = slot / sd, cc = slot % sd;
-                const int rr = lane == 1 ? (r + sd - 1) % sd : lane == 2 ? (r + 1) % sd : r;
-                const int c2 = lane == 3 ? (cc + sd - 1) % sd : lane == 4 ? (cc + 1) % sd : cc;
-                bi = rr * sd + c2;
-                bf = fc[bi];
-            }
-            warp_best(bf, bi);
-            parent[t] = bi;
-        }
-        const uint4 rc = stream_block(a.seed, kPCross, a.instance_id, gen, (uint32_t)pp, 0);
-        const bool cross = K >= 2 && (uint64_t)rc.x < a.pc_thr;
-        const int first = (i & 1) ? parent[1] : parent[0];
-        const int second = (i & 1) ? parent[0] : parent[1];
-        const int16_t *yf = Yc + (size_t)first * K, *yb = Yc + (size_t)second * K;
-        if (!cross) {
-            for (int k = lane; k < K; k += 32) w.y[k] = yf[k];
-            if (MACH == kMachGene)
-                for (int k = lane; k < K; k += 32) w.x[k] = Xc[(size_t)first * K + k];
-        } else {
-            const int cx = 1 + (int)below(rc.y, (uint32_t)(K - 1));
-            const int cy = 1 + (int)below(rc.z, (uint32_t)(K - 1));
-            const int nw = (K + 32) / 32;  // bitmap words covering values 0..K
-            for (int q = lane; q < nw; q += 32) w.bits[q] = 0;
-            __syncwarp();
-            for (int k = lane; k < cy; k += 32) {
-                const int v = yf[k];
-                w.y[k] = (int16_t)v;
-                atomicOr(&w.bits[v >> 5], 1u << (v & 31));
-            }
-            __syncwarp();
-            for (int k = cy + lane; k < K; k += 32) {  // tail values already in the head: duplicates
-                const int v = yb[k];
-                const bool dup = (w.bits[v >> 5] >> (v & 31)) & 1u;
-                w.y[k] = dup ? (int16_t)0 : (int16_t)v;
-            }
-            __syncwarp();
-            for (int k = cy + lane; k < K; k += 32) {
-                const int v = w.y[k];
-                if (v) atomicOr(&w.bits[v >> 5], 1u << (v & 31));
-            }
-            __syncwarp();
-            // Missing values, ascending, into `miss`.
-            int16_t *miss = w.inv;
-            int base = 0;
-            for (int q0 = 0; q0 < nw; q0 += 32) {
-                const int q = q0 + lane;
-                unsigned m = 0;
-                if (q < nw) {
-                    m = ~w.bits[q];
-                    if (q == 0) m &= ~1u;
-                    const int hi = K - q * 32;  // highest valid bit
-                    if (hi < 31) m &= hi >= 0 ? ((2u << hi) - 1u) : 0u;
-                }
-                const int cnt = __popc(m);
-                int incl = cnt;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int v = __shfl_up_sync(kFull, incl, off);
-                    if (lane >= off) incl += v;
-                }
-                int o = base + incl - cnt;
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    miss[o++] = (int16_t)(q * 32 + b);
-                }
-                base += __shfl_sync(kFull, incl, 31);
-            }
-            __syncwarp();
-            int rank = 0;
-            for (int k0 = cy; k0 < K; k0 += 32) {  // the r-th duplicate takes the r-th missing value
-                const int k = k0 + lane;
-                const bool dup = k < K && w.y[k] == 0;
-                const unsigned bm = __ballot_sync(kFull, dup);
-                if (dup) w.y[k] = miss[rank + __popc(bm & ((1u << lane) - 1u))];
-                rank += __popc(bm);
-            }
-            if (MACH == kMachGene)
-                for (int k = lane; k < K; k += 32)
-                    w.x[k] = k < cx ? Xc[(size_t)first * K + k] : Xc[(size_t)second * K + k];
-        }
-        __syncwarp();
-        const uint4 rm = stream_block(a.seed, kPMutate, a.instance_id, gen, (uint32_t)i, 0);
-        if ((uint64_t)rm.x < a.pm_thr) {
-            if (K >= 2 && lane == 0) {
-                const int ma = (int)below(rm.y, (uint32_t)K);
-                int mb = (int)below(rm.z, (uint32_t)(K - 1));
-                mb += mb >= ma;
-                const int16_t t = w.y[ma];
-                w.y[ma] = w.y[mb];
-                w.y[mb] = t;
-            }
-            if (MACH == kMachGene) {
-                for (int k = lane; k < K; k += 32) {
-                    const int o = T.o[T.gstg[k]];
-                    if (o >= 2) {
-                        const uint32_t u = draw(a.seed, kPMutate, a.instance_id, gen, (uint32_t)i, (uint32_t)(3 + k));
-                        const int r = (int)below(u, (uint32_t)(o - 1));
-                        w.x[k] = (int8_t)(r + (r >= w.x[k]));
-                    }
-                }
-            }
-        }
-        __syncwarp();
+        make_child<MACH>(T, w, src, i, gen, lane);
         int16_t *yo = a.Y[nx] + (size_t)i * K;
         for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
         if (MACH == kMachGene) {
@@ -410,6 +175,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
         }
         DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
         if (r.status == 1) {  // the schedule outgrew the shared slice: redo it in global memory
+            for (int k = lane; k < K; k += 32) w.y[k] = yo[k];  // the decode reused w.y
+            __syncwarp();
             uint16_t *hg = a.gscratch + (size_t)(blockIdx.x * kWarpsPerBlock + warp) * (size_t)a.H;
             r = decode_warp<ORDER, MACH>(T, hg, a.H, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
         }

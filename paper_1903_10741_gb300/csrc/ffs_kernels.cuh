@@ -80,6 +80,42 @@ struct ReplArgs {
     int init;                   // 1: generation 0 (set E_max, fitness, best-ever)
 };
 
+// One instance of a batch: its tables and device-resident GA state.
+struct BatchInst {
+    const char *blob;
+    int blob_bytes, N, M, K, H, nisl;
+    int gen;                    // generations completed
+    uint32_t iid;               // 24-bit stream id
+    long long emax;             // 0 until generation 0 has run
+    int16_t *Y[2];
+    int8_t *X[2];
+    int64_t *obj[2], *fit[2];
+    int16_t *bY, *mY;
+    int8_t *bX, *mX;
+    int64_t *bobj, *bfit, *mobj, *mfit;
+    int32_t *mw;
+};
+
+struct BatchArgs {
+    BatchInst *inst;
+    int count;
+    const int32_t *order;       // instances, largest work first
+    int32_t *next;              // unused (instances are dealt to clusters statically)
+    int generations;
+    int P, I, tour_k, side, migrate_every;
+    uint64_t pc_thr, pm_thr, seed;
+    int smem_bytes;             // dynamic shared memory of a CTA
+    uint16_t *gscratch;         // Hmax slots per (CTA, warp)
+    int Hmax;
+    int32_t *err;
+};
+
+cudaError_t prepare_batch(int order, int mach, int smem_bytes);
+// Clusters of `cluster` CTAs of the given shape that can be resident at once.
+cudaError_t batch_max_clusters(int order, int mach, int cluster, int warps, int smem_bytes, int *clusters);
+cudaError_t launch_batch(int order, int mach, const BatchArgs &a, int grid, int warps, int cluster,
+                         cudaStream_t st);
+
 // Shared memory needed by one CTA of the decode / GA kernels.
 int cta_smem_bytes(const TabHeader &h, int Hcap, bool ga, bool global_profile);
 

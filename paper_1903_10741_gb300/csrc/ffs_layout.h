@@ -74,9 +74,8 @@ FFS_HD Tabs tabs_view(const char *base) {
 //                         multiple of 8 and the slice is read and written 4 slots at a time
 //   C     int32  [N]      completion of each job's last assigned stage
 //   mfree int32  [M]      end of the last op assigned to each machine
-//   inv   int16  [2K + N] gene by priority rank, then the stage-by-stage order (or the
-//                         next gene of every job for Alg. 1)
-//   y     int16  [K], x int8 [K]   the chromosome being decoded
+//   inv   int16  [K + N]  gene by priority rank, then the next gene of every job (Alg. 1)
+//   y     int16  [K], x int8 [K]   the chromosome being decoded (y becomes the stage order)
 //   bits  uint32 [K/32+1] value bitmap for the crossover correction (GA kernels only)
 struct WarpLayout {
     int off_h, off_C, off_mfree, off_inv, off_y, off_x, off_bits, bytes;
@@ -88,7 +87,7 @@ FFS_HD WarpLayout warp_layout(int N, int M, int K, int Hcap, bool ga) {
     L.off_h = o;     o += align16(Hcap * 2);
     L.off_C = o;     o += align16(N * 4);
     L.off_mfree = o; o += align16(M * 4);
-    L.off_inv = o;   o += align16((2 * K + N) * 2);
+    L.off_inv = o;   o += align16((K + N) * 2);
     L.off_y = o;     o += align16(K * 2);
     L.off_x = o;     o += align16(K);
     L.off_bits = o;  o += ga ? align16(((K + 32) / 32) * 4) : 0;
@@ -106,6 +105,9 @@ struct GADev {
 };
 
 constexpr int kErrBadChromosome = 1, kErrOverflow = 2, kErrTimeout = 4;
+
+// Below this many profile slots per warp a shared-memory slice is not worth keeping.
+constexpr int kMinBatchSlots = 256;
 
 // Philox stream purposes.
 constexpr uint32_t kPInitY = 1, kPInitX = 2, kPSelect = 3, kPCross = 4, kPMutate = 5;

@@ -1017,3 +1017,403 @@ extern "C" int ffs_decode_noalloc(ffs_instance *in, int32_t order_mode, int32_t 
     if (e & kErrTimeout) return FFS_E_TIMEOUT;
     return e ? FFS_E_DEVICE : FFS_OK;
 }
+
+// ====================================================================== batched GA
+//
+// Many instances' GAs in one persistent kernel (see ffs_batch.cu).  All device state of a
+// batch lives in one arena so that the autotuner can snapshot and restore it with one
+// copy.
+struct ga_batch {
+    std::vector<ffs_instance *> insts;
+    std::vector<int> versions;
+    ga_params par{};
+    cudaStream_t st = nullptr;
+    int count = 0, P = 0, I = 0, nisl = 0, side = 0, Hmax = 0;
+    char *arena = nullptr, *shadow = nullptr;
+    size_t arena_bytes = 0;
+    BatchInst *d_inst = nullptr;
+    std::vector<BatchInst> h_inst;
+    int32_t *d_order = nullptr, *d_next = nullptr, *d_err = nullptr;
+    uint16_t *gscratch = nullptr;
+    size_t gscratch_elems = 0;
+    int warps = 8, smem = 112 * 1024, grid = 1, cluster = 1;
+    cudaGraphExec_t graph = nullptr;
+    int graph_gens = -1;
+    float tuned_ms = 0.f;
+
+    ~ga_batch() {
+        if (graph) cudaGraphExecDestroy(graph);
+        dfree(arena);
+        dfree(shadow);
+        dfree(d_inst);
+        dfree(d_order);
+        dfree(d_next);
+        dfree(d_err);
+        dfree(gscratch);
+    }
+};
+
+namespace {
+
+// Persistent grid: as many clusters as can be resident, at most one per instance.
+int batch_grid(ga_batch *b, int warps, int smem, int *grid) {
+    int clusters = 0;
+    FFS_CUDA(batch_max_clusters(b->par.order_mode, b->par.machine_mode, b->cluster, warps, smem, &clusters));
+    if (clusters < 1) return FFS_E_ARG;  // this shape cannot run
+    *grid = b->cluster * std::max(1, std::min(b->count, clusters));
+    return FFS_OK;
+}
+
+int batch_config(ga_batch *b, int warps, int smem, int cluster) {
+    if (warps < 1 || warps > 16 || smem < 16 * 1024 || smem > 227 * 1024 || cluster < 1 || cluster > 8 ||
+        cluster > b->nisl)
+        return FFS_E_ARG;
+    // every instance's tables and its warps' fixed workspace must fit the CTA's budget
+    for (const ffs_instance *in : b->insts) {
+        const TabHeader &h = in->hdr;
+        if (128 + ((h.bytes + 127) & ~127) + warps * warp_layout(h.N, h.M, h.K, 0, true).bytes > smem) return FFS_E_ARG;
+    }
+    FFS_CUDA(prepare_batch(b->par.order_mode, b->par.machine_mode, smem));
+    const int old_cluster = b->cluster;
+    b->cluster = cluster;
+    int grid = 0;
+    const int grc = batch_grid(b, warps, smem, &grid);
+    if (grc != FFS_OK) {
+        b->cluster = old_cluster;
+        return grc;
+    }
+    b->warps = warps;
+    b->smem = smem;
+    b->grid = grid;
+    const size_t need = (size_t)b->grid * warps * (size_t)b->Hmax;
+    if (need > b->gscratch_elems) {
+        dfree(b->gscratch);
+        FFS_CUDA(dalloc(&b->gscratch, need));
+        b->gscratch_elems = need;
+    }
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_gens = -1;
+    }
+    return FFS_OK;
+}
+
+BatchArgs batch_args(ga_batch *b, int generations) {
+    BatchArgs a{};
+    a.inst = b->d_inst;
+    a.count = b->count;
+    a.order = b->d_order;
+    a.next = b->d_next;
+    a.generations = generations;
+    a.P = b->P;
+    a.I = b->I;
+    a.tour_k = b->par.tournament_k;
+    a.side = b->side;
+    a.migrate_every = b->par.migrate_every;
+    a.pc_thr = ((uint64_t)(uint32_t)b->par.pc_num << 32) / (uint64_t)(uint32_t)b->par.pc_den;
+    a.pm_thr = ((uint64_t)(uint32_t)b->par.pm_num << 32) / (uint64_t)(uint32_t)b->par.pm_den;
+    a.seed = b->par.seed;
+    a.smem_bytes = b->smem;
+    a.gscratch = b->gscratch;
+    a.Hmax = b->Hmax;
+    a.err = b->d_err;
+    return a;
+}
+
+// Enqueues one persistent launch: reset the work queue, then every instance runs
+// `generations` generations (after generation 0 where it has not run yet).
+int batch_enqueue(ga_batch *b, int generations, cudaStream_t st) {
+    FFS_CUDA(launch_batch(b->par.order_mode, b->par.machine_mode, batch_args(b, generations), b->grid, b->warps,
+                          b->cluster, st));
+    g_launches += 1;
+    return FFS_OK;
+}
+
+int batch_check(ga_batch *b) {
+    FFS_CUDA(cudaStreamSynchronize(b->st));
+    int32_t e = 0;
+    FFS_CUDA(cudaMemcpy(&e, b->d_err, 4, cudaMemcpyDeviceToHost));
+    if (e & kErrTimeout) return FFS_E_TIMEOUT;
+    return e ? FFS_E_DEVICE : FFS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ga_batch_create(ffs_instance *const *insts, int32_t count, const ga_params *par, ga_batch **out) {
+    if (!insts || !par || !out || count < 1) return FFS_E_ARG;
+    *out = nullptr;
+    FFS_TRY(check_modes(par->order_mode, par->machine_mode));
+    const int P = par->pop, I = par->island;
+    if (P < 2 || P % 2 || I < 2 || I % 2 || P % I || par->tournament_k < 0 || par->tournament_k > 32 ||
+        par->pc_den <= 0 || par->pm_den <= 0 || par->pc_num < 0 || par->pm_num < 0 || par->pc_num > par->pc_den ||
+        par->pm_num > par->pm_den || par->migrate_every < 0 || (long long)par->instance_id + count > (1 << 24))
+        return FFS_E_ARG;
+    int side = 0;
+    if (par->tournament_k == 0) {
+        while (side * side < P) ++side;
+        if (side * side != P) return FFS_E_ARG;
+    }
+    for (int i = 0; i < count; ++i)
+        if (!insts[i] || insts[i]->K < 1) return FFS_E_ARG;
+    ga_batch *b = new (std::nothrow) ga_batch();
+    if (!b) return FFS_E_NOMEM;
+    auto fail = [&](int rc) {
+        delete b;
+        return rc;
+    };
+    b->insts.assign(insts, insts + count);
+    for (int i = 0; i < count; ++i) b->versions.push_back(insts[i]->version);
+    b->par = *par;
+    b->st = static_cast<cudaStream_t>(par->cuda_stream);
+    b->count = count;
+    b->P = P;
+    b->I = I;
+    b->nisl = P / I;
+    b->side = side;
+    b->cluster = std::min(b->nisl, 8);  // one CTA per island, up to the portable cluster size
+    // arena layout, 256-byte aligned pieces
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    std::vector<size_t> base(count);
+    size_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        const ffs_instance *in = insts[i];
+        const size_t PK = (size_t)P * in->K, NK = (size_t)b->nisl * in->K;
+        base[i] = off;
+        off += al(in->hdr.bytes) + 2 * (al(2 * PK) + al(PK) + 2 * al(8 * (size_t)P)) + 2 * (al(2 * NK) + al(NK)) +
+               4 * al(8 * (size_t)b->nisl) + al(4 * (size_t)b->nisl);
+        b->Hmax = std::max(b->Hmax, in->hdr.H);
+    }
+    b->arena_bytes = off;
+    if (dalloc(&b->arena, off) != cudaSuccess || dalloc(&b->d_inst, (size_t)count) != cudaSuccess ||
+        dalloc(&b->d_order, (size_t)count) != cudaSuccess || dalloc(&b->d_next, 1) != cudaSuccess ||
+        dalloc(&b->d_err, 1) != cudaSuccess)
+        return fail(FFS_E_NOMEM);
+    b->h_inst.resize(count);
+    std::vector<std::pair<long long, int>> work(count);
+    int rc = FFS_OK;
+    for (int i = 0; i < count && rc == FFS_OK; ++i) {
+        const ffs_instance *in = insts[i];
+        const size_t PK = (size_t)P * in->K, NK = (size_t)b->nisl * in->K;
+        char *p = b->arena + base[i];
+        auto take = [&](size_t bytes) {
+            char *q = p;
+            p += al(bytes);
+            return q;
+        };
+        BatchInst &h = b->h_inst[i];
+        h = BatchInst{};
+        char *blob = take(in->hdr.bytes);
+        h.blob = blob;
+        h.blob_bytes = in->hdr.bytes;
+        h.N = in->N;
+        h.M = in->M;
+        h.K = in->K;
+        h.H = in->hdr.H;
+        h.nisl = b->nisl;
+        h.gen = 0;
+        h.iid = (uint32_t)(par->instance_id + i) & 0xFFFFFFu;
+        h.emax = 0;
+        for (int s = 0; s < 2; ++s) {
+            h.Y[s] = reinterpret_cast<int16_t *>(take(2 * PK));
+            h.X[s] = reinterpret_cast<int8_t *>(take(PK));
+            h.obj[s] = reinterpret_cast<int64_t *>(take(8 * (size_t)P));
+            h.fit[s] = reinterpret_cast<int64_t *>(take(8 * (size_t)P));
+        }
+        h.bY = reinterpret_cast<int16_t *>(take(2 * NK));
+        h.mY = reinterpret_cast<int16_t *>(take(2 * NK));
+        h.bX = reinterpret_cast<int8_t *>(take(NK));
+        h.mX = reinterpret_cast<int8_t *>(take(NK));
+        h.bobj = reinterpret_cast<int64_t *>(take(8 * (size_t)b->nisl));
+        h.bfit = reinterpret_cast<int64_t *>(take(8 * (size_t)b->nisl));
+        h.mobj = reinterpret_cast<int64_t *>(take(8 * (size_t)b->nisl));
+        h.mfit = reinterpret_cast<int64_t *>(take(8 * (size_t)b->nisl));
+        h.mw = reinterpret_cast<int32_t *>(take(4 * (size_t)b->nisl));
+        work[i] = {-(long long)in->K * (in->N + in->hdr.H / 64), i};  // largest first
+    }
+    if (rc != FFS_OK) return fail(rc);
+    std::sort(work.begin(), work.end());
+    std::vector<int32_t> order(count);
+    for (int i = 0; i < count; ++i) order[i] = work[i].second;
+    if ((rc = cuda_rc(cudaMemset(b->arena, 0, b->arena_bytes))) != FFS_OK) return fail(rc);
+    for (int i = 0; i < count && rc == FFS_OK; ++i) {  // tables again: the memset cleared them
+        rc = cuda_rc(cudaMemcpy(const_cast<char *>(b->h_inst[i].blob), insts[i]->blob.data(), insts[i]->hdr.bytes,
+                                cudaMemcpyHostToDevice));
+    }
+    if (rc == FFS_OK) rc = cuda_rc(cudaMemcpy(b->d_inst, b->h_inst.data(), sizeof(BatchInst) * count, cudaMemcpyHostToDevice));
+    if (rc == FFS_OK) rc = cuda_rc(cudaMemcpy(b->d_order, order.data(), 4 * (size_t)count, cudaMemcpyHostToDevice));
+    if (rc == FFS_OK) rc = cuda_rc(cudaMemset(b->d_err, 0, 4));
+    if (rc == FFS_OK) {  // default mapping: the widest of these that every instance fits
+        rc = FFS_E_ARG;
+        const int def[][2] = {{8, 112 * 1024}, {4, 112 * 1024}, {4, 225 * 1024}, {1, 225 * 1024}};
+        for (const auto &d : def)
+            if ((rc = batch_config(b, d[0], d[1], b->cluster)) == FFS_OK) break;
+    }
+    if (rc == FFS_OK) rc = batch_enqueue(b, 0, b->st);  // generation 0 of every instance
+    if (rc == FFS_OK) rc = batch_check(b);
+    if (rc != FFS_OK) return fail(rc);
+    *out = b;
+    return FFS_OK;
+}
+
+int ga_batch_destroy(ga_batch *b) {
+    delete b;
+    return FFS_OK;
+}
+
+int ga_batch_set_config(ga_batch *b, const ga_batch_config *cfg) {
+    if (!b || !cfg) return FFS_E_ARG;
+    return batch_config(b, cfg->warps_per_cta, cfg->smem_bytes, cfg->cluster > 0 ? cfg->cluster : b->cluster);
+}
+
+int ga_batch_get_config(const ga_batch *b, ga_batch_config *cfg) {
+    if (!b || !cfg) return FFS_E_ARG;
+    cfg->warps_per_cta = b->warps;
+    cfg->smem_bytes = b->smem;
+    cfg->ctas = b->grid;
+    cfg->cluster = b->cluster;
+    cfg->ms_per_generation = b->tuned_ms;
+    return FFS_OK;
+}
+
+int ga_batch_run(ga_batch *b, int32_t generations, ffs_result *best) {
+    if (!b || generations < 0) return FFS_E_ARG;
+    for (int i = 0; i < b->count; ++i)
+        if (b->insts[i]->version != b->versions[i]) return FFS_E_STATE;
+    if (b->graph_gens != generations) {  // capture the launch once per generation count
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        cudaStream_t cap = nullptr;
+        FFS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        int rc = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        if (rc == FFS_OK) rc = batch_enqueue(b, generations, cap);
+        const int ce = cuda_rc(cudaStreamEndCapture(cap, &g));
+        cudaStreamDestroy(cap);
+        if (rc == FFS_OK) rc = ce;
+        if (rc == FFS_OK) rc = cuda_rc(cudaGraphInstantiate(&b->graph, g, 0));
+        if (g) cudaGraphDestroy(g);
+        if (rc != FFS_OK) return rc;
+        b->graph_gens = generations;
+        g_launches -= 1;  // counted at replay
+    }
+    FFS_CUDA(cudaGraphLaunch(b->graph, b->st));
+    g_launches += 1;
+    FFS_TRY(batch_check(b));
+    if (!best) return FFS_OK;
+    // best-ever island of every instance, decoded and committed
+    for (int i = 0; i < b->count; ++i) {
+        const BatchInst &h = b->h_inst[i];
+        std::vector<int64_t> bfit(b->nisl);
+        FFS_CUDA(cudaMemcpy(bfit.data(), h.bfit, 8 * (size_t)b->nisl, cudaMemcpyDeviceToHost));
+        int bi = 0;
+        for (int q = 1; q < b->nisl; ++q)
+            if (bfit[q] > bfit[bi]) bi = q;
+        ffs_instance *in = b->insts[i];
+        const size_t NG = (size_t)in->N * in->g;
+        int64_t *d_o = nullptr, *d_t = nullptr;
+        int32_t *d_c = nullptr, *d_S = nullptr, *d_M = nullptr;
+        int rc = FFS_OK;
+        if (dalloc(&d_o, 1) != cudaSuccess || dalloc(&d_t, 1) != cudaSuccess || dalloc(&d_c, 1) != cudaSuccess ||
+            dalloc(&d_S, NG) != cudaSuccess || dalloc(&d_M, NG) != cudaSuccess)
+            rc = FFS_E_NOMEM;
+        if (rc == FFS_OK)
+            rc = decode_impl(in, b->par.order_mode, b->par.machine_mode, h.bY + (size_t)bi * in->K,
+                             h.bX + (size_t)bi * in->K, 1, d_o, d_t, d_c, d_S, d_M, b->st);
+        if (rc == FFS_OK) rc = ffs_decode_check(in, b->st);
+        std::vector<int32_t> S(NG), M(NG);
+        int64_t o = 0, t = 0;
+        int32_t cm = 0;
+        if (rc == FFS_OK) rc = cuda_rc(cudaMemcpy(S.data(), d_S, 4 * NG, cudaMemcpyDeviceToHost));
+        if (rc == FFS_OK) rc = cuda_rc(cudaMemcpy(M.data(), d_M, 4 * NG, cudaMemcpyDeviceToHost));
+        if (rc == FFS_OK) rc = cuda_rc(cudaMemcpy(&o, d_o, 8, cudaMemcpyDeviceToHost));
+        if (rc == FFS_OK) rc = cuda_rc(cudaMemcpy(&t, d_t, 8, cudaMemcpyDeviceToHost));
+        if (rc == FFS_OK) rc = cuda_rc(cudaMemcpy(&cm, d_c, 4, cudaMemcpyDeviceToHost));
+        dfree(d_o); dfree(d_t); dfree(d_c); dfree(d_S); dfree(d_M);
+        if (rc != FFS_OK) return rc;
+        FFS_TRY(ffs_commit(in, S.data(), M.data()));
+        b->versions[i] = in->version;
+        best[i].objective = o;
+        best[i].total_tardiness = t;
+        best[i].makespan = cm;
+        best[i].n_ops = (int32_t)NG;
+        if (best[i].start) std::memcpy(best[i].start, S.data(), 4 * NG);
+        if (best[i].machine) std::memcpy(best[i].machine, M.data(), 4 * NG);
+    }
+    return FFS_OK;
+}
+
+int ga_batch_read(ga_batch *b, int32_t index, int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit, int16_t *bY,
+                  int8_t *bX, int64_t *bobj, int64_t *bfit, int64_t *emax, int32_t *generation) {
+    if (!b || index < 0 || index >= b->count) return FFS_E_ARG;
+    FFS_CUDA(cudaStreamSynchronize(b->st));
+    BatchInst h;
+    FFS_CUDA(cudaMemcpy(&h, b->d_inst + index, sizeof(h), cudaMemcpyDeviceToHost));
+    const int s = h.gen & 1;
+    const size_t PK = (size_t)b->P * h.K, NK = (size_t)b->nisl * h.K;
+    if (Y) FFS_CUDA(cudaMemcpy(Y, h.Y[s], 2 * PK, cudaMemcpyDeviceToHost));
+    if (X) FFS_CUDA(cudaMemcpy(X, h.X[s], PK, cudaMemcpyDeviceToHost));
+    if (obj) FFS_CUDA(cudaMemcpy(obj, h.obj[s], 8 * (size_t)b->P, cudaMemcpyDeviceToHost));
+    if (fit) FFS_CUDA(cudaMemcpy(fit, h.fit[s], 8 * (size_t)b->P, cudaMemcpyDeviceToHost));
+    if (bY) FFS_CUDA(cudaMemcpy(bY, h.bY, 2 * NK, cudaMemcpyDeviceToHost));
+    if (bX) FFS_CUDA(cudaMemcpy(bX, h.bX, NK, cudaMemcpyDeviceToHost));
+    if (bobj) FFS_CUDA(cudaMemcpy(bobj, h.bobj, 8 * (size_t)b->nisl, cudaMemcpyDeviceToHost));
+    if (bfit) FFS_CUDA(cudaMemcpy(bfit, h.bfit, 8 * (size_t)b->nisl, cudaMemcpyDeviceToHost));
+    if (emax) *emax = h.emax;
+    if (generation) *generation = h.gen;
+    return FFS_OK;
+}
+
+int ga_batch_tune(ga_batch *b, int32_t generations, ga_batch_config *chosen) {
+    if (!b || generations < 1) return FFS_E_ARG;
+    if (!b->shadow) FFS_CUDA(dalloc(&b->shadow, b->arena_bytes));
+    std::vector<BatchInst> saved(b->count);
+    FFS_CUDA(cudaStreamSynchronize(b->st));
+    FFS_CUDA(cudaMemcpy(saved.data(), b->d_inst, sizeof(BatchInst) * b->count, cudaMemcpyDeviceToHost));
+    FFS_CUDA(cudaMemcpy(b->shadow, b->arena, b->arena_bytes, cudaMemcpyDeviceToDevice));
+    cudaEvent_t e0, e1;
+    FFS_CUDA(cudaEventCreate(&e0));
+    FFS_CUDA(cudaEventCreate(&e1));
+    const int warps_c[] = {4, 8, 16};
+    const int smem_c[] = {56 * 1024, 75 * 1024, 112 * 1024, 225 * 1024};
+    const int cluster_c[] = {8, 4, 2};
+    float best_ms = 1e30f;
+    int bw = b->warps, bs = b->smem, bc = b->cluster, rc = FFS_OK;
+    for (int ci = 0; ci < 3 && rc == FFS_OK; ++ci) {
+        for (int wi = 0; wi < 3 && rc == FFS_OK; ++wi) {
+            for (int si = 0; si < 4 && rc == FFS_OK; ++si) {
+                // skip mappings that do not fit every instance or cannot be resident
+                if (batch_config(b, warps_c[wi], smem_c[si], cluster_c[ci]) != FFS_OK) continue;
+                rc = cuda_rc(cudaEventRecord(e0, b->st));
+                if (rc == FFS_OK) rc = batch_enqueue(b, generations, b->st);
+                if (rc == FFS_OK) rc = cuda_rc(cudaEventRecord(e1, b->st));
+                if (rc == FFS_OK) rc = batch_check(b);
+                float ms = 0.f;
+                if (rc == FFS_OK) rc = cuda_rc(cudaEventElapsedTime(&ms, e0, e1));
+                if (rc == FFS_OK && ms < best_ms) {
+                    best_ms = ms;
+                    bw = warps_c[wi];
+                    bs = smem_c[si];
+                    bc = cluster_c[ci];
+                }
+                // restore the state the trial advanced
+                if (rc == FFS_OK)
+                    rc = cuda_rc(cudaMemcpy(b->arena, b->shadow, b->arena_bytes, cudaMemcpyDeviceToDevice));
+                if (rc == FFS_OK)
+                    rc = cuda_rc(cudaMemcpy(b->d_inst, saved.data(), sizeof(BatchInst) * b->count,
+                                            cudaMemcpyHostToDevice));
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != FFS_OK) return rc;
+    FFS_TRY(batch_config(b, bw, bs, bc));
+    b->tuned_ms = best_ms / (float)generations;
+    if (chosen) FFS_TRY(ga_batch_get_config(b, chosen));
+    return FFS_OK;
+}
+
+}  // extern "C"

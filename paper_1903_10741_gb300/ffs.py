@@ -55,6 +55,11 @@ class Result_c(C.Structure):
                 ("n_ops", C.c_int32), ("start", _i32p), ("machine", _i32p)]
 
 
+class BatchConfig_c(C.Structure):
+    _fields_ = [("warps_per_cta", C.c_int32), ("smem_bytes", C.c_int32), ("ctas", C.c_int32),
+                ("cluster", C.c_int32), ("ms_per_generation", C.c_float)]
+
+
 class Info_c(C.Structure):
     _fields_ = [("n_jobs", C.c_int32), ("n_stages", C.c_int32), ("n_machines", C.c_int32),
                 ("n_genes", C.c_int32), ("rs", C.c_int32), ("horizon", C.c_int32),
@@ -85,6 +90,13 @@ _SIGS = {
     "ga_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     "ga_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "ffs_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
+    "ga_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(GAParams_c), C.POINTER(C.c_void_p)]),
+    "ga_batch_destroy": (C.c_int, [C.c_void_p]),
+    "ga_batch_run": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "ga_batch_read": (C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 10),
+    "ga_batch_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "ga_batch_get_config": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ga_batch_set_config": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ga_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "ga_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
@@ -318,3 +330,77 @@ class Population:
     def restore(self, data: bytes):
         buf = C.create_string_buffer(data, len(data))
         _check(lib().ga_restore(self._h, buf, len(data)), "ga_restore")
+
+
+class Batch:
+    """Many instances' GAs advanced by one persistent launch (``ga_batch``)."""
+
+    def __init__(self, insts, P: int, island: int = 64, tour_k: int = 2, pc=(4, 5), pm=(1, 10),
+                 order_mode=ORDER_STAGE, mach_mode=MACH_EARLIEST, migrate_every: int = 10, seed: int = 1,
+                 instance_id: int = 0, stream=None):
+        self.insts = list(insts)
+        island = min(island, P)
+        self.P, self.island, self.nisl = P, island, P // island
+        par = GAParams_c(P, island, tour_k, pc[0], pc[1], pm[0], pm[1], order_mode, mach_mode,
+                         migrate_every, instance_id, seed, _stream_ptr(stream))
+        arr = (C.c_void_p * len(self.insts))(*[i.handle.value for i in self.insts])
+        h = C.c_void_p()
+        _check(lib().ga_batch_create(arr, len(self.insts), C.byref(par), C.byref(h)), "ga_batch_create")
+        self._h = h
+        self.K = [i.K for i in self.insts]
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().ga_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, generations: int, results: bool = False):
+        if not results:
+            _check(lib().ga_batch_run(self._h, int(generations), None), "ga_batch_run")
+            return None
+        n = len(self.insts)
+        res = (Result_c * n)()
+        bufs = []
+        for i, inst in enumerate(self.insts):
+            inf = inst.info()
+            S = np.zeros((inf["n_jobs"], inf["n_stages"]), np.int32)
+            M = np.zeros_like(S)
+            bufs.append((S, M))
+            res[i].start, res[i].machine = _p(S), _p(M)
+        _check(lib().ga_batch_run(self._h, int(generations), res), "ga_batch_run")
+        return [dict(obj=int(r.objective), tard=int(r.total_tardiness), cmax=int(r.makespan), S=S, M=M)
+                for r, (S, M) in zip(res, bufs)]
+
+    def read(self, index: int) -> dict:
+        P, K, n = self.P, self.K[index], self.nisl
+        d = dict(Y=np.zeros((P, K), np.int16), X=np.zeros((P, K), np.int8), obj=np.zeros(P, np.int64),
+                 fit=np.zeros(P, np.int64), bY=np.zeros((n, K), np.int16), bX=np.zeros((n, K), np.int8),
+                 bobj=np.zeros(n, np.int64), bfit=np.zeros(n, np.int64))
+        emax = C.c_int64()
+        gen = C.c_int32()
+        _check(lib().ga_batch_read(self._h, int(index), *[d[k].ctypes.data for k in
+                                                          ("Y", "X", "obj", "fit", "bY", "bX", "bobj", "bfit")],
+                                   C.addressof(emax), C.addressof(gen)), "ga_batch_read")
+        d["emax"] = int(emax.value)
+        d["gen"] = int(gen.value)
+        return d
+
+    def tune(self, generations: int) -> dict:
+        c = BatchConfig_c()
+        _check(lib().ga_batch_tune(self._h, int(generations), C.byref(c)), "ga_batch_tune")
+        return {n: getattr(c, n) for n, _ in BatchConfig_c._fields_}
+
+    def config(self) -> dict:
+        c = BatchConfig_c()
+        _check(lib().ga_batch_get_config(self._h, C.byref(c)), "ga_batch_get_config")
+        return {n: getattr(c, n) for n, _ in BatchConfig_c._fields_}
+
+    def set_config(self, warps: int, smem_bytes: int, cluster: int = 0):
+        c = BatchConfig_c(warps, smem_bytes, 0, cluster, 0.0)
+        _check(lib().ga_batch_set_config(self._h, C.byref(c)), "ga_batch_set_config")
