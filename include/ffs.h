@@ -214,6 +214,45 @@ int ga_batch_tune(ga_batch *batch, int32_t generations, ga_batch_config *chosen)
 int ga_batch_get_config(const ga_batch *batch, ga_batch_config *config);
 int ga_batch_set_config(ga_batch *batch, const ga_batch_config *config);
 
+/* ---------------------------------------------------------------- learned surrogate */
+
+/* A learned fitness surrogate for one instance at its current rescheduling point.  Not in
+ * the paper: it lets the GA screen over-generated offspring before the exact decoder
+ * (Sec. 4.3) evaluates the kept ones.  Model: with yh = y / K and per-gene features
+ * ph = p_js / max p and dh = D_j / max |D|, the input is x = [yh_k, yh_k ph_k, yh_k dh_k]
+ * (3K values); h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2) with 256 units each, and
+ * out = w3 . h2 + b3 predicts the objective normalised over a batch (lower is better).
+ * BF16 weights and activations on the tensor cores, FP32 accumulation and FP32 master
+ * weights; training is Adam on the mean squared error to (obj - mean) / std.
+ * Parameters are one FP32 vector: W1 [256][3K] (row-major), b1 [256], W2 [256][256],
+ * b2 [256], w3 [256], b3 [1]. */
+typedef struct ffs_surrogate ffs_surrogate;
+
+/* Creates a surrogate for the instance's current genes, with batches of up to `max_batch`
+ * chromosomes (training) and weights drawn from `seed`. */
+int ffs_surrogate_create(ffs_instance *inst, int32_t max_batch, uint64_t seed, void *stream, ffs_surrogate **out);
+int ffs_surrogate_destroy(ffs_surrogate *sur);
+int ffs_surrogate_param_count(const ffs_surrogate *sur, int64_t *count);
+/* Host copies of the FP32 parameter vector; setting it also resets the Adam state. */
+int ffs_surrogate_get_params(ffs_surrogate *sur, float *params);
+int ffs_surrogate_set_params(ffs_surrogate *sur, const float *params);
+/* Scores `count` device chromosomes y [count][K] into device out [count]. */
+int ffs_surrogate_predict(ffs_surrogate *sur, const int16_t *y, int32_t count, float *out);
+/* Gradient of the loss on a device batch (y [count][K], exact objectives obj [count],
+ * count <= max_batch) into host grad [param count]; host *loss if not NULL.  No update. */
+int ffs_surrogate_gradients(ffs_surrogate *sur, const int16_t *y, const int64_t *obj, int32_t count, float *grad,
+                            float *loss);
+/* One Adam step (betas 0.9 / 0.999, eps 1e-8, learning rate lr) on a device batch; host
+ * *loss (before the step) if not NULL. */
+int ffs_surrogate_train(ffs_surrogate *sur, const int16_t *y, const int64_t *obj, int32_t count, float lr,
+                        float *loss);
+/* Surrogate-assisted generations for a population of the same instance: each generation
+ * builds `oversample` candidates per slot with the Sec. 4.4 operators, scores them all,
+ * decodes exactly only the best-scored candidate of each slot (ties to the lower
+ * candidate), then trains the surrogate one Adam step on those exact objectives.
+ * P and P * oversample must be multiples of 128 and max_batch >= P.  NULL detaches. */
+int ga_population_attach_surrogate(ga_population *pop, ffs_surrogate *sur, int32_t oversample, float lr);
+
 /* Allocation-free variant of ffs_decode, for callers that cannot allocate device memory:
  * code that runs while a CUDA stream is being captured (cudaMalloc is not permitted
  * there), hosts that fix the process's device memory at start-up, and real-time loops

@@ -1,0 +1,115 @@
+"""Oracle for the learned fitness surrogate (numpy, float64).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  The surrogate is not in the
+paper: it is a 3-layer perceptron that scores a priority chromosome from per-gene
+features so that a GA can screen over-generated offspring before the exact decoder
+(Sec. 4.3) evaluates the kept ones.
+
+Model.  A chromosome's priorities y (a permutation of 1..K) become yh = y / K.  Gene k
+carries two instance features, ph_k = p_k / max p and dh_k = D_j / max D of its job j.
+The input has 3K features, x = [yh_k, yh_k ph_k, yh_k dh_k]_k, and
+    h1 = relu(W1 x + b1)   (H units),   h2 = relu(W2 h1 + b2)   (H units),
+    out = w3 . h2 + b3     (a predicted normalised objective; lower is better).
+Training minimises the mean squared error to t = (obj - mean) / std over the batch with
+Adam (Kingma & Ba 2015).
+
+Because the features are yh times constants, W1 x = V yh with
+V[n, k] = W1[n, 3k] + ph_k W1[n, 3k+1] + dh_k W1[n, 3k+2]; `forward` computes the layer
+from the explicit 3K features and `forward_factored` from V, and a test pins their
+equality.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def gene_features(p, D, gene_job, gene_stage):
+    """(ph, dh) per gene: processing time over the largest one, due date over the largest."""
+    pk = np.array([p[j, s] for j, s in zip(gene_job, gene_stage)], dtype=np.float64)
+    dk = np.array([D[j] for j in gene_job], dtype=np.float64)
+    return pk / max(pk.max(), 1.0), dk / max(abs(dk).max(), 1.0)
+
+
+def features(Y, ph, dh):
+    """Explicit 3K-wide inputs for chromosomes Y [B, K]."""
+    B, K = Y.shape
+    yh = Y.astype(np.float64) / K
+    X = np.empty((B, 3 * K))
+    X[:, 0::3] = yh
+    X[:, 1::3] = yh * ph[None, :]
+    X[:, 2::3] = yh * dh[None, :]
+    return X
+
+
+def init_params(K, H=256, seed=0):
+    """He-uniform hidden layers, small output layer, zero biases."""
+    rng = np.random.default_rng(seed)
+    lim1 = np.sqrt(6.0 / (3 * K))
+    lim2 = np.sqrt(6.0 / H)
+    return dict(W1=rng.uniform(-lim1, lim1, (H, 3 * K)), b1=np.zeros(H),
+                W2=rng.uniform(-lim2, lim2, (H, H)), b2=np.zeros(H),
+                w3=rng.uniform(-1 / np.sqrt(H), 1 / np.sqrt(H), H), b3=np.zeros(1))
+
+
+def forward(params, X):
+    z1 = X @ params["W1"].T + params["b1"]
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ params["W2"].T + params["b2"]
+    h2 = np.maximum(z2, 0.0)
+    out = h2 @ params["w3"] + params["b3"][0]
+    return out, dict(X=X, z1=z1, h1=h1, z2=z2, h2=h2)
+
+
+def factored_V(params, ph, dh):
+    W1 = params["W1"]
+    return W1[:, 0::3] + ph[None, :] * W1[:, 1::3] + dh[None, :] * W1[:, 2::3]
+
+
+def forward_factored(params, Y, ph, dh):
+    K = Y.shape[1]
+    yh = Y.astype(np.float64) / K
+    z1 = yh @ factored_V(params, ph, dh).T + params["b1"]
+    h1 = np.maximum(z1, 0.0)
+    h2 = np.maximum(h1 @ params["W2"].T + params["b2"], 0.0)
+    return h2 @ params["w3"] + params["b3"][0]
+
+
+def targets(obj):
+    obj = np.asarray(obj, dtype=np.float64)
+    sd = obj.std()
+    return (obj - obj.mean()) / (sd if sd > 0 else 1.0)
+
+
+def loss(out, t):
+    return float(np.mean((out - t) ** 2))
+
+
+def backward(params, cache, out, t):
+    """Gradients of the mean squared error."""
+    B = out.shape[0]
+    dout = 2.0 * (out - t) / B
+    g = {}
+    g["w3"] = cache["h2"].T @ dout
+    g["b3"] = np.array([dout.sum()])
+    dz2 = np.outer(dout, params["w3"]) * (cache["z2"] > 0)
+    g["W2"] = dz2.T @ cache["h1"]
+    g["b2"] = dz2.sum(axis=0)
+    dz1 = (dz2 @ params["W2"]) * (cache["z1"] > 0)
+    g["W1"] = dz1.T @ cache["X"]
+    g["b1"] = dz1.sum(axis=0)
+    return g
+
+
+def adam(params, grads, state, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (bias-corrected), in place; `state` holds m, v and the step count."""
+    state["t"] = state.get("t", 0) + 1
+    t = state["t"]
+    for k in params:
+        m = state.setdefault("m_" + k, np.zeros_like(params[k]))
+        v = state.setdefault("v_" + k, np.zeros_like(params[k]))
+        m[...] = b1 * m + (1 - b1) * grads[k]
+        v[...] = b2 * v + (1 - b2) * grads[k] ** 2
+        mh = m / (1 - b1 ** t)
+        vh = v / (1 - b2 ** t)
+        params[k] = params[k] - lr * mh / (np.sqrt(vh) + eps)
+    return params

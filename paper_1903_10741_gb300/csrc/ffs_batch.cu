@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchArgs a) {
             const bool migrate = a.migrate_every > 0 && (int)g1 % a.migrate_every == 0 && nisl > 1;
             if (fits) {
                 const GASrc src{in->Y[cur], in->X[cur], in->fit[cur], P, I, K, a.tour_k, a.side,
-                                a.pc_thr, a.pm_thr, a.seed, in->iid};
+                                a.pc_thr, a.pm_thr, a.seed, in->iid, 1};
                 for (int isl = rank; isl < nisl; isl += CS)
                     for (int c = warp; c < I; c += W) {
                         const int i = isl * I + c;

@@ -1,0 +1,156 @@
+// ffs_internal.h -- host-side internals shared by the library's translation units: the
+// instance and population objects behind the opaque C handles, allocation helpers and
+// the error conventions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+#include "ffs.h"
+#include "ffs_kernels.cuh"
+#include "ffs_layout.h"
+
+namespace ffs_rt {
+
+extern std::atomic<unsigned long long> g_launches;  // kernels issued by this library
+extern thread_local char g_last_error[256];
+
+int num_sms();
+int cuda_rc(cudaError_t e);  // FFS_OK, or FFS_E_CUDA with the error text kept
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+}
+
+template <typename T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+#define FFS_TRY(expr)                  \
+    do {                               \
+        const int rc_ = (expr);        \
+        if (rc_ != FFS_OK) return rc_; \
+    } while (0)
+#define FFS_CUDA(expr) FFS_TRY(ffs_rt::cuda_rc(expr))
+
+}  // namespace ffs_rt
+
+using ffs_rt::dalloc;
+using ffs_rt::dfree;
+
+struct ffs_instance {
+    int N = 0, g = 0, M = 0, Qmax = 0, WT = 0, RS = 0;
+    std::vector<int32_t> o, moff, p, q, R, D;   // problem
+    std::vector<int32_t> status, S0, M0;       // plan and classification, [N*g]
+    bool has_plan = false;
+    bool dev_dirty = true;  // host tables or plan changed since the last upload
+    int K = 0, Hfull = 0;
+    std::vector<int32_t> gjob, gstg;
+    edffs::TabHeader hdr{};
+    std::vector<char> blob;
+    int version = 0;
+    // device mirrors
+    char *d_blob = nullptr;
+    size_t d_blob_cap = 0;
+    int32_t *d_S0 = nullptr, *d_M0 = nullptr, *d_status = nullptr;
+    size_t d_plan_cap = 0;
+    uint16_t *d_scratch = nullptr;  // global power profiles for the fallback decode
+    size_t d_scratch_cap = 0;
+    int32_t *d_over = nullptr;
+    size_t d_over_cap = 0;
+    int32_t *d_over_count = nullptr, *d_err = nullptr;
+
+    ~ffs_instance() {
+        dfree(d_blob);
+        dfree(d_S0);
+        dfree(d_M0);
+        dfree(d_status);
+        dfree(d_scratch);
+        dfree(d_over);
+        dfree(d_over_count);
+        dfree(d_err);
+    }
+};
+
+struct ga_population {
+    ffs_instance *inst = nullptr;
+    int version = 0;
+    ga_params par{};
+    cudaStream_t st = nullptr;
+    int P = 0, I = 0, K = 0, nisl = 0, side = 0;
+    int Hcap = 0, grid_gen = 0, grid_fb = 0;
+    edffs::TabHeader hdr{};
+    char *d_blob = nullptr;  // private copy of the instance tables at creation
+    int16_t *Y[2] = {nullptr, nullptr};
+    int8_t *X[2] = {nullptr, nullptr};
+    int64_t *obj[2] = {nullptr, nullptr}, *fit[2] = {nullptr, nullptr};
+    int16_t *bY = nullptr, *mY = nullptr;
+    int8_t *bX = nullptr, *mX = nullptr;
+    int64_t *bobj = nullptr, *bfit = nullptr, *mobj = nullptr, *mfit = nullptr;
+    int32_t *mw = nullptr, *over = nullptr, *err = nullptr, *isl_done = nullptr;
+    edffs::GADev *dev = nullptr;
+    uint16_t *scratch = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    // surrogate-assisted generations (see ffs_surrogate.cu)
+    struct ffs_surrogate *sur = nullptr;
+    int F = 1;
+    float lr = 0.f;
+    int16_t *cand_Y = nullptr;
+    int8_t *cand_X = nullptr;
+    uint16_t *cand_Yh = nullptr, *cand_H1 = nullptr, *cand_H2 = nullptr;
+    float *cand_out = nullptr;
+    int64_t *kept_obj = nullptr;
+    cudaGraphExec_t graph_sur = nullptr;
+    bool profiling = false;                 // eager launches with timed generation kernels
+    std::vector<cudaEvent_t> ev;            // event pairs, reused across ga_run calls
+    double prof_ms = 0.0;
+    int64_t prof_launches = 0;
+
+    ~ga_population() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (graph) cudaGraphExecDestroy(graph);
+        if (graph_sur) cudaGraphExecDestroy(graph_sur);
+        dfree(cand_Y);
+        dfree(cand_X);
+        dfree(cand_Yh);
+        dfree(cand_H1);
+        dfree(cand_H2);
+        dfree(cand_out);
+        dfree(kept_obj);
+        dfree(d_blob);
+        for (int b = 0; b < 2; ++b) {
+            dfree(Y[b]);
+            dfree(X[b]);
+            dfree(obj[b]);
+            dfree(fit[b]);
+        }
+        dfree(bY); dfree(bX); dfree(bobj); dfree(bfit);
+        dfree(mY); dfree(mX); dfree(mobj); dfree(mfit); dfree(mw);
+        dfree(over); dfree(err); dfree(dev); dfree(scratch); dfree(isl_done);
+    }
+};
+
+
+namespace ffs_rt {
+
+int check_modes(int32_t order_mode, int32_t machine_mode);
+int sync_device(ffs_instance *in);
+int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y, const int8_t *x, int32_t count,
+                int64_t *obj, int64_t *tard, int32_t *cmax, int32_t *S, int32_t *Mo, cudaStream_t st);
+void ga_gen_args(ga_population *pp, edffs::GenArgs *a);
+// One surrogate-assisted generation on `st` (ffs_surrogate.cu); with events, the fused
+// generation kernel is bracketed by ev0/ev1.  Kernels launched per generation:
+constexpr int kSurrogateLaunches = 27;
+int surrogate_enqueue_generation(ga_population *pp, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
+// Raises the shared-memory limits of the kernels a surrogate generation launches, so that
+// the generation can be captured.
+int prepare_surrogate_kernels(ga_population *pp);
+
+}  // namespace ffs_rt

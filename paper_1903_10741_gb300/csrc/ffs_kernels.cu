@@ -5,6 +5,7 @@
 // with a single bulk copy; each warp then keeps its chromosome, per-job completion times,
 // per-machine free times and the power headroom profile of its schedule in its own slice
 // of shared memory.  The decoder's inner step scans 32 time slots per ballot.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -163,10 +164,37 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
     const uint32_t gen = (uint32_t)a.dev->gen + 1;
     const long long emax = a.dev->emax;
     const GASrc src{a.Y[cur], a.X[cur], a.fit[cur], a.P, a.I, K, a.tour_k, a.side, a.pc_thr, a.pm_thr, a.seed,
-                    a.instance_id};
+                    a.instance_id, 1};
 
     for (int i = blockIdx.x * kWarpsPerBlock + warp; i < a.P; i += gridDim.x * kWarpsPerBlock) {
-        make_child<MACH>(T, w, src, i, gen, lane);
+        if (!a.cand_Y) {
+            make_child<MACH>(T, w, src, i, gen, lane);
+        } else {
+            // surrogate-assisted: keep the candidate with the lowest score (ties to the lower
+            // index; an undefined score counts as worst)
+            float sc = INFINITY;
+            int vi = INT_MAX;
+            if (lane < a.F) {
+                sc = a.cand_out[(size_t)i * a.F + lane];
+                if (isnan(sc)) sc = INFINITY;
+                vi = lane;
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                const float os = __shfl_xor_sync(kFull, sc, off);
+                const int ov = __shfl_xor_sync(kFull, vi, off);
+                if (os < sc || (os == sc && ov < vi)) {
+                    sc = os;
+                    vi = ov;
+                }
+            }
+            const size_t c = (size_t)i * a.F + vi;
+            for (int k = lane; k < K; k += 32) w.y[k] = a.cand_Y[c * K + k];
+            if (MACH == kMachGene)
+                for (int k = lane; k < K; k += 32) w.x[k] = a.cand_X[c * K + k];
+            for (int k = lane; k < a.Kpad; k += 32) a.kept_Yh[(size_t)i * a.Kpad + k] = a.cand_Yh[c * a.Kpad + k];
+            __syncwarp();
+        }
         int16_t *yo = a.Y[nx] + (size_t)i * K;
         for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
         if (MACH == kMachGene) {
@@ -187,9 +215,41 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
                 const long long o = (long long)T.WT * r.tard + r.cmax;
                 a.obj[nx][i] = o;
                 a.fit[nx][i] = emax - o > 0 ? emax - o : 0;
+                if (a.kept_obj) a.kept_obj[i] = o;
             }
         }
         island_finish(a, i / I, nx, (int)gen, lane);
+    }
+}
+
+// ---------------------------------------------------------------- surrogate candidates
+// Over-generation for the surrogate: candidate c is one of F children built for population
+// slot c / F with the usual operators and its own stream position; its model input, the
+// BF16 of y / K zero padded to Kpad, is written beside it.  Nothing is decoded here.
+template <int MACH>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_candidates(GenArgs a) {
+    extern __shared__ __align__(128) char smem[];
+    char *tab = smem + 128;
+    if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
+    const Tabs T = tabs_view(tab);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, 0, true, false, nullptr, warp);
+    const int K = T.K, cur = a.dev->gen & 1;
+    const uint32_t gen = (uint32_t)a.dev->gen + 1;
+    const GASrc src{a.Y[cur], a.X[cur], a.fit[cur], a.P, a.I, K, a.tour_k, a.side, a.pc_thr, a.pm_thr, a.seed,
+                    a.instance_id, a.F};
+    for (int c = blockIdx.x * kWarpsPerBlock + warp; c < a.P * a.F; c += gridDim.x * kWarpsPerBlock) {
+        make_child<MACH>(T, w, src, c, gen, lane);
+        int16_t *yo = a.cand_Y + (size_t)c * K;
+        for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
+        if (MACH == kMachGene) {
+            int8_t *xo = a.cand_X + (size_t)c * K;
+            for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
+        }
+        uint16_t *yh = a.cand_Yh + (size_t)c * a.Kpad;
+        for (int k = lane; k < a.Kpad; k += 32)
+            yh[k] = k < K ? __bfloat16_as_ushort(__float2bfloat16_rn((float)w.y[k] / (float)K)) : (uint16_t)0;
+        __syncwarp();
     }
 }
 
@@ -356,6 +416,24 @@ cudaError_t prepare_ga_generation(int order, int mach, const TabHeader &h, int H
     cudaError_t e = cudaSuccess;
     FFS_DISPATCH({ e = prepare(k_ga_generation<O_, M_>, smem); });
     return e;
+}
+
+cudaError_t prepare_candidates(int mach, const TabHeader &h) {
+    const int smem = cta_smem_bytes(h, 0, true, false);
+    return mach == kMachGene ? prepare(k_candidates<kMachGene>, smem) : prepare(k_candidates<kMachEarliest>, smem);
+}
+
+cudaError_t launch_candidates(int mach, const GenArgs &a, const TabHeader &h, int grid, cudaStream_t st) {
+    const int smem = cta_smem_bytes(h, 0, true, false);
+    cudaError_t e;
+    if (mach == kMachGene) {
+        e = prepare(k_candidates<kMachGene>, smem);
+        if (e == cudaSuccess) k_candidates<kMachGene><<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
+    } else {
+        e = prepare(k_candidates<kMachEarliest>, smem);
+        if (e == cudaSuccess) k_candidates<kMachEarliest><<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_emax(const ReplArgs &a, cudaStream_t st) {

@@ -61,6 +61,15 @@ struct GenArgs {
     int8_t *mX;
     int64_t *mobj, *mfit;
     int32_t *mw;                // worst slot of each island at migration time
+    // surrogate-assisted generations (null cand_Y: plain generations)
+    int F;                      // candidates per slot
+    int Kpad;                   // row length of the BF16 model inputs
+    int16_t *cand_Y;            // [P*F][K] candidates
+    int8_t *cand_X;
+    uint16_t *cand_Yh;          // [P*F][Kpad] BF16 bits of y / K (zero padded)
+    const float *cand_out;      // [P*F] surrogate scores, lower is better
+    uint16_t *kept_Yh;          // [P][Kpad] inputs of the kept candidates, for training
+    int64_t *kept_obj;          // [P] their exact objectives (before replacement)
 };
 
 struct ReplArgs {
@@ -126,6 +135,9 @@ cudaError_t launch_ga_init(int order, int mach, const GenArgs &a, const TabHeade
 cudaError_t launch_ga_generation(int order, int mach, const GenArgs &a, const TabHeader &h,
                                  int grid, cudaStream_t st);
 cudaError_t prepare_ga_generation(int order, int mach, const TabHeader &h, int Hcap);
+// Over-generation for the surrogate: P*F candidates (no decoding).
+cudaError_t launch_candidates(int mach, const GenArgs &a, const TabHeader &h, int grid, cudaStream_t st);
+cudaError_t prepare_candidates(int mach, const TabHeader &h);
 cudaError_t launch_emax(const ReplArgs &a, cudaStream_t st);
 cudaError_t launch_replace(const ReplArgs &a, cudaStream_t st);
 

@@ -1,0 +1,353 @@
+// ffs_mlp.cu -- kernels of the learned fitness surrogate: a 3-layer perceptron over a
+// chromosome's priorities and its genes' features (H = 256 hidden units, BF16 weights and
+// activations, FP32 accumulation), its backward pass and Adam.
+//
+// The input features are yh_k * (1, ph_k, dh_k) per gene (yh = y / K), so the first layer
+// is applied as V yh with V[n, k] = W1[n, 3k] + ph_k W1[n, 3k+1] + dh_k W1[n, 3k+2]; its
+// weight gradient is recovered exactly as dW1[n, 3k+f] = G[n, k] c_f(k) from
+// G = dZ1^T Yh.  Every contraction is one GEMM kernel, C = A B^T with both operands
+// K-contiguous, on the tensor cores (mma.sync m16n8k16 BF16 -> FP32), fed by cp.async
+// double buffering and ldmatrix; reductions run in a fixed order, so results are
+// reproducible.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ffs_mlp.cuh"
+
+namespace edffs {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 32, kPad = 8;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// C[M x N] = A[M x K] . B[N x K]^T; M, N multiples of 128, K a multiple of 32.
+// 8 warps as 2 x 4, each a 64 x 32 tile of 4 x 4 mma tiles.
+template <int EPI>
+__global__ void __launch_bounds__(256) k_gemm(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B,
+                                              int K, void *C, int ldc, const float *__restrict__ bias) {
+    __shared__ __align__(16) __nv_bfloat16 sA[2][kBM][kBK + kPad];
+    __shared__ __align__(16) __nv_bfloat16 sB[2][kBN][kBK + kPad];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bm = blockIdx.y * kBM, bn = blockIdx.x * kBN;
+    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
+    float acc[4][4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+    auto load = [&](int st, int k0) {
+#pragma unroll
+        for (int c = tid; c < kBM * kBK / 8; c += 256) {
+            const int r = c >> 2, col = (c & 3) * 8;
+            cp_async16(&sA[st][r][col], A + (size_t)(bm + r) * K + k0 + col);
+            cp_async16(&sB[st][r][col], B + (size_t)(bn + r) * K + k0 + col);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    const int nk = K / kBK;
+    load(0, 0);
+    for (int kt = 0; kt < nk; ++kt) {
+        if (kt + 1 < nk) {
+            load((kt + 1) & 1, (kt + 1) * kBK);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const int st = kt & 1;
+#pragma unroll
+        for (int ks = 0; ks < kBK; ks += 16) {
+            uint32_t af[4][4], bf[4][2];
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi) ldmatrix_x4(af[mi], &sA[st][wm + mi * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
+#pragma unroll
+            for (int ni = 0; ni < 2; ++ni) {
+                uint32_t r[4];
+                ldmatrix_x4(r, &sB[st][wn + ni * 16 + (lane & 7) + ((lane >> 4) << 3)][ks + ((lane >> 3) & 1) * 8]);
+                bf[2 * ni][0] = r[0];
+                bf[2 * ni][1] = r[1];
+                bf[2 * ni + 1][0] = r[2];
+                bf[2 * ni + 1][1] = r[3];
+            }
+#pragma unroll
+            for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+                for (int nj = 0; nj < 4; ++nj) mma_bf16(acc[mi][nj], af[mi], bf[nj][0], bf[nj][1]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int nj = 0; nj < 4; ++nj)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = bm + wm + mi * 16 + (lane >> 2) + h * 8;
+                const int col = bn + wn + nj * 8 + (lane & 3) * 2;
+                float v0 = acc[mi][nj][2 * h], v1 = acc[mi][nj][2 * h + 1];
+                if (EPI == kEpiF32) {
+                    *reinterpret_cast<float2 *>(static_cast<float *>(C) + (size_t)row * ldc + col) = make_float2(v0, v1);
+                } else {
+                    v0 = fmaxf(v0 + bias[col], 0.f);
+                    v1 = fmaxf(v1 + bias[col + 1], 0.f);
+                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(C) + (size_t)row * ldc + col) =
+                        __floats2bfloat162_rn(v0, v1);
+                }
+            }
+}
+
+// out[r] = w3 . h2[r] + b3 (BF16 operands, FP32 sum, fixed order), one warp per row.
+__global__ void k_rowdot(const __nv_bfloat16 *__restrict__ h2, const __nv_bfloat16 *__restrict__ w3, const float *b3,
+                         int rows, int H, float *out) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    float s = 0.f;
+    for (int n = lane; n < H; n += 32) s += __bfloat162float(h2[(size_t)r * H + n]) * __bfloat162float(w3[n]);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) out[r] = s + b3[0];
+}
+
+// V[n, k] = W1[n, 3k] + ph_k W1[n, 3k+1] + dh_k W1[n, 3k+2] (k < K), 0 up to Kpad.
+__global__ void k_make_v(const float *__restrict__ W1, const float *__restrict__ ph, const float *__restrict__ dh,
+                         int H, int K, int Kpad, __nv_bfloat16 *V) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= H * Kpad) return;
+    const int n = i / Kpad, k = i % Kpad;
+    float v = 0.f;
+    if (k < K) {
+        const float *w = W1 + (size_t)n * 3 * K + 3 * k;
+        v = w[0] + ph[k] * w[1] + dh[k] * w[2];
+    }
+    V[i] = __float2bfloat16_rn(v);
+}
+
+// Yh[r, k] = y[r, k] / K as BF16 (0 in padding rows and columns).
+__global__ void k_yhat(const int16_t *__restrict__ y, int rows, int rows_pad, int K, int Kpad, __nv_bfloat16 *Yh) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)rows_pad * Kpad) return;
+    const int r = (int)(i / Kpad), k = (int)(i % Kpad);
+    float v = 0.f;
+    if (r < rows && k < K) v = (float)y[(size_t)r * K + k] / (float)K;
+    Yh[i] = __float2bfloat16_rn(v);
+}
+
+// Tiled transpose of a BF16 [R x C] matrix (R, C multiples of 32) into [C x R].
+__global__ void k_transpose(const __nv_bfloat16 *__restrict__ in, int R, int C, __nv_bfloat16 *out) {
+    __shared__ __nv_bfloat16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) t[dy][threadIdx.x] = in[(size_t)(r0 + dy) * C + c0 + threadIdx.x];
+    __syncthreads();
+    for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) out[(size_t)(c0 + dy) * R + r0 + threadIdx.x] = t[threadIdx.x][dy];
+}
+
+__global__ void k_f32_to_bf16(const float *__restrict__ in, size_t n, __nv_bfloat16 *out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __float2bfloat16_rn(in[i]);
+}
+
+// Normalised targets t = (obj - mean) / std over `rows` (one block, fixed order, FP64).
+__global__ void k_targets(const int64_t *__restrict__ obj, int rows, float *t, int *step) {
+    __shared__ double s1[32], s2[32];
+    double a = 0, b = 0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        const double v = (double)obj[r];
+        a += v;
+        b += v * v;
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, off);
+        b += __shfl_xor_sync(0xffffffffu, b, off);
+    }
+    if (l == 0) {
+        s1[w] = a;
+        s2[w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            s1[0] += s1[q];
+            s2[0] += s2[q];
+        }
+        if (step) *step += 1;  // the Adam step that these targets feed
+    }
+    __syncthreads();
+    const double mean = s1[0] / rows, var = s2[0] / rows - mean * mean;
+    const double sd = var > 0 ? sqrt(var) : 1.0;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) t[r] = (float)(((double)obj[r] - mean) / sd);
+}
+
+// dout = 2 (out - t) / rows (0 in padding rows); dZ2 = dout w3 * [h2 > 0], FP32 and BF16.
+__global__ void k_dz2(const float *__restrict__ out, const float *__restrict__ t, int rows, int rows_pad,
+                      const __nv_bfloat16 *__restrict__ h2, const __nv_bfloat16 *__restrict__ w3, int H, float *dout,
+                      float *dz2, __nv_bfloat16 *dz2b) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)rows_pad * H) return;
+    const int r = (int)(i / H), n = (int)(i % H);
+    const float d = r < rows ? 2.f * (out[r] - t[r]) / (float)rows : 0.f;
+    if (n == 0) dout[r] = d;
+    const float v = __bfloat162float(h2[i]) > 0.f ? d * __bfloat162float(w3[n]) : 0.f;
+    dz2[i] = v;
+    dz2b[i] = __float2bfloat16_rn(v);
+}
+
+// dZ1 = dH1 * [h1 > 0], FP32 and BF16.
+__global__ void k_dz1(const float *__restrict__ dh1, const __nv_bfloat16 *__restrict__ h1, size_t n, float *dz1,
+                      __nv_bfloat16 *dz1b) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = __bfloat162float(h1[i]) > 0.f ? dh1[i] : 0.f;
+    dz1[i] = v;
+    dz1b[i] = __float2bfloat16_rn(v);
+}
+
+// Column sums over rows of an FP32 [rows x cols] matrix, one thread per column, in order.
+__global__ void k_colsum(const float *__restrict__ m, int rows, int cols, float *out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += m[(size_t)r * cols + c];
+    out[c] = s;
+}
+
+// gw3[n] = sum_r dout[r] h2[r, n]; gb3 = sum_r dout[r] (thread H), in order.
+__global__ void k_grad_out(const float *__restrict__ dout, const __nv_bfloat16 *__restrict__ h2, int rows, int H,
+                           float *gw3, float *gb3) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n > H) return;
+    float s = 0.f;
+    for (int r = 0; r < rows; ++r) s += dout[r] * (n < H ? __bfloat162float(h2[(size_t)r * H + n]) : 1.f);
+    if (n < H) gw3[n] = s;
+    else gb3[0] = s;
+}
+
+// dW1[n, 3k+f] = G[n, k] c_f(k), c = (1, ph, dh).
+__global__ void k_grad_w1(const float *__restrict__ G, int Kpad, const float *__restrict__ ph,
+                          const float *__restrict__ dh, int H, int K, float *gW1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= H * K) return;
+    const int n = i / K, k = i % K;
+    const float g = G[(size_t)n * Kpad + k];
+    float *o = gW1 + (size_t)n * 3 * K + 3 * k;
+    o[0] = g;
+    o[1] = g * ph[k];
+    o[2] = g * dh[k];
+}
+
+// One Adam step on n FP32 parameters (Kingma & Ba 2015), step count *step >= 1.
+__global__ void k_adam(float *p, const float *g, float *m, float *v, size_t n, float lr, float b1, float b2,
+                       float eps, const int *step) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float t = (float)*step;
+    const float bc1 = 1.f - powf(b1, t), bc2 = 1.f - powf(b2, t);
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi, vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+cudaError_t mlp_gemm(int epi, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, void *C, int ldc,
+                     const float *bias, cudaStream_t st) {
+    if (M % kBM || N % kBN || K % kBK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+    const dim3 grid(N / kBN, M / kBM);
+    if (epi == kEpiF32) k_gemm<kEpiF32><<<grid, 256, 0, st>>>(A, B, K, C, ldc, bias);
+    else k_gemm<kEpiBiasReluBf16><<<grid, 256, 0, st>>>(A, B, K, C, ldc, bias);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_rowdot(const __nv_bfloat16 *h2, const __nv_bfloat16 *w3, const float *b3, int rows, int H, float *out,
+                       cudaStream_t st) {
+    k_rowdot<<<blocks(rows, 8), 256, 0, st>>>(h2, w3, b3, rows, H, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_make_v(const float *W1, const float *ph, const float *dh, int H, int K, int Kpad, __nv_bfloat16 *V,
+                       cudaStream_t st) {
+    k_make_v<<<blocks((size_t)H * Kpad, 256), 256, 0, st>>>(W1, ph, dh, H, K, Kpad, V);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_yhat(const int16_t *y, int rows, int rows_pad, int K, int Kpad, __nv_bfloat16 *Yh, cudaStream_t st) {
+    k_yhat<<<blocks((size_t)rows_pad * Kpad, 256), 256, 0, st>>>(y, rows, rows_pad, K, Kpad, Yh);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_transpose(const __nv_bfloat16 *in, int R, int C, __nv_bfloat16 *out, cudaStream_t st) {
+    if (R % 32 || C % 32) return cudaErrorInvalidValue;
+    k_transpose<<<dim3(C / 32, R / 32), dim3(32, 8), 0, st>>>(in, R, C, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_to_bf16(const float *in, size_t n, __nv_bfloat16 *out, cudaStream_t st) {
+    k_f32_to_bf16<<<blocks(n, 256), 256, 0, st>>>(in, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_targets(const int64_t *obj, int rows, float *t, int *step, cudaStream_t st) {
+    k_targets<<<1, 1024, 0, st>>>(obj, rows, t, step);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_backward_out(const float *out, const float *t, int rows, int rows_pad, const __nv_bfloat16 *h2,
+                             const __nv_bfloat16 *w3, int H, float *dout, float *dz2, __nv_bfloat16 *dz2b, float *gw3,
+                             float *gb3, float *gb2, cudaStream_t st) {
+    k_dz2<<<blocks((size_t)rows_pad * H, 256), 256, 0, st>>>(out, t, rows, rows_pad, h2, w3, H, dout, dz2, dz2b);
+    k_grad_out<<<blocks(H + 1, 256), 256, 0, st>>>(dout, h2, rows_pad, H, gw3, gb3);
+    k_colsum<<<blocks(H, 256), 256, 0, st>>>(dz2, rows_pad, H, gb2);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_backward_hidden(const float *dh1, const __nv_bfloat16 *h1, int rows_pad, int H, float *dz1,
+                                __nv_bfloat16 *dz1b, float *gb1, cudaStream_t st) {
+    k_dz1<<<blocks((size_t)rows_pad * H, 256), 256, 0, st>>>(dh1, h1, (size_t)rows_pad * H, dz1, dz1b);
+    k_colsum<<<blocks(H, 256), 256, 0, st>>>(dz1, rows_pad, H, gb1);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_grad_w1(const float *G, int Kpad, const float *ph, const float *dh, int H, int K, float *gW1,
+                        cudaStream_t st) {
+    k_grad_w1<<<blocks((size_t)H * K, 256), 256, 0, st>>>(G, Kpad, ph, dh, H, K, gW1);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_adam(float *p, const float *g, float *m, float *v, size_t n, float lr, float b1, float b2, float eps,
+                     const int *step, cudaStream_t st) {
+    k_adam<<<blocks(n, 256), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, step);
+    return cudaGetLastError();
+}
+
+}  // namespace edffs

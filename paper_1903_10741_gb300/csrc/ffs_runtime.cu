@@ -18,12 +18,14 @@
 #include <vector>
 
 #include "ffs.h"
+#include "ffs_internal.h"
 #include "ffs_kernels.cuh"
 #include "ffs_layout.h"
 
 using namespace edffs;
+using namespace ffs_rt;
 
-namespace {
+namespace ffs_rt {
 
 std::atomic<unsigned long long> g_launches{0};  // kernels issued by this library
 
@@ -41,96 +43,9 @@ int num_sms() {
     return n;
 }
 
-template <typename T>
-cudaError_t dalloc(T **p, size_t n) {
-    *p = nullptr;
-    if (n == 0) n = 1;
-    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
-}
-
-template <typename T>
-void dfree(T *&p) {
-    if (p) cudaFree(p);
-    p = nullptr;
-}
-
 }  // namespace
 
-struct ffs_instance {
-    int N = 0, g = 0, M = 0, Qmax = 0, WT = 0, RS = 0;
-    std::vector<int32_t> o, moff, p, q, R, D;   // problem
-    std::vector<int32_t> status, S0, M0;       // plan and classification, [N*g]
-    bool has_plan = false;
-    bool dev_dirty = true;  // host tables or plan changed since the last upload
-    int K = 0, Hfull = 0;
-    std::vector<int32_t> gjob, gstg;
-    TabHeader hdr{};
-    std::vector<char> blob;
-    int version = 0;
-    // device mirrors
-    char *d_blob = nullptr;
-    size_t d_blob_cap = 0;
-    int32_t *d_S0 = nullptr, *d_M0 = nullptr, *d_status = nullptr;
-    size_t d_plan_cap = 0;
-    uint16_t *d_scratch = nullptr;  // global power profiles for the fallback decode
-    size_t d_scratch_cap = 0;
-    int32_t *d_over = nullptr;
-    size_t d_over_cap = 0;
-    int32_t *d_over_count = nullptr, *d_err = nullptr;
-
-    ~ffs_instance() {
-        dfree(d_blob);
-        dfree(d_S0);
-        dfree(d_M0);
-        dfree(d_status);
-        dfree(d_scratch);
-        dfree(d_over);
-        dfree(d_over_count);
-        dfree(d_err);
-    }
-};
-
-struct ga_population {
-    ffs_instance *inst = nullptr;
-    int version = 0;
-    ga_params par{};
-    cudaStream_t st = nullptr;
-    int P = 0, I = 0, K = 0, nisl = 0, side = 0;
-    int Hcap = 0, grid_gen = 0, grid_fb = 0;
-    TabHeader hdr{};
-    char *d_blob = nullptr;  // private copy of the instance tables at creation
-    int16_t *Y[2] = {nullptr, nullptr};
-    int8_t *X[2] = {nullptr, nullptr};
-    int64_t *obj[2] = {nullptr, nullptr}, *fit[2] = {nullptr, nullptr};
-    int16_t *bY = nullptr, *mY = nullptr;
-    int8_t *bX = nullptr, *mX = nullptr;
-    int64_t *bobj = nullptr, *bfit = nullptr, *mobj = nullptr, *mfit = nullptr;
-    int32_t *mw = nullptr, *over = nullptr, *err = nullptr, *isl_done = nullptr;
-    GADev *dev = nullptr;
-    uint16_t *scratch = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    bool profiling = false;                 // eager launches with timed generation kernels
-    std::vector<cudaEvent_t> ev;            // event pairs, reused across ga_run calls
-    double prof_ms = 0.0;
-    int64_t prof_launches = 0;
-
-    ~ga_population() {
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        if (graph) cudaGraphExecDestroy(graph);
-        dfree(d_blob);
-        for (int b = 0; b < 2; ++b) {
-            dfree(Y[b]);
-            dfree(X[b]);
-            dfree(obj[b]);
-            dfree(fit[b]);
-        }
-        dfree(bY); dfree(bX); dfree(bobj); dfree(bfit);
-        dfree(mY); dfree(mX); dfree(mobj); dfree(mfit); dfree(mw);
-        dfree(over); dfree(err); dfree(dev); dfree(scratch); dfree(isl_done);
-    }
-};
-
-namespace {
+namespace ffs_rt {
 
 thread_local char g_last_error[256] = "";
 
@@ -140,12 +55,6 @@ int cuda_rc(cudaError_t e) {
     return FFS_E_CUDA;
 }
 
-#define FFS_TRY(expr)                 \
-    do {                              \
-        const int rc_ = (expr);       \
-        if (rc_ != FFS_OK) return rc_; \
-    } while (0)
-#define FFS_CUDA(expr) FFS_TRY(cuda_rc(expr))
 
 // Rebuilds the gene map, the profile bound and the table blob, and uploads them.
 int rebuild(ffs_instance *in) {
@@ -557,7 +466,9 @@ static int ga_replace_args(ga_population *pp, ReplArgs *r, int init) {
     return FFS_OK;
 }
 
-static void ga_gen_args(ga_population *pp, GenArgs *a) {
+}  // extern "C"
+
+void ffs_rt::ga_gen_args(ga_population *pp, GenArgs *a) {
     *a = GenArgs{};
     a->blob = pp->d_blob;
     a->blob_bytes = pp->hdr.bytes;
@@ -588,6 +499,8 @@ static void ga_gen_args(ga_population *pp, GenArgs *a) {
     a->over_list = pp->over;
     a->err = pp->err;
 }
+
+extern "C" {
 
 static void ga_fallback_args(ga_population *pp, DecodeArgs *d, bool ga_mode) {
     *d = DecodeArgs{};
@@ -752,9 +665,25 @@ int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
     if (!pp || generations < 0) return FFS_E_ARG;
     ffs_instance *in = pp->inst;
     if (pp->version != in->version) return FFS_E_STATE;
+    const unsigned long long per_gen = pp->sur ? kSurrogateLaunches : 1;
+    if (pp->sur && !pp->graph_sur && !pp->profiling) {  // capture the surrogate generation once
+        FFS_TRY(prepare_surrogate_kernels(pp));
+        cudaStream_t cap = nullptr;
+        FFS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        int rc = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        if (rc == FFS_OK) rc = surrogate_enqueue_generation(pp, cap, nullptr, nullptr);
+        const int ce = cuda_rc(cudaStreamEndCapture(cap, &g));
+        cudaStreamDestroy(cap);
+        if (rc == FFS_OK) rc = ce;
+        if (rc == FFS_OK) rc = cuda_rc(cudaGraphInstantiate(&pp->graph_sur, g, 0));
+        if (g) cudaGraphDestroy(g);
+        if (rc != FFS_OK) return rc;
+    }
     if (!pp->profiling) {
-        for (int i = 0; i < generations; ++i) FFS_CUDA(cudaGraphLaunch(pp->graph, pp->st));
-        g_launches += (unsigned long long)generations;
+        cudaGraphExec_t gx = pp->sur ? pp->graph_sur : pp->graph;
+        for (int i = 0; i < generations; ++i) FFS_CUDA(cudaGraphLaunch(gx, pp->st));
+        g_launches += per_gen * (unsigned long long)generations;
         FFS_CUDA(cudaStreamSynchronize(pp->st));
     } else {
         while ((int)pp->ev.size() < 2 * generations) {
@@ -762,8 +691,11 @@ int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
             FFS_CUDA(cudaEventCreate(&e));
             pp->ev.push_back(e);
         }
-        for (int i = 0; i < generations; ++i) FFS_TRY(ga_enqueue_generation(pp, pp->ev[2 * i], pp->ev[2 * i + 1]));
-        g_launches += (unsigned long long)generations;
+        for (int i = 0; i < generations; ++i) {
+            if (pp->sur) FFS_TRY(surrogate_enqueue_generation(pp, pp->st, pp->ev[2 * i], pp->ev[2 * i + 1]));
+            else FFS_TRY(ga_enqueue_generation(pp, pp->ev[2 * i], pp->ev[2 * i + 1]));
+        }
+        g_launches += per_gen * (unsigned long long)generations;
         FFS_CUDA(cudaStreamSynchronize(pp->st));
         for (int i = 0; i < generations; ++i) {
             float ms = 0.f;

@@ -90,6 +90,15 @@ _SIGS = {
     "ga_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
     "ga_restore": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "ffs_kernel_launches": (C.c_int, [C.POINTER(C.c_uint64)]),
+    "ffs_surrogate_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "ffs_surrogate_destroy": (C.c_int, [C.c_void_p]),
+    "ffs_surrogate_param_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "ffs_surrogate_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ffs_surrogate_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ffs_surrogate_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
+    "ffs_surrogate_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "ffs_surrogate_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p]),
+    "ga_population_attach_surrogate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_float]),
     "ga_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(GAParams_c), C.POINTER(C.c_void_p)]),
     "ga_batch_destroy": (C.c_int, [C.c_void_p]),
     "ga_batch_run": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
@@ -310,6 +319,12 @@ class Population:
         d["gen"] = int(gen.value)
         return d
 
+    def attach_surrogate(self, sur, oversample: int = 8, lr: float = 1e-3):
+        """Surrogate-assisted generations from now on (None detaches)."""
+        _check(lib().ga_population_attach_surrogate(self._h, sur._h if sur is not None else None, int(oversample),
+                                                    float(lr)), "ga_population_attach_surrogate")
+        self._sur = sur
+
     def set_profiling(self, enable: bool):
         _check(lib().ga_set_profiling(self._h, 1 if enable else 0), "ga_set_profiling")
 
@@ -404,3 +419,77 @@ class Batch:
     def set_config(self, warps: int, smem_bytes: int, cluster: int = 0):
         c = BatchConfig_c(warps, smem_bytes, 0, cluster, 0.0)
         _check(lib().ga_batch_set_config(self._h, C.byref(c)), "ga_batch_set_config")
+
+
+class Surrogate:
+    """The learned fitness surrogate of one instance (``ffs_surrogate``)."""
+
+    H = 256
+
+    def __init__(self, inst: Instance, max_batch: int, seed: int = 0, stream=None):
+        h = C.c_void_p()
+        _check(lib().ffs_surrogate_create(inst.handle, int(max_batch), int(seed), _stream_ptr(stream), C.byref(h)),
+               "ffs_surrogate_create")
+        self._h = h
+        self.K = inst.K
+        n = C.c_int64()
+        _check(lib().ffs_surrogate_param_count(self._h, C.byref(n)), "ffs_surrogate_param_count")
+        self.n_params = int(n.value)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().ffs_surrogate_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self):
+        """Name -> (offset, shape) of the blocks of the parameter vector."""
+        H, K = self.H, self.K
+        out, off = {}, 0
+        for name, shape in (("W1", (H, 3 * K)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("w3", (H,)),
+                            ("b3", (1,))):
+            out[name] = (off, shape)
+            off += int(np.prod(shape))
+        return out
+
+    def unpack(self, vec):
+        return {k: np.asarray(vec[o:o + int(np.prod(s))]).reshape(s) for k, (o, s) in self.layout().items()}
+
+    def pack(self, params):
+        vec = np.zeros(self.n_params, np.float32)
+        for k, (o, s) in self.layout().items():
+            vec[o:o + int(np.prod(s))] = np.asarray(params[k], np.float32).ravel()
+        return vec
+
+    def get_params(self):
+        v = np.zeros(self.n_params, np.float32)
+        _check(lib().ffs_surrogate_get_params(self._h, v.ctypes.data), "ffs_surrogate_get_params")
+        return v
+
+    def set_params(self, vec):
+        v = np.ascontiguousarray(vec, np.float32)
+        _check(lib().ffs_surrogate_set_params(self._h, v.ctypes.data), "ffs_surrogate_set_params")
+
+    def predict(self, y):
+        import torch
+        out = torch.empty(int(y.shape[0]), dtype=torch.float32, device=y.device)
+        _check(lib().ffs_surrogate_predict(self._h, _dptr(y), int(y.shape[0]), _dptr(out)), "ffs_surrogate_predict")
+        return out
+
+    def gradients(self, y, obj):
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_float()
+        _check(lib().ffs_surrogate_gradients(self._h, _dptr(y), _dptr(obj), int(y.shape[0]), g.ctypes.data,
+                                             C.addressof(loss)), "ffs_surrogate_gradients")
+        return g, float(loss.value)
+
+    def train(self, y, obj, lr: float = 1e-3) -> float:
+        loss = C.c_float()
+        _check(lib().ffs_surrogate_train(self._h, _dptr(y), _dptr(obj), int(y.shape[0]), float(lr),
+                                         C.addressof(loss)), "ffs_surrogate_train")
+        return float(loss.value)
