@@ -354,6 +354,79 @@ def bench_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- surrogate
+SUR_WORKLOAD = ("surrogate-assisted GA: 200 jobs, 8 stages, machines U{2..6}, p U{1..99}, q U{5..50} kW, peak 50%; "
+                "population 4096 (islands of 64); the plain GA runs G generations, the surrogate GA over-generates 8 "
+                "candidates per slot, scores them with the BF16 MLP (256-256-1), decodes the best of each 8 exactly and "
+                "trains online; time until its best total tardiness is within 0.5% of the plain GA's final value")
+
+
+def bench_surrogate(args):
+    import torch
+
+    from paper_1903_10741_gb300 import ffs
+
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    stream = torch.cuda.current_stream()
+    prob = wl.surrogate_large(1)
+    G, P, chunk = args.generations, 4096, args.chunk
+    kw = dict(P=P, island=64, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE, seed=SEED, stream=stream)
+
+    def plain_run():
+        inst = ffs.Instance(prob)
+        pop = ffs.Population(inst, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        curve = []
+        for g in range(0, G, chunk):
+            r = pop.run(min(chunk, G - g), want_schedule=False)
+            curve.append((g + min(chunk, G - g), time.perf_counter() - t0, r["tard"], r["obj"]))
+        return curve
+
+    def surrogate_run(target_tard, cap):
+        inst = ffs.Instance(prob)
+        pop = ffs.Population(inst, **kw)
+        sur = ffs.Surrogate(inst, max_batch=P, seed=SEED)
+        pop.attach_surrogate(sur, oversample=8, lr=args.lr, train_steps=args.train_steps,
+                             pretrain_steps=args.pretrain_steps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        curve, reached = [], None
+        for g in range(0, cap, chunk):
+            r = pop.run(min(chunk, cap - g), want_schedule=False)
+            el = time.perf_counter() - t0
+            curve.append((g + min(chunk, cap - g), el, r["tard"], r["obj"]))
+            if reached is None and r["tard"] <= target_tard * 1.005:
+                reached = (g + min(chunk, cap - g), el)
+                break
+        return curve, reached
+
+    for _ in range(args.warmup):  # compile paths, caches
+        inst = ffs.Instance(prob)
+        ffs.Population(inst, **kw).run(2, want_schedule=False)
+    plain = plain_run()
+    target = plain[-1][2]
+    sur_curve, reached = surrogate_run(target, args.surrogate_cap or 2 * G)
+    # the plain GA's own time to the same target (first chunk at or below it)
+    plain_to_target = next((c for c in plain if c[2] <= target * 1.005), plain[-1])
+    line = {
+        "metric": "time-to-objective, surrogate vs plain GA", "unit": "s", "higher_is_better": False,
+        "value": reached[1] if reached else None, "n_gpus": 1, "dtype": "int32 decode / bf16 surrogate",
+        "data": "synthetic",
+        "config": {"workload": SUR_WORKLOAD, "generations_plain": G, "chunk": chunk, "lr": args.lr,
+                   "train_steps_per_generation": args.train_steps, "pretrain_steps": args.pretrain_steps,
+                   "target_total_tardiness": target, "plain_final_objective": plain[-1][3],
+                   "plain_time_s": plain[-1][1], "plain_time_to_target_s": plain_to_target[1],
+                   "plain_generations_to_target": plain_to_target[0],
+                   "surrogate_generations_to_target": reached[0] if reached else None,
+                   "speedup_vs_plain_full_run": (plain[-1][1] / reached[1]) if reached else None,
+                   "plain_decodes_per_s": P * G / plain[-1][1],
+                   "plain_curve": plain[:: max(1, len(plain) // 12)],
+                   "surrogate_curve": sur_curve[:: max(1, len(sur_curve) // 12)]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # Oracle-measured slot checks per decode of the batched workload (python -m
 # oracle.work_per_decode --workload batched); None until measured.
 BATCH_SLOTS_PER_DECODE = None
@@ -422,8 +495,14 @@ def main():
     ap.add_argument("--ref-generations", type=int, default=2, help="oracle generations per reference step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["dynamic", "batched"], default="dynamic",
-                    help="dynamic: the headline rescheduling job; batched: 256 uneven instances")
+    ap.add_argument("--workload", choices=["dynamic", "batched", "surrogate"], default="dynamic",
+                    help="dynamic: the headline rescheduling job; batched: 256 uneven instances; "
+                         "surrogate: time-to-objective of the surrogate-assisted GA")
+    ap.add_argument("--chunk", type=int, default=20, help="generations between progress checks (surrogate)")
+    ap.add_argument("--lr", type=float, default=1e-3, help="surrogate learning rate")
+    ap.add_argument("--surrogate-cap", type=int, default=0, help="generation cap of the surrogate run")
+    ap.add_argument("--train-steps", type=int, default=2, help="surrogate Adam steps per generation")
+    ap.add_argument("--pretrain-steps", type=int, default=50, help="surrogate Adam steps on generation 0")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--tune-generations", type=int, default=3)
     ap.add_argument("--eager", action="store_true",
@@ -436,6 +515,10 @@ def main():
         if args.generations == 500:
             args.generations = 300
         bench_batched(args)
+    elif args.workload == "surrogate":
+        if args.generations == 500:
+            args.generations = 1000
+        bench_surrogate(args)
     else:
         bench_ours(args)
 

@@ -218,7 +218,8 @@ int ga_batch_set_config(ga_batch *batch, const ga_batch_config *config);
 
 /* A learned fitness surrogate for one instance at its current rescheduling point.  Not in
  * the paper: it lets the GA screen over-generated offspring before the exact decoder
- * (Sec. 4.3) evaluates the kept ones.  Model: with yh = y / K and per-gene features
+ * (Sec. 4.3) evaluates the kept ones.  Model: with yh_k = 1 - r_k / n_s (r_k the rank of
+ * gene k by y among the n_s genes of its stage, 0 for the highest) and per-gene features
  * ph = p_js / max p and dh = D_j / max |D|, the input is x = [yh_k, yh_k ph_k, yh_k dh_k]
  * (3K values); h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2) with 256 units each, and
  * out = w3 . h2 + b3 predicts the objective normalised over a batch (lower is better).
@@ -248,10 +249,17 @@ int ffs_surrogate_train(ffs_surrogate *sur, const int16_t *y, const int64_t *obj
                         float *loss);
 /* Surrogate-assisted generations for a population of the same instance: each generation
  * builds `oversample` candidates per slot with the Sec. 4.4 operators, scores them all,
- * decodes exactly only the best-scored candidate of each slot (ties to the lower
- * candidate), then trains the surrogate one Adam step on those exact objectives.
- * P and P * oversample must be multiples of 128 and max_batch >= P.  NULL detaches. */
-int ga_population_attach_surrogate(ga_population *pop, ffs_surrogate *sur, int32_t oversample, float lr);
+ * decodes exactly only the best-scored offspring of each slot (ties to the lower
+ * candidate; a parent's plain copy only when the slot has no offspring), then trains the
+ * surrogate `train_steps` Adam steps on those exact objectives.  P and P * oversample
+ * must be multiples of 128 and max_batch >= P.  NULL detaches. */
+int ga_population_attach_surrogate(ga_population *pop, ffs_surrogate *sur, int32_t oversample, float lr,
+                                   int32_t train_steps);
+
+/* `steps` Adam steps on the population's current members and their exact objectives (for
+ * example generation 0, before surrogate-assisted generations begin); host *loss after
+ * the last step's forward pass if not NULL. */
+int ffs_surrogate_pretrain(ffs_surrogate *sur, ga_population *pop, int32_t steps, float lr, float *loss);
 
 /* Allocation-free variant of ffs_decode, for callers that cannot allocate device memory:
  * code that runs while a CUDA stream is being captured (cudaMalloc is not permitted

@@ -5,9 +5,11 @@ paper: it is a 3-layer perceptron that scores a priority chromosome from per-gen
 features so that a GA can screen over-generated offspring before the exact decoder
 (Sec. 4.3) evaluates the kept ones.
 
-Model.  A chromosome's priorities y (a permutation of 1..K) become yh = y / K.  Gene k
-carries two instance features, ph_k = p_k / max p and dh_k = D_j / max D of its job j.
-The input has 3K features, x = [yh_k, yh_k ph_k, yh_k dh_k]_k, and
+Model.  A chromosome's priorities y (a permutation of 1..K) become, per gene, its rank
+among the genes of its stage: yh_k = 1 - r_k / n_s, where r_k = 0 for the stage's highest
+priority and n_s is the stage's gene count (the stage-by-stage decoder reads exactly this
+order).  Gene k carries two instance features, ph_k = p_k / max p and dh_k = D_j / max D
+of its job j.  The input has 3K features, x = [yh_k, yh_k ph_k, yh_k dh_k]_k, and
     h1 = relu(W1 x + b1)   (H units),   h2 = relu(W2 h1 + b2)   (H units),
     out = w3 . h2 + b3     (a predicted normalised objective; lower is better).
 Training minimises the mean squared error to t = (obj - mean) / std over the batch with
@@ -30,10 +32,26 @@ def gene_features(p, D, gene_job, gene_stage):
     return pk / max(pk.max(), 1.0), dk / max(abs(dk).max(), 1.0)
 
 
-def features(Y, ph, dh):
+def stage_rank(Y, gene_stage):
+    """yh [B, K]: 1 - (rank of gene k among its stage's genes by y descending) / n_s."""
+    B, K = Y.shape
+    gs = np.asarray(gene_stage)
+    yh = np.empty((B, K))
+    for s in np.unique(gs):
+        idx = np.nonzero(gs == s)[0]
+        n = len(idx)
+        order = np.argsort(-Y[:, idx], axis=1, kind="stable")  # y unique: no ties
+        ranks = np.empty_like(order)
+        rows = np.arange(B)[:, None]
+        ranks[rows, order] = np.arange(n)[None, :]
+        yh[:, idx] = 1.0 - ranks / n
+    return yh
+
+
+def features(Y, ph, dh, gene_stage):
     """Explicit 3K-wide inputs for chromosomes Y [B, K]."""
     B, K = Y.shape
-    yh = Y.astype(np.float64) / K
+    yh = stage_rank(Y, gene_stage)
     X = np.empty((B, 3 * K))
     X[:, 0::3] = yh
     X[:, 1::3] = yh * ph[None, :]
@@ -65,9 +83,8 @@ def factored_V(params, ph, dh):
     return W1[:, 0::3] + ph[None, :] * W1[:, 1::3] + dh[None, :] * W1[:, 2::3]
 
 
-def forward_factored(params, Y, ph, dh):
-    K = Y.shape[1]
-    yh = Y.astype(np.float64) / K
+def forward_factored(params, Y, ph, dh, gene_stage):
+    yh = stage_rank(Y, gene_stage)
     z1 = yh @ factored_V(params, ph, dh).T + params["b1"]
     h1 = np.maximum(z1, 0.0)
     h2 = np.maximum(h1 @ params["W2"].T + params["b2"], 0.0)

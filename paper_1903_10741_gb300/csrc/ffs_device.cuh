@@ -1,7 +1,9 @@
 // ffs_device.cuh -- device building blocks: Philox4x32-10, bounded bulk-copy staging of the
 // instance tables into shared memory, and the warp-cooperative EDFFS decoder.
 #pragma once
+#include <cuda_bf16.h>
 #include <stdint.h>
+
 #include <climits>
 
 #include "ffs_layout.h"
@@ -354,6 +356,39 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
         cmax = max(cmax, __shfl_xor_sync(kFull, cmax, off));
     }
     return {tard, cmax, 0};
+}
+
+// Surrogate input of one chromosome: f_k = 1 - r_k / n_s, where r_k is gene k's rank (0 =
+// highest y) among the n_s genes of its stage.  BF16 bits go to row[0 .. Kpad), zero
+// padded; `inv` is K entries of warp scratch.  Values of y outside 1..K are ignored (their
+// genes keep 0), so a malformed row cannot index out of bounds.
+__device__ __forceinline__ void stage_rank_row(const int16_t *y, int K, int Kpad, const int8_t *gstg,
+                                               const int32_t *soff, int g, int16_t *inv, uint16_t *row, int lane) {
+    for (int i = lane; i < K; i += 32) inv[i] = -1;
+    for (int k = lane; k < Kpad; k += 32) row[k] = 0;
+    __syncwarp();
+    for (int k = lane; k < K; k += 32) {
+        const int v = y[k];
+        if (v >= 1 && v <= K) inv[K - v] = (int16_t)k;
+    }
+    __syncwarp();
+    for (int s = 0; s < g; ++s) {
+        const int n = soff[s + 1] - soff[s];
+        if (n <= 0) continue;
+        int pos = 0;
+        for (int base = 0; base < K; base += 32) {
+            const int i = base + lane;
+            const int k = i < K ? inv[i] : -1;
+            const bool sel = k >= 0 && gstg[k] == s;
+            const unsigned mask = __ballot_sync(kFull, sel);
+            if (sel) {
+                const int r = pos + __popc(mask & ((1u << lane) - 1u));
+                row[k] = __bfloat16_as_ushort(__float2bfloat16_rn(1.f - (float)r / (float)n));
+            }
+            pos += __popc(mask);
+        }
+    }
+    __syncwarp();
 }
 
 }  // namespace edffs

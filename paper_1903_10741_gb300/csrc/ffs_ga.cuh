@@ -66,8 +66,10 @@ struct GASrc {
 // are selected from the counter-based stream, so the two children of a pair can be built
 // by different warps.  With s.F > 1, child i is one of F candidates for population slot
 // i / F and draws its parents from that slot's island (or neighbourhood).
+// Returns true if the child differs from a plain copy of a parent (crossover or mutation
+// was applied).
 template <int MACH>
-__device__ __forceinline__ void make_child(const Tabs &T, const WarpPtrs &w, const GASrc &s, int i, uint32_t gen,
+__device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, const GASrc &s, int i, uint32_t gen,
                                            int lane) {
     const int K = s.K, I = s.I;
     const int pp = i >> 1;
@@ -189,6 +191,7 @@ __device__ __forceinline__ void make_child(const Tabs &T, const WarpPtrs &w, con
         }
     }
     __syncwarp();
+    return cross || (uint64_t)rm.x < s.pm_thr;
 }
 
 // Generation 0 of individual i (Sec. 4.3): Y a Fisher-Yates permutation of 1..K, X uniform

@@ -106,7 +106,9 @@ struct ga_population {
     int8_t *cand_X = nullptr;
     uint16_t *cand_Yh = nullptr, *cand_H1 = nullptr, *cand_H2 = nullptr;
     float *cand_out = nullptr;
+    uint8_t *cand_new = nullptr;
     int64_t *kept_obj = nullptr;
+    int train_steps = 1;
     cudaGraphExec_t graph_sur = nullptr;
     bool profiling = false;                 // eager launches with timed generation kernels
     std::vector<cudaEvent_t> ev;            // event pairs, reused across ga_run calls
@@ -123,6 +125,7 @@ struct ga_population {
         dfree(cand_H1);
         dfree(cand_H2);
         dfree(cand_out);
+        dfree(cand_new);
         dfree(kept_obj);
         dfree(d_blob);
         for (int b = 0; b < 2; ++b) {
@@ -147,7 +150,7 @@ int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y,
 void ga_gen_args(ga_population *pp, edffs::GenArgs *a);
 // One surrogate-assisted generation on `st` (ffs_surrogate.cu); with events, the fused
 // generation kernel is bracketed by ev0/ev1.  Kernels launched per generation:
-constexpr int kSurrogateLaunches = 27;
+constexpr int kSurrogateFixedLaunches = 12, kSurrogateStepLaunches = 18;
 int surrogate_enqueue_generation(ga_population *pp, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
 // Raises the shared-memory limits of the kernels a surrogate generation launches, so that
 // the generation can be captured.

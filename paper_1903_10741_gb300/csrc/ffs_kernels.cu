@@ -170,11 +170,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
         if (!a.cand_Y) {
             make_child<MACH>(T, w, src, i, gen, lane);
         } else {
-            // surrogate-assisted: keep the candidate with the lowest score (ties to the lower
-            // index; an undefined score counts as worst)
+            // surrogate-assisted: keep the offspring with the lowest score (ties to the lower
+            // index; an undefined score counts as worst); a parent's plain copy is kept only
+            // when no candidate of the slot is an offspring
+            const bool any_new = __any_sync(kFull, lane < a.F && a.cand_new[(size_t)i * a.F + lane]);
             float sc = INFINITY;
             int vi = INT_MAX;
-            if (lane < a.F) {
+            if (lane < a.F && (!any_new || a.cand_new[(size_t)i * a.F + lane])) {
                 sc = a.cand_out[(size_t)i * a.F + lane];
                 if (isnan(sc)) sc = INFINITY;
                 vi = lane;
@@ -224,8 +226,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
 
 // ---------------------------------------------------------------- surrogate candidates
 // Over-generation for the surrogate: candidate c is one of F children built for population
-// slot c / F with the usual operators and its own stream position; its model input, the
-// BF16 of y / K zero padded to Kpad, is written beside it.  Nothing is decoded here.
+// slot c / F with the usual operators and its own stream position; its model input (the
+// within-stage rank features, BF16, zero padded to Kpad) is written beside it.  Nothing is
+// decoded here.
 template <int MACH>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_candidates(GenArgs a) {
     extern __shared__ __align__(128) char smem[];
@@ -239,17 +242,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_candidates(GenArgs a) {
     const GASrc src{a.Y[cur], a.X[cur], a.fit[cur], a.P, a.I, K, a.tour_k, a.side, a.pc_thr, a.pm_thr, a.seed,
                     a.instance_id, a.F};
     for (int c = blockIdx.x * kWarpsPerBlock + warp; c < a.P * a.F; c += gridDim.x * kWarpsPerBlock) {
-        make_child<MACH>(T, w, src, c, gen, lane);
+        const bool fresh = make_child<MACH>(T, w, src, c, gen, lane);
+        if (lane == 0) a.cand_new[c] = fresh ? 1 : 0;
         int16_t *yo = a.cand_Y + (size_t)c * K;
         for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
         if (MACH == kMachGene) {
             int8_t *xo = a.cand_X + (size_t)c * K;
             for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
         }
-        uint16_t *yh = a.cand_Yh + (size_t)c * a.Kpad;
-        for (int k = lane; k < a.Kpad; k += 32)
-            yh[k] = k < K ? __bfloat16_as_ushort(__float2bfloat16_rn((float)w.y[k] / (float)K)) : (uint16_t)0;
-        __syncwarp();
+        stage_rank_row(w.y, K, a.Kpad, T.gstg, T.soff, T.g, w.inv, a.cand_Yh + (size_t)c * a.Kpad, lane);
     }
 }
 

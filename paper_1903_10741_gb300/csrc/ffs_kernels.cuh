@@ -66,8 +66,9 @@ struct GenArgs {
     int Kpad;                   // row length of the BF16 model inputs
     int16_t *cand_Y;            // [P*F][K] candidates
     int8_t *cand_X;
-    uint16_t *cand_Yh;          // [P*F][Kpad] BF16 bits of y / K (zero padded)
+    uint16_t *cand_Yh;          // [P*F][Kpad] BF16 within-stage rank features (zero padded)
     const float *cand_out;      // [P*F] surrogate scores, lower is better
+    uint8_t *cand_new;          // [P*F] 1 if the candidate is an offspring, 0 if a parent's copy
     uint16_t *kept_Yh;          // [P][Kpad] inputs of the kept candidates, for training
     int64_t *kept_obj;          // [P] their exact objectives (before replacement)
 };

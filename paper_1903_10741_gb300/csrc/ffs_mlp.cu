@@ -13,6 +13,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
+#include "ffs_device.cuh"
 #include "ffs_mlp.cuh"
 
 namespace edffs {
@@ -148,14 +151,21 @@ __global__ void k_make_v(const float *__restrict__ W1, const float *__restrict__
     V[i] = __float2bfloat16_rn(v);
 }
 
-// Yh[r, k] = y[r, k] / K as BF16 (0 in padding rows and columns).
-__global__ void k_yhat(const int16_t *__restrict__ y, int rows, int rows_pad, int K, int Kpad, __nv_bfloat16 *Yh) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (size_t)rows_pad * Kpad) return;
-    const int r = (int)(i / Kpad), k = (int)(i % Kpad);
-    float v = 0.f;
-    if (r < rows && k < K) v = (float)y[(size_t)r * K + k] / (float)K;
-    Yh[i] = __float2bfloat16_rn(v);
+// Model inputs of `rows` chromosomes (within-stage rank features), one warp per row, zero
+// rows up to rows_pad; each warp uses K int16 of dynamic shared memory.
+__global__ void k_stage_features(const int16_t *__restrict__ y, int rows, int rows_pad, int K, int Kpad,
+                                 const int8_t *__restrict__ gstg, const int32_t *__restrict__ soff, int g,
+                                 __nv_bfloat16 *Yh) {
+    extern __shared__ int16_t s_inv[];
+    const int wpb = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * wpb + warp;
+    if (r >= rows_pad) return;
+    uint16_t *row = reinterpret_cast<uint16_t *>(Yh) + (size_t)r * Kpad;
+    if (r >= rows) {
+        for (int k = lane; k < Kpad; k += 32) row[k] = 0;
+        return;
+    }
+    stage_rank_row(y + (size_t)r * K, K, Kpad, gstg, soff, g, s_inv + (size_t)warp * K, row, lane);
 }
 
 // Tiled transpose of a BF16 [R x C] matrix (R, C multiples of 32) into [C x R].
@@ -301,8 +311,15 @@ cudaError_t mlp_make_v(const float *W1, const float *ph, const float *dh, int H,
     return cudaGetLastError();
 }
 
-cudaError_t mlp_yhat(const int16_t *y, int rows, int rows_pad, int K, int Kpad, __nv_bfloat16 *Yh, cudaStream_t st) {
-    k_yhat<<<blocks((size_t)rows_pad * Kpad, 256), 256, 0, st>>>(y, rows, rows_pad, K, Kpad, Yh);
+cudaError_t mlp_stage_features(const int16_t *y, int rows, int rows_pad, int K, int Kpad, const int8_t *gstg,
+                               const int32_t *soff, int g, __nv_bfloat16 *Yh, cudaStream_t st) {
+    const int wpb = std::max(1, std::min(8, (40 * 1024) / (2 * K)));
+    const int smem = wpb * 2 * K;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_stage_features, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_stage_features<<<blocks(rows_pad, wpb), wpb * 32, smem, st>>>(y, rows, rows_pad, K, Kpad, gstg, soff, g, Yh);
     return cudaGetLastError();
 }
 

@@ -17,7 +17,9 @@ cudaError_t mlp_rowdot(const __nv_bfloat16 *h2, const __nv_bfloat16 *w3, const f
                        cudaStream_t st);
 cudaError_t mlp_make_v(const float *W1, const float *ph, const float *dh, int H, int K, int Kpad, __nv_bfloat16 *V,
                        cudaStream_t st);
-cudaError_t mlp_yhat(const int16_t *y, int rows, int rows_pad, int K, int Kpad, __nv_bfloat16 *Yh, cudaStream_t st);
+// Within-stage rank features of `rows` chromosomes y [rows][K] into Yh [rows_pad][Kpad].
+cudaError_t mlp_stage_features(const int16_t *y, int rows, int rows_pad, int K, int Kpad, const int8_t *gstg,
+                               const int32_t *soff, int g, __nv_bfloat16 *Yh, cudaStream_t st);
 cudaError_t mlp_transpose(const __nv_bfloat16 *in, int R, int C, __nv_bfloat16 *out, cudaStream_t st);
 cudaError_t mlp_to_bf16(const float *in, size_t n, __nv_bfloat16 *out, cudaStream_t st);
 cudaError_t mlp_targets(const int64_t *obj, int rows, float *t, int *step, cudaStream_t st);

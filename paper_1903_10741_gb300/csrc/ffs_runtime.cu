@@ -665,7 +665,8 @@ int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
     if (!pp || generations < 0) return FFS_E_ARG;
     ffs_instance *in = pp->inst;
     if (pp->version != in->version) return FFS_E_STATE;
-    const unsigned long long per_gen = pp->sur ? kSurrogateLaunches : 1;
+    const unsigned long long per_gen =
+        pp->sur ? (unsigned long long)(kSurrogateFixedLaunches + kSurrogateStepLaunches * pp->train_steps) : 1;
     if (pp->sur && !pp->graph_sur && !pp->profiling) {  // capture the surrogate generation once
         FFS_TRY(prepare_surrogate_kernels(pp));
         cudaStream_t cap = nullptr;

@@ -1,6 +1,8 @@
 // ffs_surrogate.cu -- the learned fitness surrogate and surrogate-assisted GA generations.
 //
-// A surrogate belongs to one instance at its current rescheduling point.  Its parameters
+// A surrogate belongs to one instance at its current rescheduling point.  Its input is, per
+// gene, the gene's rank among its stage's genes (the order the stage-by-stage decoder
+// follows), scaled to (0, 1], times (1, p / max p, D / max D).  Its parameters
 // (W1 [H x 3K], b1 [H], W2 [H x H], b2 [H], w3 [H], b3, FP32 masters with BF16 copies for
 // the tensor cores) are trained online by Adam on the exact objectives of the children the
 // GA keeps.  With a surrogate attached, a generation over-generates F candidates per slot,
@@ -32,13 +34,16 @@ struct ffs_surrogate {
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
     int *step = nullptr;
     float *ph = nullptr, *dh = nullptr;
+    int8_t *gstg = nullptr;   // stage of every gene
+    int32_t *soff = nullptr;  // [g+1] first gene of every stage in stage order
+    int g = 0;
     __nv_bfloat16 *V = nullptr, *W2b = nullptr, *W2Tb = nullptr, *w3b = nullptr;
     __nv_bfloat16 *Yh = nullptr, *YhT = nullptr, *H1 = nullptr, *H2 = nullptr, *dz2b = nullptr, *dz2T = nullptr,
                   *H1T = nullptr, *dz1b = nullptr, *dz1T = nullptr;
     float *out = nullptr, *t = nullptr, *dout = nullptr, *dz2 = nullptr, *dh1 = nullptr, *dz1 = nullptr, *G = nullptr;
 
     ~ffs_surrogate() {
-        dfree(params); dfree(grads); dfree(m); dfree(v); dfree(step); dfree(ph); dfree(dh);
+        dfree(params); dfree(grads); dfree(m); dfree(v); dfree(step); dfree(ph); dfree(dh); dfree(gstg); dfree(soff);
         dfree(V); dfree(W2b); dfree(W2Tb); dfree(w3b);
         dfree(Yh); dfree(YhT); dfree(H1); dfree(H2); dfree(dz2b); dfree(dz2T); dfree(H1T); dfree(dz1b); dfree(dz1T);
         dfree(out); dfree(t); dfree(dout); dfree(dz2); dfree(dh1); dfree(dz1); dfree(G);
@@ -145,6 +150,7 @@ int ffs_surrogate_create(ffs_instance *in, int32_t max_batch, uint64_t seed, voi
     bool ok = dalloc(&s->params, NP) == cudaSuccess && dalloc(&s->grads, NP) == cudaSuccess &&
               dalloc(&s->m, NP) == cudaSuccess && dalloc(&s->v, NP) == cudaSuccess && dalloc(&s->step, 1) == cudaSuccess &&
               dalloc(&s->ph, (size_t)K) == cudaSuccess && dalloc(&s->dh, (size_t)K) == cudaSuccess &&
+              dalloc(&s->gstg, (size_t)K) == cudaSuccess && dalloc(&s->soff, (size_t)in->g + 1) == cudaSuccess &&
               dalloc(&s->V, (size_t)H * Kp) == cudaSuccess && dalloc(&s->W2b, (size_t)H * H) == cudaSuccess &&
               dalloc(&s->W2Tb, (size_t)H * H) == cudaSuccess && dalloc(&s->w3b, (size_t)H) == cudaSuccess &&
               dalloc(&s->Yh, R * Kp) == cudaSuccess && dalloc(&s->YhT, Kp * R) == cudaSuccess &&
@@ -178,7 +184,17 @@ int ffs_surrogate_create(ffs_instance *in, int32_t max_batch, uint64_t seed, voi
     for (size_t i = 0; i < (size_t)H * 3 * K; ++i) p0[s->off_W1 + i] = uni(std::sqrt(6.0 / (3.0 * K)));
     for (size_t i = 0; i < (size_t)H * H; ++i) p0[s->off_W2 + i] = uni(std::sqrt(6.0 / H));
     for (int i = 0; i < H; ++i) p0[s->off_w3 + i] = uni(1.0 / std::sqrt((double)H));
+    s->g = in->g;
+    std::vector<int8_t> gs(K);
+    std::vector<int32_t> so(in->g + 1, 0);
+    for (int k = 0; k < K; ++k) {
+        gs[k] = (int8_t)in->gstg[k];
+        so[in->gstg[k] + 1]++;
+    }
+    for (int q = 0; q < in->g; ++q) so[q + 1] += so[q];
     int rc = cuda_rc(cudaMemcpy(s->ph, phf.data(), 4 * (size_t)K, cudaMemcpyHostToDevice));
+    if (rc == FFS_OK) rc = cuda_rc(cudaMemcpy(s->gstg, gs.data(), (size_t)K, cudaMemcpyHostToDevice));
+    if (rc == FFS_OK) rc = cuda_rc(cudaMemcpy(s->soff, so.data(), 4 * ((size_t)in->g + 1), cudaMemcpyHostToDevice));
     if (rc == FFS_OK) rc = cuda_rc(cudaMemcpy(s->dh, dhf.data(), 4 * (size_t)K, cudaMemcpyHostToDevice));
     if (rc == FFS_OK) rc = ffs_surrogate_set_params(s, p0.data());
     if (rc != FFS_OK) return fail(rc);
@@ -220,7 +236,8 @@ int ffs_surrogate_predict(ffs_surrogate *s, const int16_t *y, int32_t count, flo
     FFS_TRY(sync_weights(s, s->st));
     for (int base = 0; base < count; base += s->rows_cap) {
         const int rows = std::min(s->rows_cap, count - base), rows_pad = round_up(rows, 128);
-        FFS_CUDA(mlp_yhat(y + (size_t)base * s->K, rows, rows_pad, s->K, s->Kpad, s->Yh, s->st));
+        FFS_CUDA(mlp_stage_features(y + (size_t)base * s->K, rows, rows_pad, s->K, s->Kpad, s->gstg, s->soff, s->g,
+                                    s->Yh, s->st));
         FFS_TRY(forward(s, s->Yh, rows_pad, s->H1, s->H2, s->out, s->st));
         FFS_CUDA(cudaMemcpyAsync(out + base, s->out, 4 * (size_t)rows, cudaMemcpyDeviceToDevice, s->st));
     }
@@ -234,7 +251,7 @@ int ffs_surrogate_gradients(ffs_surrogate *s, const int16_t *y, const int64_t *o
     if (!y || !obj) return FFS_E_ARG;
     const int rows_pad = round_up(count, 128);
     FFS_TRY(sync_weights(s, s->st));
-    FFS_CUDA(mlp_yhat(y, count, rows_pad, s->K, s->Kpad, s->Yh, s->st));
+    FFS_CUDA(mlp_stage_features(y, count, rows_pad, s->K, s->Kpad, s->gstg, s->soff, s->g, s->Yh, s->st));
     FFS_TRY(forward(s, s->Yh, rows_pad, s->H1, s->H2, s->out, s->st));
     FFS_TRY(backward(s, obj, count, rows_pad, false, 0.f, s->st));
     if (loss_host) FFS_TRY(host_loss(s, count, loss_host));
@@ -251,7 +268,7 @@ int ffs_surrogate_train(ffs_surrogate *s, const int16_t *y, const int64_t *obj, 
     if (!y || !obj || !(lr > 0.f)) return FFS_E_ARG;
     const int rows_pad = round_up(count, 128);
     FFS_TRY(sync_weights(s, s->st));
-    FFS_CUDA(mlp_yhat(y, count, rows_pad, s->K, s->Kpad, s->Yh, s->st));
+    FFS_CUDA(mlp_stage_features(y, count, rows_pad, s->K, s->Kpad, s->gstg, s->soff, s->g, s->Yh, s->st));
     FFS_TRY(forward(s, s->Yh, rows_pad, s->H1, s->H2, s->out, s->st));
     FFS_TRY(backward(s, obj, count, rows_pad, true, lr, s->st));
     // the targets exist once the backward pass has run; the outputs are the pre-step ones
@@ -259,20 +276,23 @@ int ffs_surrogate_train(ffs_surrogate *s, const int16_t *y, const int64_t *obj, 
     return FFS_OK;
 }
 
-int ga_population_attach_surrogate(ga_population *pp, ffs_surrogate *s, int32_t oversample, float lr) {
+int ga_population_attach_surrogate(ga_population *pp, ffs_surrogate *s, int32_t oversample, float lr,
+                                   int32_t train_steps) {
     if (!pp) return FFS_E_ARG;
     if (!s) {  // detach
         pp->sur = nullptr;
         return FFS_OK;
     }
     if (s->inst != pp->inst || s->version != pp->version || oversample < 1 || oversample > 32 || !(lr > 0.f) ||
+        train_steps < 0 || train_steps > 64 ||
         (pp->P * oversample) % 128 || s->rows_cap < pp->P || pp->P % 128)
         return FFS_E_ARG;
     const size_t C = (size_t)pp->P * oversample;
     if (pp->F != oversample || !pp->cand_Y) {
         dfree(pp->cand_Y); dfree(pp->cand_X); dfree(pp->cand_Yh); dfree(pp->cand_H1); dfree(pp->cand_H2);
         dfree(pp->cand_out);
-        if (dalloc(&pp->cand_Y, C * pp->K) != cudaSuccess || dalloc(&pp->cand_X, C * pp->K) != cudaSuccess ||
+        dfree(pp->cand_new);
+        if (dalloc(&pp->cand_new, C) != cudaSuccess || dalloc(&pp->cand_Y, C * pp->K) != cudaSuccess || dalloc(&pp->cand_X, C * pp->K) != cudaSuccess ||
             dalloc(&pp->cand_Yh, C * s->Kpad) != cudaSuccess || dalloc(&pp->cand_H1, C * s->H) != cudaSuccess ||
             dalloc(&pp->cand_H2, C * s->H) != cudaSuccess || dalloc(&pp->cand_out, C) != cudaSuccess)
             return FFS_E_NOMEM;
@@ -281,10 +301,30 @@ int ga_population_attach_surrogate(ga_population *pp, ffs_surrogate *s, int32_t 
     pp->sur = s;
     pp->F = oversample;
     pp->lr = lr;
+    pp->train_steps = train_steps;
     if (pp->graph_sur) {
         cudaGraphExecDestroy(pp->graph_sur);
         pp->graph_sur = nullptr;
     }
+    return FFS_OK;
+}
+
+int ffs_surrogate_pretrain(ffs_surrogate *s, ga_population *pp, int32_t steps, float lr, float *loss) {
+    if (!s || !pp || steps < 0 || !(lr > 0.f) || s->inst != pp->inst || s->version != pp->version ||
+        pp->P > s->rows_cap)
+        return FFS_E_ARG;
+    FFS_CUDA(cudaStreamSynchronize(pp->st));
+    GADev dv;
+    FFS_CUDA(cudaMemcpy(&dv, pp->dev, sizeof(dv), cudaMemcpyDeviceToHost));
+    const int b = dv.gen & 1, rows_pad = round_up(pp->P, 128);
+    FFS_CUDA(mlp_stage_features(pp->Y[b], pp->P, rows_pad, s->K, s->Kpad, s->gstg, s->soff, s->g, s->Yh, s->st));
+    for (int i = 0; i < steps; ++i) {
+        FFS_TRY(sync_weights(s, s->st));
+        FFS_TRY(forward(s, s->Yh, rows_pad, s->H1, s->H2, s->out, s->st));
+        FFS_TRY(backward(s, pp->obj[b], pp->P, rows_pad, true, lr, s->st));
+    }
+    if (loss && steps > 0) FFS_TRY(host_loss(s, pp->P, loss));
+    FFS_CUDA(cudaStreamSynchronize(s->st));
     return FFS_OK;
 }
 
@@ -302,6 +342,7 @@ int ffs_rt::surrogate_enqueue_generation(ga_population *pp, cudaStream_t st, cud
     a.cand_X = pp->cand_X;
     a.cand_Yh = pp->cand_Yh;
     a.cand_out = pp->cand_out;
+    a.cand_new = pp->cand_new;
     a.kept_Yh = reinterpret_cast<uint16_t *>(s->Yh);
     a.kept_obj = pp->kept_obj;
     const int C = pp->P * pp->F;
@@ -314,9 +355,12 @@ int ffs_rt::surrogate_enqueue_generation(ga_population *pp, cudaStream_t st, cud
     if (ev0) FFS_CUDA(cudaEventRecord(ev0, st));
     FFS_CUDA(launch_ga_generation(pp->par.order_mode, pp->par.machine_mode, a, pp->hdr, pp->grid_gen, st));
     if (ev1) FFS_CUDA(cudaEventRecord(ev1, st));
-    // one training step on the kept children (inputs gathered into s->Yh, objectives in kept_obj)
-    FFS_TRY(forward(s, s->Yh, pp->P, s->H1, s->H2, s->out, st));
-    FFS_TRY(backward(s, pp->kept_obj, pp->P, pp->P, true, pp->lr, st));
+    // training steps on the kept children (inputs gathered into s->Yh, objectives in kept_obj)
+    for (int step = 0; step < pp->train_steps; ++step) {
+        if (step) FFS_TRY(sync_weights(s, st));
+        FFS_TRY(forward(s, s->Yh, pp->P, s->H1, s->H2, s->out, st));
+        FFS_TRY(backward(s, pp->kept_obj, pp->P, pp->P, true, pp->lr, st));
+    }
     return FFS_OK;
 }
 

@@ -28,7 +28,7 @@ def _setup(seed=1, N=30, g=5, batch=256):
     params = mlp.init_params(orc_i.K, seed=seed)
     for k in params:
         params[k] = params[k] + rng.normal(0, 0.05, params[k].shape)
-    return prob, lib_i, orc_i, ph, dh, Y, params
+    return prob, lib_i, orc_i, ph, dh, Y, params, gs
 
 
 def _rel(a, b):
@@ -37,11 +37,11 @@ def _rel(a, b):
 
 def test_forward_matches_oracle():
     torch = _torch()
-    prob, lib_i, orc_i, ph, dh, Y, params = _setup()
+    prob, lib_i, orc_i, ph, dh, Y, params, gs = _setup()
     sur = ffs.Surrogate(lib_i, max_batch=256)
     sur.set_params(sur.pack(params))
     got = sur.predict(torch.from_numpy(Y).cuda()).cpu().numpy().astype(np.float64)
-    ref = mlp.forward(params, mlp.features(Y, ph, dh))[0]
+    ref = mlp.forward(params, mlp.features(Y, ph, dh, gs))[0]
     # BF16 inputs, weights and activations (8-bit significands), FP32 accumulation
     assert _rel(got, ref) < 0.03, _rel(got, ref)
     assert np.corrcoef(got, ref)[0, 1] > 0.999
@@ -49,13 +49,13 @@ def test_forward_matches_oracle():
 
 def test_gradients_match_oracle():
     torch = _torch()
-    prob, lib_i, orc_i, ph, dh, Y, params = _setup(seed=2)
+    prob, lib_i, orc_i, ph, dh, Y, params, gs = _setup(seed=2)
     rng = np.random.default_rng(5)
     obj = rng.integers(10_000, 90_000, size=len(Y)).astype(np.int64)
     sur = ffs.Surrogate(lib_i, max_batch=256)
     sur.set_params(sur.pack(params))
     g, loss = sur.gradients(torch.from_numpy(Y).cuda(), torch.from_numpy(obj).cuda())
-    X = mlp.features(Y, ph, dh)
+    X = mlp.features(Y, ph, dh, gs)
     out, cache = mlp.forward(params, X)
     t = mlp.targets(obj)
     ref = mlp.backward(params, cache, out, t)
@@ -69,7 +69,7 @@ def test_adam_step_is_adam():
     """The update applied by training equals one Adam step (Kingma & Ba) of the oracle
     taken with the GPU's own gradient."""
     torch = _torch()
-    prob, lib_i, orc_i, ph, dh, Y, params = _setup(seed=3)
+    prob, lib_i, orc_i, ph, dh, Y, params, gs = _setup(seed=3)
     obj = np.random.default_rng(1).integers(1000, 5000, size=len(Y)).astype(np.int64)
     sur = ffs.Surrogate(lib_i, max_batch=256)
     vec = sur.pack(params)
@@ -85,7 +85,7 @@ def test_adam_step_is_adam():
 
 def test_training_reduces_loss():
     torch = _torch()
-    prob, lib_i, orc_i, ph, dh, Y, params = _setup(seed=4)
+    prob, lib_i, orc_i, ph, dh, Y, params, gs = _setup(seed=4)
     obj = np.array([orc_i.decode(y)["obj"] for y in Y], dtype=np.int64)
     sur = ffs.Surrogate(lib_i, max_batch=256, seed=9)
     yd, od = torch.from_numpy(Y).cuda(), torch.from_numpy(obj).cuda()
