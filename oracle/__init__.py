@@ -89,6 +89,8 @@ def lib():
         L.orc_mutate.argtypes = [C.c_int32, _i32p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]
         L.orc_ga_init.restype = C.c_int32
         L.orc_ga_init.argtypes = [C.POINTER(_Inst), C.POINTER(_GAParams), C.POINTER(_GAState)]
+        L.orc_ga_init_from.restype = C.c_int32
+        L.orc_ga_init_from.argtypes = [C.POINTER(_Inst), C.POINTER(_GAParams), C.POINTER(_GAState)]
         L.orc_ga_step.restype = C.c_int32
         L.orc_ga_step.argtypes = [C.POINTER(_Inst), C.POINTER(_GAParams), C.POINTER(_GAState)]
         _lib = L
@@ -280,6 +282,16 @@ class GA:
             raise RuntimeError(f"oracle GA init failed ({rc})")
         return self
 
+    def init_from(self, Y, X=None):
+        """Generation 0 from given rows (a warm start) instead of random ones."""
+        P = self.Y.shape[0]
+        self.Y[:, :self.K] = np.asarray(Y, dtype=np.int16).reshape(P, self.K)
+        self.X[:, :self.K] = 0 if X is None else np.asarray(X, dtype=np.int8).reshape(P, self.K)
+        rc = lib().orc_ga_init_from(C.byref(self._ic()), C.byref(self.par), C.byref(self.st))
+        if rc:
+            raise RuntimeError(f"oracle GA init failed ({rc})")
+        return self
+
     def step(self, n: int = 1):
         for _ in range(n):
             rc = lib().orc_ga_step(C.byref(self._ic()), C.byref(self.par), C.byref(self.st))
@@ -299,3 +311,43 @@ class GA:
         """Best-ever individual over all islands (largest fitness, lowest island)."""
         i = int(np.argmax(self.bfit))
         return self.bY[i, :self.K].copy(), self.bX[i, :self.K].copy(), int(self.bobj[i])
+
+
+# ------------------------------------------------------------------ warm start
+
+def gene_keys(inst: Instance) -> np.ndarray:
+    """Identity of each gene across rescheduling points: job * g + stage (jobs only append)."""
+    gj, gs = inst.gene_map()
+    return gj.astype(np.int64) * inst.g + gs
+
+
+def warm_remap(Y_old, X_old, keys_old, keys_new, P_new):
+    """Warm-start population for a rescheduled instance (not in the paper, which restarts
+    its GA at every rescheduling point, Sec. 4.1).
+
+    Row r of the result comes from old row r mod P_old.  A gene present before and after
+    keeps its machine gene, and the surviving genes keep their relative priority order,
+    taking the top priorities n_new+1 .. K_new (ascending old priority -> ascending new
+    one).  The n_new genes that did not exist before (operations of new jobs) take the
+    priorities below them, n_new .. 1, in ascending gene index, with machine gene 0.
+    """
+    Y_old = np.asarray(Y_old)
+    X_old = np.asarray(X_old)
+    keys_old = list(np.asarray(keys_old).tolist())
+    keys_new = list(np.asarray(keys_new).tolist())
+    pos_old = {k: i for i, k in enumerate(keys_old)}
+    surv = [i for i, k in enumerate(keys_new) if k in pos_old]
+    fresh = [i for i, k in enumerate(keys_new) if k not in pos_old]
+    n_new, K_new = len(fresh), len(keys_new)
+    src = np.array([pos_old[keys_new[i]] for i in surv], dtype=np.int64)
+    Y = np.zeros((P_new, K_new), np.int16)
+    X = np.zeros((P_new, K_new), np.int8)
+    for r in range(P_new):
+        yo, xo = Y_old[r % len(Y_old)], X_old[r % len(X_old)]
+        order = np.argsort(yo[src], kind="stable")          # survivors by old priority, ascending
+        for rank, t in enumerate(order):
+            Y[r, surv[t]] = n_new + 1 + rank
+            X[r, surv[t]] = xo[src[t]]
+        for q, i in enumerate(fresh):
+            Y[r, i] = n_new - q
+    return Y, X

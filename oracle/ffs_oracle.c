@@ -486,16 +486,41 @@ static void island_best_worst(const int64_t *fit, int32_t lo, int32_t hi, int32_
     *worst = w;
 }
 
-/* Generation 0: random X and a Fisher-Yates permutation Y per individual (Sec. 4.3),
- * decode, E_max = 10^a for the smallest a >= 1 above every initial objective (Sec. 5),
- * fitness, and the best-ever individual of each island. */
-int32_t orc_ga_init(const orc_inst *in, const orc_ga_params *par, orc_ga_state *st)
+/* Generation-0 bookkeeping over the rows already in st->Y / st->X: decode every row,
+ * E_max = 10^a for the smallest a >= 1 above every initial objective (Sec. 5), fitness
+ * (Eq. 13), and the best-ever individual of each island (largest fitness, lowest index). */
+int32_t orc_ga_init_from(const orc_inst *in, const orc_ga_params *par, orc_ga_state *st)
 {
     const int32_t P = par->P, K = st->K, I = par->I;
+    int32_t rc = 0;
+    for (int32_t i = 0; i < P; i++)
+        rc |= decode_one(in, par, st->Y + (size_t)i * K, st->X + (size_t)i * K, &st->obj[i]);
+    int64_t mx = 0;
+    for (int32_t i = 0; i < P; i++) if (st->obj[i] > mx) mx = st->obj[i];
+    int64_t e = 10;
+    while (e <= mx) e *= 10;
+    st->emax = e;
+    for (int32_t i = 0; i < P; i++) st->fit[i] = fitness(e, st->obj[i]);
+    for (int32_t isl = 0; isl < P / I; isl++) {
+        int32_t b, w;
+        island_best_worst(st->fit, isl * I, isl * I + I, &b, &w);
+        memcpy(st->bY + (size_t)isl * K, st->Y + (size_t)b * K, sizeof(int16_t) * (size_t)K);
+        memcpy(st->bX + (size_t)isl * K, st->X + (size_t)b * K, (size_t)K);
+        st->bobj[isl] = st->obj[b];
+        st->bfit[isl] = st->fit[b];
+    }
+    st->gen = 0;
+    return rc;
+}
+
+/* Generation 0: random X and a Fisher-Yates permutation Y per individual (Sec. 4.3), then
+ * the bookkeeping of orc_ga_init_from. */
+int32_t orc_ga_init(const orc_inst *in, const orc_ga_params *par, orc_ga_state *st)
+{
+    const int32_t P = par->P, K = st->K;
     int32_t *gstg = (int32_t *)calloc((size_t)K + 1, sizeof(int32_t));
     int32_t *gjob = (int32_t *)calloc((size_t)K + 1, sizeof(int32_t));
     orc_gene_map(in, gjob, gstg);
-    int32_t rc = 0;
     for (int32_t i = 0; i < P; i++) {
         int16_t *y = st->Y + (size_t)i * K;
         int8_t *x = st->X + (size_t)i * K;
@@ -513,26 +538,10 @@ int32_t orc_ga_init(const orc_inst *in, const orc_ga_params *par, orc_ga_state *
                 x[k] = 0;
             }
         }
-        rc |= decode_one(in, par, y, x, &st->obj[i]);
     }
-    int64_t mx = 0;
-    for (int32_t i = 0; i < P; i++) if (st->obj[i] > mx) mx = st->obj[i];
-    int64_t e = 10;
-    while (e <= mx) e *= 10;
-    st->emax = e;
-    for (int32_t i = 0; i < P; i++) st->fit[i] = fitness(e, st->obj[i]);
-    for (int32_t isl = 0; isl < P / I; isl++) {
-        int32_t b, w;
-        island_best_worst(st->fit, isl * I, isl * I + I, &b, &w);
-        memcpy(st->bY + (size_t)isl * K, st->Y + (size_t)b * K, sizeof(int16_t) * (size_t)K);
-        memcpy(st->bX + (size_t)isl * K, st->X + (size_t)b * K, (size_t)K);
-        st->bobj[isl] = st->obj[b];
-        st->bfit[isl] = st->fit[b];
-    }
-    st->gen = 0;
     free(gstg);
     free(gjob);
-    return rc;
+    return orc_ga_init_from(in, par, st);
 }
 
 /* One generation (Sec. 4.4): selection -> paired crossover + correction -> mutation ->

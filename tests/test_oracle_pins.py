@@ -415,3 +415,69 @@ def test_ga_paper_mode_runs():
     gm = inst.gene_machines()
     assert (ga.X[:, :inst.K] < gm[None, :]).all() and (ga.X >= 0).all()
     assert int(ga.bobj.min()) <= first
+
+
+# ---------------------------------------------------------------- warm start (not in the paper)
+
+def test_warm_remap_worked_example():
+    # genes (keys) 0..3 before; keys 0 and 2 froze, keys 4 and 5 belong to a new job.
+    # Survivors by old priority: key 1 (y=1) then key 3 (y=2) -> priorities 3 and 4;
+    # new genes in index order take 2 and 1.
+    Y, X = oracle.warm_remap(np.array([[3, 1, 4, 2]]), np.array([[1, 0, 1, 2]]), [0, 1, 2, 3],
+                             [1, 3, 4, 5], 1)
+    assert Y.tolist() == [[3, 4, 2, 1]]
+    assert X.tolist() == [[0, 2, 0, 0]]
+
+
+def test_warm_remap_identity_and_row_cycling():
+    rng = np.random.default_rng(3)
+    Y0 = np.stack([rng.permutation(9) + 1 for _ in range(4)]).astype(np.int16)
+    X0 = rng.integers(0, 3, size=(4, 9)).astype(np.int8)
+    keys = list(range(0, 18, 2))
+    Y, X = oracle.warm_remap(Y0, X0, keys, keys, 10)
+    for r in range(10):  # nothing froze, nothing arrived: row r is old row r mod 4
+        assert np.array_equal(Y[r], Y0[r % 4]) and np.array_equal(X[r], X0[r % 4])
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_warm_remap_properties_after_reschedule(seed):
+    rng = np.random.default_rng(seed)
+    pr = wl.random_instance(rng, 12, 3, 1, 3, 30, 5, 20, 60)
+    inst = oracle.Instance(pr)
+    keys0 = oracle.gene_keys(inst)
+    ga = oracle.GA(inst, P=16, island=8, seed=seed, mach_mode=MACH_GENE).init().step(3)
+    y, x, _ = ga.best()
+    r = inst.decode(y, x, mach_mode=MACH_GENE)
+    inst.commit(r["S"], r["M"])
+    t_now = r["cmax"] // 3
+    inst.reschedule(wl.random_arrivals(rng, 4, 3, t_now, 30), t_now)
+    keys1 = oracle.gene_keys(inst)
+    Y, X = oracle.warm_remap(ga.Y[:, :ga.K], ga.X[:, :ga.K], keys0, keys1, 24)
+    K1 = len(keys1)
+    old = {k: i for i, k in enumerate(keys0.tolist())}
+    surv = [i for i, k in enumerate(keys1.tolist()) if k in old]
+    fresh = [i for i, k in enumerate(keys1.tolist()) if k not in old]
+    assert fresh and len(surv) < len(keys0)  # some genes froze, a job arrived
+    for r_ in range(24):
+        yo, xo = ga.Y[r_ % 16, :ga.K], ga.X[r_ % 16, :ga.K]
+        assert sorted(Y[r_].tolist()) == list(range(1, K1 + 1))
+        assert min(Y[r_, surv]) > max(Y[r_, fresh])  # new genes below every survivor
+        # survivors in the same relative order, with their machine genes
+        for a in surv:
+            assert X[r_, a] == xo[old[keys1[a]]]
+            for b in surv:
+                assert (Y[r_, a] < Y[r_, b]) == (yo[old[keys1[a]]] < yo[old[keys1[b]]])
+        assert [Y[r_, i] for i in fresh] == list(range(len(fresh), 0, -1))
+        inst.decode(Y[r_], X[r_], mach_mode=MACH_GENE)  # a valid chromosome of the new instance
+
+
+def test_ga_init_from_random_rows_equals_init():
+    inst = oracle.Instance(wl.static_small(2))
+    a = oracle.GA(inst, P=32, island=8, seed=5, mach_mode=MACH_GENE).init()
+    b = oracle.GA(inst, P=32, island=8, seed=5, mach_mode=MACH_GENE).init_from(a.Y, a.X)
+    for f in ("Y", "X", "obj", "fit", "bY", "bX", "bobj", "bfit"):
+        assert np.array_equal(getattr(a, f), getattr(b, f)), f
+    assert a.emax == b.emax and b.gen == 0
+    a.step(4)
+    b.step(4)
+    assert np.array_equal(a.Y, b.Y) and np.array_equal(a.bobj, b.bobj)
