@@ -427,9 +427,87 @@ def bench_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
-# Oracle-measured slot checks per decode of the batched workload (python -m
-# oracle.work_per_decode --workload batched); None until measured.
-BATCH_SLOTS_PER_DECODE = None
+# Slot checks per decode of the batched workload, measured by the oracle (python -m
+# oracle.work_per_decode --workload batched --samples 8): mean over the 256 rescheduling
+# snapshots of 8 uniformly random chromosomes each (min 6038, max 392743 per instance).
+BATCH_SLOTS_PER_DECODE = 112338.4
+
+
+# ----------------------------------------------------------------------------- service
+SVC_WORKLOAD = ("rescheduling service: 16 instances (N U{50..500}, g U{5..10}, machines U{2..8}, p U{1..199}, "
+                "q U{5..30} kW, peak U{40..70}%); requests arrive as a Poisson process (50/s), each for a uniform "
+                "instance: its first request solves it at t=0, later ones advance its clock by U{5..15}% of its "
+                "stage load and bring U{5..50} jobs; population 2048 (islands of 64) warm-started from the "
+                "instance's last population, 200 generations per request")
+
+
+def bench_service(args):
+    import torch
+
+    from paper_1903_10741_gb300 import ffs
+
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    G, Ps = args.generations, 2048
+    ga_kw = dict(P=Ps, island=64, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE, seed=SEED)
+    # warm-up: load the kernels and set their shared-memory limits on a small stream
+    warm = wl.service_small(seed=99, n_instances=3, n_requests=max(3, args.warmup))
+    wi = [ffs.Instance(p) for p in warm.problems]
+    svc = ffs.Service(max_active=args.max_active, memory_bytes=1 << 30, **ga_kw)
+    for t in [svc.submit(wi[r.instance], r.arrivals, r.t_now, 5) for r in warm.requests]:
+        svc.wait(t, schedule=False)
+    svc.close()
+
+    work = wl.service(seed=1, n_requests=args.service_requests, rate=args.rate)
+    insts = [ffs.Instance(p) for p in work.problems]
+    h2d = sum(np.asarray(a, np.int32).nbytes for p in work.problems for a in (p.o, p.p, p.q, p.R, p.D))
+    h2d += sum(r.arrivals.p.nbytes + r.arrivals.R.nbytes + r.arrivals.D.nbytes
+               for r in work.requests if r.arrivals is not None)
+    svc = ffs.Service(max_active=args.max_active, memory_bytes=int(args.service_memory_gb * (1 << 30)), **ga_kw)
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ffs.kernel_launches()
+    t0 = time.perf_counter()
+    tickets = []
+    for r in work.requests:
+        dt = t0 + r.at - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(svc.submit(insts[r.instance], r.arrivals, r.t_now, G))
+    infos = [svc.wait(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    launches = ffs.kernel_launches() - launches0
+    clk = clocks.stop()
+    stats = svc.stats()
+    svc.close()
+    lat = sorted((i["done_ns"] - i["submit_ns"]) / 1e6 for i in infos)
+    queue = sorted((i["admit_ns"] - i["submit_ns"]) / 1e6 for i in infos)
+    run = sorted((i["done_ns"] - i["admit_ns"]) / 1e6 for i in infos)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(round(q / 100 * (len(v) - 1))))]
+
+    decodes = sum(Ps * (i["generations"] + 1) + 1 for i in infos)
+    d2h = sum(8 * i["n_ops"] + 20 for i in infos)
+    line = {
+        "metric": METRIC, "value": decodes / wall, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
+        "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": SVC_WORKLOAD, "requests": len(infos), "offered_rate_per_s": args.rate,
+                   "arrival_window_s": work.requests[-1].at, "generations_per_request": G,
+                   "max_active": args.max_active, "service_memory_gb": args.service_memory_gb,
+                   "genes": [min(i.K for i in insts), max(i.K for i in insts)]},
+        "service": {"p50_latency_ms": pct(lat, 50), "p99_latency_ms": pct(lat, 99),
+                    "p50_queue_ms": pct(queue, 50), "p99_queue_ms": pct(queue, 99),
+                    "p50_run_ms": pct(run, 50), "p99_run_ms": pct(run, 99),
+                    "requests_per_s": len(infos) / wall, "warm_starts": sum(i["warm"] for i in infos),
+                    "peak_memory_bytes": stats["peak_bytes"], "failed": stats["failed"]},
+        "e2e": {"value": decodes / wall, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "note": "the whole run is end to end: host arrays in, host schedules out, through ffs_service_*"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
 
 
 # ----------------------------------------------------------------------------- oracle
@@ -495,9 +573,14 @@ def main():
     ap.add_argument("--ref-generations", type=int, default=2, help="oracle generations per reference step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["dynamic", "batched", "surrogate"], default="dynamic",
+    ap.add_argument("--workload", choices=["dynamic", "batched", "surrogate", "service"], default="dynamic",
                     help="dynamic: the headline rescheduling job; batched: 256 uneven instances; "
-                         "surrogate: time-to-objective of the surrogate-assisted GA")
+                         "surrogate: time-to-objective of the surrogate-assisted GA; service: Poisson "
+                         "rescheduling requests through the continuous-batching service")
+    ap.add_argument("--service-requests", type=int, default=48)
+    ap.add_argument("--rate", type=float, default=50.0, help="service request arrival rate (1/s)")
+    ap.add_argument("--max-active", type=int, default=8, help="service requests on the device at once")
+    ap.add_argument("--service-memory-gb", type=float, default=32.0)
     ap.add_argument("--chunk", type=int, default=20, help="generations between progress checks (surrogate)")
     ap.add_argument("--lr", type=float, default=1e-3, help="surrogate learning rate")
     ap.add_argument("--surrogate-cap", type=int, default=0, help="generation cap of the surrogate run")
@@ -519,6 +602,10 @@ def main():
         if args.generations == 500:
             args.generations = 1000
         bench_surrogate(args)
+    elif args.workload == "service":
+        if args.generations == 500:
+            args.generations = 200
+        bench_service(args)
     else:
         bench_ours(args)
 

@@ -293,6 +293,25 @@ int ffs_decode_check(ffs_instance *inst, void *stream);
  * (Eq. 13) and the best-ever individual of every island. */
 int ga_population_create(ffs_instance *inst, const ga_params *params, ga_population **out);
 
+/* Warm start (an addition to the paper, whose GA restarts from random at every
+ * rescheduling point, Sec. 4.1).  Like ga_population_create, except that generation 0 is
+ * `prev`'s current population carried over to the instance's present gene set: row r
+ * comes from prev's row r mod prev's pop; a gene (job j, stage s) present in both keeps
+ * its machine gene and the surviving genes keep their relative priority order, taking
+ * priorities n_new+1 .. K; the n_new genes of newly arrived jobs take n_new .. 1 in gene
+ * order (gene = free operation, job-major), with machine gene 0.  prev must be a
+ * population of the same instance (created before or at its current rescheduling
+ * point), not in profiling mode; it is read on prev's stream order and left unchanged.
+ * Synchronises the new population's stream. */
+int ga_population_create_warm(ffs_instance *inst, const ga_params *params, ga_population *prev,
+                              ga_population **out);
+
+/* Device bytes a population of the instance (at its current rescheduling point) with
+ * `params` holds: both generation buffers (Y int16 and X int8 per gene, objective and
+ * fitness per individual), island bests and migrants, tables, global profile scratch and
+ * the best-schedule buffers, each rounded up to 256 bytes. */
+int ga_population_footprint(const ffs_instance *inst, const ga_params *params, int64_t *bytes);
+
 /* Frees a population.  NULL is accepted. */
 int ga_population_destroy(ga_population *pop);
 
@@ -328,6 +347,95 @@ int ga_set_profiling(ga_population *pop, int32_t enable);
 /* Summed duration (milliseconds) and launch count of the fused generation kernel measured
  * since profiling was enabled. */
 int ga_profile_read(ga_population *pop, double *kernel_ms, int64_t *launches);
+
+/* ---------------------------------------------------------------- rescheduling service
+ *
+ * Continuous batching of rescheduling requests on one GPU (an addition to the paper,
+ * which solves one rescheduling point at a time, Sec. 4.1).  A request names an instance,
+ * the jobs that arrived and the rescheduling point t_now: the service applies
+ * ffs_reschedule (Alg. 1 freeze, new jobs appended), runs `generations` generations of
+ * the GA and commits the best schedule to the instance, exactly as ffs_reschedule +
+ * ga_population_create(_warm) + ga_run would.  A worker thread owned by the service
+ *   - admits queued requests first come first served while fewer than max_active are on
+ *     the device and the request's population (ga_population_footprint) fits in the
+ *     service's memory; a request whose instance already has one queued ahead or running
+ *     waits for it, and later requests of other instances may pass it;
+ *   - gives each admitted request its own stream, so the generations of all active
+ *     requests overlap on the GPU; finished requests are retired as their streams drain,
+ *     and their slots and memory go to the next requests;
+ *   - keeps each instance's last population on the device and starts the instance's next
+ *     request from it (ga_population_create_warm); kept populations are dropped, least
+ *     recently used first, when an admission needs their memory, and the request then
+ *     starts cold (ffs_request_info.warm = 0).
+ * Every request of an instance draws from Philox stream id ga.instance_id + (the number
+ * of the instance's earlier requests in this service), so its result depends only on the
+ * instance, the request and whether it started warm: not on the other requests, their
+ * timing or max_active.
+ * The caller must not use an instance (nor destroy it) between submitting a request for
+ * it and that request's completion; ffs_service_forget releases an idle instance. */
+typedef struct ffs_service ffs_service;
+
+typedef struct {
+    int32_t max_active;       /* requests on the device at once, >= 1                      */
+    int32_t pad;
+    int64_t memory_bytes;     /* device memory for populations, reserved at creation, > 0 */
+    ga_params ga;             /* GA settings of every request; cuda_stream and
+                                 instance_id are taken as described above            */
+} ffs_service_config;
+
+#define FFS_REQ_QUEUED  0
+#define FFS_REQ_ACTIVE  1
+#define FFS_REQ_DONE    2
+#define FFS_REQ_FAILED  3
+
+typedef struct {
+    int32_t state;            /* FFS_REQ_*                                                */
+    int32_t status;           /* FFS_OK, or the failed request's error code             */
+    int32_t warm;             /* 1 if generation 0 came from the instance's last population */
+    int32_t generations;
+    int64_t submit_ns, admit_ns, done_ns;  /* steady-clock times (ns) of the three events  */
+    int64_t footprint;        /* device bytes of the request's population                */
+    int32_t n_ops;            /* N * g of the instance after this request's arrivals      */
+    int32_t pad;
+} ffs_request_info;
+
+typedef struct {
+    int32_t active, queued, warm;   /* requests on the device, waiting; kept populations   */
+    int32_t pad;
+    int64_t completed, failed;
+    int64_t memory_bytes, used_bytes, peak_bytes;  /* arena size, in use now, high-water mark */
+} ffs_service_stats;
+
+/* Reserves cfg->memory_bytes of device memory on the current device, creates
+ * cfg->max_active streams and starts the worker thread.  FFS_E_ARG for invalid settings
+ * (as ga_population_create), FFS_E_NOMEM if the reservation fails. */
+int ffs_service_create(const ffs_service_config *cfg, ffs_service **out);
+
+/* Stops admitting, waits for the active requests, fails the queued ones (FFS_E_STATE),
+ * stops the worker and frees every population, stream and the reserved memory.  NULL is
+ * accepted.  Results of finished requests are lost. */
+int ffs_service_destroy(ffs_service *svc);
+
+/* Queues a request; copies `arrivals` (may be NULL: no new jobs).  The arguments are
+ * checked when the request is admitted (ffs_reschedule's rules), and a request that fails
+ * there finishes in state FFS_REQ_FAILED.  generations >= 0.  *ticket identifies it. */
+int ffs_service_submit(ffs_service *svc, ffs_instance *inst, const ffs_arrivals *arrivals, int32_t t_now,
+                       int32_t generations, int64_t *ticket);
+
+/* Waits up to timeout_ms (0: just look; < 0: no limit) for a request to finish and fills
+ * *info (if not NULL).  When it has finished, fills *best like ga_run: best->start and
+ * best->machine (if not NULL) must hold info->n_ops entries.  Returns FFS_OK once the
+ * request is done, the request's error code if it failed (ffs_last_error() then gives
+ * the worker's CUDA error text, if any), FFS_E_TIMEOUT if it is still queued or active,
+ * FFS_E_ARG for an unknown ticket. */
+int ffs_service_wait(ffs_service *svc, int64_t ticket, int32_t timeout_ms, ffs_request_info *info,
+                     ffs_result *best);
+
+/* Drops the instance's kept population and its request count.  FFS_E_STATE while a
+ * request of the instance is queued or active. */
+int ffs_service_forget(ffs_service *svc, ffs_instance *inst);
+
+int ffs_service_stats_read(ffs_service *svc, ffs_service_stats *stats);
 
 /* Number of kernels this library has launched in the process so far (graph replays count
  * each kernel node).  For benchmark accounting. */

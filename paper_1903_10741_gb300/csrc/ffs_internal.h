@@ -20,16 +20,34 @@ extern thread_local char g_last_error[256];
 int num_sms();
 int cuda_rc(cudaError_t e);  // FFS_OK, or FFS_E_CUDA with the error text kept
 
+// Device memory comes from cudaMalloc, or, while a thread has an arena set (a service
+// allocating inside its fixed budget), from that arena; a block is returned to whichever
+// arena holds it, without the device-wide synchronisation of cudaFree.
+struct Arena;
+extern thread_local Arena *t_arena;
+constexpr size_t kArenaAlign = 256;
+cudaError_t raw_alloc(void **p, size_t bytes);
+void raw_free(void *p);
+
+// Suspends the thread's arena for the guard's lifetime.
+struct NoArena {
+    Arena *saved;
+    NoArena() : saved(t_arena) { t_arena = nullptr; }
+    ~NoArena() { t_arena = saved; }
+    NoArena(const NoArena &) = delete;
+    NoArena &operator=(const NoArena &) = delete;
+};
+
 template <typename T>
 cudaError_t dalloc(T **p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
-    return cudaMalloc(reinterpret_cast<void **>(p), n * sizeof(T));
+    return raw_alloc(reinterpret_cast<void **>(p), n * sizeof(T));
 }
 
 template <typename T>
 void dfree(T *&p) {
-    if (p) cudaFree(p);
+    if (p) raw_free(p);
     p = nullptr;
 }
 
@@ -98,6 +116,11 @@ struct ga_population {
     edffs::GADev *dev = nullptr;
     uint16_t *scratch = nullptr;
     cudaGraphExec_t graph = nullptr;
+    std::vector<int64_t> gkey;              // job * g + stage of each gene at creation
+    // decode of the best-ever individual (ga_finish)
+    int64_t *r_obj = nullptr, *r_tard = nullptr;
+    int32_t *r_cm = nullptr, *r_S = nullptr, *r_M = nullptr, *r_over = nullptr, *r_cnt = nullptr;
+    int NG = 0;
     // surrogate-assisted generations (see ffs_surrogate.cu)
     struct ffs_surrogate *sur = nullptr;
     int F = 1;
@@ -137,6 +160,7 @@ struct ga_population {
         dfree(bY); dfree(bX); dfree(bobj); dfree(bfit);
         dfree(mY); dfree(mX); dfree(mobj); dfree(mfit); dfree(mw);
         dfree(over); dfree(err); dfree(dev); dfree(scratch); dfree(isl_done);
+        dfree(r_obj); dfree(r_tard); dfree(r_cm); dfree(r_S); dfree(r_M); dfree(r_over); dfree(r_cnt);
     }
 };
 
@@ -148,6 +172,14 @@ int sync_device(ffs_instance *in);
 int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y, const int8_t *x, int32_t count,
                 int64_t *obj, int64_t *tard, int32_t *cmax, int32_t *S, int32_t *Mo, cudaStream_t st);
 void ga_gen_args(ga_population *pp, edffs::GenArgs *a);
+// Enqueues `generations` generations on the population's stream without waiting.
+int ga_enqueue(ga_population *pp, int32_t generations);
+// Waits for the population's stream, then decodes, commits and returns the best-ever schedule.
+int ga_finish(ga_population *pp, ffs_result *best);
+// Device bytes a population of `in` with `par` holds (each buffer rounded to kArenaAlign).
+int population_footprint(ffs_instance *in, const ga_params *par, int64_t *bytes);
+// ga_population_create / ga_population_create_warm (prev may be null).
+int population_create(ffs_instance *in, const ga_params *par, ga_population *prev, ga_population **out);
 // One surrogate-assisted generation on `st` (ffs_surrogate.cu); with events, the fused
 // generation kernel is bracketed by ev0/ev1.  Kernels launched per generation:
 constexpr int kSurrogateFixedLaunches = 12, kSurrogateStepLaunches = 18;

@@ -93,12 +93,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_init(GenArgs a) {
     const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, true, false, nullptr, warp);
     const int K = T.K;
     for (int i = blockIdx.x * kWarpsPerBlock + warp; i < a.P; i += gridDim.x * kWarpsPerBlock) {
-        make_initial<MACH>(T, w, a.seed, a.instance_id, i, lane);
         int16_t *yo = a.Y[0] + (size_t)i * K;
-        for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
-        if (MACH == kMachGene) {
-            int8_t *xo = a.X[0] + (size_t)i * K;
-            for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
+        int8_t *xo = a.X[0] + (size_t)i * K;
+        if (a.warm) {
+            for (int k = lane; k < K; k += 32) w.y[k] = yo[k];
+            if (MACH == kMachGene)
+                for (int k = lane; k < K; k += 32) w.x[k] = xo[k];
+            __syncwarp();
+        } else {
+            make_initial<MACH>(T, w, a.seed, a.instance_id, i, lane);
+            for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
+            if (MACH == kMachGene)
+                for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
         }
         const DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x,
                                                      nullptr, nullptr, lane);
@@ -203,7 +209,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
             int8_t *xo = a.X[nx] + (size_t)i * K;
             for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
         }
-        DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
+        DecodeOut r{0, 0, 1};
+        if (a.Hcap > 0)
+            r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
         if (r.status == 1) {  // the schedule outgrew the shared slice: redo it in global memory
             for (int k = lane; k < K; k += 32) w.y[k] = yo[k];  // the decode reused w.y
             __syncwarp();
@@ -221,6 +229,70 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
             }
         }
         island_finish(a, i / I, nx, (int)gen, lane);
+    }
+}
+
+// ---------------------------------------------------------------- warm start
+// One CTA per new row.  Survivor priorities: a bit per old priority value marks the
+// values held by genes that survive; the rank of value v among them is a popcount
+// prefix, so survivors keep their relative order on top (n_new + rank) and the fresh
+// genes take n_new .. 1 in index order.
+constexpr int kRemapThreads = 256;
+constexpr int kRemapWords = (kMaxK + 32) / 32;
+
+__global__ void __launch_bounds__(kRemapThreads) k_warm_remap(WarmArgs a) {
+    __shared__ uint32_t bits[kRemapWords];
+    __shared__ int32_t pre[kRemapWords];
+    const int nw = (a.Ko + 31) >> 5;
+    const int ob = a.odev->gen & 1;
+    for (int r = blockIdx.x; r < a.P; r += gridDim.x) {
+        const int16_t *yo = a.Yo[ob] + (size_t)(r % a.Po) * a.Ko;
+        const int8_t *xo = a.Xo[ob] + (size_t)(r % a.Po) * a.Ko;
+        int16_t *y = a.Y + (size_t)r * a.K;
+        int8_t *x = a.X + (size_t)r * a.K;
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) bits[i] = 0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < a.Ko; k += blockDim.x) {
+            if (a.map[k] < 0) continue;
+            const int v = yo[k] - 1;
+            if (v < 0 || v >= a.Ko) {
+                atomicOr(a.err, kErrBadChromosome);
+                continue;
+            }
+            atomicOr(&bits[v >> 5], 1u << (v & 31));
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {  // exclusive prefix of the words' popcounts
+            const int lane = threadIdx.x, per = (nw + 31) / 32;
+            const int lo = min(nw, lane * per), hi = min(nw, lo + per);
+            int s = 0;
+            for (int i = lo; i < hi; ++i) s += __popc(bits[i]);
+            int inc = s;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_up_sync(kFull, inc, off);
+                if (lane >= off) inc += t;
+            }
+            int run = inc - s;
+            for (int i = lo; i < hi; ++i) {
+                pre[i] = run;
+                run += __popc(bits[i]);
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < a.Ko; k += blockDim.x) {
+            const int d = a.map[k];
+            const int v = yo[k] - 1;
+            if (d < 0 || v < 0 || v >= a.Ko) continue;
+            const int rank = pre[v >> 5] + __popc(bits[v >> 5] & (0xFFFFFFFFu >> (31 - (v & 31))));
+            y[d] = (int16_t)(a.n_new + rank);
+            x[d] = xo[k];
+        }
+        for (int q = threadIdx.x; q < a.n_new; q += blockDim.x) {
+            y[a.fresh[q]] = (int16_t)(a.n_new - q);
+            x[a.fresh[q]] = 0;
+        }
+        __syncthreads();  // the next row reuses bits / pre
     }
 }
 
@@ -435,6 +507,13 @@ cudaError_t launch_candidates(int mach, const GenArgs &a, const TabHeader &h, in
         if (e == cudaSuccess) k_candidates<kMachEarliest><<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
     }
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_warm_remap(const WarmArgs &a, cudaStream_t st) {
+    if (a.Ko > kMaxK || a.K > kMaxK) return cudaErrorInvalidValue;
+    const int grid = a.P < 1216 ? a.P : 1216;
+    k_warm_remap<<<grid, kRemapThreads, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_emax(const ReplArgs &a, cudaStream_t st) {

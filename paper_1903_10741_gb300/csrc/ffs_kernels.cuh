@@ -71,6 +71,23 @@ struct GenArgs {
     uint8_t *cand_new;          // [P*F] 1 if the candidate is an offspring, 0 if a parent's copy
     uint16_t *kept_Yh;          // [P][Kpad] inputs of the kept candidates, for training
     int64_t *kept_obj;          // [P] their exact objectives (before replacement)
+    int warm;                   // generation 0 decodes the rows already in Y[0] / X[0]
+};
+
+// Warm start: the rows of an earlier population of the same instance, carried over to
+// the gene set of a later rescheduling point (see k_warm_remap).
+struct WarmArgs {
+    const int16_t *Yo[2];       // old population, both buffers; the current one is odev->gen & 1
+    const int8_t *Xo[2];
+    const GADev *odev;
+    int Po, Ko;
+    const int32_t *map;         // [Ko] new gene index of old gene k, or -1 if it froze
+    const int32_t *fresh;       // [n_new] genes with no old counterpart, ascending
+    int n_new;
+    int16_t *Y;                 // [P][K] generation-0 rows
+    int8_t *X;
+    int P, K;
+    int32_t *err;
 };
 
 struct ReplArgs {
@@ -139,6 +156,7 @@ cudaError_t prepare_ga_generation(int order, int mach, const TabHeader &h, int H
 // Over-generation for the surrogate: P*F candidates (no decoding).
 cudaError_t launch_candidates(int mach, const GenArgs &a, const TabHeader &h, int grid, cudaStream_t st);
 cudaError_t prepare_candidates(int mach, const TabHeader &h);
+cudaError_t launch_warm_remap(const WarmArgs &a, cudaStream_t st);
 cudaError_t launch_emax(const ReplArgs &a, cudaStream_t st);
 cudaError_t launch_replace(const ReplArgs &a, cudaStream_t st);
 

@@ -105,6 +105,7 @@ struct GADev {
 };
 
 constexpr int kErrBadChromosome = 1, kErrOverflow = 2, kErrTimeout = 4;
+constexpr int kMaxK = 32767;  // genes per chromosome: priorities are int16
 
 // Below this many profile slots per warp a shared-memory slice is not worth keeping.
 constexpr int kMinBatchSlots = 256;

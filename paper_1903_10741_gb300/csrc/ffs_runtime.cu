@@ -91,7 +91,7 @@ int rebuild(ffs_instance *in) {
     // start times are packed with a 5-bit machine index into 32-bit keys
     if (H >= (1ll << 26) || (long long)RS + H > INT32_MAX) return FFS_E_ARG;
     in->K = (int)in->gjob.size();
-    if (in->K > kMaxN) return FFS_E_ARG;
+    if (in->K > kMaxK) return FFS_E_ARG;
     in->Hfull = (int)H;
     const int E0 = (int)(exec_end - RS);
     std::vector<uint16_t> h0(E0, (uint16_t)in->Qmax);
@@ -168,6 +168,7 @@ int rebuild(ffs_instance *in) {
 // Uploads the tables and the committed plan if the host copy changed since the last upload.
 int sync_device(ffs_instance *in) {
     if (!in->dev_dirty) return FFS_OK;
+    const NoArena plain;  // instance tables outlive any service arena
     const int off = in->hdr.bytes;
     if ((size_t)off > in->d_blob_cap) {
         dfree(in->d_blob);
@@ -247,6 +248,7 @@ int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y,
     a.err = in->d_err;
     const int slots = smem_slots(h, false);
     const int sms = num_sms();
+    const NoArena plain;  // per-instance buffers outlive any service arena
     if (slots > 0) {
         if ((size_t)count > in->d_over_cap) {
             dfree(in->d_over);
@@ -532,56 +534,104 @@ static int ga_enqueue_generation(ga_population *pp, cudaEvent_t ev0 = nullptr, c
     return FFS_OK;
 }
 
-int ga_population_create(ffs_instance *in, const ga_params *par, ga_population **out) {
-    if (!in || !par || !out) return FFS_E_ARG;
-    *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+int check_ga_params(const ga_params *par, int *side) {
     FFS_TRY(check_modes(par->order_mode, par->machine_mode));
     const int P = par->pop, I = par->island;
     if (P < 2 || P % 2 || I < 2 || I % 2 || P % I || par->tournament_k < 0 || par->tournament_k > 32 ||
         par->pc_den <= 0 || par->pm_den <= 0 || par->pc_num < 0 || par->pm_num < 0 ||
         par->pc_num > par->pc_den || par->pm_num > par->pm_den || par->migrate_every < 0)
         return FFS_E_ARG;
-    int side = 0;
+    *side = 0;
     if (par->tournament_k == 0) {
-        while (side * side < P) ++side;
-        if (side * side != P) return FFS_E_ARG;
+        int s = 0;
+        while (s * s < P) ++s;
+        if (s * s != P) return FFS_E_ARG;
+        *side = s;
     }
+    return FFS_OK;
+}
+
+// Sizes of a population of `in` (no allocation).
+void pop_shape(ga_population *pp, ffs_instance *in, const ga_params *par, int side) {
+    pp->inst = in;
+    pp->version = in->version;
+    pp->par = *par;
+    pp->st = static_cast<cudaStream_t>(par->cuda_stream);
+    pp->P = par->pop;
+    pp->I = par->island;
+    pp->K = in->K;
+    pp->nisl = pp->P / pp->I;
+    pp->side = side;
+    pp->hdr = in->hdr;
+    pp->NG = in->N * in->g;
+    pp->Hcap = smem_slots(pp->hdr, true);
+    const int P = pp->P;
+    pp->grid_gen = std::max(1, std::min((P + kWarpsPerBlock - 1) / kWarpsPerBlock,
+                                        num_sms() * std::max(1, (228 * 1024) / (cta_smem_bytes(pp->hdr, pp->Hcap, true, false) + 1024))));
+    pp->grid_fb = std::max(1, std::min((P + kWarpsPerBlock - 1) / kWarpsPerBlock, num_sms() * 2));
+}
+
+// Every device buffer of a population, in allocation order: f(pointer, element count).
+template <typename F>
+void pop_buffers(ga_population *pp, F &&f) {
+    const size_t PK = (size_t)pp->P * pp->K, NK = (size_t)pp->nisl * pp->K, nisl = pp->nisl;
+    f(pp->d_blob, (size_t)pp->hdr.bytes);
+    for (int b = 0; b < 2; ++b) {
+        f(pp->Y[b], PK);
+        f(pp->X[b], PK);
+        f(pp->obj[b], (size_t)pp->P);
+        f(pp->fit[b], (size_t)pp->P);
+    }
+    f(pp->bY, NK); f(pp->bX, NK); f(pp->bobj, nisl); f(pp->bfit, nisl);
+    f(pp->mY, NK); f(pp->mX, NK); f(pp->mobj, nisl); f(pp->mfit, nisl); f(pp->mw, nisl);
+    f(pp->over, (size_t)pp->P);
+    f(pp->err, (size_t)1);
+    f(pp->dev, (size_t)1);
+    f(pp->isl_done, nisl);
+    f(pp->scratch, (size_t)std::max(pp->grid_fb, pp->grid_gen) * kWarpsPerBlock * pp->hdr.H);
+    f(pp->r_obj, (size_t)1); f(pp->r_tard, (size_t)1); f(pp->r_cm, (size_t)1);
+    f(pp->r_S, (size_t)pp->NG); f(pp->r_M, (size_t)pp->NG);
+    f(pp->r_over, (size_t)1); f(pp->r_cnt, (size_t)1);
+}
+
+size_t pop_bytes(ga_population *pp) {
+    size_t total = 0;
+    pop_buffers(pp, [&](auto *&ptr, size_t n) {
+        const size_t bytes = std::max<size_t>(n, 1) * sizeof(*ptr);
+        total += (bytes + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+    });
+    return total;
+}
+
+// Creates a population; with `prev` (an earlier population of the same instance),
+// generation 0 is prev's current population carried over to the present gene set.
+int create_population(ffs_instance *in, const ga_params *par, ga_population *prev, ga_population **out) {
+    if (!in || !par || !out) return FFS_E_ARG;
+    *out = nullptr;
+    int side = 0;
+    FFS_TRY(check_ga_params(par, &side));
     if (in->K < 1) return FFS_E_STATE;
+    if (prev && (prev->inst != in || prev->version > in->version || prev->profiling)) return FFS_E_ARG;
+    FFS_TRY(sync_device(in));
     ga_population *pp = new (std::nothrow) ga_population();
     if (!pp) return FFS_E_NOMEM;
     auto fail = [&](int rc) {
         delete pp;
         return rc;
     };
-    pp->inst = in;
-    pp->version = in->version;
-    pp->par = *par;
-    pp->st = static_cast<cudaStream_t>(par->cuda_stream);
-    pp->P = P;
-    pp->I = I;
-    pp->K = in->K;
-    pp->nisl = P / I;
-    pp->side = side;
-    pp->hdr = in->hdr;
-    const size_t PK = (size_t)P * pp->K, NK = (size_t)pp->nisl * pp->K;
-    bool ok = dalloc(&pp->d_blob, (size_t)in->hdr.bytes) == cudaSuccess;
-    for (int b = 0; b < 2 && ok; ++b)
-        ok = dalloc(&pp->Y[b], PK) == cudaSuccess && dalloc(&pp->X[b], PK) == cudaSuccess &&
-             dalloc(&pp->obj[b], P) == cudaSuccess && dalloc(&pp->fit[b], P) == cudaSuccess;
-    ok = ok && dalloc(&pp->bY, NK) == cudaSuccess && dalloc(&pp->bX, NK) == cudaSuccess &&
-         dalloc(&pp->bobj, pp->nisl) == cudaSuccess && dalloc(&pp->bfit, pp->nisl) == cudaSuccess &&
-         dalloc(&pp->mY, NK) == cudaSuccess && dalloc(&pp->mX, NK) == cudaSuccess &&
-         dalloc(&pp->mobj, pp->nisl) == cudaSuccess && dalloc(&pp->mfit, pp->nisl) == cudaSuccess &&
-         dalloc(&pp->mw, pp->nisl) == cudaSuccess && dalloc(&pp->over, P) == cudaSuccess &&
-         dalloc(&pp->err, 1) == cudaSuccess && dalloc(&pp->dev, 1) == cudaSuccess &&
-         dalloc(&pp->isl_done, pp->nisl) == cudaSuccess;
+    pop_shape(pp, in, par, side);
+    bool ok = true;
+    pop_buffers(pp, [&](auto *&ptr, size_t n) {
+        if (ok) ok = dalloc(&ptr, n) == cudaSuccess;
+    });
     if (!ok) return fail(FFS_E_NOMEM);
-    pp->Hcap = smem_slots(pp->hdr, true);
-    pp->grid_gen = std::max(1, std::min((P + kWarpsPerBlock - 1) / kWarpsPerBlock,
-                                        num_sms() * std::max(1, (228 * 1024) / (cta_smem_bytes(pp->hdr, pp->Hcap, true, false) + 1024))));
-    pp->grid_fb = std::max(1, std::min((P + kWarpsPerBlock - 1) / kWarpsPerBlock, num_sms() * 2));
-    if (dalloc(&pp->scratch, (size_t)std::max(pp->grid_fb, pp->grid_gen) * kWarpsPerBlock * pp->hdr.H) != cudaSuccess)
-        return fail(FFS_E_NOMEM);
+    pp->gkey.resize(pp->K);
+    for (int k = 0; k < pp->K; ++k) pp->gkey[k] = (int64_t)in->gjob[k] * in->g + in->gstg[k];
+    const size_t PK = (size_t)pp->P * pp->K;
     cudaStream_t st = pp->st;
     int rc = FFS_OK;
     auto step = [&](cudaError_t e) {
@@ -592,8 +642,54 @@ int ga_population_create(ffs_instance *in, const ga_params *par, ga_population *
     step(cudaMemsetAsync(pp->err, 0, 4, st));
     step(cudaMemsetAsync(pp->dev, 0, sizeof(GADev), st));
     step(cudaMemsetAsync(pp->isl_done, 0, 4 * (size_t)pp->nisl, st));
+    int32_t *d_map = nullptr;
+    if (prev && rc == FFS_OK) {
+        // old gene -> new gene (or -1 once frozen); new genes with no old counterpart
+        std::vector<int32_t> slot((size_t)in->N * in->g, -1), map(prev->K), fresh;
+        for (int k = 0; k < pp->K; ++k) slot[pp->gkey[k]] = k;
+        std::vector<char> seen(pp->K, 0);
+        for (int k = 0; k < prev->K; ++k) {
+            const int64_t key = prev->gkey[k];
+            map[k] = key < (int64_t)slot.size() ? slot[key] : -1;
+            if (map[k] >= 0) seen[map[k]] = 1;
+        }
+        for (int k = 0; k < pp->K; ++k)
+            if (!seen[k]) fresh.push_back(k);
+        if (dalloc(&d_map, (size_t)prev->K + fresh.size()) != cudaSuccess) return fail(FFS_E_NOMEM);
+        // the old rows are read on this stream once prev's queued work is done
+        cudaEvent_t ev = nullptr;
+        step(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        if (rc == FFS_OK) {
+            step(cudaEventRecord(ev, prev->st));
+            step(cudaStreamWaitEvent(st, ev, 0));
+            cudaEventDestroy(ev);
+        }
+        step(cudaMemcpyAsync(d_map, map.data(), 4 * map.size(), cudaMemcpyHostToDevice, st));
+        if (!fresh.empty())
+            step(cudaMemcpyAsync(d_map + prev->K, fresh.data(), 4 * fresh.size(), cudaMemcpyHostToDevice, st));
+        WarmArgs w{};
+        for (int b = 0; b < 2; ++b) {
+            w.Yo[b] = prev->Y[b];
+            w.Xo[b] = prev->X[b];
+        }
+        w.odev = prev->dev;
+        w.Po = prev->P;
+        w.Ko = prev->K;
+        w.map = d_map;
+        w.fresh = d_map + prev->K;
+        w.n_new = (int)fresh.size();
+        w.Y = pp->Y[0];
+        w.X = pp->X[0];
+        w.P = pp->P;
+        w.K = pp->K;
+        w.err = pp->err;
+        step(launch_warm_remap(w, st));
+        if (rc == FFS_OK) g_launches += 1;
+        // pageable sources: the copies have been staged once cudaMemcpyAsync returned
+    }
     GenArgs a;
     ga_gen_args(pp, &a);
+    a.warm = prev ? 1 : 0;
     step(launch_ga_init(par->order_mode, par->machine_mode, a, pp->hdr, pp->grid_gen, st));
     DecodeArgs d;
     ga_fallback_args(pp, &d, false);
@@ -603,36 +699,76 @@ int ga_population_create(ffs_instance *in, const ga_params *par, ga_population *
     step(launch_emax(r, st));
     step(launch_replace(r, st));
     step(cudaMemsetAsync(&pp->dev->nover, 0, 4, st));
-    if (rc != FFS_OK) return fail(rc);
+    if (rc != FFS_OK) {
+        cudaStreamSynchronize(st);
+        dfree(d_map);
+        return fail(rc);
+    }
     g_launches += 4;  // init, fallback decode, E_max, island bests
     // Capture one generation once; ga_run replays it.
-    if (prepare_ga_generation(par->order_mode, par->machine_mode, pp->hdr, pp->Hcap) != cudaSuccess)
+    if (prepare_ga_generation(par->order_mode, par->machine_mode, pp->hdr, pp->Hcap) != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        dfree(d_map);
         return fail(FFS_E_CUDA);
+    }
     // The caller's stream may be the legacy default stream, which cannot be captured: the
     // graph is recorded on a private stream and later launched on the caller's.
     cudaGraph_t graph = nullptr;
     cudaStream_t cap = nullptr;
-    if ((rc = cuda_rc(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking))) != FFS_OK) return fail(rc);
-    cudaStream_t user = pp->st;
-    pp->st = cap;
-    rc = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    const int erc = rc == FFS_OK ? ga_enqueue_generation(pp) : rc;
-    const int ce = rc == FFS_OK ? cuda_rc(cudaStreamEndCapture(cap, &graph)) : rc;
-    pp->st = user;
-    cudaStreamDestroy(cap);
-    if (erc != FFS_OK || ce != FFS_OK) {
+    rc = cuda_rc(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    if (rc == FFS_OK) {
+        cudaStream_t user = pp->st;
+        pp->st = cap;
+        rc = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        const int erc = rc == FFS_OK ? ga_enqueue_generation(pp) : rc;
+        const int ce = rc == FFS_OK ? cuda_rc(cudaStreamEndCapture(cap, &graph)) : rc;
+        pp->st = user;
+        cudaStreamDestroy(cap);
+        rc = erc != FFS_OK ? erc : ce;
+        if (rc == FFS_OK) rc = cuda_rc(cudaGraphInstantiate(&pp->graph, graph, 0));
         if (graph) cudaGraphDestroy(graph);
-        return fail(erc != FFS_OK ? erc : ce);
     }
-    rc = cuda_rc(cudaGraphInstantiate(&pp->graph, graph, 0));
-    cudaGraphDestroy(graph);
+    const int sync_rc = cuda_rc(cudaStreamSynchronize(st));
+    dfree(d_map);
     if (rc != FFS_OK) return fail(rc);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(FFS_E_CUDA);
+    if (sync_rc != FFS_OK) return fail(sync_rc);
     int32_t e = 0;
     if (cudaMemcpy(&e, pp->err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return fail(FFS_E_CUDA);
     if (e) return fail(e & kErrTimeout ? FFS_E_TIMEOUT : FFS_E_DEVICE);
     *out = pp;
     return FFS_OK;
+}
+
+}  // namespace
+
+int ffs_rt::population_footprint(ffs_instance *in, const ga_params *par, int64_t *bytes) {
+    int side = 0;
+    FFS_TRY(check_ga_params(par, &side));
+    if (in->K < 1) return FFS_E_STATE;
+    ga_population shape;
+    pop_shape(&shape, in, par, side);
+    *bytes = (int64_t)pop_bytes(&shape);
+    return FFS_OK;
+}
+
+int ffs_rt::population_create(ffs_instance *in, const ga_params *par, ga_population *prev, ga_population **out) {
+    return create_population(in, par, prev, out);
+}
+
+extern "C" {
+
+int ga_population_create(ffs_instance *in, const ga_params *par, ga_population **out) {
+    return create_population(in, par, nullptr, out);
+}
+
+int ga_population_create_warm(ffs_instance *in, const ga_params *par, ga_population *prev, ga_population **out) {
+    if (!prev) return FFS_E_ARG;
+    return create_population(in, par, prev, out);
+}
+
+int ga_population_footprint(const ffs_instance *in, const ga_params *par, int64_t *bytes) {
+    if (!in || !par || !bytes) return FFS_E_ARG;
+    return population_footprint(const_cast<ffs_instance *>(in), par, bytes);
 }
 
 int ga_population_destroy(ga_population *pp) {
@@ -661,7 +797,9 @@ int ga_population_read(ga_population *pp, int16_t *Y, int8_t *X, int64_t *obj, i
     return FFS_OK;
 }
 
-int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
+}  // extern "C"
+
+int ffs_rt::ga_enqueue(ga_population *pp, int32_t generations) {
     if (!pp || generations < 0) return FFS_E_ARG;
     ffs_instance *in = pp->inst;
     if (pp->version != in->version) return FFS_E_STATE;
@@ -681,30 +819,16 @@ int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
         if (g) cudaGraphDestroy(g);
         if (rc != FFS_OK) return rc;
     }
-    if (!pp->profiling) {
-        cudaGraphExec_t gx = pp->sur ? pp->graph_sur : pp->graph;
-        for (int i = 0; i < generations; ++i) FFS_CUDA(cudaGraphLaunch(gx, pp->st));
-        g_launches += per_gen * (unsigned long long)generations;
-        FFS_CUDA(cudaStreamSynchronize(pp->st));
-    } else {
-        while ((int)pp->ev.size() < 2 * generations) {
-            cudaEvent_t e;
-            FFS_CUDA(cudaEventCreate(&e));
-            pp->ev.push_back(e);
-        }
-        for (int i = 0; i < generations; ++i) {
-            if (pp->sur) FFS_TRY(surrogate_enqueue_generation(pp, pp->st, pp->ev[2 * i], pp->ev[2 * i + 1]));
-            else FFS_TRY(ga_enqueue_generation(pp, pp->ev[2 * i], pp->ev[2 * i + 1]));
-        }
-        g_launches += per_gen * (unsigned long long)generations;
-        FFS_CUDA(cudaStreamSynchronize(pp->st));
-        for (int i = 0; i < generations; ++i) {
-            float ms = 0.f;
-            FFS_CUDA(cudaEventElapsedTime(&ms, pp->ev[2 * i], pp->ev[2 * i + 1]));
-            pp->prof_ms += ms;
-        }
-        pp->prof_launches += generations;
-    }
+    if (pp->profiling) return FFS_E_STATE;
+    cudaGraphExec_t gx = pp->sur ? pp->graph_sur : pp->graph;
+    for (int i = 0; i < generations; ++i) FFS_CUDA(cudaGraphLaunch(gx, pp->st));
+    g_launches += per_gen * (unsigned long long)generations;
+    return FFS_OK;
+}
+
+int ffs_rt::ga_finish(ga_population *pp, ffs_result *best) {
+    ffs_instance *in = pp->inst;
+    FFS_CUDA(cudaStreamSynchronize(pp->st));
     int32_t e = 0;
     FFS_CUDA(cudaMemcpy(&e, pp->err, 4, cudaMemcpyDeviceToHost));
     if (e) return e & kErrTimeout ? FFS_E_TIMEOUT : FFS_E_DEVICE;
@@ -714,28 +838,55 @@ int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
     int bi = 0;
     for (int i = 1; i < pp->nisl; ++i)
         if (bfit[i] > bfit[bi]) bi = i;
-    const size_t NG = (size_t)in->N * in->g;
-    int64_t *d_obj = nullptr, *d_tard = nullptr;
-    int32_t *d_cm = nullptr, *d_S = nullptr, *d_M = nullptr;
-    int rc = FFS_OK;
-    if (dalloc(&d_obj, 1) != cudaSuccess || dalloc(&d_tard, 1) != cudaSuccess || dalloc(&d_cm, 1) != cudaSuccess ||
-        dalloc(&d_S, NG) != cudaSuccess || dalloc(&d_M, NG) != cudaSuccess)
-        rc = FFS_E_NOMEM;
-    if (rc == FFS_OK)
-        rc = decode_impl(in, pp->par.order_mode, pp->par.machine_mode, pp->bY + (size_t)bi * pp->K,
-                         pp->bX + (size_t)bi * pp->K, 1, d_obj, d_tard, d_cm, d_S, d_M, pp->st);
+    // Decode it into the population's own buffers: shared-memory profile first, the
+    // global-memory one (whole bound) if the schedule outgrows it.
+    FFS_TRY(sync_device(in));  // frozen operations' plan
+    const TabHeader &h = pp->hdr;
+    DecodeArgs a{};
+    a.blob = pp->d_blob;
+    a.blob_bytes = h.bytes;
+    a.Y[0] = a.Y[1] = pp->bY + (size_t)bi * pp->K;
+    a.X[0] = a.X[1] = pp->bX + (size_t)bi * pp->K;
+    a.count = 1;
+    a.obj[0] = a.obj[1] = pp->r_obj;
+    a.tard = pp->r_tard;
+    a.cmax = pp->r_cm;
+    a.S = pp->r_S;
+    a.Mo = pp->r_M;
+    a.S0 = in->d_S0;
+    a.M0 = in->d_M0;
+    a.status = in->d_status;
+    a.err = pp->err;
+    const int order = pp->par.order_mode, mach = pp->par.machine_mode;
+    const int slots = smem_slots(h, false);
+    if (slots > 0) {
+        FFS_CUDA(cudaMemsetAsync(pp->r_cnt, 0, 4, pp->st));
+        a.Hcap = slots;
+        a.over_list = pp->r_over;
+        a.over_count = pp->r_cnt;
+        FFS_CUDA(launch_decode(order, mach, false, a, h, 1, pp->st));
+        g_launches += 1;
+        a.list = pp->r_over;
+        a.list_count = pp->r_cnt;
+    }
+    if (slots < h.H) {
+        a.gscratch = pp->scratch;
+        a.Hcap = h.H;
+        FFS_CUDA(launch_decode(order, mach, true, a, h, 1, pp->st));
+        g_launches += 1;
+    }
+    FFS_CUDA(cudaStreamSynchronize(pp->st));
+    FFS_CUDA(cudaMemcpy(&e, pp->err, 4, cudaMemcpyDeviceToHost));
+    if (e) return e & kErrTimeout ? FFS_E_TIMEOUT : FFS_E_DEVICE;
+    const size_t NG = (size_t)pp->NG;
     std::vector<int32_t> S(NG), M(NG);
     int64_t o = 0, t = 0;
     int32_t cm = 0;
-    if (rc == FFS_OK) rc = ffs_decode_check(in, pp->st);
-    if (rc == FFS_OK)
-        rc = cuda_rc(cudaMemcpy(S.data(), d_S, 4 * NG, cudaMemcpyDeviceToHost)) |
-             cuda_rc(cudaMemcpy(M.data(), d_M, 4 * NG, cudaMemcpyDeviceToHost)) |
-             cuda_rc(cudaMemcpy(&o, d_obj, 8, cudaMemcpyDeviceToHost)) |
-             cuda_rc(cudaMemcpy(&t, d_tard, 8, cudaMemcpyDeviceToHost)) |
-             cuda_rc(cudaMemcpy(&cm, d_cm, 4, cudaMemcpyDeviceToHost));
-    dfree(d_obj); dfree(d_tard); dfree(d_cm); dfree(d_S); dfree(d_M);
-    if (rc != FFS_OK) return rc < 0 ? rc : FFS_E_CUDA;
+    FFS_CUDA(cudaMemcpy(S.data(), pp->r_S, 4 * NG, cudaMemcpyDeviceToHost));
+    FFS_CUDA(cudaMemcpy(M.data(), pp->r_M, 4 * NG, cudaMemcpyDeviceToHost));
+    FFS_CUDA(cudaMemcpy(&o, pp->r_obj, 8, cudaMemcpyDeviceToHost));
+    FFS_CUDA(cudaMemcpy(&t, pp->r_tard, 8, cudaMemcpyDeviceToHost));
+    FFS_CUDA(cudaMemcpy(&cm, pp->r_cm, 4, cudaMemcpyDeviceToHost));
     FFS_TRY(ffs_commit(in, S.data(), M.data()));
     if (best) {
         best->objective = o;
@@ -746,6 +897,40 @@ int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
         if (best->machine) std::memcpy(best->machine, M.data(), 4 * NG);
     }
     return FFS_OK;
+}
+
+
+extern "C" {
+
+int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
+    if (!pp || generations < 0) return FFS_E_ARG;
+    if (pp->version != pp->inst->version) return FFS_E_STATE;
+    if (!pp->profiling) {
+        FFS_TRY(ga_enqueue(pp, generations));
+        return ga_finish(pp, best);
+    }
+    // profiling: every generation launched eagerly between two events
+    const unsigned long long per_gen =
+        pp->sur ? (unsigned long long)(kSurrogateFixedLaunches + kSurrogateStepLaunches * pp->train_steps) : 1;
+    if (pp->sur) FFS_TRY(prepare_surrogate_kernels(pp));
+    while ((int)pp->ev.size() < 2 * generations) {
+        cudaEvent_t e;
+        FFS_CUDA(cudaEventCreate(&e));
+        pp->ev.push_back(e);
+    }
+    for (int i = 0; i < generations; ++i) {
+        if (pp->sur) FFS_TRY(surrogate_enqueue_generation(pp, pp->st, pp->ev[2 * i], pp->ev[2 * i + 1]));
+        else FFS_TRY(ga_enqueue_generation(pp, pp->ev[2 * i], pp->ev[2 * i + 1]));
+    }
+    g_launches += per_gen * (unsigned long long)generations;
+    FFS_CUDA(cudaStreamSynchronize(pp->st));
+    for (int i = 0; i < generations; ++i) {
+        float ms = 0.f;
+        FFS_CUDA(cudaEventElapsedTime(&ms, pp->ev[2 * i], pp->ev[2 * i + 1]));
+        pp->prof_ms += ms;
+    }
+    pp->prof_launches += generations;
+    return ga_finish(pp, best);
 }
 
 int ga_set_profiling(ga_population *pp, int32_t enable) {

@@ -60,6 +60,23 @@ class BatchConfig_c(C.Structure):
                 ("cluster", C.c_int32), ("ms_per_generation", C.c_float)]
 
 
+class ServiceConfig_c(C.Structure):
+    _fields_ = [("max_active", C.c_int32), ("pad", C.c_int32), ("memory_bytes", C.c_int64),
+                ("ga", GAParams_c)]
+
+
+class RequestInfo_c(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("warm", C.c_int32), ("generations", C.c_int32),
+                ("submit_ns", C.c_int64), ("admit_ns", C.c_int64), ("done_ns", C.c_int64),
+                ("footprint", C.c_int64), ("n_ops", C.c_int32), ("pad", C.c_int32)]
+
+
+class ServiceStats_c(C.Structure):
+    _fields_ = [("active", C.c_int32), ("queued", C.c_int32), ("warm", C.c_int32), ("pad", C.c_int32),
+                ("completed", C.c_int64), ("failed", C.c_int64), ("memory_bytes", C.c_int64),
+                ("used_bytes", C.c_int64), ("peak_bytes", C.c_int64)]
+
+
 class Info_c(C.Structure):
     _fields_ = [("n_jobs", C.c_int32), ("n_stages", C.c_int32), ("n_machines", C.c_int32),
                 ("n_genes", C.c_int32), ("rs", C.c_int32), ("horizon", C.c_int32),
@@ -85,6 +102,15 @@ _SIGS = {
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ga_population_create": (C.c_int, [C.c_void_p, C.POINTER(GAParams_c), C.POINTER(C.c_void_p)]),
     "ga_population_destroy": (C.c_int, [C.c_void_p]),
+    "ga_population_create_warm": (C.c_int, [C.c_void_p, C.POINTER(GAParams_c), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "ga_population_footprint": (C.c_int, [C.c_void_p, C.POINTER(GAParams_c), C.POINTER(C.c_int64)]),
+    "ffs_service_create": (C.c_int, [C.POINTER(ServiceConfig_c), C.POINTER(C.c_void_p)]),
+    "ffs_service_destroy": (C.c_int, [C.c_void_p]),
+    "ffs_service_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Arrivals_c), C.c_int32, C.c_int32,
+                                     C.POINTER(C.c_int64)]),
+    "ffs_service_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(RequestInfo_c), C.POINTER(Result_c)]),
+    "ffs_service_forget": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ffs_service_stats_read": (C.c_int, [C.c_void_p, C.POINTER(ServiceStats_c)]),
     "ga_run": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Result_c)]),
     "ga_population_read": (C.c_int, [C.c_void_p] + [C.c_void_p] * 10),
     "ga_checkpoint": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
@@ -266,21 +292,42 @@ class Instance:
         return {"obj": obj, "tard": tard, "cmax": cmax}
 
 
+def ga_params(P: int, island: int = 64, tour_k: int = 2, pc=(4, 5), pm=(1, 10), order_mode=ORDER_STAGE,
+              mach_mode=MACH_EARLIEST, migrate_every: int = 10, seed: int = 1, instance_id: int = 0,
+              stream_ptr=None) -> GAParams_c:
+    return GAParams_c(P, min(island, P), tour_k, pc[0], pc[1], pm[0], pm[1], order_mode, mach_mode,
+                      migrate_every, instance_id, seed, stream_ptr)
+
+
+def footprint(inst: Instance, P: int, **kw) -> int:
+    """Device bytes of a population of ``inst`` (``ga_population_footprint``)."""
+    n = C.c_int64()
+    par = ga_params(P, **kw)
+    _check(lib().ga_population_footprint(inst.handle, C.byref(par), C.byref(n)), "ga_population_footprint")
+    return int(n.value)
+
+
 class Population:
-    """A device-resident GA population (``ga_population``)."""
+    """A device-resident GA population (``ga_population``).  With ``prev`` (an earlier
+    population of the same instance), generation 0 is ``prev``'s population carried over
+    to the instance's present genes (``ga_population_create_warm``)."""
 
     def __init__(self, inst: Instance, P: int, island: int = 64, tour_k: int = 2, pc=(4, 5),
                  pm=(1, 10), order_mode=ORDER_STAGE, mach_mode=MACH_EARLIEST, migrate_every: int = 10,
-                 seed: int = 1, instance_id: int = 0, stream=None):
+                 seed: int = 1, instance_id: int = 0, stream=None, prev: "Population" = None):
         self.inst = inst
         island = min(island, P)
         self.P, self.island = P, island
         self.nisl = P // island
         self.mach_mode = mach_mode
-        par = GAParams_c(P, island, tour_k, pc[0], pc[1], pm[0], pm[1], order_mode, mach_mode,
-                         migrate_every, instance_id, seed, _stream_ptr(stream))
+        par = ga_params(P, island, tour_k, pc, pm, order_mode, mach_mode, migrate_every, seed, instance_id,
+                        _stream_ptr(stream))
         h = C.c_void_p()
-        _check(lib().ga_population_create(inst.handle, C.byref(par), C.byref(h)), "ga_population_create")
+        if prev is None:
+            _check(lib().ga_population_create(inst.handle, C.byref(par), C.byref(h)), "ga_population_create")
+        else:
+            _check(lib().ga_population_create_warm(inst.handle, C.byref(par), prev._h, C.byref(h)),
+                   "ga_population_create_warm")
         self._h = h
         self.K = inst.K
 
@@ -500,3 +547,70 @@ class Surrogate:
         _check(lib().ffs_surrogate_train(self._h, _dptr(y), _dptr(obj), int(y.shape[0]), float(lr),
                                          C.addressof(loss)), "ffs_surrogate_train")
         return float(loss.value)
+
+
+class Service:
+    """The rescheduling service (``ffs_service``): requests (instance, arrivals, t_now,
+    generations) are queued, admitted by memory and run concurrently on the GPU by the
+    library's worker thread; each instance's last population stays on the device."""
+
+    def __init__(self, P: int, max_active: int = 8, memory_bytes: int = 8 << 30, **ga_kw):
+        cfg = ServiceConfig_c(int(max_active), 0, int(memory_bytes), ga_params(P, **ga_kw))
+        h = C.c_void_p()
+        _check(lib().ffs_service_create(C.byref(cfg), C.byref(h)), "ffs_service_create")
+        self._h = h
+        self._n_ops = {}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().ffs_service_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, inst: Instance, arrivals=None, t_now: int = 0, generations: int = 200) -> int:
+        t = C.c_int64()
+        if arrivals is None:
+            _check(lib().ffs_service_submit(self._h, inst.handle, None, int(t_now), int(generations), C.byref(t)),
+                   "ffs_service_submit")
+        else:
+            p, R, D = _i32(arrivals.p), _i32(arrivals.R), _i32(arrivals.D)
+            a = Arrivals_c(int(p.shape[0]), _p(p), _p(R), _p(D))
+            _check(lib().ffs_service_submit(self._h, inst.handle, C.byref(a), int(t_now), int(generations),
+                                            C.byref(t)), "ffs_service_submit")
+        return int(t.value)
+
+    def info(self, ticket: int) -> dict:
+        """State of a request without waiting."""
+        i = RequestInfo_c()
+        rc = lib().ffs_service_wait(self._h, int(ticket), 0, C.byref(i), None)
+        if rc not in (FFS_OK, -5) and i.state != 3:
+            _check(rc, "ffs_service_wait")
+        return {n: getattr(i, n) for n, _ in RequestInfo_c._fields_ if n != "pad"}
+
+    def wait(self, ticket: int, timeout_ms: int = -1, schedule: bool = True) -> dict:
+        """Waits for a request; returns its info and best schedule (raises if it failed)."""
+        i = RequestInfo_c()
+        rc = lib().ffs_service_wait(self._h, int(ticket), int(timeout_ms), C.byref(i), None)
+        _check(rc, "ffs_service_wait")
+        S = np.zeros(max(i.n_ops, 1), np.int32)
+        M = np.zeros_like(S)
+        r = Result_c(0, 0, 0, 0, _p(S) if schedule else None, _p(M) if schedule else None)
+        _check(lib().ffs_service_wait(self._h, int(ticket), 0, None, C.byref(r)), "ffs_service_wait")
+        out = {n: getattr(i, n) for n, _ in RequestInfo_c._fields_ if n != "pad"}
+        out.update(obj=int(r.objective), tard=int(r.total_tardiness), cmax=int(r.makespan))
+        if schedule:
+            out.update(S=S[:i.n_ops], M=M[:i.n_ops])
+        return out
+
+    def forget(self, inst: Instance):
+        _check(lib().ffs_service_forget(self._h, inst.handle), "ffs_service_forget")
+
+    def stats(self) -> dict:
+        s = ServiceStats_c()
+        _check(lib().ffs_service_stats_read(self._h, C.byref(s)), "ffs_service_stats_read")
+        return {n: getattr(s, n) for n, _ in ServiceStats_c._fields_ if n != "pad"}

@@ -191,6 +191,63 @@ def batched(count: int = 256, seed: int = 1, n_lo: int = 20, n_hi: int = 200,
     return out
 
 
+@dataclass
+class ServiceRequest:
+    """One rescheduling request of the service workload."""
+
+    at: float                 # arrival time in seconds after the start (Poisson process)
+    instance: int             # index into the workload's instance pool
+    t_now: int                # rescheduling point; 0 for an instance's first request
+    arrivals: Arrivals = None  # new jobs (None for an instance's first request)
+
+
+@dataclass
+class ServiceWorkload:
+    problems: List[Problem]
+    requests: List[ServiceRequest]
+
+
+def service(seed: int = 1, n_instances: int = 16, n_requests: int = 48, rate: float = 50.0,
+            n_range=(50, 500), g_range=(5, 10), o_range=(2, 8), p_hi: int = 199, q_range=(5, 30),
+            pct_range=(40, 70), new_jobs=(5, 50), advance_pct=(5, 15)) -> ServiceWorkload:
+    """Rescheduling service: a pool of instances (N ~ U{50..500}, g ~ U{5..10}, machines
+    U{2..8} per stage, p ~ U{1..199}, q ~ U{5..30}, peak U{40..70}% of the all-on power) and
+    requests arriving as a Poisson process of the given rate, each for a uniformly drawn
+    instance.  An instance's first request solves it from scratch at t_now = 0; every
+    later one moves its clock on by U{5..15}% of W = max_s (sum_j p_js) / o_s and brings
+    U{5..50} jobs released at t_now (due factor U{1.2..2.0} of their work)."""
+    rng = np.random.default_rng(seed)
+    problems, clock, width = [], [], []
+    for _ in range(n_instances):
+        N = int(_u(rng, *n_range))
+        g = int(_u(rng, *g_range))
+        pct = int(_u(rng, *pct_range))
+        prob = random_instance(rng, N, g, o_range[0], o_range[1], p_hi, q_range[0], q_range[1], pct)
+        problems.append(prob)
+        clock.append(None)
+        width.append(int(max(prob.p[:, s].sum() // prob.o[s] for s in range(g))))
+    reqs, t = [], 0.0
+    for _ in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        i = int(rng.integers(0, n_instances))
+        if clock[i] is None:
+            clock[i] = 0
+            reqs.append(ServiceRequest(at=t, instance=i, t_now=0, arrivals=None))
+            continue
+        clock[i] += max(1, width[i] * int(_u(rng, *advance_pct)) // 100)
+        n = int(_u(rng, *new_jobs))
+        reqs.append(ServiceRequest(at=t, instance=i, t_now=clock[i],
+                                   arrivals=random_arrivals(rng, n, problems[i].g, clock[i], p_hi)))
+    return ServiceWorkload(problems=problems, requests=reqs)
+
+
+def service_small(seed: int = 1, n_instances: int = 5, n_requests: int = 15) -> ServiceWorkload:
+    """A small service workload for parity tests: N ~ U{8..20}, g ~ U{2..4}, machines
+    U{1..3}, p ~ U{1..30}, new jobs U{1..4}."""
+    return service(seed, n_instances, n_requests, rate=1000.0, n_range=(8, 20), g_range=(2, 4),
+                   o_range=(1, 3), p_hi=30, new_jobs=(1, 4), advance_pct=(10, 30))
+
+
 def surrogate_large(seed: int = 1) -> Problem:
     """Surrogate-assisted workload: 200 jobs, 8 stages, machines U{2..6}, p ~ U{1..99},
     q ~ U{5..50}, Qmax = floor(50% of all-on power)."""
