@@ -48,7 +48,7 @@ SLOTS_PER_DECODE = 64865.5
 # DRAM bytes (read + write) of one generation-kernel launch from the ncu capture of the
 # current kernel (dram__bytes_read.sum + dram__bytes_write.sum, initial solve); None once
 # the kernel changes until it is captured again.
-TRAFFIC_BYTES = 418816
+TRAFFIC_BYTES = 419328
 # INT32 issue ceiling: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (lane-ops/s).
 ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
@@ -313,7 +313,12 @@ def bench_batched(args):
     batch = ffs.Batch(insts, P=512, island=64, tour_k=2, pc=PC, pm=PM, migrate_every=MIGRATE, seed=SEED,
                       stream=stream)
     create_s = time.perf_counter() - t0
-    chosen = batch.tune(args.tune_generations)
+    if args.batch_mapping:
+        w, sm, cl = (int(v) for v in args.batch_mapping.split(","))
+        batch.set_config(w, sm, cl)
+        chosen = batch.config()
+    else:
+        chosen = batch.tune(args.tune_generations)
     for _ in range(args.warmup):
         batch.run(args.tune_generations)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -588,6 +593,8 @@ def main():
     ap.add_argument("--pretrain-steps", type=int, default=50, help="surrogate Adam steps on generation 0")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--tune-generations", type=int, default=3)
+    ap.add_argument("--batch-mapping", default="",
+                    help="warps,smem_bytes,cluster of the batched kernel instead of autotuning")
     ap.add_argument("--eager", action="store_true",
                     help="launch every generation directly instead of replaying its CUDA graph "
                          "(for profilers that cannot follow graph launches)")
