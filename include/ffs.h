@@ -348,6 +348,16 @@ int ga_set_profiling(ga_population *pop, int32_t enable);
  * since profiling was enabled. */
 int ga_profile_read(ga_population *pop, double *kernel_ms, int64_t *launches);
 
+/* The surrogate's dense contraction, exposed for verification (not in the paper):
+ * C = A . B^T with A [M][K] and B [N][K] row-major BF16 device matrices, accumulated in
+ * FP32 on the tcgen05 tensor cores.  relu_bf16 = 0: C is [M][N] FP32; relu_bf16 = 1:
+ * C = relu(A . B^T + bias) rounded to BF16, bias [N] FP32.  M and N multiples of 128, K a
+ * multiple of 64, pointers 16-byte aligned, else FFS_E_ARG.  Asynchronous on `stream`;
+ * FFS_E_TIMEOUT (at the next synchronising call of the surrogate, or here when
+ * synchronous = 1) if a bounded wait inside the kernel ran out. */
+int ffs_tensor_gemm(const void *A, const void *B, int32_t M, int32_t N, int32_t K, const float *bias, void *C,
+                    int32_t relu_bf16, int32_t synchronous, void *stream);
+
 /* ---------------------------------------------------------------- rescheduling service
  *
  * Continuous batching of rescheduling requests on one GPU (an addition to the paper,

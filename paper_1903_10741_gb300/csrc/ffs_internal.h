@@ -183,6 +183,9 @@ int population_create(ffs_instance *in, const ga_params *par, ga_population *pre
 // One surrogate-assisted generation on `st` (ffs_surrogate.cu); with events, the fused
 // generation kernel is bracketed by ev0/ev1.  Kernels launched per generation:
 constexpr int kSurrogateFixedLaunches = 12, kSurrogateStepLaunches = 18;
+// FFS_E_TIMEOUT if a tensor-core GEMM recorded a wait timeout since the last call (and
+// clears it).  Synchronous.
+int surrogate_status();
 int surrogate_enqueue_generation(ga_population *pp, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
 // Raises the shared-memory limits of the kernels a surrogate generation launches, so that
 // the generation can be captured.

@@ -2,13 +2,13 @@
 // chromosome's priorities and its genes' features (H = 256 hidden units, BF16 weights and
 // activations, FP32 accumulation), its backward pass and Adam.
 //
-// The input features are yh_k * (1, ph_k, dh_k) per gene (yh = y / K), so the first layer
-// is applied as V yh with V[n, k] = W1[n, 3k] + ph_k W1[n, 3k+1] + dh_k W1[n, 3k+2]; its
-// weight gradient is recovered exactly as dW1[n, 3k+f] = G[n, k] c_f(k) from
-// G = dZ1^T Yh.  Every contraction is one GEMM kernel, C = A B^T with both operands
-// K-contiguous, on the tensor cores (mma.sync m16n8k16 BF16 -> FP32), fed by cp.async
-// double buffering and ldmatrix; reductions run in a fixed order, so results are
-// reproducible.
+// The input features are yh_k * (1, ph_k, dh_k) per gene (yh_k = 1 - r_k / n_s, the gene's
+// rank among its stage's genes), so the first layer is applied as V yh with
+// V[n, k] = W1[n, 3k] + ph_k W1[n, 3k+1] + dh_k W1[n, 3k+2]; its weight gradient is
+// recovered exactly as dW1[n, 3k+f] = G[n, k] c_f(k) from G = dZ1^T Yh.  Every
+// contraction is one tcgen05 GEMM (ffs_umma.cu), C = A B^T with both operands
+// K-contiguous; the other kernels here are elementwise or reductions in a fixed order, so
+// results are reproducible.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -21,109 +21,6 @@
 namespace edffs {
 
 namespace {
-
-constexpr int kBM = 128, kBN = 128, kBK = 32, kPad = 8;
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%0, %1, %2, %3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// C[M x N] = A[M x K] . B[N x K]^T; M, N multiples of 128, K a multiple of 32.
-// 8 warps as 2 x 4, each a 64 x 32 tile of 4 x 4 mma tiles.
-template <int EPI>
-__global__ void __launch_bounds__(256) k_gemm(const __nv_bfloat16 *__restrict__ A, const __nv_bfloat16 *__restrict__ B,
-                                              int K, void *C, int ldc, const float *__restrict__ bias) {
-    __shared__ __align__(16) __nv_bfloat16 sA[2][kBM][kBK + kPad];
-    __shared__ __align__(16) __nv_bfloat16 sB[2][kBN][kBK + kPad];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int bm = blockIdx.y * kBM, bn = blockIdx.x * kBN;
-    const int wm = (warp >> 2) * 64, wn = (warp & 3) * 32;
-    float acc[4][4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-
-    auto load = [&](int st, int k0) {
-#pragma unroll
-        for (int c = tid; c < kBM * kBK / 8; c += 256) {
-            const int r = c >> 2, col = (c & 3) * 8;
-            cp_async16(&sA[st][r][col], A + (size_t)(bm + r) * K + k0 + col);
-            cp_async16(&sB[st][r][col], B + (size_t)(bn + r) * K + k0 + col);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    const int nk = K / kBK;
-    load(0, 0);
-    for (int kt = 0; kt < nk; ++kt) {
-        if (kt + 1 < nk) {
-            load((kt + 1) & 1, (kt + 1) * kBK);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
-        __syncthreads();
-        const int st = kt & 1;
-#pragma unroll
-        for (int ks = 0; ks < kBK; ks += 16) {
-            uint32_t af[4][4], bf[4][2];
-#pragma unroll
-            for (int mi = 0; mi < 4; ++mi) ldmatrix_x4(af[mi], &sA[st][wm + mi * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
-#pragma unroll
-            for (int ni = 0; ni < 2; ++ni) {
-                uint32_t r[4];
-                ldmatrix_x4(r, &sB[st][wn + ni * 16 + (lane & 7) + ((lane >> 4) << 3)][ks + ((lane >> 3) & 1) * 8]);
-                bf[2 * ni][0] = r[0];
-                bf[2 * ni][1] = r[1];
-                bf[2 * ni + 1][0] = r[2];
-                bf[2 * ni + 1][1] = r[3];
-            }
-#pragma unroll
-            for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-                for (int nj = 0; nj < 4; ++nj) mma_bf16(acc[mi][nj], af[mi], bf[nj][0], bf[nj][1]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int mi = 0; mi < 4; ++mi)
-#pragma unroll
-        for (int nj = 0; nj < 4; ++nj)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = bm + wm + mi * 16 + (lane >> 2) + h * 8;
-                const int col = bn + wn + nj * 8 + (lane & 3) * 2;
-                float v0 = acc[mi][nj][2 * h], v1 = acc[mi][nj][2 * h + 1];
-                if (EPI == kEpiF32) {
-                    *reinterpret_cast<float2 *>(static_cast<float *>(C) + (size_t)row * ldc + col) = make_float2(v0, v1);
-                } else {
-                    v0 = fmaxf(v0 + bias[col], 0.f);
-                    v1 = fmaxf(v1 + bias[col + 1], 0.f);
-                    *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(C) + (size_t)row * ldc + col) =
-                        __floats2bfloat162_rn(v0, v1);
-                }
-            }
-}
 
 // out[r] = w3 . h2[r] + b3 (BF16 operands, FP32 sum, fixed order), one warp per row.
 __global__ void k_rowdot(const __nv_bfloat16 *__restrict__ h2, const __nv_bfloat16 *__restrict__ w3, const float *b3,
@@ -290,14 +187,6 @@ unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
 
-cudaError_t mlp_gemm(int epi, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, void *C, int ldc,
-                     const float *bias, cudaStream_t st) {
-    if (M % kBM || N % kBN || K % kBK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
-    const dim3 grid(N / kBN, M / kBM);
-    if (epi == kEpiF32) k_gemm<kEpiF32><<<grid, 256, 0, st>>>(A, B, K, C, ldc, bias);
-    else k_gemm<kEpiBiasReluBf16><<<grid, 256, 0, st>>>(A, B, K, C, ldc, bias);
-    return cudaGetLastError();
-}
 
 cudaError_t mlp_rowdot(const __nv_bfloat16 *h2, const __nv_bfloat16 *w3, const float *b3, int rows, int H, float *out,
                        cudaStream_t st) {

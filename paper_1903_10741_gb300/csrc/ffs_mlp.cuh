@@ -9,10 +9,14 @@ namespace edffs {
 constexpr int kEpiF32 = 0;            // C = A B^T, FP32
 constexpr int kEpiBiasReluBf16 = 1;   // C = relu(A B^T + bias), BF16
 
-// C[M x N] = A[M x K] B[N x K]^T (BF16 operands, FP32 accumulation); M, N multiples of 128,
-// K a multiple of 32; ldc in elements.
+// C[M x N] = A[M x K] B[N x K]^T (BF16 operands, FP32 accumulation) on the tcgen05 tensor
+// cores (ffs_umma.cu); M, N multiples of 128, K a multiple of 64; ldc in elements, a
+// multiple of 8; A, B and C 16-byte aligned.
 cudaError_t mlp_gemm(int epi, const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, void *C, int ldc,
                      const float *bias, cudaStream_t st);
+// Error bits (kErrTimeout) that GEMM launches recorded since the last call, and clears
+// them.  Synchronous.
+int32_t mlp_gemm_take_error();
 cudaError_t mlp_rowdot(const __nv_bfloat16 *h2, const __nv_bfloat16 *w3, const float *b3, int rows, int H, float *out,
                        cudaStream_t st);
 cudaError_t mlp_make_v(const float *W1, const float *ph, const float *dh, int H, int K, int Kpad, __nv_bfloat16 *V,

@@ -829,6 +829,7 @@ int ffs_rt::ga_enqueue(ga_population *pp, int32_t generations) {
 int ffs_rt::ga_finish(ga_population *pp, ffs_result *best) {
     ffs_instance *in = pp->inst;
     FFS_CUDA(cudaStreamSynchronize(pp->st));
+    if (pp->sur) FFS_TRY(surrogate_status());
     int32_t e = 0;
     FFS_CUDA(cudaMemcpy(&e, pp->err, 4, cudaMemcpyDeviceToHost));
     if (e) return e & kErrTimeout ? FFS_E_TIMEOUT : FFS_E_DEVICE;

@@ -111,6 +111,7 @@ int check_batch(ffs_surrogate *s, int count) {
 int host_loss(ffs_surrogate *s, int rows, float *loss) {
     std::vector<float> o(rows), t(rows);
     FFS_CUDA(cudaStreamSynchronize(s->st));
+    FFS_TRY(ffs_rt::surrogate_status());
     FFS_CUDA(cudaMemcpy(o.data(), s->out, 4 * (size_t)rows, cudaMemcpyDeviceToHost));
     FFS_CUDA(cudaMemcpy(t.data(), s->t, 4 * (size_t)rows, cudaMemcpyDeviceToHost));
     double acc = 0;
@@ -257,6 +258,7 @@ int ffs_surrogate_gradients(ffs_surrogate *s, const int16_t *y, const int64_t *o
     if (loss_host) FFS_TRY(host_loss(s, count, loss_host));
     if (grad_host) {
         FFS_CUDA(cudaStreamSynchronize(s->st));
+        FFS_TRY(ffs_rt::surrogate_status());
         FFS_CUDA(cudaMemcpy(grad_host, s->grads, 4 * s->n_params, cudaMemcpyDeviceToHost));
     }
     return FFS_OK;
@@ -274,6 +276,20 @@ int ffs_surrogate_train(ffs_surrogate *s, const int16_t *y, const int64_t *obj, 
     // the targets exist once the backward pass has run; the outputs are the pre-step ones
     if (loss_host) FFS_TRY(host_loss(s, count, loss_host));
     return FFS_OK;
+}
+
+int ffs_tensor_gemm(const void *A, const void *B, int32_t M, int32_t N, int32_t K, const float *bias, void *C,
+                    int32_t relu_bf16, int32_t synchronous, void *stream) {
+    if (!A || !B || !C || (relu_bf16 && !bias)) return FFS_E_ARG;
+    const cudaError_t e = mlp_gemm(relu_bf16 ? kEpiBiasReluBf16 : kEpiF32, static_cast<const __nv_bfloat16 *>(A),
+                                   static_cast<const __nv_bfloat16 *>(B), M, N, K, C, N, bias,
+                                   static_cast<cudaStream_t>(stream));
+    if (e == cudaErrorInvalidValue) return FFS_E_ARG;
+    FFS_CUDA(e);
+    ffs_rt::g_launches += 1;
+    if (!synchronous) return FFS_OK;
+    FFS_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return ffs_rt::surrogate_status();
 }
 
 int ga_population_attach_surrogate(ga_population *pp, ffs_surrogate *s, int32_t oversample, float lr,
@@ -325,10 +341,12 @@ int ffs_surrogate_pretrain(ffs_surrogate *s, ga_population *pp, int32_t steps, f
     }
     if (loss && steps > 0) FFS_TRY(host_loss(s, pp->P, loss));
     FFS_CUDA(cudaStreamSynchronize(s->st));
-    return FFS_OK;
+    return ffs_rt::surrogate_status();
 }
 
 }  // extern "C"
+
+int ffs_rt::surrogate_status() { return mlp_gemm_take_error() ? FFS_E_TIMEOUT : FFS_OK; }
 
 // One surrogate-assisted generation: candidates, their scores, the fused select + decode +
 // replacement kernel, then one training step on the kept children's exact objectives.

@@ -133,6 +133,8 @@ _SIGS = {
     "ga_batch_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "ga_batch_get_config": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ga_batch_set_config": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ffs_tensor_gemm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                  C.c_int32, C.c_int32, C.c_void_p]),
     "ga_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "ga_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
@@ -305,6 +307,18 @@ def footprint(inst: Instance, P: int, **kw) -> int:
     par = ga_params(P, **kw)
     _check(lib().ga_population_footprint(inst.handle, C.byref(par), C.byref(n)), "ga_population_footprint")
     return int(n.value)
+
+
+def tensor_gemm(A, B, bias=None, relu_bf16: bool = False, stream=None):
+    """C = A . B^T on the tcgen05 tensor cores (``ffs_tensor_gemm``): A [M, K] and B [N, K]
+    BF16 CUDA tensors; FP32 [M, N] result, or relu(A . B^T + bias) as BF16."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.bfloat16 if relu_bf16 else torch.float32, device=A.device)
+    _check(lib().ffs_tensor_gemm(_dptr(A), _dptr(B), M, N, K, _dptr(bias), _dptr(C), 1 if relu_bf16 else 0, 1,
+                                 _stream_ptr(stream)), "ffs_tensor_gemm")
+    return C
 
 
 class Population:
