@@ -361,9 +361,10 @@ def bench_batched(args):
 
 # ----------------------------------------------------------------------------- surrogate
 SUR_WORKLOAD = ("surrogate-assisted GA: 200 jobs, 8 stages, machines U{2..6}, p U{1..99}, q U{5..50} kW, peak 50%; "
-                "population 4096 (islands of 64); the plain GA runs G generations, the surrogate GA over-generates 8 "
-                "candidates per slot, scores them with the BF16 MLP (256-256-1), decodes the best of each 8 exactly and "
-                "trains online; time until its best total tardiness is within 0.5% of the plain GA's final value")
+                "population 4096 (islands of 64); the plain GA runs G generations, the surrogate GA over-generates F "
+                "candidates per slot, scores them with the BF16 MLP (256-256-1); a screened offspring slot keeps its "
+                "best-scored offspring, the others the plain child; kept children are decoded exactly and train the "
+                "model online; time until its best total tardiness is within 0.5% of the plain GA's final value")
 
 
 def bench_surrogate(args):
@@ -392,7 +393,7 @@ def bench_surrogate(args):
         inst = ffs.Instance(prob)
         pop = ffs.Population(inst, **kw)
         sur = ffs.Surrogate(inst, max_batch=P, seed=SEED)
-        pop.attach_surrogate(sur, oversample=8, lr=args.lr, train_steps=args.train_steps,
+        pop.attach_surrogate(sur, oversample=args.oversample, lr=args.lr, train_steps=args.train_steps, screen=args.screen,
                              pretrain_steps=args.pretrain_steps)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -419,6 +420,7 @@ def bench_surrogate(args):
         "value": reached[1] if reached else None, "n_gpus": 1, "dtype": "int32 decode / bf16 surrogate",
         "data": "synthetic",
         "config": {"workload": SUR_WORKLOAD, "generations_plain": G, "chunk": chunk, "lr": args.lr,
+                   "oversample": args.oversample, "screen": args.screen,
                    "train_steps_per_generation": args.train_steps, "pretrain_steps": args.pretrain_steps,
                    "target_total_tardiness": target, "plain_final_objective": plain[-1][3],
                    "plain_time_s": plain[-1][1], "plain_time_to_target_s": plain_to_target[1],
@@ -590,6 +592,8 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3, help="surrogate learning rate")
     ap.add_argument("--surrogate-cap", type=int, default=0, help="generation cap of the surrogate run")
     ap.add_argument("--train-steps", type=int, default=2, help="surrogate Adam steps per generation")
+    ap.add_argument("--oversample", type=int, default=2, help="surrogate candidates per population slot")
+    ap.add_argument("--screen", type=float, default=0.5, help="fraction of offspring slots that take the surrogate's pick")
     ap.add_argument("--pretrain-steps", type=int, default=50, help="surrogate Adam steps on generation 0")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--tune-generations", type=int, default=3)

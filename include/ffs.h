@@ -248,13 +248,16 @@ int ffs_surrogate_gradients(ffs_surrogate *sur, const int16_t *y, const int64_t 
 int ffs_surrogate_train(ffs_surrogate *sur, const int16_t *y, const int64_t *obj, int32_t count, float lr,
                         float *loss);
 /* Surrogate-assisted generations for a population of the same instance: each generation
- * builds `oversample` candidates per slot with the Sec. 4.4 operators, scores them all,
- * decodes exactly only the best-scored offspring of each slot (ties to the lower
- * candidate; a parent's plain copy only when the slot has no offspring), then trains the
- * surrogate `train_steps` Adam steps on those exact objectives.  P and P * oversample
- * must be multiples of 128 and max_batch >= P.  NULL detaches. */
+ * builds `oversample` candidates per slot with the Sec. 4.4 operators and scores them all.
+ * A slot whose first candidate is a parent's plain copy keeps it, as a plain generation
+ * would.  Otherwise the slot is screened with probability screen_permille / 1000 (a
+ * Philox draw, purpose 6, per slot and generation) and then keeps the best-scored
+ * offspring among its candidates (ties to the lower candidate); an unscreened slot keeps
+ * its first candidate.  Only the kept children are decoded exactly; the surrogate then
+ * takes `train_steps` Adam steps on their exact objectives.  P and P * oversample must be
+ * multiples of 128, max_batch >= P, 0 <= screen_permille <= 1000.  NULL detaches. */
 int ga_population_attach_surrogate(ga_population *pop, ffs_surrogate *sur, int32_t oversample, float lr,
-                                   int32_t train_steps);
+                                   int32_t train_steps, int32_t screen_permille);
 
 /* `steps` Adam steps on the population's current members and their exact objectives (for
  * example generation 0, before surrogate-assisted generations begin); host *loss after

@@ -59,13 +59,15 @@ struct GASrc {
     int P, I, K, tour_k, side;
     uint64_t pc_thr, pm_thr, seed;
     uint32_t iid;        // 24-bit instance id of the stream
-    int F;               // children per population slot (1; 8 when over-generating for a surrogate)
+    int F;               // children per population slot (1; more when over-generating for a surrogate)
 };
 
 // Builds child i of generation `gen` into the warp's w.y / w.x: both parents of its pair
 // are selected from the counter-based stream, so the two children of a pair can be built
-// by different warps.  With s.F > 1, child i is one of F candidates for population slot
-// i / F and draws its parents from that slot's island (or neighbourhood).
+// by different warps.  With s.F > 1, child i = f P + j is candidate f of population slot
+// j: it draws its parents from slot j's island (or neighbourhood), candidate f of slots
+// 2q and 2q+1 are the two children of one pair, and candidate 0 is exactly the child a
+// plain generation builds for slot j.
 // Returns true if the child differs from a plain copy of a parent (crossover or mutation
 // was applied).
 template <int MACH>
@@ -81,13 +83,13 @@ __device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, con
         int bi = INT_MAX;
         if (s.tour_k > 0) {
             if (lane < s.tour_k) {
-                const int lo = ((slot / s.F) / I) * I;  // the island of the slot the child is for
+                const int lo = ((s.F > 1 ? slot % s.P : slot) / I) * I;  // the island of the slot the child is for
                 bi = lo + (int)below(draw(s.seed, kPSelect, s.iid, gen, (uint32_t)slot, (uint32_t)lane),
                                      (uint32_t)I);
                 bf = s.fc[bi];
             }
         } else if (lane < 5) {  // the cell and its N, S, W, E neighbours on the torus
-            const int sd = s.side, base = slot / s.F, r = base / sd, cc = base % sd;
+            const int sd = s.side, base = s.F > 1 ? slot % s.P : slot, r = base / sd, cc = base % sd;
             const int rr = lane == 1 ? (r + sd - 1) % sd : lane == 2 ? (r + 1) % sd : r;
             const int c2 = lane == 3 ? (cc + sd - 1) % sd : lane == 4 ? (cc + 1) % sd : cc;
             bi = rr * sd + c2;

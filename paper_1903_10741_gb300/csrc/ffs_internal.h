@@ -132,6 +132,7 @@ struct ga_population {
     uint8_t *cand_new = nullptr;
     int64_t *kept_obj = nullptr;
     int train_steps = 1;
+    uint64_t screen_thr = (uint64_t)1 << 32;  // floor(screen probability * 2^32)
     cudaGraphExec_t graph_sur = nullptr;
     bool profiling = false;                 // eager launches with timed generation kernels
     std::vector<cudaEvent_t> ev;            // event pairs, reused across ga_run calls

@@ -176,14 +176,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
         if (!a.cand_Y) {
             make_child<MACH>(T, w, src, i, gen, lane);
         } else {
-            // surrogate-assisted: keep the offspring with the lowest score (ties to the lower
-            // index; an undefined score counts as worst); a parent's plain copy is kept only
-            // when no candidate of the slot is an offspring
-            const bool any_new = __any_sync(kFull, lane < a.F && a.cand_new[(size_t)i * a.F + lane]);
+            // surrogate-assisted: the slot's first candidate decides, as a plain generation
+            // would, between a parent's plain copy (kept as it is) and an offspring; a
+            // screened offspring slot keeps the offspring with the lowest score among its
+            // candidates (ties to the lower index; an undefined score counts as worst), an
+            // unscreened one its first candidate
+            const bool screen = a.cand_new[i] &&
+                                (uint64_t)draw(a.seed, kPScreen, a.instance_id, gen, (uint32_t)i, 0) < a.screen_thr;
             float sc = INFINITY;
-            int vi = INT_MAX;
-            if (lane < a.F && (!any_new || a.cand_new[(size_t)i * a.F + lane])) {
-                sc = a.cand_out[(size_t)i * a.F + lane];
+            int vi = screen ? INT_MAX : 0;
+            // candidate f of slot i is row f P + i
+            if (screen && lane < a.F && a.cand_new[(size_t)lane * a.P + i]) {
+                sc = a.cand_out[(size_t)lane * a.P + i];
                 if (isnan(sc)) sc = INFINITY;
                 vi = lane;
             }
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
                     vi = ov;
                 }
             }
-            const size_t c = (size_t)i * a.F + vi;
+            const size_t c = (size_t)vi * a.P + i;
             for (int k = lane; k < K; k += 32) w.y[k] = a.cand_Y[c * K + k];
             if (MACH == kMachGene)
                 for (int k = lane; k < K; k += 32) w.x[k] = a.cand_X[c * K + k];
@@ -297,10 +301,10 @@ __global__ void __launch_bounds__(kRemapThreads) k_warm_remap(WarmArgs a) {
 }
 
 // ---------------------------------------------------------------- surrogate candidates
-// Over-generation for the surrogate: candidate c is one of F children built for population
-// slot c / F with the usual operators and its own stream position; its model input (the
-// within-stage rank features, BF16, zero padded to Kpad) is written beside it.  Nothing is
-// decoded here.
+// Over-generation for the surrogate: candidate c = f P + j is candidate f of population slot
+// j, built with the usual operators from its own stream position (candidate 0 is the plain
+// generation's child); its model input (the within-stage rank features, BF16, zero padded
+// to Kpad) is written beside it.  Nothing is decoded here.
 template <int MACH>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_candidates(GenArgs a) {
     extern __shared__ __align__(128) char smem[];

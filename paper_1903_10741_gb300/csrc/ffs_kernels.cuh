@@ -71,6 +71,7 @@ struct GenArgs {
     uint8_t *cand_new;          // [P*F] 1 if the candidate is an offspring, 0 if a parent's copy
     uint16_t *kept_Yh;          // [P][Kpad] inputs of the kept candidates, for training
     int64_t *kept_obj;          // [P] their exact objectives (before replacement)
+    uint64_t screen_thr;        // an offspring slot takes the model's pick iff its draw < this
     int warm;                   // generation 0 decodes the rows already in Y[0] / X[0]
 };
 

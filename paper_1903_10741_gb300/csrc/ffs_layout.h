@@ -112,5 +112,6 @@ constexpr int kMinBatchSlots = 256;
 
 // Philox stream purposes.
 constexpr uint32_t kPInitY = 1, kPInitX = 2, kPSelect = 3, kPCross = 4, kPMutate = 5;
+constexpr uint32_t kPScreen = 6;  // surrogate: whether an offspring slot takes the model's pick
 
 }  // namespace edffs

@@ -293,14 +293,14 @@ int ffs_tensor_gemm(const void *A, const void *B, int32_t M, int32_t N, int32_t 
 }
 
 int ga_population_attach_surrogate(ga_population *pp, ffs_surrogate *s, int32_t oversample, float lr,
-                                   int32_t train_steps) {
+                                   int32_t train_steps, int32_t screen_permille) {
     if (!pp) return FFS_E_ARG;
     if (!s) {  // detach
         pp->sur = nullptr;
         return FFS_OK;
     }
     if (s->inst != pp->inst || s->version != pp->version || oversample < 1 || oversample > 32 || !(lr > 0.f) ||
-        train_steps < 0 || train_steps > 64 ||
+        train_steps < 0 || train_steps > 64 || screen_permille < 0 || screen_permille > 1000 ||
         (pp->P * oversample) % 128 || s->rows_cap < pp->P || pp->P % 128)
         return FFS_E_ARG;
     const size_t C = (size_t)pp->P * oversample;
@@ -318,6 +318,7 @@ int ga_population_attach_surrogate(ga_population *pp, ffs_surrogate *s, int32_t 
     pp->F = oversample;
     pp->lr = lr;
     pp->train_steps = train_steps;
+    pp->screen_thr = (uint64_t)(uint32_t)screen_permille * ((uint64_t)1 << 32) / 1000u;
     if (pp->graph_sur) {
         cudaGraphExecDestroy(pp->graph_sur);
         pp->graph_sur = nullptr;
@@ -363,6 +364,7 @@ int ffs_rt::surrogate_enqueue_generation(ga_population *pp, cudaStream_t st, cud
     a.cand_new = pp->cand_new;
     a.kept_Yh = reinterpret_cast<uint16_t *>(s->Yh);
     a.kept_obj = pp->kept_obj;
+    a.screen_thr = pp->screen_thr;
     const int C = pp->P * pp->F;
     const int grid_c = std::max(1, std::min((C + kWarpsPerBlock - 1) / kWarpsPerBlock, num_sms() * 8));
     FFS_CUDA(launch_candidates(pp->par.machine_mode, a, pp->hdr, grid_c, st));

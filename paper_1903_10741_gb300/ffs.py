@@ -124,7 +124,7 @@ _SIGS = {
     "ffs_surrogate_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ffs_surrogate_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "ffs_surrogate_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p]),
-    "ga_population_attach_surrogate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_int32]),
+    "ga_population_attach_surrogate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_int32, C.c_int32]),
     "ffs_surrogate_pretrain": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p]),
     "ga_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(GAParams_c), C.POINTER(C.c_void_p)]),
     "ga_batch_destroy": (C.c_int, [C.c_void_p]),
@@ -382,7 +382,7 @@ class Population:
         return d
 
     def attach_surrogate(self, sur, oversample: int = 8, lr: float = 1e-3, train_steps: int = 1,
-                         pretrain_steps: int = 0):
+                         pretrain_steps: int = 0, screen: float = 1.0):
         """Surrogate-assisted generations from now on (None detaches); optionally first
         trains the surrogate on the current population."""
         if sur is not None and pretrain_steps > 0:
@@ -390,7 +390,8 @@ class Population:
             _check(lib().ffs_surrogate_pretrain(sur._h, self._h, int(pretrain_steps), float(lr), C.addressof(loss)),
                    "ffs_surrogate_pretrain")
         _check(lib().ga_population_attach_surrogate(self._h, sur._h if sur is not None else None, int(oversample),
-                                                    float(lr), int(train_steps)), "ga_population_attach_surrogate")
+                                                    float(lr), int(train_steps), int(round(screen * 1000))),
+               "ga_population_attach_surrogate")
         self._sur = sur
 
     def set_profiling(self, enable: bool):
