@@ -21,7 +21,7 @@ _LIB = os.path.join(_LIB_DIR, "libffs_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ST_FREE, ST_EXEC, ST_DONE = 0, 1, 2
+ST_FREE, ST_EXEC, ST_DONE, ST_FIXED = 0, 1, 2, 3
 ORDER_TOPO, ORDER_STAGE, ORDER_GIVEN = 0, 1, 2
 MACH_GENE, MACH_EARLIEST = 0, 1
 
@@ -75,6 +75,7 @@ def lib():
         L.orc_draw.restype = C.c_uint32
         L.orc_draw.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]
         L.orc_classify.argtypes = [C.c_int32, C.c_int32, _i32p, _i32p, C.c_int32, _i32p]
+        L.orc_classify_static.argtypes = [C.c_int32, C.c_int32, _i32p, _i32p, C.c_int32, _i32p]
         L.orc_gene_count.restype = C.c_int32
         L.orc_gene_count.argtypes = [C.POINTER(_Inst)]
         L.orc_gene_map.argtypes = [C.POINTER(_Inst), _i32p, _i32p]
@@ -192,12 +193,15 @@ class Instance:
         self.S0 = np.ascontiguousarray(S, dtype=np.int32).copy()
         self.M0 = np.ascontiguousarray(M, dtype=np.int32).copy()
 
-    def reschedule(self, arrivals, t_now: int):
-        """Freeze at t_now using the committed plan (Alg. 1), append the new jobs."""
+    def reschedule(self, arrivals, t_now: int, static: bool = False):
+        """Freeze at t_now using the committed plan (Alg. 1), append the new jobs.  With
+        ``static``, the traditional static approach: every op of the plan not yet completed
+        keeps its start and machine, and only the new jobs are scheduled."""
         if t_now < self.RS:
             raise ValueError("t_now must not precede the previous rescheduling point")
         st = np.zeros_like(self.status)
-        lib().orc_classify(self.N, self.g, _p32(self.p), _p32(self.S0), int(t_now), _p32(st))
+        fn = lib().orc_classify_static if static else lib().orc_classify
+        fn(self.N, self.g, _p32(self.p), _p32(self.S0), int(t_now), _p32(st))
         n = arrivals.n
         g = self.g
         self.status = np.concatenate([st, np.zeros((n, g), np.int32)])

@@ -24,7 +24,7 @@
 
 /* ---------------------------------------------------------------- constants */
 
-enum { ST_FREE = 0, ST_EXEC = 1, ST_DONE = 2 };           /* Alg. 1 classification  */
+enum { ST_FREE = 0, ST_EXEC = 1, ST_DONE = 2, ST_FIXED = 3 };  /* Alg. 1 classification; FIXED: static approach */
 enum { ORDER_TOPO = 0, ORDER_STAGE = 1, ORDER_GIVEN = 2 };  /* how Z is built         */
 enum { MACH_GENE = 0, MACH_EARLIEST = 1 };                  /* how M_js is chosen     */
 enum { P_INIT_Y = 1, P_INIT_X = 2, P_SELECT = 3, P_CROSS = 4, P_MUTATE = 5 };
@@ -93,7 +93,7 @@ typedef struct {
     const int32_t *p;       /* [N*g]    processing time (identical machines)      */
     const int32_t *q;       /* [sum o]  power of each machine, stage-major        */
     const int32_t *R, *D;   /* [N]      release and due times                     */
-    const int32_t *status;  /* [N*g]    ST_FREE / ST_EXEC / ST_DONE               */
+    const int32_t *status;  /* [N*g]    ST_FREE / ST_EXEC / ST_DONE / ST_FIXED    */
     const int32_t *S0;      /* [N*g]    committed start of frozen ops             */
     const int32_t *M0;      /* [N*g]    committed stage-local machine of frozen ops */
 } orc_inst;
@@ -127,6 +127,18 @@ void orc_classify(int32_t N, int32_t g, const int32_t *p, const int32_t *S, int3
                 status_out[k] = ST_FREE;
         }
     }
+}
+
+/* The traditional static approach (Sec. 4.1, Fig. 7; Sec. 5.3): the executed plan is kept.
+ * S + P <= RS: completed; S < RS < S + P: being executed; S >= RS: fixed, i.e. it keeps its
+ * planned start and machine and draws power over [S, S + P).  Only new jobs are free. */
+void orc_classify_static(int32_t N, int32_t g, const int32_t *p, const int32_t *S, int32_t RS,
+                         int32_t *status_out)
+{
+    orc_classify(N, g, p, S, RS, status_out);
+    for (int32_t k = 0; k < N * g; k++)
+        if (status_out[k] == ST_FREE)
+            status_out[k] = ST_FIXED;
 }
 
 /* Number of free ops (genes) K = g(n+n') - r, Sec. 4.3. */
@@ -220,7 +232,7 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
         if (in->R[j] > base) base = in->R[j];
         for (int32_t s = 0; s < g; s++) {
             int32_t k = j * g + s;
-            if (in->status[k] == ST_EXEC && in->S0[k] + in->p[k] > base)
+            if ((in->status[k] == ST_EXEC || in->status[k] == ST_FIXED) && in->S0[k] + in->p[k] > base)
                 base = in->S0[k] + in->p[k];
             if (in->status[k] == ST_FREE)
                 work += in->p[k];
@@ -243,10 +255,11 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
             C[j] = end;                                   /* frozen ops are a prefix */
             S_out[k] = in->S0[k];
             M_out[k] = in->M0[k];
-            if (in->status[k] == ST_EXEC) {               /* keeps running past RS */
+            if (in->status[k] == ST_EXEC || in->status[k] == ST_FIXED) {  /* draws power past RS */
                 int32_t mg = moff[s] + in->M0[k];
                 if (end > mfree[mg]) mfree[mg] = end;
-                for (int32_t t = RS; t < end; t++)
+                int32_t from = in->S0[k] > RS ? in->S0[k] : RS;
+                for (int32_t t = from; t < end; t++)
                     Qt[t - RS] += in->q[mg];
             }
         }

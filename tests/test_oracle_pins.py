@@ -481,3 +481,102 @@ def test_ga_init_from_random_rows_equals_init():
     a.step(4)
     b.step(4)
     assert np.array_equal(a.Y, b.Y) and np.array_equal(a.bobj, b.bobj)
+
+
+# ---------------------------------------------------------------- static approach (Sec. 5.3)
+
+def _worked_example_static():
+    ex = json.load(open(os.path.join(GOLDEN, "worked_example.json")))
+    n0 = ex["n_original"]
+    pst = np.array(ex["p_per_stage"])
+    prob = wl.Problem(o=ex["o"], p=np.tile(pst, (n0, 1)), q=np.full(sum(ex["o"]), ex["q"]),
+                      R=ex["R"][:n0], D=np.full(n0, 10**6), Qmax=ex["Qmax"], WT=ex["WT"])
+    inst = oracle.Instance(prob)
+    inst.commit(np.array(ex["S_original"]), np.array(ex["M_original"]))
+    n1 = len(ex["R"]) - n0
+    inst.reschedule(wl.Arrivals(p=np.tile(pst, (n1, 1)), R=ex["R"][n0:], D=[10**6] * n1), ex["RS"], static=True)
+    return ex, inst
+
+
+def _check_static(inst, S, M):
+    """The plan is kept; every new op follows the last planned op of its machine."""
+    N, g = inst.p.shape
+    frozen = inst.status != oracle.ST_FREE
+    assert np.array_equal(S[frozen], inst.S0[frozen]) and np.array_equal(M[frozen], inst.M0[frozen])
+    for s in range(g):
+        for m in range(inst.o[s]):
+            last = max([int(inst.S0[j, s] + inst.p[j, s]) for j in range(N)
+                        if frozen[j, s] and inst.M0[j, s] == m] + [inst.RS])
+            for j in range(N):
+                if not frozen[j, s] and M[j, s] == m:
+                    assert S[j, s] >= last, (j, s, m)
+
+
+def test_static_worked_example_fig7():
+    """Fig. 7 (static environment) on Table 4 at RS = 7: the original plan is kept, jobs 6
+    and 7 are the only genes, and the best makespan over every order and machine choice
+    of their six ops is 19.91, the figure's C_max (Fig. 8's reactive schedule has 20.42)."""
+    ex, inst = _worked_example_static()
+    assert inst.K == 6
+    assert (inst.status[:6] != oracle.ST_FREE).all() and (inst.status[6:] == oracle.ST_FREE).all()
+    # ops not yet completed at RS are being executed (Z = 0 cells) or fixed in the plan
+    Z = ex["Z_printed"]
+    for j in range(6):
+        for s in range(3):
+            want = oracle.ST_DONE if Z[j][s] == "C" else oracle.ST_EXEC if Z[j][s] == 0 else oracle.ST_FIXED
+            assert inst.status[j, s] == want, (j, s)
+    best = None
+    for perm in itertools.permutations(range(1, 7)):
+        y = np.array(perm, np.int16)
+        for xm in range(64):
+            x = np.array([(xm >> k) & 1 for k in range(6)], np.int8)
+            r = inst.decode(y, x, ORDER_STAGE, MACH_GENE)
+            best = r["cmax"] if best is None else min(best, r["cmax"])
+        r = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST)
+        assert r["cmax"] == 1991
+    assert best == 1991
+    check_invariants(inst, r["S"], r["M"], obj=r["obj"], tard=r["tard"], cmax=r["cmax"])
+    _check_static(inst, r["S"], r["M"])
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_static_chain_invariants(seed):
+    """Static rescheduling chains on random instances: schedules satisfy Eq. (4)-(10), the
+    kept plan never moves, and new ops follow each machine's last planned op."""
+    rng = np.random.default_rng(seed)
+    pr = wl.random_instance(rng, 10, 3, 1, 3, 20, 5, 20, 55)
+    inst = oracle.Instance(pr)
+    ga = oracle.GA(inst, P=32, island=16, seed=seed, mach_mode=MACH_GENE).init().step(3)
+    y, x, _ = ga.best()
+    r = inst.decode(y, x, mach_mode=MACH_GENE)
+    inst.commit(r["S"], r["M"])
+    t_now = 0
+    for ev in range(3):
+        t_now = t_now + max(1, r["cmax"] // 5)
+        inst.reschedule(wl.random_arrivals(rng, 3, 3, t_now, 20), t_now, static=True)
+        assert inst.K == 9  # only the new jobs are genes
+        yy = rng.permutation(inst.K).astype(np.int16) + 1
+        for mode in (MACH_EARLIEST, MACH_GENE):
+            xx = (rng.random(inst.K) * inst.gene_machines()).astype(np.int8)
+            r = inst.decode(yy, xx, ORDER_STAGE, mode)
+            check_invariants(inst, r["S"], r["M"], obj=r["obj"], tard=r["tard"], cmax=r["cmax"])
+            _check_static(inst, r["S"], r["M"])
+        inst.commit(r["S"], r["M"])
+
+
+def test_static_equals_reactive_without_plan_left():
+    """When every op of the plan has completed by RS, nothing is kept and the two
+    approaches give the same instance: the same genes and the same decoded schedules."""
+    rng = np.random.default_rng(4)
+    pr = wl.random_instance(rng, 8, 3, 1, 2, 20, 5, 20, 60)
+    a, b = oracle.Instance(pr), oracle.Instance(pr)
+    y = (rng.permutation(a.K) + 1).astype(np.int16)
+    r = a.decode(y)
+    for inst in (a, b):
+        inst.commit(r["S"], r["M"])
+    arr = wl.random_arrivals(rng, 4, 3, r["cmax"], 20)
+    a.reschedule(arr, r["cmax"])
+    b.reschedule(arr, r["cmax"], static=True)
+    assert np.array_equal(a.status, b.status) and a.K == b.K == 12
+    y2 = (rng.permutation(a.K) + 1).astype(np.int16)
+    assert a.decode(y2)["obj"] == b.decode(y2)["obj"]
