@@ -434,6 +434,60 @@ def bench_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- static vs reactive
+SVR_WORKLOAD = ("reactive vs traditional static rescheduling (Sec. 5.3, Table 10 analogue): the Test 3 setting of "
+                "Sec. 5 and Table 5 -- 10 jobs, 3 stages x 2 identical machines, p U[1,5], unit power, peak 4, "
+                "R U[0,Pbar], D = R + Pbar(1+U[0,2]), times on a 1/100 grid; a plan optimised by G generations is "
+                "interrupted at RS = ratio x its makespan by round(ratio x 10) new jobs (R = RS + U[0,Pbar]); each "
+                "arm then runs G generations; population 4096 (islands of 64), tournament 2, pc 0.9, pm 0.1; "
+                "objective (Eq. 1) averaged over the seeds")
+
+
+def bench_static_vs_reactive(args):
+    import torch
+
+    from paper_1903_10741_gb300 import ffs
+
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    G, Ps = args.generations, 4096
+    kw = dict(P=Ps, island=ISLAND, tour_k=TOUR_K, pc=(9, 10), pm=(1, 10), migrate_every=MIGRATE, seed=SEED)
+    rows, decodes = [], 0
+    t0 = time.perf_counter()
+    for ratio in (20, 40, 60, 80):
+        obj = {"static": [], "reactive": [], "reactive_warm": []}
+        for seed in range(1, args.svr_seeds + 1):
+            prob = wl.table5_instance(10, 3, 2, 4, seed=seed)
+            for arm in obj:
+                inst = ffs.Instance(prob)
+                plan = ffs.Population(inst, **kw, instance_id=0)
+                r0 = plan.run(G)  # the original plan, committed
+                rs = ratio * r0["cmax"] // 100
+                arr = wl.table5_arrivals(np.random.default_rng(1000 * ratio + seed), (ratio * prob.N + 50) // 100,
+                                         prob.g, rs)
+                inst.reschedule(arr, rs, static=arm == "static")
+                pop = ffs.Population(inst, **kw, instance_id=1, prev=plan if arm == "reactive_warm" else None)
+                obj[arm].append(pop.run(G)["obj"])
+                decodes += 2 * (Ps * (G + 1) + 1)
+        m = {k: float(np.mean(v)) for k, v in obj.items()}
+        rows.append({"ratio_pct": ratio, **m, "static_over_reactive": m["static"] / m["reactive"],
+                     "static_over_reactive_warm": m["static"] / m["reactive_warm"]})
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    line = {
+        "metric": "objective ratio, traditional static / predictive-reactive (Table 10 analogue)",
+        "value": rows[0]["static_over_reactive_warm"], "unit": "ratio at RS = 20% of the makespan, warm reactive",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": SVR_WORKLOAD, "generations": G, "seeds": args.svr_seeds, "rows": rows,
+                   "arms": "static: plan kept, new jobs appended (ffs_reschedule_static); reactive: complete "
+                           "rescheduling from a random population (the paper's); reactive_warm: complete "
+                           "rescheduling from the plan's population carried over (ga_population_create_warm)",
+                   "paper_table10_improvement": {"20": 2.28, "40": 1.50, "60": 1.17, "80": 1.01},
+                   "note": "paper values are for its own instance (K40 runs); shown for the trend only"},
+        "decodes_per_s": decodes / wall, "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # Slot checks per decode of the batched workload, measured by the oracle (python -m
 # oracle.work_per_decode --workload batched --samples 8): mean over the 256 rescheduling
 # snapshots of 8 uniformly random chromosomes each (min 6038, max 392743 per instance).
@@ -580,11 +634,13 @@ def main():
     ap.add_argument("--ref-generations", type=int, default=2, help="oracle generations per reference step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["dynamic", "batched", "surrogate", "service"], default="dynamic",
+    ap.add_argument("--workload", choices=["dynamic", "batched", "surrogate", "service", "static-vs-reactive"],
+                    default="dynamic",
                     help="dynamic: the headline rescheduling job; batched: 256 uneven instances; "
                          "surrogate: time-to-objective of the surrogate-assisted GA; service: Poisson "
                          "rescheduling requests through the continuous-batching service")
     ap.add_argument("--service-requests", type=int, default=48)
+    ap.add_argument("--svr-seeds", type=int, default=20, help="instances per ratio (static-vs-reactive)")
     ap.add_argument("--rate", type=float, default=50.0, help="service request arrival rate (1/s)")
     ap.add_argument("--max-active", type=int, default=8, help="service requests on the device at once")
     ap.add_argument("--service-memory-gb", type=float, default=32.0)
@@ -613,6 +669,10 @@ def main():
         if args.generations == 500:
             args.generations = 1000
         bench_surrogate(args)
+    elif args.workload == "static-vs-reactive":
+        if args.generations == 500:
+            args.generations = 100
+        bench_static_vs_reactive(args)
     elif args.workload == "service":
         if args.generations == 500:
             args.generations = 200

@@ -127,7 +127,7 @@ int ffs_instance_info(const ffs_instance *inst, ffs_info *info);
 int ffs_instance_genes(const ffs_instance *inst, int32_t *gene_job, int32_t *gene_stage);
 
 /* Per-op status at the current rescheduling point: host [n][g], 0 free, 1 being executed,
- * 2 completed (Alg. 1, first branch). */
+ * 2 completed (Alg. 1, first branch), 3 fixed in the kept plan (ffs_reschedule_static). */
 int ffs_instance_status(const ffs_instance *inst, int32_t *status);
 
 /* Makes (start, machine) -- host [n][g], stage-local machines -- the plan being executed.
@@ -141,6 +141,14 @@ int ffs_commit(ffs_instance *inst, const int32_t *start, const int32_t *machine)
  * the previous rescheduling point (FFS_E_ARG); a plan must have been committed unless
  * every op is still free at t_now (FFS_E_STATE). */
 int ffs_reschedule(ffs_instance *inst, const ffs_arrivals *arrivals, int32_t t_now);
+
+/* The traditional static approach of Sec. 4.1 (Fig. 7) and Sec. 5.3 (Table 10), as the
+ * comparison for ffs_reschedule: at t_now, ops of the committed plan that completed are
+ * done and those running are being executed, as in Alg. 1; every other op of the plan is
+ * fixed (status 3): it keeps its planned start and machine and draws its power over
+ * [S, S + P).  Only the new jobs are genes, and each of their ops starts after the last
+ * planned op of its machine.  Arguments and errors as ffs_reschedule. */
+int ffs_reschedule_static(ffs_instance *inst, const ffs_arrivals *arrivals, int32_t t_now);
 
 /* ---------------------------------------------------------------- decoding */
 

@@ -18,6 +18,7 @@ struct uint2 { unsigned int x, y; };
 namespace edffs {
 
 constexpr int kStFree = 0, kStExec = 1, kStDone = 2;  // Alg. 1 classification
+constexpr int kStFixed = 3;  // static approach: a planned op kept at its start and machine
 
 // Header at the start of the table blob.  Offsets are bytes from the blob start, each a
 // multiple of 16 so the whole blob is one cp.async.bulk copy.

@@ -78,7 +78,7 @@ int rebuild(ffs_instance *in) {
             } else {
                 const int end = in->S0[k] + in->p[k];
                 C0[j] = end;  // frozen ops form a prefix of the job's stages
-                if (in->status[k] == kStExec) {
+                if (in->status[k] == kStExec || in->status[k] == kStFixed) {  // draws power past RS
                     const int mg = in->moff[s] + in->M0[k];
                     mfree0[mg] = std::max(mfree0[mg], end);
                     exec_end = std::max<long long>(exec_end, end);
@@ -98,9 +98,10 @@ int rebuild(ffs_instance *in) {
     for (int j = 0; j < N; ++j)
         for (int s = 0; s < g; ++s) {
             const int k = j * g + s;
-            if (in->status[k] != kStExec) continue;
+            if (in->status[k] != kStExec && in->status[k] != kStFixed) continue;
             const int q = in->q[in->moff[s] + in->M0[k]];
-            for (int t = RS; t < in->S0[k] + in->p[k]; ++t) h0[t - RS] = (uint16_t)(h0[t - RS] - q);
+            for (int t = std::max(RS, in->S0[k]); t < in->S0[k] + in->p[k]; ++t)
+                h0[t - RS] = (uint16_t)(h0[t - RS] - q);
         }
 
     TabHeader h{};
@@ -390,7 +391,14 @@ int ffs_commit(ffs_instance *in, const int32_t *start, const int32_t *machine) {
     return FFS_OK;
 }
 
-int ffs_reschedule(ffs_instance *in, const ffs_arrivals *arr, int32_t t_now) {
+}  // extern "C"
+
+namespace {
+
+// Alg. 1 at t_now against the committed plan, then the new jobs appended.  static_plan:
+// ops that have not started keep their start and machine (the traditional static
+// approach) instead of becoming free.
+int reschedule_impl(ffs_instance *in, const ffs_arrivals *arr, int32_t t_now, bool static_plan) {
     if (!in || t_now < in->RS) return FFS_E_ARG;
     const int n1 = arr ? arr->job_count : 0;
     if (n1 < 0 || in->N + n1 > kMaxN || (n1 > 0 && (!arr->proc || !arr->release || !arr->due))) return FFS_E_ARG;
@@ -401,10 +409,12 @@ int ffs_reschedule(ffs_instance *in, const ffs_arrivals *arr, int32_t t_now) {
     if (!in->has_plan && t_now != in->RS) return FFS_E_STATE;
     const int g = in->g;
     if (in->has_plan) {
-        // Alg. 1: S + P <= RS completed, S < RS < S + P being executed, otherwise free.
+        // Alg. 1: S + P <= RS completed, S < RS < S + P being executed, otherwise free
+        // (or, in the static approach, fixed in the plan).
+        const int later = static_plan ? kStFixed : kStFree;
         for (int i = 0; i < in->N * g; ++i) {
             const int st = in->S0[i], en = in->S0[i] + in->p[i];
-            in->status[i] = en <= t_now ? kStDone : st < t_now ? kStExec : kStFree;
+            in->status[i] = en <= t_now ? kStDone : st < t_now ? kStExec : later;
         }
     }
     for (int j = 0; j < n1; ++j) {
@@ -421,6 +431,18 @@ int ffs_reschedule(ffs_instance *in, const ffs_arrivals *arr, int32_t t_now) {
     in->RS = t_now;
     in->has_plan = false;
     return rebuild(in);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ffs_reschedule(ffs_instance *in, const ffs_arrivals *arr, int32_t t_now) {
+    return reschedule_impl(in, arr, t_now, false);
+}
+
+int ffs_reschedule_static(ffs_instance *in, const ffs_arrivals *arr, int32_t t_now) {
+    return reschedule_impl(in, arr, t_now, true);
 }
 
 int ffs_decode(ffs_instance *in, int32_t order_mode, int32_t machine_mode, const int16_t *y,

@@ -17,7 +17,7 @@ from . import build as _build
 FFS_OK = 0
 ORDER_TOPO, ORDER_STAGE = 0, 1
 MACH_GENE, MACH_EARLIEST = 0, 1
-ST_FREE, ST_EXEC, ST_DONE = 0, 1, 2
+ST_FREE, ST_EXEC, ST_DONE, ST_FIXED = 0, 1, 2, 3
 
 _i32p = C.POINTER(C.c_int32)
 _lib = None
@@ -93,6 +93,7 @@ _SIGS = {
     "ffs_instance_status": (C.c_int, [C.c_void_p, _i32p]),
     "ffs_commit": (C.c_int, [C.c_void_p, _i32p, _i32p]),
     "ffs_reschedule": (C.c_int, [C.c_void_p, C.POINTER(Arrivals_c), C.c_int32]),
+    "ffs_reschedule_static": (C.c_int, [C.c_void_p, C.POINTER(Arrivals_c), C.c_int32]),
     "ffs_decode": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ffs_decode_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
@@ -246,10 +247,13 @@ class Instance:
         S, M = _i32(S), _i32(M)
         _check(lib().ffs_commit(self._h, _p(S), _p(M)), "ffs_commit")
 
-    def reschedule(self, arrivals, t_now: int):
+    def reschedule(self, arrivals, t_now: int, static: bool = False):
+        """Rescheduling point t_now with new jobs (Sec. 4.1); ``static`` keeps the executed
+        plan and schedules only the new jobs after it (``ffs_reschedule_static``)."""
         p, R, D = _i32(arrivals.p), _i32(arrivals.R), _i32(arrivals.D)
         a = Arrivals_c(int(p.shape[0]), _p(p), _p(R), _p(D))
-        _check(lib().ffs_reschedule(self._h, C.byref(a), int(t_now)), "ffs_reschedule")
+        fn = lib().ffs_reschedule_static if static else lib().ffs_reschedule
+        _check(fn(self._h, C.byref(a), int(t_now)), "ffs_reschedule_static" if static else "ffs_reschedule")
 
     def decode(self, y, x=None, order_mode=ORDER_STAGE, mach_mode=MACH_EARLIEST, stream=None,
                schedule=False, check=True):

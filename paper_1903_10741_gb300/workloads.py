@@ -270,6 +270,17 @@ def table5_instance(n: int, g: int, o: int, qmax: int, seed: int = 1, scale: int
     return Problem(o=o_arr, p=p, q=q, R=R, D=D, Qmax=qmax, WT=WT_DEFAULT)
 
 
+def table5_arrivals(rng: np.random.Generator, n: int, g: int, t_now: int, scale: int = 100) -> Arrivals:
+    """New jobs for a Table 5 instance at rescheduling point t_now: p ~ U[1, 5] per stage,
+    R = t_now + U[0, Pbar], D = R + Pbar (1 + sigma), sigma ~ U[0, 2], on the same 1/scale
+    grid as table5_instance."""
+    p = np.rint(rng.uniform(1, 5, size=(n, g)) * scale).astype(np.int64)
+    pbar = p.sum(axis=1)
+    R = t_now + np.rint(rng.uniform(0, 1, size=n) * pbar).astype(np.int64)
+    D = R + np.rint(pbar * (1 + rng.uniform(0, 2, size=n))).astype(np.int64)
+    return Arrivals(p=p, R=R, D=D)
+
+
 def random_chromosomes(rng: np.random.Generator, count: int, K: int, gene_machines: np.ndarray):
     """``count`` random chromosomes over K genes: Y rows are permutations of 1..K
     (int16), X rows are uniform machine indices below ``gene_machines[k]`` (int8)."""

@@ -75,6 +75,30 @@ def test_reschedule_chain_matches_oracle(seed):
         assert inf["rs"] == t_now and inf["n_jobs"] == orc_i.N and inf["n_genes"] == orc_i.K
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_static_reschedule_chain_matches_oracle(seed):
+    """The static approach's classification (completed / executing / fixed) and gene
+    numbering (new jobs only) on the library's host side equal the oracle's."""
+    dyn = wl.dynamic_medium(seed + 1)
+    lib_i, orc_i = _pair(dyn.problem)
+    rng = np.random.default_rng(seed)
+    for t_now, arr in dyn.events:
+        y = rng.permutation(orc_i.K) + 1
+        r = orc_i.decode(y, None, oracle.ORDER_STAGE, oracle.MACH_EARLIEST)
+        orc_i.commit(r["S"], r["M"])
+        lib_i.commit(r["S"], r["M"])
+        orc_i.reschedule(arr, t_now, static=True)
+        lib_i.reschedule(arr, t_now, static=True)
+        assert np.array_equal(lib_i.status(), orc_i.status)
+        assert (orc_i.status == oracle.ST_FIXED).any()
+        gj, gs = lib_i.genes()
+        ogj, ogs = orc_i.gene_map()
+        assert np.array_equal(gj, ogj) and np.array_equal(gs, ogs) and orc_i.K == arr.n * dyn.problem.g
+        inf = lib_i.info()
+        # the bound covers the kept plan's end plus every new op back to back
+        assert inf["horizon"] >= int((orc_i.S0 + orc_i.p)[orc_i.status == oracle.ST_FIXED].max()) - t_now
+
+
 def test_reschedule_rules():
     lib_i = ffs.Instance(wl.static_small(1))
     arr = wl.Arrivals(p=np.ones((1, 3)), R=[5], D=[50])
