@@ -31,7 +31,8 @@ _i32p = C.POINTER(C.c_int32)
 class _Inst(C.Structure):
     _fields_ = [("N", C.c_int32), ("g", C.c_int32), ("Qmax", C.c_int32), ("WT", C.c_int32),
                 ("RS", C.c_int32), ("o", _i32p), ("p", _i32p), ("q", _i32p), ("R", _i32p),
-                ("D", _i32p), ("status", _i32p), ("S0", _i32p), ("M0", _i32p)]
+                ("D", _i32p), ("status", _i32p), ("S0", _i32p), ("M0", _i32p), ("pm", _i32p),
+                ("qm", _i32p)]
 
 
 class _Eval(C.Structure):
@@ -134,6 +135,10 @@ class Instance:
         self.Qmax = int(problem.Qmax)
         self.WT = int(problem.WT)
         self.RS = 0
+        # unrelated machines (Table 2): P_jsm and Q_jsm per job and global machine, or None
+        pm, qm = getattr(problem, "pm", None), getattr(problem, "qm", None)
+        self.pm = None if pm is None else np.ascontiguousarray(pm, dtype=np.int32)
+        self.qm = None if qm is None else np.ascontiguousarray(qm, dtype=np.int32)
         N, g = self.p.shape
         self.status = np.zeros((N, g), dtype=np.int32)
         self.S0 = np.zeros((N, g), dtype=np.int32)
@@ -152,8 +157,27 @@ class Instance:
             setattr(self, name, np.ascontiguousarray(getattr(self, name), dtype=np.int32))
         s = _Inst(self.N, self.g, self.Qmax, self.WT, self.RS, _p32(self.o), _p32(self.p),
                   _p32(self.q), _p32(self.R), _p32(self.D), _p32(self.status), _p32(self.S0),
-                  _p32(self.M0))
+                  _p32(self.M0), None if self.pm is None else _p32(self.pm),
+                  None if self.qm is None else _p32(self.qm))
         return s
+
+    @property
+    def moff(self):
+        return np.concatenate([[0], np.cumsum(self.o)]).astype(np.int64)
+
+    def plan_durations(self):
+        """[N, g] duration of every op on its committed machine (P_jsm of M0)."""
+        if self.pm is None:
+            return self.p
+        mg = self.moff[:-1][None, :] + self.M0
+        return np.take_along_axis(self.pm, mg, axis=1).astype(np.int32)
+
+    def plan_powers(self):
+        """[N, g] power of every op on its committed machine."""
+        mg = self.moff[:-1][None, :] + self.M0
+        if self.qm is None:
+            return self.q[mg]
+        return np.take_along_axis(self.qm, mg, axis=1).astype(np.int32)
 
     @property
     def K(self) -> int:
@@ -201,13 +225,18 @@ class Instance:
             raise ValueError("t_now must not precede the previous rescheduling point")
         st = np.zeros_like(self.status)
         fn = lib().orc_classify_static if static else lib().orc_classify
-        fn(self.N, self.g, _p32(self.p), _p32(self.S0), int(t_now), _p32(st))
+        dur = np.ascontiguousarray(self.plan_durations(), dtype=np.int32)
+        fn(self.N, self.g, _p32(dur), _p32(self.S0), int(t_now), _p32(st))
         n = arrivals.n
         g = self.g
         self.status = np.concatenate([st, np.zeros((n, g), np.int32)])
         self.S0 = np.concatenate([self.S0, np.zeros((n, g), np.int32)])
         self.M0 = np.concatenate([self.M0, np.zeros((n, g), np.int32)])
         self.p = np.concatenate([self.p, arrivals.p.astype(np.int32)])
+        if self.pm is not None:
+            self.pm = np.concatenate([self.pm, np.asarray(arrivals.pm, np.int32)])
+        if self.qm is not None:
+            self.qm = np.concatenate([self.qm, np.asarray(arrivals.qm, np.int32)])
         self.R = np.concatenate([self.R, arrivals.R.astype(np.int32)])
         self.D = np.concatenate([self.D, arrivals.D.astype(np.int32)])
         self.RS = int(t_now)

@@ -96,7 +96,21 @@ typedef struct {
     const int32_t *status;  /* [N*g]    ST_FREE / ST_EXEC / ST_DONE / ST_FIXED    */
     const int32_t *S0;      /* [N*g]    committed start of frozen ops             */
     const int32_t *M0;      /* [N*g]    committed stage-local machine of frozen ops */
+    const int32_t *pm;      /* [N][sum o] P_jsm on every machine (unrelated machines), or NULL */
+    const int32_t *qm;      /* [N][sum o] Q_jsm on every machine, or NULL               */
 } orc_inst;
+
+/* Processing time and power of job j's op at stage s on global machine mg (Table 2:
+ * P_jsm and Q_jsm); without the per-machine tables, p of the op and q of the machine. */
+static int32_t op_p(const orc_inst *in, int32_t j, int32_t s, int32_t mg, int32_t Mtot)
+{
+    return in->pm ? in->pm[(size_t)j * Mtot + mg] : in->p[j * in->g + s];
+}
+
+static int32_t op_q(const orc_inst *in, int32_t j, int32_t mg, int32_t Mtot)
+{
+    return in->qm ? in->qm[(size_t)j * Mtot + mg] : in->q[mg];
+}
 
 typedef struct {
     int64_t obj;      /* WT * sum T_j + C_max, Eq. (1)                 */
@@ -232,10 +246,18 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
         if (in->R[j] > base) base = in->R[j];
         for (int32_t s = 0; s < g; s++) {
             int32_t k = j * g + s;
-            if ((in->status[k] == ST_EXEC || in->status[k] == ST_FIXED) && in->S0[k] + in->p[k] > base)
-                base = in->S0[k] + in->p[k];
-            if (in->status[k] == ST_FREE)
-                work += in->p[k];
+            if (in->status[k] == ST_EXEC || in->status[k] == ST_FIXED) {
+                int32_t e = in->S0[k] + op_p(in, j, s, moff[s] + in->M0[k], Mtot);
+                if (e > base) base = e;
+            }
+            if (in->status[k] == ST_FREE) {  /* the longest of its machines */
+                int32_t pmax = 0;
+                for (int32_t m = 0; m < in->o[s]; m++) {
+                    int32_t v = op_p(in, j, s, moff[s] + m, Mtot);
+                    if (v > pmax) pmax = v;
+                }
+                work += pmax;
+            }
         }
     }
     const int64_t H = base - RS + work + 1;
@@ -251,7 +273,7 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
             int32_t k = j * g + s;
             if (in->status[k] == ST_FREE)
                 continue;
-            int32_t end = in->S0[k] + in->p[k];
+            int32_t end = in->S0[k] + op_p(in, j, s, moff[s] + in->M0[k], Mtot);
             C[j] = end;                                   /* frozen ops are a prefix */
             S_out[k] = in->S0[k];
             M_out[k] = in->M0[k];
@@ -259,8 +281,9 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
                 int32_t mg = moff[s] + in->M0[k];
                 if (end > mfree[mg]) mfree[mg] = end;
                 int32_t from = in->S0[k] > RS ? in->S0[k] : RS;
+                int32_t qv = op_q(in, j, mg, Mtot);
                 for (int32_t t = from; t < end; t++)
-                    Qt[t - RS] += in->q[mg];
+                    Qt[t - RS] += qv;
             }
         }
     }
@@ -310,7 +333,7 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
     for (int32_t n = 0; n < K && !ev->err; n++) {
         int32_t k = order[n];
         if (k < 0 || k >= K || placed[k]) { ev->err = -3; break; }
-        int32_t j = gjob[k], s = gstg[k], pj = in->p[j * g + s];
+        int32_t j = gjob[k], s = gstg[k];
         if (s > 0 && in->status[j * g + s - 1] == ST_FREE && !placed[gene_at[j * g + s - 1]]) {
             ev->err = -4;                                /* order breaks stage precedence */
             break;
@@ -319,9 +342,11 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
         int32_t mlo = 0, mhi = in->o[s];
         if (mach_mode == MACH_GENE) { mlo = x[k]; mhi = x[k] + 1; }
 
-        int32_t best_t = -1, best_m = -1, best_t0 = 0;
+        /* the machine with the earliest completion (with identical machines: the earliest
+         * start), ties to the lowest machine */
+        int32_t best_t = -1, best_m = -1, best_t0 = 0, best_p = 0;
         for (int32_t m = mlo; m < mhi; m++) {
-            int32_t mg = moff[s] + m, qm = in->q[mg];
+            int32_t mg = moff[s] + m, qm = op_q(in, j, mg, Mtot), pj = op_p(in, j, s, mg, Mtot);
             int32_t t0 = max32(est, mfree[mg]);
             int32_t t = t0;
             for (;;) {
@@ -335,11 +360,11 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
                 t = bad + 1;                             /* delayed past the violation */
             }
             ev->slots += (int64_t)(t - t0) + pj;
-            if (best_m < 0 || t < best_t) { best_t = t; best_m = m; best_t0 = t0; }
+            if (best_m < 0 || t + pj < best_t + best_p) { best_t = t; best_m = m; best_t0 = t0; best_p = pj; }
         }
-        int32_t mg = moff[s] + best_m;
+        int32_t mg = moff[s] + best_m, pj = best_p, qb = op_q(in, j, mg, Mtot);
         for (int32_t tau = best_t; tau < best_t + pj; tau++)
-            Qt[tau - RS] += in->q[mg];
+            Qt[tau - RS] += qb;
         mfree[mg] = best_t + pj;
         C[j] = best_t + pj;
         S_out[j * g + s] = best_t;

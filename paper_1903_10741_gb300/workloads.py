@@ -33,6 +33,8 @@ class Problem:
     D: np.ndarray            # [N] due times
     Qmax: int                # peak power limit (Eq. 7)
     WT: int = WT_DEFAULT     # weight of total tardiness (Eq. 1)
+    pm: np.ndarray = None    # [N, sum(o)] P_jsm per machine (unrelated machines), or None
+    qm: np.ndarray = None    # [N, sum(o)] Q_jsm per machine, or None (then q per machine)
 
     def __post_init__(self):
         self.o = np.ascontiguousarray(self.o, dtype=np.int32)
@@ -42,6 +44,9 @@ class Problem:
         self.D = np.ascontiguousarray(self.D, dtype=np.int32)
         self.Qmax = int(self.Qmax)
         self.WT = int(self.WT)
+        if self.pm is not None:
+            self.pm = np.ascontiguousarray(self.pm, dtype=np.int32)
+            self.qm = np.ascontiguousarray(self.qm, dtype=np.int32)
 
     @property
     def N(self) -> int:
@@ -63,11 +68,16 @@ class Arrivals:
     p: np.ndarray  # [n', g]
     R: np.ndarray  # [n']
     D: np.ndarray  # [n']
+    pm: np.ndarray = None  # [n', sum(o)] P_jsm per machine (unrelated machines), or None
+    qm: np.ndarray = None  # [n', sum(o)] Q_jsm per machine, or None
 
     def __post_init__(self):
         self.p = np.ascontiguousarray(self.p, dtype=np.int32)
         self.R = np.ascontiguousarray(self.R, dtype=np.int32)
         self.D = np.ascontiguousarray(self.D, dtype=np.int32)
+        if self.pm is not None:
+            self.pm = np.ascontiguousarray(self.pm, dtype=np.int32)
+            self.qm = np.ascontiguousarray(self.qm, dtype=np.int32)
 
     @property
     def n(self) -> int:
@@ -268,6 +278,40 @@ def table5_instance(n: int, g: int, o: int, qmax: int, seed: int = 1, scale: int
     o_arr = np.full(g, o, dtype=np.int32)
     q = np.ones(g * o, dtype=np.int32)
     return Problem(o=o_arr, p=p, q=q, R=R, D=D, Qmax=qmax, WT=WT_DEFAULT)
+
+
+def _unrelated_tables(rng, n: int, o: np.ndarray, p_lo: int, p_hi: int, q_lo: int, q_hi: int):
+    """P_jsm ~ U{p_lo..p_hi}, Q_jsm ~ U{q_lo..q_hi} per job and machine; p [n, g] is the
+    fastest machine's time of each op (a per-op summary; schedules read pm)."""
+    M = int(o.sum())
+    pm = _u(rng, p_lo, p_hi, size=(n, M)).astype(np.int32)
+    qm = _u(rng, q_lo, q_hi, size=(n, M)).astype(np.int32)
+    off = np.concatenate([[0], np.cumsum(o)])
+    p = np.stack([pm[:, off[s]:off[s + 1]].min(axis=1) for s in range(len(o))], axis=1)
+    return p, pm, qm
+
+
+def unrelated_instance(rng: np.random.Generator, N: int, g: int, o_lo: int, o_hi: int, p_hi: int,
+                       q_lo: int, q_hi: int, pct: int, f_lo: int = 1200, f_hi: int = 2000) -> Problem:
+    """Unrelated parallel machines (Table 2: P_jsm and Q_jsm differ per job and machine):
+    P_jsm ~ U{1..p_hi}, Q_jsm ~ U{q_lo..q_hi}, Qmax = floor(pct% of the sum over machines of
+    their largest Q_jsm), raised to the largest single Q_jsm; releases 0, D = floor(work *
+    U{f_lo..f_hi} / 1000) with work the sum of the fastest machines' times."""
+    o = _u(rng, o_lo, o_hi, size=g).astype(np.int32)
+    p, pm, qm = _unrelated_tables(rng, N, o, 1, p_hi, q_lo, q_hi)
+    qmax = max(int(qm.max(axis=0).sum()) * pct // 100, int(qm.max()))
+    R = np.zeros(N, dtype=np.int32)
+    D = _due(rng, R, p.sum(axis=1), f_lo, f_hi)
+    return Problem(o=o, p=p, q=qm.max(axis=0), R=R, D=D, Qmax=qmax, pm=pm, qm=qm)
+
+
+def unrelated_arrivals(rng: np.random.Generator, n: int, o: np.ndarray, t_now: int, p_hi: int, q_lo: int,
+                       q_hi: int, qmax: int, f_lo: int = 1200, f_hi: int = 2000) -> Arrivals:
+    """New jobs for an unrelated-machine instance, released at t_now; powers capped at Qmax."""
+    p, pm, qm = _unrelated_tables(rng, n, np.asarray(o), 1, p_hi, q_lo, q_hi)
+    qm = np.minimum(qm, qmax).astype(np.int32)
+    R = np.full(n, t_now, dtype=np.int64)
+    return Arrivals(p=p, R=R, D=_due(rng, R, p.sum(axis=1), f_lo, f_hi), pm=pm, qm=qm)
 
 
 def table5_arrivals(rng: np.random.Generator, n: int, g: int, t_now: int, scale: int = 100) -> Arrivals:

@@ -17,13 +17,33 @@ def machine_offsets(o):
     return off
 
 
+def op_p(inst, j, s, m):
+    """P_jsm (Table 2): per machine when the instance has per-machine tables."""
+    pm = getattr(inst, "pm", None)
+    if pm is None:
+        return int(inst.p[j, s])
+    return int(pm[j, machine_offsets(inst.o)[s] + m])
+
+
+def op_q(inst, j, s, m):
+    """Q_jsm (Table 2)."""
+    qm = getattr(inst, "qm", None)
+    mg = machine_offsets(inst.o)[s] + m
+    return int(inst.q[mg]) if qm is None else int(qm[j, mg])
+
+
+def durations(inst, M):
+    N, g = inst.p.shape
+    return np.array([[op_p(inst, j, s, int(M[j, s])) for s in range(g)] for j in range(N)], dtype=np.int64)
+
+
 def check_invariants(inst, S, M, obj=None, tard=None, cmax=None):
     """Eq. (2)-(10) on a schedule of `inst` (an oracle.Instance-like object with arrays
     p, q, o, R, D, status, S0, M0 and scalars Qmax, WT, RS).  Raises AssertionError."""
     N, g = inst.p.shape
     RS = inst.RS
     off = machine_offsets(inst.o)
-    end = S + inst.p
+    end = S + durations(inst, M)
     for j in range(N):
         for s in range(g):
             assert 0 <= M[j, s] < inst.o[s], "machine out of range"
@@ -48,7 +68,7 @@ def check_invariants(inst, S, M, obj=None, tard=None, cmax=None):
             for s in range(g):
                 a, b = max(int(S[j, s]), RS), int(end[j, s])
                 if b > a:
-                    Qt[a - RS:b - RS] += inst.q[off[s] + M[j, s]]
+                    Qt[a - RS:b - RS] += op_q(inst, j, s, int(M[j, s]))
         assert Qt.max() <= inst.Qmax, "Eq. (7): peak power exceeded"
     # Eq. (1)-(3)
     Cj = end[:, g - 1]
@@ -60,7 +80,8 @@ def check_invariants(inst, S, M, obj=None, tard=None, cmax=None):
     if obj is not None:
         assert obj == inst.WT * int(T.sum()) + int(Cj.max())
     # makespan lower bound: every job needs its own work after its release
-    lb = max(int(inst.R[j]) + int(inst.p[j].sum()) for j in range(N))
+    lb = max(int(inst.R[j]) + sum(min(op_p(inst, j, s, m) for m in range(inst.o[s])) for s in range(g))
+             for j in range(N))
     assert int(Cj.max()) >= min(lb, int(Cj.max())), "impossible"
     if RS == 0:
         assert int(Cj.max()) >= lb, "C_max below the longest job's work"
@@ -84,15 +105,16 @@ def gene_map(inst):
 
 
 def check_greedy_earliest(inst, order, S, M, any_machine: bool):
-    """Replay `order` and verify each op starts at the earliest integer instant (and, if
-    `any_machine`, on the lowest-index machine among those with that instant) at which it
+    """Replay `order` and verify each op starts at the earliest integer instant at which it
     is available, its machine has finished every op assigned to it before, and the power
-    of the ops assigned before it plus its own stays within Qmax at every instant."""
+    of the ops assigned before it plus its own stays within Qmax at every instant; with
+    `any_machine`, on the machine where that start gives the earliest completion (lowest
+    index among equals; with identical machines, the earliest start)."""
     N, g = inst.p.shape
     RS = inst.RS
     off = machine_offsets(inst.o)
     gj, gs = gene_map(inst)
-    end_all = S + inst.p
+    end_all = S + durations(inst, M)
     H = int(end_all.max()) + 2
     Qt = np.zeros(max(H - RS, 1), dtype=np.int64)
     mfree = np.full(int(off[-1]), RS, dtype=np.int64)
@@ -104,16 +126,15 @@ def check_greedy_earliest(inst, order, S, M, any_machine: bool):
                 if inst.status[j, s] == ST_EXEC:
                     mg = off[s] + M[j, s]
                     mfree[mg] = max(mfree[mg], end_all[j, s])
-                    Qt[0:end_all[j, s] - RS] += inst.q[mg]
+                    Qt[0:end_all[j, s] - RS] += op_q(inst, j, s, int(M[j, s]))
     for k in order:
         j, s = int(gj[k]), int(gs[k])
-        p = int(inst.p[j, s])
         est = max(RS, int(inst.R[j]), int(Cj[j]))
         machines = range(inst.o[s]) if any_machine else [int(M[j, s])]
         best = None
         for m in machines:
             mg = off[s] + m
-            qm = int(inst.q[mg])
+            qm, p = op_q(inst, j, s, m), op_p(inst, j, s, m)
             t = max(est, int(mfree[mg]))
             while True:
                 if t + p - RS > len(Qt):
@@ -121,10 +142,11 @@ def check_greedy_earliest(inst, order, S, M, any_machine: bool):
                 if int(Qt[t - RS:t - RS + p].max()) + qm <= inst.Qmax:
                     break
                 t += 1
-            if best is None or t < best[0]:
-                best = (t, m)
-        assert (int(S[j, s]), int(M[j, s])) == best, f"op ({j},{s}) not at its earliest slot: {S[j, s], M[j, s]} vs {best}"
+            if best is None or t + p < best[0] + best[2]:
+                best = (t, m, p)
+        assert (int(S[j, s]), int(M[j, s])) == best[:2], f"op ({j},{s}) not at its earliest slot: {S[j, s], M[j, s]} vs {best}"
         mg = off[s] + best[1]
-        Qt[best[0] - RS:best[0] - RS + p] += inst.q[mg]
+        p = best[2]
+        Qt[best[0] - RS:best[0] - RS + p] += op_q(inst, j, s, best[1])
         mfree[mg] = best[0] + p
         Cj[j] = best[0] + p

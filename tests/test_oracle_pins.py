@@ -580,3 +580,82 @@ def test_static_equals_reactive_without_plan_left():
     assert np.array_equal(a.status, b.status) and a.K == b.K == 12
     y2 = (rng.permutation(a.K) + 1).astype(np.int16)
     assert a.decode(y2)["obj"] == b.decode(y2)["obj"]
+
+
+# ---------------------------------------------------------------- unrelated machines (Table 2)
+
+def test_unrelated_hand_example_earliest_completion():
+    """One stage, two machines, no binding peak.  Job 0 takes 5 on machine 0 and 2 on
+    machine 1: both start at 0, so earliest start would pick machine 0 but earliest
+    completion picks machine 1 (0..2).  Job 1 takes 3 / 4: machine 0 completes at 3,
+    machine 1 at 2 + 4 = 6, so machine 0 (0..3).  C_max = 3."""
+    pr = wl.Problem(o=[2], p=[[2], [3]], q=[1, 1], R=[0, 0], D=[100, 100], Qmax=10,
+                    pm=[[5, 2], [3, 4]], qm=[[1, 1], [1, 1]])
+    inst = oracle.Instance(pr)
+    r = inst.decode(np.array([2, 1], np.int16), None, ORDER_STAGE, MACH_EARLIEST)
+    assert r["S"].ravel().tolist() == [0, 0] and r["M"].ravel().tolist() == [1, 0]
+    assert r["cmax"] == 3
+    # machine genes: job 0 on machine 0 takes 5
+    r = inst.decode(np.array([2, 1], np.int16), np.array([0, 1], np.int8), ORDER_STAGE, MACH_GENE)
+    assert r["S"].ravel().tolist() == [0, 0] and r["cmax"] == 5
+
+
+def test_unrelated_hand_example_power():
+    """Q_jsm per job: job 0 draws 3 on machine 0 and 1 on machine 1, job 1 draws 2 on
+    either; peak 3.  Job 0 (p 2 / 2) goes to machine 0 at 0 (ties to the lower index).
+    Job 1 (p 1 / 1): machine 1 is free but 3 + 2 > 3 until job 0 ends at 2, on either
+    machine; machine 0 is free at 2 as well, so job 1 runs on machine 0 at 2..3."""
+    pr = wl.Problem(o=[2], p=[[2], [1]], q=[3, 2], R=[0, 0], D=[100, 100], Qmax=3,
+                    pm=[[2, 2], [1, 1]], qm=[[3, 1], [2, 2]])
+    inst = oracle.Instance(pr)
+    r = inst.decode(np.array([2, 1], np.int16), None, ORDER_STAGE, MACH_EARLIEST)
+    assert r["S"].ravel().tolist() == [0, 2] and r["M"].ravel().tolist() == [0, 0]
+    check_invariants(inst, r["S"], r["M"], obj=r["obj"], tard=r["tard"], cmax=r["cmax"])
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_unrelated_replicated_tables_equal_identical_machines(seed):
+    """Per-machine tables that repeat each op's time and each machine's power reduce to the
+    identical-machine model: the same schedules in every mode, along a rescheduling chain."""
+    rng = np.random.default_rng(seed)
+    pr = wl.random_instance(rng, 12, 3, 1, 3, 30, 5, 20, 55)
+    off = np.concatenate([[0], np.cumsum(pr.o)])
+    rep = lambda p: np.concatenate([np.repeat(p[:, s:s + 1], pr.o[s], axis=1) for s in range(pr.g)], axis=1)
+    pr_u = wl.Problem(o=pr.o, p=pr.p, q=pr.q, R=pr.R, D=pr.D, Qmax=pr.Qmax, pm=rep(pr.p),
+                      qm=np.tile(pr.q, (pr.N, 1)))
+    a, b = oracle.Instance(pr), oracle.Instance(pr_u)
+    for ev in range(3):
+        Y, X = wl.random_chromosomes(rng, 20, a.K, a.gene_machines())
+        for i in range(20):
+            for order, mach in ((ORDER_STAGE, MACH_EARLIEST), (ORDER_TOPO, MACH_GENE), (ORDER_STAGE, MACH_GENE)):
+                ra, rb = a.decode(Y[i], X[i], order, mach), b.decode(Y[i], X[i], order, mach)
+                assert ra["obj"] == rb["obj"] and np.array_equal(ra["S"], rb["S"]) and np.array_equal(ra["M"], rb["M"])
+        r = a.decode(Y[0], X[0])
+        t_now = a.RS + (r["cmax"] - a.RS) // 3
+        arr = wl.random_arrivals(rng, 2, pr.g, t_now, 30)
+        arr_u = wl.Arrivals(p=arr.p, R=arr.R, D=arr.D, pm=rep(arr.p), qm=np.tile(pr.q, (arr.n, 1)))
+        for inst, ar in ((a, arr), (b, arr_u)):
+            inst.commit(r["S"], r["M"])
+            inst.reschedule(ar, t_now)
+        assert np.array_equal(a.status, b.status)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_unrelated_invariants_and_greedy(seed):
+    """Eq. (4)-(10) with per-machine times and powers, and every placement the earliest
+    completion (earliest feasible start on each machine, then the earliest end), checked
+    on an independent per-instant replay, along a rescheduling chain."""
+    rng = np.random.default_rng(seed)
+    pr = wl.unrelated_instance(rng, 14, 3, 1, 3, 30, 2, 15, 50)
+    inst = oracle.Instance(pr)
+    for ev in range(3):
+        Y, X = wl.random_chromosomes(rng, 6, inst.K, inst.gene_machines())
+        for i in range(6):
+            for mach in (MACH_EARLIEST, MACH_GENE):
+                r = inst.decode(Y[i], X[i], ORDER_STAGE, mach)
+                check_invariants(inst, r["S"], r["M"], obj=r["obj"], tard=r["tard"], cmax=r["cmax"])
+                check_greedy_earliest(inst, stage_order(inst, Y[i]), r["S"], r["M"],
+                                      any_machine=mach == MACH_EARLIEST)
+        inst.commit(r["S"], r["M"])
+        t_now = inst.RS + (r["cmax"] - inst.RS) // 3
+        inst.reschedule(wl.unrelated_arrivals(rng, 3, pr.o, t_now, 30, 2, 15, pr.Qmax), t_now)
