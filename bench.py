@@ -434,6 +434,56 @@ def bench_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- unrelated machines
+UNREL_WORKLOAD = ("unrelated parallel machines (Table 2: P_jsm, Q_jsm per job and machine), earliest-completion "
+                  "machine choice: 50 jobs, 5 stages x U{2..4} machines, P_jsm U{1..99}, Q_jsm U{5..30}, peak 55% "
+                  "of the sum of each machine's largest power; population 1024 (16 islands of 64), tournament 2, "
+                  "pc 0.8, pm 0.1; G generations of one solve per step")
+
+
+def bench_unrelated(args):
+    import torch
+
+    from paper_1903_10741_gb300 import ffs
+
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    stream = torch.cuda.current_stream()
+    prob = wl.unrelated_instance(np.random.default_rng(1), 50, 5, 2, 4, 99, 5, 30, 55)
+    G = args.generations
+    kw = dict(P=P, island=ISLAND, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE, seed=SEED, stream=stream)
+    for _ in range(args.warmup):
+        ffs.Population(ffs.Instance(prob), **kw).run(5, want_schedule=False)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(_env_int("LOCAL_RANK", 0))
+    clocks.start()
+    launches0 = ffs.kernel_launches()
+    total_ms, best = 0.0, []
+    for k in range(args.steps):
+        inst = ffs.Instance(prob)
+        pop = ffs.Population(inst, **kw)
+        flush.fill_(float(k))
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        r = pop.run(G, want_schedule=False)
+        e.record(stream)
+        e.synchronize()
+        total_ms += s.elapsed_time(e)
+        best.append(r["obj"])
+    launches = ffs.kernel_launches() - launches0
+    clk = clocks.stop()
+    decodes = P * G * args.steps
+    line = {
+        "metric": METRIC, "value": decodes / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": UNREL_WORKLOAD, "generations_per_step": G, "genes": int(inst.K),
+                   "best_objectives": best, "l2": "flushed between steps (256 MiB write)",
+                   "timing": "CUDA events around ga_run (its final best-schedule decode included)"},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- static vs reactive
 SVR_WORKLOAD = ("reactive vs traditional static rescheduling (Sec. 5.3, Table 10 analogue): the Test 3 setting of "
                 "Sec. 5 and Table 5 -- 10 jobs, 3 stages x 2 identical machines, p U[1,5], unit power, peak 4, "
@@ -634,7 +684,8 @@ def main():
     ap.add_argument("--ref-generations", type=int, default=2, help="oracle generations per reference step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["dynamic", "batched", "surrogate", "service", "static-vs-reactive"],
+    ap.add_argument("--workload", choices=["dynamic", "batched", "surrogate", "service", "static-vs-reactive",
+                                           "unrelated"],
                     default="dynamic",
                     help="dynamic: the headline rescheduling job; batched: 256 uneven instances; "
                          "surrogate: time-to-objective of the surrogate-assisted GA; service: Poisson "
@@ -669,6 +720,8 @@ def main():
         if args.generations == 500:
             args.generations = 1000
         bench_surrogate(args)
+    elif args.workload == "unrelated":
+        bench_unrelated(args)
     elif args.workload == "static-vs-reactive":
         if args.generations == 500:
             args.generations = 100

@@ -50,30 +50,44 @@ extern "C" {
 #define FFS_ORDER_TOPO      0  /* Alg. 1: largest y among the next free op of every job   */
 #define FFS_ORDER_STAGE     1  /* stage by stage, y descending within a stage            */
 #define FFS_MACH_GENE       0  /* machine of op (j, s) is x_js, Eq. (10)                 */
-#define FFS_MACH_EARLIEST   1  /* machine with the earliest power-feasible start          */
+#define FFS_MACH_EARLIEST   1  /* machine with the earliest power-feasible start (completion,
+                                  with unrelated machines)                                 */
 
 typedef struct ffs_instance ffs_instance;      /* opaque: problem + rescheduling state    */
 typedef struct ga_population ga_population;    /* opaque: device-resident GA state        */
 
-/* An EDFFS instance, Table 2 of the paper.  All arrays are host memory. */
+/* An EDFFS instance, Table 2 of the paper.  All arrays are host memory.
+ * Identical parallel machines: proc and power give P_js and each machine's Q, and
+ * proc_machine / power_machine are NULL.  Unrelated machines (Table 2's P_jsm and Q_jsm):
+ * proc_machine and power_machine give every job's processing time and power on every
+ * machine, [n][sum o_s] with machines stage-major; proc and power are then ignored (may be
+ * NULL).  With unrelated machines, FFS_MACH_EARLIEST picks the machine with the earliest
+ * power-feasible completion (with identical machines that is the earliest start), and a
+ * machine gene's op takes that machine's time and power. */
 typedef struct {
     int32_t n_jobs;                      /* n                                           */
     int32_t n_stages;                    /* g                                           */
-    const int32_t *machines_per_stage;   /* [g]  o_s >= 1, identical parallel machines  */
+    const int32_t *machines_per_stage;   /* [g]  o_s >= 1 parallel machines              */
     const int32_t *proc;                 /* [n][g] P_js (the same on every machine of s) */
     const int32_t *power;                /* [sum o_s] Q of each machine, stage-major     */
     const int32_t *release;              /* [n]  R_j                                    */
     const int32_t *due;                  /* [n]  D_j                                    */
     int32_t peak_power;                  /* Q_max, Eq. (7)                              */
     int32_t wt;                          /* WT, Eq. (1)                                 */
+    const int32_t *proc_machine;         /* [n][sum o_s] P_jsm, or NULL                  */
+    const int32_t *power_machine;        /* [n][sum o_s] Q_jsm, or NULL                  */
 } ffs_problem;
 
-/* New jobs J' arriving at a rescheduling point (Sec. 4.1).  Host arrays. */
+/* New jobs J' arriving at a rescheduling point (Sec. 4.1).  Host arrays.  For an
+ * instance with unrelated machines proc_machine / power_machine are required and proc is
+ * ignored; otherwise proc is required and they are ignored. */
 typedef struct {
     int32_t job_count;                   /* n'                                          */
     const int32_t *proc;                 /* [n'][g]                                     */
     const int32_t *release;              /* [n']                                        */
     const int32_t *due;                  /* [n']                                        */
+    const int32_t *proc_machine;         /* [n'][sum o_s] P_jsm, or NULL                 */
+    const int32_t *power_machine;        /* [n'][sum o_s] Q_jsm, or NULL                 */
 } ffs_arrivals;
 
 /* GA settings (Sec. 4.2, 4.4). */
@@ -193,7 +207,7 @@ typedef struct {
 /* Copies the `count` instances' current tables and runs generation 0 of every one.  All
  * share `params` (pop, island, operators, modes, seed, stream); instance i draws from
  * stream id params->instance_id + i, so its run equals ga_population_create + ga_run
- * with that id.  The instances must not be rescheduled while the batch is used. */
+ * with that id.  The instances must not be rescheduled while the batch is used. * Instances with unrelated machines are refused (FFS_E_ARG). */
 int ga_batch_create(ffs_instance *const *insts, int32_t count, const ga_params *params, ga_batch **out);
 
 /* Frees a batch.  NULL is accepted. */

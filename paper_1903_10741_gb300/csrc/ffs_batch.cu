@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(512) k_batch(BatchArgs a) {
     uint32_t phase = 0;
     uint16_t *hg = a.gscratch + (size_t)(blockIdx.x * W + warp) * (size_t)a.Hmax;
     const int P = a.P, I = a.I;
-    const bool gene = MACH == kMachGene;
+    const bool gene = mach_gene(MACH);
     // Every CTA of a cluster follows the same control flow, so the cluster barriers below
     // are reached by all of them.
     for (int item = cid; item < a.count; item += ncl) {

@@ -13,6 +13,11 @@ namespace edffs {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kOrderTopo = 0, kOrderStage = 1;
 constexpr int kMachGene = 0, kMachEarliest = 1;
+// Kernel-side machine modes add the unrelated-machine variants (per-gene p and q per
+// machine, the earliest completion instead of the earliest start).
+constexpr int kMachGeneU = 2, kMachEarliestU = 3;
+__host__ __device__ constexpr bool mach_gene(int m) { return (m & 1) == 0; }
+__host__ __device__ constexpr bool mach_unrel(int m) { return m >= 2; }
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror & Shaw, SC'11: ten rounds of the 4x32 Philox S-box with
@@ -190,6 +195,37 @@ __device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int 
     }
 }
 
+// Unrelated machines: lane m < os holds its machine's availability t0, power q2 and the
+// op's processing time p on it.  Returns the lexicographic minimum of (earliest completion
+// of a power-feasible start, machine) and that machine's p.  The machine whose completion
+// bound t0 + p is lowest is scanned first; another only if its bound could still win.
+__device__ __forceinline__ void earliest_machine_u(const uint16_t *h, int hw, int t0, uint32_t q2, int p, int os,
+                                                   int lane, int &best_t, int &best_m, int &best_p) {
+    const int c0 = lane < os ? t0 + p : INT_MAX;
+    const unsigned key = lane < os ? ((unsigned)c0 << 5) | (unsigned)lane : 0xFFFFFFFFu;
+    const unsigned kmin = __reduce_min_sync(kFull, key);
+    best_m = (int)(kmin & 31u);
+    best_p = __shfl_sync(kFull, p, best_m);
+    best_t = earliest_start(h, hw, __shfl_sync(kFull, t0, best_m), best_p, __shfl_sync(kFull, q2, best_m), INT_MAX,
+                            lane);
+    int best_c = best_t + best_p;
+    unsigned cand = __ballot_sync(kFull, lane < os && lane != best_m && c0 < best_c + (lane < best_m));
+    while (cand) {
+        const int m = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const int tm = __shfl_sync(kFull, t0, m), pm = __shfl_sync(kFull, p, m);
+        const int lim = best_c - pm + (m < best_m ? 1 : 0);  // starts below this complete earlier
+        if (tm >= lim) continue;
+        const int t = earliest_start(h, hw, tm, pm, __shfl_sync(kFull, q2, m), lim, lane);
+        if (t < lim) {
+            best_t = t;
+            best_m = m;
+            best_p = pm;
+            best_c = t + pm;
+        }
+    }
+}
+
 // Decodes one chromosome with the whole warp (Sec. 4.3, Alg. 1-2).  State lives in the
 // caller's workspace: h [Hcap] headroom, C [N], mfree [M], inv [K+N], y [K], x [K].  In
 // stage order the priority list overwrites y once its inverse is built, so y must be a
@@ -218,7 +254,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
         const int v = y[k];
         if (v < 1 || v > K) bad = true;
         else inv[K - v] = (int16_t)k;
-        if (MACH == kMachGene) {
+        if (mach_gene(MACH)) {
             const int xm = x[k];
             if (xm < 0 || xm >= T.o[T.gstg[k]]) bad = true;
         }
@@ -265,19 +301,29 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 const int kn = order[min(n + 1, hi - 1)];
                 const uint2 grn = T.grec[kn];
                 const int cjn = C[grn.x & 0xFFFFu];
-                const int j = (int)(gr.x & 0xFFFFu), p = (int)(gr.y & 0xFFFFu);
+                const int j = (int)(gr.x & 0xFFFFu);
+                int p = (int)(gr.y & 0xFFFFu);
+                uint32_t qo2 = q2;  // this op's power on the lane's machine
+                if (mach_unrel(MACH)) {
+                    const uint32_t pq = lane < os ? T.gm[(size_t)k * T.maxo + lane] : 0u;
+                    p = (int)(pq & 0xFFFFu);
+                    qo2 = (pq >> 16) * 0x10001u;
+                }
                 const int est = max(cj - RS, 0);
                 int best_t, best_m;
-                if (MACH == kMachGene) {
+                if (mach_gene(MACH)) {
                     best_m = x[k];
+                    if (mach_unrel(MACH)) p = __shfl_sync(kFull, p, best_m);
                     best_t = earliest_start(h, hw, max(est, __shfl_sync(kFull, mf, best_m)), p,
-                                            __shfl_sync(kFull, q2, best_m), INT_MAX, lane);
+                                            __shfl_sync(kFull, qo2, best_m), INT_MAX, lane);
+                } else if (mach_unrel(MACH)) {
+                    earliest_machine_u(h, hw, max(est, mf), qo2, p, os, lane, best_t, best_m, p);
                 } else {
                     earliest_machine(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m);
                 }
                 const int e = best_t + p;
                 if (e > Hcap) return {0, 0, 1};
-                commit_power(h, hw, best_t, e, __shfl_sync(kFull, q2, best_m), Q2, lane);
+                commit_power(h, hw, best_t, e, __shfl_sync(kFull, qo2, best_m), Q2, lane);
                 if (lane == best_m) mf = e;
                 if (lane == 0) {
                     C[j] = e + RS;
@@ -308,19 +354,28 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             const int k = nxt[bestj];
             const uint2 gr = T.grec[k];
             const int j = (int)(gr.x & 0xFFFFu), s = (int)((gr.x >> 16) & 0xFFu), os = (int)(gr.x >> 24);
-            const int p = (int)(gr.y & 0xFFFFu), mo = (int)(gr.y >> 16);
+            int p = (int)(gr.y & 0xFFFFu);
+            const int mo = (int)(gr.y >> 16);
             int mf = INT_MAX;
             uint32_t q2 = 0;
             if (lane < os) {
                 mf = mfree[mo + lane] - RS;
                 q2 = (uint32_t)T.q[mo + lane] * 0x10001u;
             }
+            if (mach_unrel(MACH)) {
+                const uint32_t pq = lane < os ? T.gm[(size_t)k * T.maxo + lane] : 0u;
+                p = (int)(pq & 0xFFFFu);
+                q2 = (pq >> 16) * 0x10001u;
+            }
             const int est = max(C[j] - RS, 0);
             int best_t, best_m;
-            if (MACH == kMachGene) {
+            if (mach_gene(MACH)) {
                 best_m = x[k];
+                if (mach_unrel(MACH)) p = __shfl_sync(kFull, p, best_m);
                 best_t = earliest_start(h, hw, max(est, __shfl_sync(kFull, mf, best_m)), p,
                                         __shfl_sync(kFull, q2, best_m), INT_MAX, lane);
+            } else if (mach_unrel(MACH)) {
+                earliest_machine_u(h, hw, max(est, mf), q2, p, os, lane, best_t, best_m, p);
             } else {
                 earliest_machine(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m);
             }

@@ -105,7 +105,7 @@ __device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, con
     const int16_t *yf = s.Yc + (size_t)first * K, *yb = s.Yc + (size_t)second * K;
     if (!cross) {
         for (int k = lane; k < K; k += 32) w.y[k] = yf[k];
-        if (MACH == kMachGene)
+        if (mach_gene(MACH))
             for (int k = lane; k < K; k += 32) w.x[k] = s.Xc[(size_t)first * K + k];
     } else {
         const int cx = 1 + (int)below(rc.y, (uint32_t)(K - 1));
@@ -166,7 +166,7 @@ __device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, con
             if (dup) w.y[k] = miss[rank + __popc(bm & ((1u << lane) - 1u))];
             rank += __popc(bm);
         }
-        if (MACH == kMachGene)
+        if (mach_gene(MACH))
             for (int k = lane; k < K; k += 32)
                 w.x[k] = k < cx ? s.Xc[(size_t)first * K + k] : s.Xc[(size_t)second * K + k];
     }
@@ -181,7 +181,7 @@ __device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, con
             w.y[ma] = w.y[mb];
             w.y[mb] = t;
         }
-        if (MACH == kMachGene) {
+        if (mach_gene(MACH)) {
             for (int k = lane; k < K; k += 32) {
                 const int o = T.o[T.gstg[k]];
                 if (o >= 2) {
@@ -219,7 +219,7 @@ __device__ __forceinline__ void make_initial(const Tabs &T, const WarpPtrs &w, u
         }
     }
     __syncwarp();
-    if (MACH == kMachGene) {
+    if (mach_gene(MACH)) {
         for (int k = lane; k < K; k += 32) {
             const uint32_t u = draw(seed, kPInitX, iid, 0, (uint32_t)i, (uint32_t)k);
             w.x[k] = (int8_t)below(u, (uint32_t)T.o[T.gstg[k]]);

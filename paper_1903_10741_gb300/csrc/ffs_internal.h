@@ -63,9 +63,18 @@ void dfree(T *&p) {
 using ffs_rt::dalloc;
 using ffs_rt::dfree;
 
+struct ffs_instance;
+namespace ffs_rt {
+// P_jsm and Q_jsm (Table 2) of job j's op at stage s on stage-local machine m.
+int op_p(const ffs_instance *in, int j, int s, int m);
+int op_q(const ffs_instance *in, int j, int s, int m);
+}  // namespace ffs_rt
+
 struct ffs_instance {
     int N = 0, g = 0, M = 0, Qmax = 0, WT = 0, RS = 0;
     std::vector<int32_t> o, moff, p, q, R, D;   // problem
+    bool unrel = false;                         // unrelated machines: P_jsm, Q_jsm per job and machine
+    std::vector<int32_t> pm, qm;                // [N][M] when unrel
     std::vector<int32_t> status, S0, M0;       // plan and classification, [N*g]
     bool has_plan = false;
     bool dev_dirty = true;  // host tables or plan changed since the last upload

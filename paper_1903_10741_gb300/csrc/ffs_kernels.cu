@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_decode(DecodeArgs a) {
         const int idx = a.list ? a.list[c] : c;
         const int16_t *yg = a.Y[buf] + (size_t)idx * K;
         for (int k = lane; k < K; k += 32) w.y[k] = yg[k];
-        if (MACH == kMachGene) {
+        if (mach_gene(MACH)) {
             const int8_t *xg = a.X[buf] + (size_t)idx * K;
             for (int k = lane; k < K; k += 32) w.x[k] = xg[k];
         }
@@ -97,13 +97,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_init(GenArgs a) {
         int8_t *xo = a.X[0] + (size_t)i * K;
         if (a.warm) {
             for (int k = lane; k < K; k += 32) w.y[k] = yo[k];
-            if (MACH == kMachGene)
+            if (mach_gene(MACH))
                 for (int k = lane; k < K; k += 32) w.x[k] = xo[k];
             __syncwarp();
         } else {
             make_initial<MACH>(T, w, a.seed, a.instance_id, i, lane);
             for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
-            if (MACH == kMachGene)
+            if (mach_gene(MACH))
                 for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
         }
         const DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x,
@@ -202,14 +202,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
             }
             const size_t c = (size_t)vi * a.P + i;
             for (int k = lane; k < K; k += 32) w.y[k] = a.cand_Y[c * K + k];
-            if (MACH == kMachGene)
+            if (mach_gene(MACH))
                 for (int k = lane; k < K; k += 32) w.x[k] = a.cand_X[c * K + k];
             for (int k = lane; k < a.Kpad; k += 32) a.kept_Yh[(size_t)i * a.Kpad + k] = a.cand_Yh[c * a.Kpad + k];
             __syncwarp();
         }
         int16_t *yo = a.Y[nx] + (size_t)i * K;
         for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
-        if (MACH == kMachGene) {
+        if (mach_gene(MACH)) {
             int8_t *xo = a.X[nx] + (size_t)i * K;
             for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
         }
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_candidates(GenArgs a) {
         if (lane == 0) a.cand_new[c] = fresh ? 1 : 0;
         int16_t *yo = a.cand_Y + (size_t)c * K;
         for (int k = lane; k < K; k += 32) yo[k] = w.y[k];
-        if (MACH == kMachGene) {
+        if (mach_gene(MACH)) {
             int8_t *xo = a.cand_X + (size_t)c * K;
             for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
         }
@@ -433,21 +433,25 @@ int cta_smem_bytes(const TabHeader &h, int Hcap, bool ga, bool global_profile) {
 }
 
 // Runs the body with O_/M_ bound to the (order, mach) pair of the enclosing scope.
-#define FFS_DISPATCH(...)                                                                        \
-    do {                                                                                         \
-        if (order == kOrderStage && mach == kMachEarliest) {                                     \
-            constexpr int O_ = kOrderStage, M_ = kMachEarliest;                                  \
-            __VA_ARGS__;                                                                         \
-        } else if (order == kOrderStage && mach == kMachGene) {                                  \
-            constexpr int O_ = kOrderStage, M_ = kMachGene;                                      \
-            __VA_ARGS__;                                                                         \
-        } else if (order == kOrderTopo && mach == kMachEarliest) {                               \
-            constexpr int O_ = kOrderTopo, M_ = kMachEarliest;                                   \
-            __VA_ARGS__;                                                                         \
-        } else {                                                                                 \
-            constexpr int O_ = kOrderTopo, M_ = kMachGene;                                       \
-            __VA_ARGS__;                                                                         \
-        }                                                                                        \
+// The machine mode of a public call (gene or earliest) and the instance's machine model
+// (identical, or unrelated with per-gene p and q) give the kernel's machine mode.
+#define FFS_CASE(O, M, ...)                                    \
+    if (order == O && kmach == M) {                            \
+        constexpr int O_ = O, M_ = M;                          \
+        __VA_ARGS__;                                           \
+    }
+#define FFS_DISPATCH(...)                                                                  \
+    do {                                                                                   \
+        const int kmach = mach + (h.unrel ? 2 : 0);                                        \
+        FFS_CASE(kOrderStage, kMachEarliest, __VA_ARGS__)                                  \
+        else FFS_CASE(kOrderStage, kMachGene, __VA_ARGS__)                                 \
+        else FFS_CASE(kOrderTopo, kMachEarliest, __VA_ARGS__)                              \
+        else FFS_CASE(kOrderTopo, kMachGene, __VA_ARGS__)                                  \
+        else FFS_CASE(kOrderStage, kMachEarliestU, __VA_ARGS__)                            \
+        else FFS_CASE(kOrderStage, kMachGeneU, __VA_ARGS__)                                \
+        else FFS_CASE(kOrderTopo, kMachEarliestU, __VA_ARGS__)                             \
+        else FFS_CASE(kOrderTopo, kMachGeneU, __VA_ARGS__)                                 \
+        else e = cudaErrorInvalidValue;                                                    \
     } while (0)
 
 cudaError_t launch_decode(int order, int mach, bool global_profile, const DecodeArgs &a,

@@ -25,11 +25,12 @@ constexpr int kStFixed = 3;  // static approach: a planned op kept at its start 
 struct TabHeader {
     int32_t N, g, M, K;           // jobs, stages, machines, genes
     int32_t RS, Qmax, WT, H;      // rescheduling point, peak, weight, profile bound (slots past RS)
-    int32_t E0, bytes, maxo, pad0;// slots of initial profile (executing ops), blob size, max o_s
+    int32_t E0, bytes, maxo, unrel;// slots of initial profile (executing ops), blob size, max o_s,
+                                   // 1 for unrelated machines (per-gene, per-machine p and q)
     int32_t off_o, off_moff, off_q, off_p;
     int32_t off_R, off_D, off_C0, off_mfree0;
     int32_t off_gjob, off_gstg, off_gfirst, off_gcnt;
-    int32_t off_h0, off_grec, off_soff, pad3;
+    int32_t off_h0, off_grec, off_soff, off_gm;
 };
 static_assert(sizeof(TabHeader) == 112, "header layout");
 
@@ -45,6 +46,10 @@ struct Tabs {
     // Per gene, packed: x = job | stage << 16 | o_stage << 24, y = p | first machine << 16.
     const uint2 *grec;
     const int32_t *soff;  // [g+1] first gene index of each stage in the stage-major order
+    // Unrelated machines: [K][maxo] p | q << 16 of gene k on stage-local machine m (P_jsm,
+    // Q_jsm of Table 2); null for identical machines.
+    int maxo;
+    const uint32_t *gm;
 };
 
 FFS_HD Tabs tabs_view(const char *base) {
@@ -67,6 +72,8 @@ FFS_HD Tabs tabs_view(const char *base) {
     t.h0 = reinterpret_cast<const uint16_t *>(base + h->off_h0);
     t.grec = reinterpret_cast<const uint2 *>(base + h->off_grec);
     t.soff = reinterpret_cast<const int32_t *>(base + h->off_soff);
+    t.maxo = h->maxo;
+    t.gm = h->unrel ? reinterpret_cast<const uint32_t *>(base + h->off_gm) : nullptr;
     return t;
 }
 

@@ -56,6 +56,14 @@ int cuda_rc(cudaError_t e) {
 }
 
 
+int op_p(const ffs_instance *in, int j, int s, int m) {
+    return in->unrel ? in->pm[(size_t)j * in->M + in->moff[s] + m] : in->p[j * in->g + s];
+}
+
+int op_q(const ffs_instance *in, int j, int s, int m) {
+    return in->unrel ? in->qm[(size_t)j * in->M + in->moff[s] + m] : in->q[in->moff[s] + m];
+}
+
 // Rebuilds the gene map, the profile bound and the table blob, and uploads them.
 int rebuild(ffs_instance *in) {
     const int N = in->N, g = in->g, M = in->M, RS = in->RS;
@@ -74,9 +82,11 @@ int rebuild(ffs_instance *in) {
                 gcnt[j]++;
                 in->gjob.push_back(j);
                 in->gstg.push_back(s);
-                work += in->p[k];
+                int pmax = 0;  // the slowest of the op's machines
+                for (int m = 0; m < in->o[s]; ++m) pmax = std::max(pmax, op_p(in, j, s, m));
+                work += pmax;
             } else {
-                const int end = in->S0[k] + in->p[k];
+                const int end = in->S0[k] + op_p(in, j, s, in->M0[k]);
                 C0[j] = end;  // frozen ops form a prefix of the job's stages
                 if (in->status[k] == kStExec || in->status[k] == kStFixed) {  // draws power past RS
                     const int mg = in->moff[s] + in->M0[k];
@@ -99,8 +109,8 @@ int rebuild(ffs_instance *in) {
         for (int s = 0; s < g; ++s) {
             const int k = j * g + s;
             if (in->status[k] != kStExec && in->status[k] != kStFixed) continue;
-            const int q = in->q[in->moff[s] + in->M0[k]];
-            for (int t = std::max(RS, in->S0[k]); t < in->S0[k] + in->p[k]; ++t)
+            const int q = op_q(in, j, s, in->M0[k]);
+            for (int t = std::max(RS, in->S0[k]); t < in->S0[k] + op_p(in, j, s, in->M0[k]); ++t)
                 h0[t - RS] = (uint16_t)(h0[t - RS] - q);
         }
 
@@ -128,6 +138,8 @@ int rebuild(ffs_instance *in) {
     take(h.off_h0, 2 * E0);
     take(h.off_grec, 8 * in->K);
     take(h.off_soff, 4 * (g + 1));
+    h.unrel = in->unrel ? 1 : 0;
+    if (in->unrel) take(h.off_gm, 4 * in->K * h.maxo);
     h.bytes = off;
     in->hdr = h;
     in->blob.assign(off, 0);
@@ -159,6 +171,14 @@ int rebuild(ffs_instance *in) {
         const int j = in->gjob[k], s = in->gstg[k];
         gr[2 * k] = (uint32_t)j | ((uint32_t)s << 16) | ((uint32_t)in->o[s] << 24);
         gr[2 * k + 1] = (uint32_t)in->p[j * g + s] | ((uint32_t)in->moff[s] << 16);
+    }
+    if (in->unrel) {
+        uint32_t *gm = reinterpret_cast<uint32_t *>(b + h.off_gm);
+        for (int k = 0; k < in->K; ++k) {
+            const int j = in->gjob[k], s = in->gstg[k];
+            for (int m = 0; m < in->o[s]; ++m)
+                gm[(size_t)k * h.maxo + m] = (uint32_t)op_p(in, j, s, m) | ((uint32_t)op_q(in, j, s, m) << 16);
+        }
     }
 
     in->dev_dirty = true;
@@ -301,8 +321,10 @@ int ffs_instance_create(const ffs_problem *pr, ffs_instance **out) {
     if (!pr || !out) return FFS_E_ARG;
     *out = nullptr;
     const int N = pr->n_jobs, g = pr->n_stages;
-    if (N < 1 || N > kMaxN || g < 1 || g > kMaxG || !pr->machines_per_stage || !pr->proc || !pr->power ||
-        !pr->release || !pr->due || pr->peak_power < 0 || pr->peak_power > kMaxQ || pr->wt < 0)
+    const bool unrel = pr->proc_machine != nullptr;
+    if (N < 1 || N > kMaxN || g < 1 || g > kMaxG || !pr->machines_per_stage || (!unrel && (!pr->proc || !pr->power)) ||
+        (unrel != (pr->power_machine != nullptr)) || !pr->release || !pr->due || pr->peak_power < 0 ||
+        pr->peak_power > kMaxQ || pr->wt < 0)
         return FFS_E_ARG;
     int M = 0;
     for (int s = 0; s < g; ++s) {
@@ -312,11 +334,18 @@ int ffs_instance_create(const ffs_problem *pr, ffs_instance **out) {
         M += o;
     }
     if (M > kMaxM) return FFS_E_ARG;
-    for (int i = 0; i < N * g; ++i)
-        if (pr->proc[i] < 0 || pr->proc[i] > kMaxP) return FFS_E_ARG;
-    for (int m = 0; m < M; ++m) {
-        if (pr->power[m] < 0) return FFS_E_ARG;
-        if (pr->power[m] > pr->peak_power) return FFS_E_INFEASIBLE;
+    if (unrel) {
+        for (size_t i = 0; i < (size_t)N * M; ++i) {
+            if (pr->proc_machine[i] < 0 || pr->proc_machine[i] > kMaxP || pr->power_machine[i] < 0) return FFS_E_ARG;
+            if (pr->power_machine[i] > pr->peak_power) return FFS_E_INFEASIBLE;
+        }
+    } else {
+        for (int i = 0; i < N * g; ++i)
+            if (pr->proc[i] < 0 || pr->proc[i] > kMaxP) return FFS_E_ARG;
+        for (int m = 0; m < M; ++m) {
+            if (pr->power[m] < 0) return FFS_E_ARG;
+            if (pr->power[m] > pr->peak_power) return FFS_E_INFEASIBLE;
+        }
     }
     for (int j = 0; j < N; ++j)
         if (pr->release[j] < 0) return FFS_E_ARG;
@@ -326,8 +355,28 @@ int ffs_instance_create(const ffs_problem *pr, ffs_instance **out) {
     in->o.assign(pr->machines_per_stage, pr->machines_per_stage + g);
     in->moff.assign(g + 1, 0);
     for (int s = 0; s < g; ++s) in->moff[s + 1] = in->moff[s] + in->o[s];
-    in->p.assign(pr->proc, pr->proc + N * g);
-    in->q.assign(pr->power, pr->power + M);
+    if (unrel) {
+        in->unrel = true;
+        in->pm.assign(pr->proc_machine, pr->proc_machine + (size_t)N * M);
+        in->qm.assign(pr->power_machine, pr->power_machine + (size_t)N * M);
+        // per-op summary (gene records, surrogate features): the fastest machine's time;
+        // per-machine summary: the largest power any job draws on it
+        in->p.assign((size_t)N * g, 0);
+        in->q.assign(M, 0);
+        for (int j = 0; j < N; ++j)
+            for (int s = 0; s < g; ++s) {
+                int best = INT_MAX;
+                for (int m = 0; m < in->o[s]; ++m) {
+                    const int mg = in->moff[s] + m;
+                    best = std::min(best, in->pm[(size_t)j * M + mg]);
+                    in->q[mg] = std::max(in->q[mg], in->qm[(size_t)j * M + mg]);
+                }
+                in->p[j * g + s] = best;
+            }
+    } else {
+        in->p.assign(pr->proc, pr->proc + N * g);
+        in->q.assign(pr->power, pr->power + M);
+    }
     in->R.assign(pr->release, pr->release + N);
     in->D.assign(pr->due, pr->due + N);
     in->status.assign(N * g, kStFree);
@@ -401,9 +450,17 @@ namespace {
 int reschedule_impl(ffs_instance *in, const ffs_arrivals *arr, int32_t t_now, bool static_plan) {
     if (!in || t_now < in->RS) return FFS_E_ARG;
     const int n1 = arr ? arr->job_count : 0;
-    if (n1 < 0 || in->N + n1 > kMaxN || (n1 > 0 && (!arr->proc || !arr->release || !arr->due))) return FFS_E_ARG;
-    for (int i = 0; i < n1 * in->g; ++i)
-        if (arr->proc[i] < 0 || arr->proc[i] > kMaxP) return FFS_E_ARG;
+    if (n1 < 0 || in->N + n1 > kMaxN || (n1 > 0 && (!arr->release || !arr->due))) return FFS_E_ARG;
+    if (n1 > 0 && (in->unrel ? (!arr->proc_machine || !arr->power_machine) : !arr->proc)) return FFS_E_ARG;
+    if (in->unrel) {
+        for (size_t i = 0; i < (size_t)n1 * in->M; ++i) {
+            if (arr->proc_machine[i] < 0 || arr->proc_machine[i] > kMaxP || arr->power_machine[i] < 0) return FFS_E_ARG;
+            if (arr->power_machine[i] > in->Qmax) return FFS_E_INFEASIBLE;
+        }
+    } else {
+        for (int i = 0; i < n1 * in->g; ++i)
+            if (arr->proc[i] < 0 || arr->proc[i] > kMaxP) return FFS_E_ARG;
+    }
     for (int j = 0; j < n1; ++j)
         if (arr->release[j] < 0) return FFS_E_ARG;
     if (!in->has_plan && t_now != in->RS) return FFS_E_STATE;
@@ -413,19 +470,34 @@ int reschedule_impl(ffs_instance *in, const ffs_arrivals *arr, int32_t t_now, bo
         // (or, in the static approach, fixed in the plan).
         const int later = static_plan ? kStFixed : kStFree;
         for (int i = 0; i < in->N * g; ++i) {
-            const int st = in->S0[i], en = in->S0[i] + in->p[i];
+            const int st = in->S0[i], en = in->S0[i] + op_p(in, i / g, i % g, in->M0[i]);
             in->status[i] = en <= t_now ? kStDone : st < t_now ? kStExec : later;
         }
     }
     for (int j = 0; j < n1; ++j) {
         for (int s = 0; s < g; ++s) {
-            in->p.push_back(arr->proc[j * g + s]);
+            int pv;
+            if (in->unrel) {
+                pv = INT_MAX;
+                for (int m = 0; m < in->o[s]; ++m) {
+                    const size_t i = (size_t)j * in->M + in->moff[s] + m;
+                    pv = std::min(pv, arr->proc_machine[i]);
+                    in->q[in->moff[s] + m] = std::max(in->q[in->moff[s] + m], arr->power_machine[i]);
+                }
+            } else {
+                pv = arr->proc[j * g + s];
+            }
+            in->p.push_back(pv);
             in->status.push_back(kStFree);
             in->S0.push_back(0);
             in->M0.push_back(0);
         }
         in->R.push_back(arr->release[j]);
         in->D.push_back(arr->due[j]);
+    }
+    if (in->unrel) {
+        in->pm.insert(in->pm.end(), arr ? arr->proc_machine : nullptr, arr ? arr->proc_machine + (size_t)n1 * in->M : nullptr);
+        in->qm.insert(in->qm.end(), arr ? arr->power_machine : nullptr, arr ? arr->power_machine + (size_t)n1 * in->M : nullptr);
     }
     in->N += n1;
     in->RS = t_now;
@@ -1286,6 +1358,12 @@ extern "C" {
 int ga_batch_create(ffs_instance *const *insts, int32_t count, const ga_params *par, ga_batch **out) {
     if (!insts || !par || !out || count < 1) return FFS_E_ARG;
     *out = nullptr;
+    for (int i = 0; i < count; ++i)
+        if (insts[i] && insts[i]->unrel) {
+            std::snprintf(ffs_rt::g_last_error, sizeof(ffs_rt::g_last_error),
+                          "batched runs take identical-machine instances only");
+            return FFS_E_ARG;
+        }
     FFS_TRY(check_modes(par->order_mode, par->machine_mode));
     const int P = par->pop, I = par->island;
     if (P < 2 || P % 2 || I < 2 || I % 2 || P % I || par->tournament_k < 0 || par->tournament_k > 32 ||

@@ -129,7 +129,7 @@ struct Request {
     ffs_instance *inst = nullptr;
     bool has_arrivals = false;
     int32_t n_arr = 0, t_now = 0, generations = 0;
-    std::vector<int32_t> proc, release, due;
+    std::vector<int32_t> proc, release, due, proc_machine, power_machine;
     bool prepared = false;          // ffs_reschedule applied, footprint known
     ga_params par{};
     ffs_request_info info{};
@@ -237,7 +237,9 @@ bool evict_one(ffs_service *s, ffs_instance *keep) {
 AdmitResult admit(ffs_service *s, Slot &slot, Request *r) {
     InstState &is = *inst_state(s, r->inst);
     if (!r->prepared) {
-        ffs_arrivals a{r->n_arr, r->proc.data(), r->release.data(), r->due.data()};
+        ffs_arrivals a{r->n_arr, r->proc.data(), r->release.data(), r->due.data(),
+                       r->proc_machine.empty() ? nullptr : r->proc_machine.data(),
+                       r->power_machine.empty() ? nullptr : r->power_machine.data()};
         int rc = ffs_reschedule(r->inst, r->has_arrivals ? &a : nullptr, r->t_now);
         if (rc == FFS_OK) rc = sync_device(r->inst);
         r->par = s->cfg.ga;
@@ -509,10 +511,15 @@ int ffs_service_submit(ffs_service *s, ffs_instance *inst, const ffs_arrivals *a
     r->generations = generations;
     if (arr) {
         const int n = arr->job_count;
-        if (n < 0 || (n > 0 && (!arr->proc || !arr->release || !arr->due))) return FFS_E_ARG;
+        if (n < 0 || (n > 0 && (!arr->release || !arr->due))) return FFS_E_ARG;
+        if (n > 0 && (inst->unrel ? (!arr->proc_machine || !arr->power_machine) : !arr->proc)) return FFS_E_ARG;
         r->has_arrivals = true;
         r->n_arr = n;
-        r->proc.assign(arr->proc, arr->proc + (size_t)n * inst->g);
+        if (arr->proc) r->proc.assign(arr->proc, arr->proc + (size_t)n * inst->g);
+        if (inst->unrel && n > 0) {
+            r->proc_machine.assign(arr->proc_machine, arr->proc_machine + (size_t)n * inst->M);
+            r->power_machine.assign(arr->power_machine, arr->power_machine + (size_t)n * inst->M);
+        }
         r->release.assign(arr->release, arr->release + n);
         r->due.assign(arr->due, arr->due + n);
     }

@@ -35,11 +35,24 @@ class FFSError(RuntimeError):
 class Problem_c(C.Structure):
     _fields_ = [("n_jobs", C.c_int32), ("n_stages", C.c_int32), ("machines_per_stage", _i32p),
                 ("proc", _i32p), ("power", _i32p), ("release", _i32p), ("due", _i32p),
-                ("peak_power", C.c_int32), ("wt", C.c_int32)]
+                ("peak_power", C.c_int32), ("wt", C.c_int32), ("proc_machine", _i32p),
+                ("power_machine", _i32p)]
 
 
 class Arrivals_c(C.Structure):
-    _fields_ = [("job_count", C.c_int32), ("proc", _i32p), ("release", _i32p), ("due", _i32p)]
+    _fields_ = [("job_count", C.c_int32), ("proc", _i32p), ("release", _i32p), ("due", _i32p),
+                ("proc_machine", _i32p), ("power_machine", _i32p)]
+
+
+def _arrivals_c(arrivals, keep: list):
+    p, R, D = _i32(arrivals.p), _i32(arrivals.R), _i32(arrivals.D)
+    pm = getattr(arrivals, "pm", None)
+    qm = getattr(arrivals, "qm", None)
+    pm = None if pm is None else _i32(pm)
+    qm = None if qm is None else _i32(qm)
+    keep.extend([p, R, D, pm, qm])
+    return Arrivals_c(int(p.shape[0]), _p(p), _p(R), _p(D), None if pm is None else _p(pm),
+                      None if qm is None else _p(qm))
 
 
 class GAParams_c(C.Structure):
@@ -199,8 +212,13 @@ class Instance:
     def __init__(self, problem):
         self._keep = [_i32(problem.o), _i32(problem.p), _i32(problem.q), _i32(problem.R), _i32(problem.D)]
         o, p, q, R, D = self._keep
+        pm, qm = getattr(problem, "pm", None), getattr(problem, "qm", None)
+        pm = None if pm is None else _i32(pm)
+        qm = None if qm is None else _i32(qm)
+        self._keep += [pm, qm]
         pr = Problem_c(int(p.shape[0]), int(o.shape[0]), _p(o), _p(p), _p(q), _p(R), _p(D),
-                       int(problem.Qmax), int(problem.WT))
+                       int(problem.Qmax), int(problem.WT), None if pm is None else _p(pm),
+                       None if qm is None else _p(qm))
         h = C.c_void_p()
         _check(lib().ffs_instance_create(C.byref(pr), C.byref(h)), "ffs_instance_create")
         self._h = h
@@ -250,8 +268,8 @@ class Instance:
     def reschedule(self, arrivals, t_now: int, static: bool = False):
         """Rescheduling point t_now with new jobs (Sec. 4.1); ``static`` keeps the executed
         plan and schedules only the new jobs after it (``ffs_reschedule_static``)."""
-        p, R, D = _i32(arrivals.p), _i32(arrivals.R), _i32(arrivals.D)
-        a = Arrivals_c(int(p.shape[0]), _p(p), _p(R), _p(D))
+        keep = []
+        a = _arrivals_c(arrivals, keep)
         fn = lib().ffs_reschedule_static if static else lib().ffs_reschedule
         _check(fn(self._h, C.byref(a), int(t_now)), "ffs_reschedule_static" if static else "ffs_reschedule")
 
@@ -597,8 +615,8 @@ class Service:
             _check(lib().ffs_service_submit(self._h, inst.handle, None, int(t_now), int(generations), C.byref(t)),
                    "ffs_service_submit")
         else:
-            p, R, D = _i32(arrivals.p), _i32(arrivals.R), _i32(arrivals.D)
-            a = Arrivals_c(int(p.shape[0]), _p(p), _p(R), _p(D))
+            keep = []
+            a = _arrivals_c(arrivals, keep)
             _check(lib().ffs_service_submit(self._h, inst.handle, C.byref(a), int(t_now), int(generations),
                                             C.byref(t)), "ffs_service_submit")
         return int(t.value)

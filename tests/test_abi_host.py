@@ -99,6 +99,25 @@ def test_static_reschedule_chain_matches_oracle(seed):
         assert inf["horizon"] >= int((orc_i.S0 + orc_i.p)[orc_i.status == oracle.ST_FIXED].max()) - t_now
 
 
+def test_unrelated_instance_validation():
+    """Per-machine tables: both or neither; a job's power on a machine above the peak is
+    infeasible; arrivals of such an instance need their own tables."""
+    rng = np.random.default_rng(1)
+    pr = wl.unrelated_instance(rng, 6, 2, 1, 3, 20, 2, 10, 60)
+    inst = ffs.Instance(pr)
+    assert inst.info()["n_genes"] == 12
+    bad = wl.Problem(o=pr.o, p=pr.p, q=pr.q, R=pr.R, D=pr.D, Qmax=pr.Qmax, pm=pr.pm, qm=pr.qm.copy())
+    bad.qm[0, 0] = pr.Qmax + 1
+    with pytest.raises(ffs.FFSError) as e:
+        ffs.Instance(bad)
+    assert e.value.code == -2
+    # arrivals without per-machine tables are refused by an unrelated instance
+    with pytest.raises(ffs.FFSError):
+        inst.reschedule(wl.Arrivals(p=np.ones((1, 2)), R=[0], D=[9]), 0)
+    inst.reschedule(wl.unrelated_arrivals(rng, 2, pr.o, 0, 20, 2, 10, pr.Qmax), 0)
+    assert inst.info()["n_genes"] == 16
+
+
 def test_reschedule_rules():
     lib_i = ffs.Instance(wl.static_small(1))
     arr = wl.Arrivals(p=np.ones((1, 3)), R=[5], D=[50])
