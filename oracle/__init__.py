@@ -24,6 +24,7 @@ _lib = None
 ST_FREE, ST_EXEC, ST_DONE, ST_FIXED = 0, 1, 2, 3
 ORDER_TOPO, ORDER_STAGE, ORDER_GIVEN = 0, 1, 2
 MACH_GENE, MACH_EARLIEST = 0, 1
+PLACE_INSERT = 4  # or-ed into the machine mode: back-fill machine idle gaps
 
 _i32p = C.POINTER(C.c_int32)
 

@@ -27,6 +27,7 @@
 enum { ST_FREE = 0, ST_EXEC = 1, ST_DONE = 2, ST_FIXED = 3 };  /* Alg. 1 classification; FIXED: static approach */
 enum { ORDER_TOPO = 0, ORDER_STAGE = 1, ORDER_GIVEN = 2 };  /* how Z is built         */
 enum { MACH_GENE = 0, MACH_EARLIEST = 1 };                  /* how M_js is chosen     */
+enum { PLACE_INSERT = 4 };  /* flag on the machine mode: back-fill machine idle gaps */
 enum { P_INIT_Y = 1, P_INIT_X = 2, P_SELECT = 3, P_CROSS = 4, P_MUTATE = 5 };
 
 /* ---------------------------------------------------------------- Philox4x32-10 */
@@ -198,6 +199,10 @@ static int32_t max32(int32_t a, int32_t b) { return a > b ? a : b; }
  * appended to machines in assignment order).  It starts at the smallest integer t from
  * there on such that, for every instant tau in [t, t+p), the power already drawn Q_tau
  * (Eq. 8-9) plus its own power stays within Qmax (Eq. 7).  Otherwise it is delayed.
+ * With PLACE_INSERT or-ed into the machine mode (an option, not the paper's Alg. 2), an
+ * op may instead fill an idle gap: on machine m it starts at the smallest integer
+ * t >= max(est, end of m's frozen ops) such that m is idle at every instant of [t, t+p)
+ * (no op assigned before it overlaps) and the power check holds.
  *
  * The power profile is a literal per-instant array Q_tau over [RS, RS+H), with H an upper
  * bound on the makespan (all free ops run back to back after the latest release or
@@ -208,6 +213,8 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
                    int32_t *S_out, int32_t *M_out, orc_eval *ev)
 {
     const int32_t N = in->N, g = in->g, RS = in->RS, Qmax = in->Qmax;
+    const int insert = (mach_mode & PLACE_INSERT) != 0;
+    mach_mode &= 1;
     memset(ev, 0, sizeof(*ev));
 
     int32_t *moff = (int32_t *)calloc((size_t)g + 1, sizeof(int32_t));
@@ -229,7 +236,7 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
             break;
         }
         seen[v] = 1;
-        if (mach_mode == MACH_GENE && (x[k] < 0 || x[k] >= in->o[gstg[k]])) {
+        if ((mach_mode & 1) == MACH_GENE && (x[k] < 0 || x[k] >= in->o[gstg[k]])) {
             ev->err = -2;
             break;
         }
@@ -264,6 +271,8 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
     int32_t *Qt = (int32_t *)calloc((size_t)H, sizeof(int32_t));     /* Q_tau - at RS+i */
     int32_t *mfree = (int32_t *)calloc((size_t)Mtot, sizeof(int32_t)); /* end of last op on m */
     int32_t *C = (int32_t *)calloc((size_t)N + 1, sizeof(int32_t));   /* C_{j, last placed} */
+    /* insertion: instants at which each machine runs an op placed by this decode */
+    uint8_t *busy = insert ? (uint8_t *)calloc((size_t)Mtot * (size_t)H, 1) : NULL;
 
     for (int32_t m = 0; m < Mtot; m++)
         mfree[m] = RS;
@@ -355,6 +364,7 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
                 for (int32_t tau = t; tau < t + pj; tau++) {
                     ev->probes++;
                     if (Qt[tau - RS] + qm > Qmax) bad = tau;
+                    if (insert && busy[(size_t)mg * H + (tau - RS)]) bad = tau;
                 }
                 if (bad < 0) break;
                 t = bad + 1;                             /* delayed past the violation */
@@ -365,7 +375,11 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
         int32_t mg = moff[s] + best_m, pj = best_p, qb = op_q(in, j, mg, Mtot);
         for (int32_t tau = best_t; tau < best_t + pj; tau++)
             Qt[tau - RS] += qb;
-        mfree[mg] = best_t + pj;
+        if (insert) {
+            for (int32_t tau = best_t; tau < best_t + pj; tau++) busy[(size_t)mg * H + (tau - RS)] = 1;
+        } else {
+            mfree[mg] = best_t + pj;
+        }
         C[j] = best_t + pj;
         S_out[j * g + s] = best_t;
         M_out[j * g + s] = best_m;
@@ -388,7 +402,7 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
         ev->obj = (int64_t)in->WT * tard + cmax;
     }
 
-    free(placed); free(order); free(gene_at); free(Qt); free(mfree); free(C);
+    free(placed); free(order); free(gene_at); free(Qt); free(mfree); free(C); free(busy);
     free(moff); free(gjob); free(gstg);
     return ev->err;
 }
@@ -569,7 +583,7 @@ int32_t orc_ga_init(const orc_inst *in, const orc_ga_params *par, orc_ga_state *
             int16_t t = y[a]; y[a] = y[b]; y[b] = t;
         }
         for (int32_t k = 0; k < K; k++) {
-            if (par->mach_mode == MACH_GENE) {
+            if ((par->mach_mode & 1) == MACH_GENE) {
                 uint32_t u = orc_draw(par->seed, P_INIT_X, par->instance_id, 0, i, k);
                 x[k] = (int8_t)below(u, (uint32_t)in->o[gstg[k]]);
             } else {
@@ -590,7 +604,7 @@ int32_t orc_ga_step(const orc_inst *in, const orc_ga_params *par, orc_ga_state *
     const int32_t gen = st->gen + 1;
     const uint64_t seed = par->seed;
     const int32_t iid = par->instance_id;
-    const int gene_mode = par->mach_mode == MACH_GENE;
+    const int gene_mode = (par->mach_mode & 1) == MACH_GENE;
 
     int32_t *gstg = (int32_t *)calloc((size_t)K + 1, sizeof(int32_t));
     int32_t *gjob = (int32_t *)calloc((size_t)K + 1, sizeof(int32_t));

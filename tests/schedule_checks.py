@@ -104,12 +104,14 @@ def gene_map(inst):
     return np.array(gj, dtype=np.int64), np.array(gs, dtype=np.int64)
 
 
-def check_greedy_earliest(inst, order, S, M, any_machine: bool):
+def check_greedy_earliest(inst, order, S, M, any_machine: bool, insert: bool = False):
     """Replay `order` and verify each op starts at the earliest integer instant at which it
     is available, its machine has finished every op assigned to it before, and the power
     of the ops assigned before it plus its own stays within Qmax at every instant; with
     `any_machine`, on the machine where that start gives the earliest completion (lowest
-    index among equals; with identical machines, the earliest start)."""
+    index among equals; with identical machines, the earliest start).  With `insert`, an
+    op may start in any idle gap of its machine after the machine's frozen ops, instead of
+    after the op assigned to it last."""
     N, g = inst.p.shape
     RS = inst.RS
     off = machine_offsets(inst.o)
@@ -119,6 +121,7 @@ def check_greedy_earliest(inst, order, S, M, any_machine: bool):
     Qt = np.zeros(max(H - RS, 1), dtype=np.int64)
     mfree = np.full(int(off[-1]), RS, dtype=np.int64)
     Cj = np.zeros(N, dtype=np.int64)
+    placed = [[] for _ in range(int(off[-1]))]  # intervals of ops placed on each machine
     for j in range(N):
         for s in range(g):
             if inst.status[j, s] != ST_FREE:
@@ -139,7 +142,8 @@ def check_greedy_earliest(inst, order, S, M, any_machine: bool):
             while True:
                 if t + p - RS > len(Qt):
                     Qt = np.concatenate([Qt, np.zeros(t + p - RS - len(Qt) + 1, np.int64)])
-                if int(Qt[t - RS:t - RS + p].max()) + qm <= inst.Qmax:
+                idle = all(t + p <= a or b <= t for a, b in placed[mg]) if insert else True
+                if idle and (p == 0 or int(Qt[t - RS:t - RS + p].max()) + qm <= inst.Qmax):
                     break
                 t += 1
             if best is None or t + p < best[0] + best[2]:
@@ -148,5 +152,8 @@ def check_greedy_earliest(inst, order, S, M, any_machine: bool):
         mg = off[s] + best[1]
         p = best[2]
         Qt[best[0] - RS:best[0] - RS + p] += op_q(inst, j, s, best[1])
-        mfree[mg] = best[0] + p
+        if insert:
+            placed[mg].append((best[0], best[0] + p))
+        else:
+            mfree[mg] = best[0] + p
         Cj[j] = best[0] + p

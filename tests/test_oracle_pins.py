@@ -659,3 +659,87 @@ def test_unrelated_invariants_and_greedy(seed):
         inst.commit(r["S"], r["M"])
         t_now = inst.RS + (r["cmax"] - inst.RS) // 3
         inst.reschedule(wl.unrelated_arrivals(rng, 3, pr.o, t_now, 30, 2, 15, pr.Qmax), t_now)
+
+
+# ---------------------------------------------------------------- idle-gap insertion (option)
+
+def test_insert_hand_example():
+    """One machine.  Job A (released at 10, p 5) is assigned first and runs 10..15.  Job B
+    (released at 0, p 3) comes second: appended it waits for A (15..18); inserted it fills
+    the idle gap before A (0..3)."""
+    pr = wl.Problem(o=[1], p=[[5], [3]], q=[1], R=[10, 0], D=[100, 100], Qmax=5)
+    inst = oracle.Instance(pr)
+    y = np.array([2, 1], np.int16)
+    a = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST)
+    b = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST | oracle.PLACE_INSERT)
+    assert a["S"].ravel().tolist() == [10, 15] and a["cmax"] == 18
+    assert b["S"].ravel().tolist() == [10, 0] and b["cmax"] == 15
+
+
+def test_insert_gap_too_short_or_power_bound():
+    """The gap before A (0..10) holds B only if B fits in it and the power allows: with
+    p_B = 11 it does not fit, so B follows A; with a second job C drawing power over 0..4
+    that leaves no room for B, B starts once C ends."""
+    pr = wl.Problem(o=[1, 1], p=[[5, 1], [11, 1], [4, 1]], q=[2, 2], R=[10, 0, 0], D=[99] * 3, Qmax=3)
+    inst = oracle.Instance(pr)
+    # genes job-major: A0 A1 B0 B1 C0 C1; stage 0 order A, B, C (B too long for the gap)
+    y = np.array([6, 3, 5, 2, 4, 1], np.int16)
+    r = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST | oracle.PLACE_INSERT)
+    assert r["S"][1, 0] == 15  # after A
+    # C (p 4) fits the gap 0..10 on machine 0 of stage 0
+    assert r["S"][2, 0] == 0
+    check_invariants(inst, r["S"], r["M"], obj=r["obj"], tard=r["tard"], cmax=r["cmax"])
+    # stage 1 (one machine, power 2 each, peak 3): ops cannot overlap each other in power
+    # either; A1 after A0 ends (15), C1 fills the gap before it
+    assert r["S"][2, 1] == 4
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_insert_invariants_and_greedy(seed):
+    """Eq. (4)-(10) on insertion schedules and every placement the earliest idle, power-
+    feasible start (earliest completion across machines), checked by the independent
+    replay; identical and unrelated machines, along a rescheduling chain."""
+    rng = np.random.default_rng(seed)
+    for pr in (wl.random_instance(rng, 12, 3, 1, 3, 30, 5, 20, 55, release_hi=40),
+               wl.unrelated_instance(rng, 12, 3, 1, 3, 30, 2, 15, 50)):
+        inst = oracle.Instance(pr)
+        for ev in range(3):
+            Y, X = wl.random_chromosomes(rng, 5, inst.K, inst.gene_machines())
+            for i in range(5):
+                for mach in (MACH_EARLIEST, MACH_GENE):
+                    r = inst.decode(Y[i], X[i], ORDER_STAGE, mach | oracle.PLACE_INSERT)
+                    check_invariants(inst, r["S"], r["M"], obj=r["obj"], tard=r["tard"], cmax=r["cmax"])
+                    check_greedy_earliest(inst, stage_order(inst, Y[i]), r["S"], r["M"],
+                                          any_machine=mach == MACH_EARLIEST, insert=True)
+            inst.commit(r["S"], r["M"])
+            t_now = inst.RS + (r["cmax"] - inst.RS) // 3
+            arr = (wl.random_arrivals(rng, 3, pr.g, t_now, 30) if pr.pm is None else
+                   wl.unrelated_arrivals(rng, 3, pr.o, t_now, 30, 2, 15, pr.Qmax))
+            inst.reschedule(arr, t_now)
+
+
+def test_insert_equals_append_without_gaps():
+    """One stage, every release at 0 and a peak no schedule reaches: each machine runs its
+    ops back to back from 0, no gap ever opens, and insertion gives the appended schedule."""
+    rng = np.random.default_rng(9)
+    pr = wl.random_instance(rng, 10, 1, 3, 3, 30, 5, 20, 100)
+    pr.Qmax = int(pr.q.sum())
+    inst = oracle.Instance(pr)
+    for _ in range(10):
+        y = (rng.permutation(inst.K) + 1).astype(np.int16)
+        a = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST)
+        b = inst.decode(y, None, ORDER_STAGE, MACH_EARLIEST | oracle.PLACE_INSERT)
+        assert np.array_equal(a["S"], b["S"]) and np.array_equal(a["M"], b["M"])
+
+
+def test_insert_ga_runs():
+    """The GA with insertion keeps valid populations and is elitist."""
+    inst = oracle.Instance(wl.static_small(3))
+    ga = oracle.GA(inst, P=32, island=16, seed=2, mach_mode=MACH_GENE | oracle.PLACE_INSERT).init()
+    best = ga.bobj.min()
+    for _ in range(5):
+        ga.step()
+        assert ga.bobj.min() <= best
+        best = ga.bobj.min()
+    for i in range(32):
+        assert sorted(ga.Y[i, :ga.K].tolist()) == list(range(1, ga.K + 1))
