@@ -434,6 +434,51 @@ def bench_surrogate(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- insertion placement
+INS_WORKLOAD = ("idle-gap insertion placement vs Alg. 2's append placement on the dynamic rescheduling job "
+                "(50 initial jobs, 5 stages x U{2..4} machines, events at t=100,250,400 adding 10 jobs; population "
+                "1024, 500 generations per solve, stage-by-stage order, earliest machine)")
+
+
+def bench_insert(args):
+    import torch
+
+    from paper_1903_10741_gb300 import ffs
+
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    stream = torch.cuda.current_stream()
+    dyn = wl.dynamic_medium(1)
+    G = args.generations
+    out = {}
+    for name, mach in (("insert", ffs.MACH_EARLIEST | ffs.PLACE_INSERT), ("append", ffs.MACH_EARLIEST)):
+        for rep in range(args.warmup + args.steps):
+            inst = ffs.Instance(dyn.problem)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            objs, decodes = [], 0
+            for solve in range(len(dyn.events) + 1):
+                pop = ffs.Population(inst, P=P, island=ISLAND, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE,
+                                     seed=SEED, instance_id=solve, mach_mode=mach, stream=stream)
+                objs.append(pop.run(G, want_schedule=False)["obj"])
+                decodes += P * (G + 1) + 1
+                if solve < len(dyn.events):
+                    inst.reschedule(dyn.events[solve][1], dyn.events[solve][0])
+            e.record(stream)
+            e.synchronize()
+            if rep >= args.warmup:
+                out.setdefault(name, []).append((decodes / (s.elapsed_time(e) / 1e3), objs))
+    v = float(np.mean([d for d, _ in out["insert"]]))
+    line = {
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": INS_WORKLOAD, "generations_per_solve": G,
+                   "append_decodes_per_s": float(np.mean([d for d, _ in out["append"]])),
+                   "best_objectives_insert": out["insert"][-1][1], "best_objectives_append": out["append"][-1][1],
+                   "timing": "CUDA events around each whole job, instance creation and commits included"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- unrelated machines
 UNREL_WORKLOAD = ("unrelated parallel machines (Table 2: P_jsm, Q_jsm per job and machine), earliest-completion "
                   "machine choice: 50 jobs, 5 stages x U{2..4} machines, P_jsm U{1..99}, Q_jsm U{5..30}, peak 55% "
@@ -685,7 +730,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["dynamic", "batched", "surrogate", "service", "static-vs-reactive",
-                                           "unrelated"],
+                                           "unrelated", "insert"],
                     default="dynamic",
                     help="dynamic: the headline rescheduling job; batched: 256 uneven instances; "
                          "surrogate: time-to-objective of the surrogate-assisted GA; service: Poisson "
@@ -720,6 +765,8 @@ def main():
         if args.generations == 500:
             args.generations = 1000
         bench_surrogate(args)
+    elif args.workload == "insert":
+        bench_insert(args)
     elif args.workload == "unrelated":
         bench_unrelated(args)
     elif args.workload == "static-vs-reactive":

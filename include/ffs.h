@@ -52,6 +52,11 @@ extern "C" {
 #define FFS_MACH_GENE       0  /* machine of op (j, s) is x_js, Eq. (10)                 */
 #define FFS_MACH_EARLIEST   1  /* machine with the earliest power-feasible start (completion,
                                   with unrelated machines)                                 */
+/* Or-ed into a machine mode: idle-gap insertion placement (an option; the paper's Alg. 2
+ * appends each op after the op last assigned to its machine).  An op may start in any
+ * idle gap of its machine after the machine's frozen ops, with the same power check
+ * (Eq. 7).  Only with FFS_ORDER_STAGE, and not in batched runs. */
+#define FFS_PLACE_INSERT    4
 
 typedef struct ffs_instance ffs_instance;      /* opaque: problem + rescheduling state    */
 typedef struct ga_population ga_population;    /* opaque: device-resident GA state        */
@@ -207,7 +212,7 @@ typedef struct {
 /* Copies the `count` instances' current tables and runs generation 0 of every one.  All
  * share `params` (pop, island, operators, modes, seed, stream); instance i draws from
  * stream id params->instance_id + i, so its run equals ga_population_create + ga_run
- * with that id.  The instances must not be rescheduled while the batch is used. * Instances with unrelated machines are refused (FFS_E_ARG). */
+ * with that id.  The instances must not be rescheduled while the batch is used. * Instances with unrelated machines are refused (FFS_E_ARG). FFS_PLACE_INSERT is refused too. */
 int ga_batch_create(ffs_instance *const *insts, int32_t count, const ga_params *params, ga_batch **out);
 
 /* Frees a batch.  NULL is accepted. */

@@ -16,8 +16,12 @@ constexpr int kMachGene = 0, kMachEarliest = 1;
 // Kernel-side machine modes add the unrelated-machine variants (per-gene p and q per
 // machine, the earliest completion instead of the earliest start).
 constexpr int kMachGeneU = 2, kMachEarliestU = 3;
+// Bit 2 (kPlaceInsert) selects idle-gap insertion placement.
+constexpr int kPlaceInsert = 4;
 __host__ __device__ constexpr bool mach_gene(int m) { return (m & 1) == 0; }
-__host__ __device__ constexpr bool mach_unrel(int m) { return m >= 2; }
+__host__ __device__ constexpr bool mach_unrel(int m) { return (m & 2) != 0; }
+__host__ __device__ constexpr bool mach_insert(int m) { return (m & kPlaceInsert) != 0; }
+
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror & Shaw, SC'11: ten rounds of the 4x32 Philox S-box with
@@ -126,9 +130,30 @@ __device__ __forceinline__ uint32_t halves(unsigned m) {
 // borrow crosses into the next halfword.  A ballot finds the last violating slot and the
 // candidate jumps past it.  Returns `limit` as soon as the answer cannot be below it.
 // Loads stay below hw <= Hcap (Hcap a multiple of 4); lanes past the window read slot 0.
+// First slot >= t at which a machine is idle, from its occupancy bitmap (nw words): each
+// step the warp looks at 32 words (1024 slots).  At least 32 nw if there is none below.
+__device__ __forceinline__ int next_idle(const uint32_t *bm, int nw, int t, int lane) {
+    for (int w0 = t >> 5; w0 < nw; w0 += 32) {
+        const int w = w0 + lane;
+        uint32_t fr = w < nw ? ~bm[w] : 0u;
+        if (w == (t >> 5)) fr &= ~((1u << (t & 31)) - 1u);  // slots below t do not count
+        const unsigned any = __ballot_sync(kFull, fr != 0u);
+        if (any) {
+            const int l = __ffs(any) - 1;
+            return 32 * (w0 + l) + __ffs(__shfl_sync(kFull, fr, l)) - 1;
+        }
+    }
+    return t > 32 * nw ? t : 32 * nw;
+}
+
+// With INS, `bm` is the machine's occupancy bitmap (nw words; bit t: busy at slot t) and a
+// slot also violates when the machine is busy there; a candidate start that falls in a
+// busy stretch moves to the stretch's end directly.  Bits are only set below hw.
+template <bool INS = false>
 __device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0, int p, uint32_t q2,
-                                              int limit, int lane) {
+                                              int limit, int lane, const uint32_t *bm = nullptr, int nw = 0) {
     int run = t0;
+    if (INS && run < limit) run = next_idle(bm, nw, run, lane);
     if (run >= limit) return limit;
     int end = min(run + p, hw);
     int c = run & ~3;
@@ -138,14 +163,17 @@ __device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0,
         const uint2 w = *reinterpret_cast<const uint2 *>(h + (in ? b : 0));
         const uint32_t dx = (w.x | 0x80008000u) - q2, dy = (w.y | 0x80008000u) - q2;
         const unsigned good = ((dx >> 15) & 1u) | ((dx >> 30) & 2u) | ((dy >> 13) & 4u) | ((dy >> 28) & 8u);
-        const unsigned badm = in ? (~good & range4(b, run, end)) : 0u;  // bit i: slot b + i violates
-        const unsigned bm = __ballot_sync(kFull, badm != 0);
-        if (bm == 0) {
+        unsigned busy = 0u;
+        if (INS && in) busy = (bm[b >> 5] >> (b & 31)) & 0xFu;
+        const unsigned badm = in ? ((~good | busy) & range4(b, run, end)) : 0u;  // bit i: slot b + i violates
+        const unsigned vm = __ballot_sync(kFull, badm != 0);
+        if (vm == 0) {
             c += 128;
         } else {
-            const int l = 31 - __clz(bm);
+            const int l = 31 - __clz(vm);
             const unsigned lm = __shfl_sync(kFull, badm, l);
             run = c + 4 * l + (31 - __clz(lm)) + 1;  // one past the last violating slot
+            if (INS && run < limit) run = next_idle(bm, nw, run, lane);
             if (run >= limit) return limit;
             end = min(run + p, hw);
             c = run & ~3;
@@ -170,16 +198,29 @@ __device__ __forceinline__ void commit_power(uint16_t *h, int &hw, int t, int e,
     hw = max(hw, e);
 }
 
+// Marks slots [t, e) busy in a machine's occupancy bitmap; lane l takes word (t >> 5) + l
+// (+ 32 i), so no word has two writers.
+__device__ __forceinline__ void commit_busy(uint32_t *bm, int t, int e, int lane) {
+    for (int w = (t >> 5) + lane; w <= ((e - 1) >> 5); w += 32) {
+        const int lo = max(t - 32 * w, 0), hi = min(e - 32 * w, 32);
+        const uint32_t hm = hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u);
+        bm[w] |= hm & ~((1u << lo) - 1u);
+    }
+}
+
 // Machine choice for one op among the lanes m < os of a stage, each holding its machine's
 // availability t0 (slots past RS; INT_MAX elsewhere) and power q2.  Returns the
 // lexicographic minimum of (earliest power-feasible start, machine): the machine that
 // frees first is scanned first, another only if it could still start earlier.
+template <bool INS = false>
 __device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int t0, uint32_t q2, int os,
-                                                 int p, int lane, int &best_t, int &best_m) {
+                                                 int p, int lane, int &best_t, int &best_m,
+                                                 const uint32_t *busy = nullptr, int words = 0) {
     const unsigned key = lane < os ? ((unsigned)t0 << 5) | (unsigned)lane : 0xFFFFFFFFu;
     const unsigned kmin = __reduce_min_sync(kFull, key);
     best_m = (int)(kmin & 31u);
-    best_t = earliest_start(h, hw, (int)(kmin >> 5), p, __shfl_sync(kFull, q2, best_m), INT_MAX, lane);
+    best_t = earliest_start<INS>(h, hw, (int)(kmin >> 5), p, __shfl_sync(kFull, q2, best_m), INT_MAX, lane,
+                                 busy + (size_t)best_m * words, words);
     unsigned cand = __ballot_sync(kFull, lane < os && lane != best_m && t0 < best_t + (lane < best_m));
     while (cand) {
         const int m = __ffs(cand) - 1;
@@ -187,7 +228,8 @@ __device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int 
         const int tm = __shfl_sync(kFull, t0, m);
         const int lim = best_t + (m < best_m ? 1 : 0);
         if (tm >= lim) continue;
-        const int t = earliest_start(h, hw, tm, p, __shfl_sync(kFull, q2, m), lim, lane);
+        const int t = earliest_start<INS>(h, hw, tm, p, __shfl_sync(kFull, q2, m), lim, lane,
+                                          busy + (size_t)m * words, words);
         if (t < lim) {
             best_t = t;
             best_m = m;
@@ -199,15 +241,17 @@ __device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int 
 // op's processing time p on it.  Returns the lexicographic minimum of (earliest completion
 // of a power-feasible start, machine) and that machine's p.  The machine whose completion
 // bound t0 + p is lowest is scanned first; another only if its bound could still win.
+template <bool INS = false>
 __device__ __forceinline__ void earliest_machine_u(const uint16_t *h, int hw, int t0, uint32_t q2, int p, int os,
-                                                   int lane, int &best_t, int &best_m, int &best_p) {
+                                                   int lane, int &best_t, int &best_m, int &best_p,
+                                                   const uint32_t *busy = nullptr, int words = 0) {
     const int c0 = lane < os ? t0 + p : INT_MAX;
     const unsigned key = lane < os ? ((unsigned)c0 << 5) | (unsigned)lane : 0xFFFFFFFFu;
     const unsigned kmin = __reduce_min_sync(kFull, key);
     best_m = (int)(kmin & 31u);
     best_p = __shfl_sync(kFull, p, best_m);
-    best_t = earliest_start(h, hw, __shfl_sync(kFull, t0, best_m), best_p, __shfl_sync(kFull, q2, best_m), INT_MAX,
-                            lane);
+    best_t = earliest_start<INS>(h, hw, __shfl_sync(kFull, t0, best_m), best_p, __shfl_sync(kFull, q2, best_m),
+                                 INT_MAX, lane, busy + (size_t)best_m * words, words);
     int best_c = best_t + best_p;
     unsigned cand = __ballot_sync(kFull, lane < os && lane != best_m && c0 < best_c + (lane < best_m));
     while (cand) {
@@ -216,7 +260,8 @@ __device__ __forceinline__ void earliest_machine_u(const uint16_t *h, int hw, in
         const int tm = __shfl_sync(kFull, t0, m), pm = __shfl_sync(kFull, p, m);
         const int lim = best_c - pm + (m < best_m ? 1 : 0);  // starts below this complete earlier
         if (tm >= lim) continue;
-        const int t = earliest_start(h, hw, tm, pm, __shfl_sync(kFull, q2, m), lim, lane);
+        const int t = earliest_start<INS>(h, hw, tm, pm, __shfl_sync(kFull, q2, m), lim, lane,
+                                          busy + (size_t)m * words, words);
         if (t < lim) {
             best_t = t;
             best_m = m;
@@ -245,6 +290,13 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
     for (int j = lane; j < N; j += 32) C[j] = T.gcnt[j] > 0 ? max(T.C0[j], T.R[j]) : T.C0[j];
     for (int i = lane; i < T.E0; i += 32) h[i] = T.h0[i];
     int hw = T.E0;
+    // Insertion placement: occupancy bitmaps of the current stage's machines after the
+    // profile slice (the caller sized it with profile_bytes(Hcap, maxo)).
+    constexpr bool INS = mach_insert(MACH) && ORDER == kOrderStage;
+    const int words = busy_words(Hcap);
+    uint32_t *busy = reinterpret_cast<uint32_t *>(h + Hcap);
+    if (INS)
+        for (int i = lane; i < T.maxo * words; i += 32) busy[i] = 0u;
 
     // Validate Y (a permutation of 1..K) and X, and build inv[K - y] = gene.
     for (int i = lane; i < K; i += 32) inv[i] = -1;
@@ -286,7 +338,15 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             const int lo = T.soff[s], hi = T.soff[s + 1];
             if (lo == hi) continue;
             const int mo = T.moff[s], os = T.o[s];
-            int mf = INT_MAX;  // lane m < os: end of the last op on machine m, past RS
+            if (INS) {  // every bit set so far lies below hw
+                __syncwarp();
+                const int hwords = busy_words(hw);
+                for (int i = lane; i < os * hwords; i += 32) busy[(i / hwords) * words + i % hwords] = 0u;
+                __syncwarp();
+            }
+            // lane m < os: end of the last op on machine m past RS (with insertion: the end
+            // of its frozen ops, before which it stays unavailable)
+            int mf = INT_MAX;
             uint32_t q2 = 0;
             if (lane < os) {
                 mf = T.mfree0[mo + lane] - RS;
@@ -314,17 +374,20 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 if (mach_gene(MACH)) {
                     best_m = x[k];
                     if (mach_unrel(MACH)) p = __shfl_sync(kFull, p, best_m);
-                    best_t = earliest_start(h, hw, max(est, __shfl_sync(kFull, mf, best_m)), p,
-                                            __shfl_sync(kFull, qo2, best_m), INT_MAX, lane);
+                    best_t = earliest_start<INS>(h, hw, max(est, __shfl_sync(kFull, mf, best_m)), p,
+                                                 __shfl_sync(kFull, qo2, best_m), INT_MAX, lane,
+                                                 busy + (size_t)best_m * words, words);
                 } else if (mach_unrel(MACH)) {
-                    earliest_machine_u(h, hw, max(est, mf), qo2, p, os, lane, best_t, best_m, p);
+                    earliest_machine_u<INS>(h, hw, max(est, mf), qo2, p, os, lane, best_t, best_m, p, busy, words);
                 } else {
-                    earliest_machine(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m);
+                    earliest_machine<INS>(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m,
+                                          busy, words);
                 }
                 const int e = best_t + p;
                 if (e > Hcap) return {0, 0, 1};
                 commit_power(h, hw, best_t, e, __shfl_sync(kFull, qo2, best_m), Q2, lane);
-                if (lane == best_m) mf = e;
+                if (INS) commit_busy(busy + (size_t)best_m * words, best_t, e, lane);
+                else if (lane == best_m) mf = e;
                 if (lane == 0) {
                     C[j] = e + RS;
                     if (S_out) {

@@ -22,11 +22,15 @@ namespace edffs {
 namespace {
 
 // Views of warp `warp`'s slice after the staged tables.
+// With insertion placement the profile slice (shared, or global with gprof) is followed by
+// the occupancy bitmaps of up to maxo machines.
 __device__ __forceinline__ WarpPtrs warp_ptrs(char *tab, int blob_bytes, const Tabs &T, int Hcap,
-                                              bool ga, bool gprof, uint16_t *gscratch, int warp) {
-    const WarpLayout L = warp_layout(T.N, T.M, T.K, gprof ? 0 : Hcap, ga);
+                                              bool ga, bool gprof, uint16_t *gscratch, int warp, bool insert = false) {
+    const WarpLayout L = warp_layout(T.N, T.M, T.K, gprof ? 0 : Hcap, ga, insert && !gprof ? T.maxo : 0);
     char *ws = tab + ((blob_bytes + 127) & ~127) + warp * L.bytes;
-    return warp_view(ws, L, gprof ? gscratch + (size_t)(blockIdx.x * kWarpsPerBlock + warp) * (size_t)Hcap : nullptr);
+    return warp_view(ws, L, gprof ? gscratch + (size_t)(blockIdx.x * kWarpsPerBlock + warp) *
+                                                   gwork_stride(Hcap, T.maxo, insert)
+                                  : nullptr);
 }
 
 // ---------------------------------------------------------------- decode kernel
@@ -37,7 +41,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_decode(DecodeArgs a) {
     if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
     const Tabs T = tabs_view(tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, false, GPROF, a.gscratch, warp);
+    const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, false, GPROF, a.gscratch, warp, mach_insert(MACH));
     const int buf = a.gdev ? ((a.gdev->gen + 1) & 1) : 0;
     const int n = a.list ? *a.list_count : a.count;
     const int K = T.K, NG = T.N * T.g;
@@ -90,7 +94,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_init(GenArgs a) {
     if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
     const Tabs T = tabs_view(tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, true, false, nullptr, warp);
+    const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, true, false, nullptr, warp, mach_insert(MACH));
     const int K = T.K;
     for (int i = blockIdx.x * kWarpsPerBlock + warp; i < a.P; i += gridDim.x * kWarpsPerBlock) {
         int16_t *yo = a.Y[0] + (size_t)i * K;
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
     if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
     const Tabs T = tabs_view(tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, true, false, nullptr, warp);
+    const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, true, false, nullptr, warp, mach_insert(MACH));
     const int K = T.K, I = a.I;
     const int cur = a.dev->gen & 1, nx = cur ^ 1;
     const uint32_t gen = (uint32_t)a.dev->gen + 1;
@@ -219,7 +223,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
         if (r.status == 1) {  // the schedule outgrew the shared slice: redo it in global memory
             for (int k = lane; k < K; k += 32) w.y[k] = yo[k];  // the decode reused w.y
             __syncwarp();
-            uint16_t *hg = a.gscratch + (size_t)(blockIdx.x * kWarpsPerBlock + warp) * (size_t)a.H;
+            uint16_t *hg = a.gscratch + (size_t)(blockIdx.x * kWarpsPerBlock + warp) *
+                                            gwork_stride(a.H, T.maxo, mach_insert(MACH));
             r = decode_warp<ORDER, MACH>(T, hg, a.H, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
         }
         if (lane == 0) {
@@ -427,8 +432,8 @@ cudaError_t prepare(KernelT kernel, int smem) {
 
 }  // namespace
 
-int cta_smem_bytes(const TabHeader &h, int Hcap, bool ga, bool global_profile) {
-    const WarpLayout L = warp_layout(h.N, h.M, h.K, global_profile ? 0 : Hcap, ga);
+int cta_smem_bytes(const TabHeader &h, int Hcap, bool ga, bool global_profile, bool insert) {
+    const WarpLayout L = warp_layout(h.N, h.M, h.K, global_profile ? 0 : Hcap, ga, insert && !global_profile ? h.maxo : 0);
     return 128 + ((h.bytes + 127) & ~127) + kWarpsPerBlock * L.bytes;
 }
 
@@ -436,13 +441,13 @@ int cta_smem_bytes(const TabHeader &h, int Hcap, bool ga, bool global_profile) {
 // The machine mode of a public call (gene or earliest) and the instance's machine model
 // (identical, or unrelated with per-gene p and q) give the kernel's machine mode.
 #define FFS_CASE(O, M, ...)                                    \
-    if (order == O && kmach == M) {                            \
-        constexpr int O_ = O, M_ = M;                          \
+    if (order == (O) && kmach == (M)) {                        \
+        constexpr int O_ = (O), M_ = (M);                      \
         __VA_ARGS__;                                           \
     }
 #define FFS_DISPATCH(...)                                                                  \
     do {                                                                                   \
-        const int kmach = mach + (h.unrel ? 2 : 0);                                        \
+        const int kmach = mach + (h.unrel ? 2 : 0);  /* mach carries kPlaceInsert */       \
         FFS_CASE(kOrderStage, kMachEarliest, __VA_ARGS__)                                  \
         else FFS_CASE(kOrderStage, kMachGene, __VA_ARGS__)                                 \
         else FFS_CASE(kOrderTopo, kMachEarliest, __VA_ARGS__)                              \
@@ -451,12 +456,16 @@ int cta_smem_bytes(const TabHeader &h, int Hcap, bool ga, bool global_profile) {
         else FFS_CASE(kOrderStage, kMachGeneU, __VA_ARGS__)                                \
         else FFS_CASE(kOrderTopo, kMachEarliestU, __VA_ARGS__)                             \
         else FFS_CASE(kOrderTopo, kMachGeneU, __VA_ARGS__)                                 \
+        else FFS_CASE(kOrderStage, kMachEarliest | kPlaceInsert, __VA_ARGS__)              \
+        else FFS_CASE(kOrderStage, kMachGene | kPlaceInsert, __VA_ARGS__)                  \
+        else FFS_CASE(kOrderStage, kMachEarliestU | kPlaceInsert, __VA_ARGS__)             \
+        else FFS_CASE(kOrderStage, kMachGeneU | kPlaceInsert, __VA_ARGS__)                 \
         else e = cudaErrorInvalidValue;                                                    \
     } while (0)
 
 cudaError_t launch_decode(int order, int mach, bool global_profile, const DecodeArgs &a,
                           const TabHeader &h, int grid, cudaStream_t st) {
-    const int smem = cta_smem_bytes(h, a.Hcap, false, global_profile);
+    const int smem = cta_smem_bytes(h, a.Hcap, false, global_profile, mach_insert(mach));
     cudaError_t e = cudaSuccess;
     FFS_DISPATCH({
         if (global_profile) {
@@ -472,7 +481,7 @@ cudaError_t launch_decode(int order, int mach, bool global_profile, const Decode
 
 cudaError_t launch_ga_init(int order, int mach, const GenArgs &a, const TabHeader &h, int grid,
                            cudaStream_t st) {
-    const int smem = cta_smem_bytes(h, a.Hcap, true, false);
+    const int smem = cta_smem_bytes(h, a.Hcap, true, false, mach_insert(mach));
     cudaError_t e = cudaSuccess;
     FFS_DISPATCH({
         e = prepare(k_ga_init<O_, M_>, smem);
@@ -483,7 +492,7 @@ cudaError_t launch_ga_init(int order, int mach, const GenArgs &a, const TabHeade
 
 cudaError_t launch_ga_generation(int order, int mach, const GenArgs &a, const TabHeader &h,
                                  int grid, cudaStream_t st) {
-    const int smem = cta_smem_bytes(h, a.Hcap, true, false);
+    const int smem = cta_smem_bytes(h, a.Hcap, true, false, mach_insert(mach));
     cudaError_t e = cudaSuccess;
     FFS_DISPATCH({
         e = prepare(k_ga_generation<O_, M_>, smem);
@@ -493,7 +502,7 @@ cudaError_t launch_ga_generation(int order, int mach, const GenArgs &a, const Ta
 }
 
 cudaError_t prepare_ga_generation(int order, int mach, const TabHeader &h, int Hcap) {
-    const int smem = cta_smem_bytes(h, Hcap, true, false);
+    const int smem = cta_smem_bytes(h, Hcap, true, false, mach_insert(mach));
     cudaError_t e = cudaSuccess;
     FFS_DISPATCH({ e = prepare(k_ga_generation<O_, M_>, smem); });
     return e;
@@ -501,13 +510,13 @@ cudaError_t prepare_ga_generation(int order, int mach, const TabHeader &h, int H
 
 cudaError_t prepare_candidates(int mach, const TabHeader &h) {
     const int smem = cta_smem_bytes(h, 0, true, false);
-    return mach == kMachGene ? prepare(k_candidates<kMachGene>, smem) : prepare(k_candidates<kMachEarliest>, smem);
+    return mach_gene(mach) ? prepare(k_candidates<kMachGene>, smem) : prepare(k_candidates<kMachEarliest>, smem);
 }
 
 cudaError_t launch_candidates(int mach, const GenArgs &a, const TabHeader &h, int grid, cudaStream_t st) {
     const int smem = cta_smem_bytes(h, 0, true, false);
     cudaError_t e;
-    if (mach == kMachGene) {
+    if (mach_gene(mach)) {
         e = prepare(k_candidates<kMachGene>, smem);
         if (e == cudaSuccess) k_candidates<kMachGene><<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
     } else {

@@ -145,7 +145,7 @@ cudaError_t launch_batch(int order, int mach, const BatchArgs &a, int grid, int 
                          cudaStream_t st);
 
 // Shared memory needed by one CTA of the decode / GA kernels.
-int cta_smem_bytes(const TabHeader &h, int Hcap, bool ga, bool global_profile);
+int cta_smem_bytes(const TabHeader &h, int Hcap, bool ga, bool global_profile, bool insert = false);
 
 cudaError_t launch_decode(int order, int mach, bool global_profile, const DecodeArgs &a,
                           const TabHeader &h, int grid, cudaStream_t st);

@@ -89,10 +89,21 @@ struct WarpLayout {
     int off_h, off_C, off_mfree, off_inv, off_y, off_x, off_bits, bytes;
 };
 
-FFS_HD WarpLayout warp_layout(int N, int M, int K, int Hcap, bool ga) {
+// Insertion placement keeps, after the Hcap profile slots, one occupancy bitmap of
+// busy_words(Hcap) words for each machine of the current stage (nmach of them).
+FFS_HD int busy_words(int Hcap) { return (Hcap + 31) / 32; }
+FFS_HD int profile_bytes(int Hcap, int nmach) { return align16(Hcap * 2 + nmach * 4 * busy_words(Hcap)); }
+// Global-memory workspace of one warp in uint16 units: the profile bound H and, with
+// insertion, the occupancy bitmaps of up to maxo machines.
+FFS_HD size_t gwork_stride(int H, int maxo, bool insert) {
+    const size_t words = insert ? (size_t)maxo * (size_t)((H + 31) / 32) : 0;
+    return ((size_t)H * 2 + words * 4 + 15) / 16 * 8;
+}
+
+FFS_HD WarpLayout warp_layout(int N, int M, int K, int Hcap, bool ga, int nmach = 0) {
     WarpLayout L;
     int o = 0;
-    L.off_h = o;     o += align16(Hcap * 2);
+    L.off_h = o;     o += profile_bytes(Hcap, nmach);
     L.off_C = o;     o += align16(N * 4);
     L.off_mfree = o; o += align16(M * 4);
     L.off_inv = o;   o += align16((K + N) * 2);

@@ -219,11 +219,16 @@ int sync_device(ffs_instance *in) {
     return FFS_OK;
 }
 
-// Profile slots per warp that fit the shared-memory budget (0 if too few to be useful).
-int smem_slots(const TabHeader &h, bool ga) {
+// Profile slots per warp that fit the shared-memory budget (0 if too few to be useful);
+// with insertion each slot also needs a bit per machine of the widest stage.
+int smem_slots(const TabHeader &h, bool ga, bool insert) {
     const int fixed = cta_smem_bytes(h, 0, ga, true);
     const int per_warp = (kSmemBudget - fixed) / kWarpsPerBlock;
     int slots = per_warp / 2 / 8 * 8;
+    if (insert) {
+        slots = (int)((long long)per_warp * 32 / (64 + 4 * h.maxo)) / 32 * 32;
+        while (slots > 0 && profile_bytes(slots, h.maxo) > per_warp) slots -= 32;
+    }
     if (slots < kMinSmemSlots) return 0;
     return std::min(slots, h.H);
 }
@@ -238,9 +243,14 @@ int ensure_scratch(uint16_t **p, size_t *cap, size_t elems) {
 }
 
 int check_modes(int32_t order_mode, int32_t machine_mode) {
+    const int mach = machine_mode & ~FFS_PLACE_INSERT;
     if ((order_mode != FFS_ORDER_TOPO && order_mode != FFS_ORDER_STAGE) ||
-        (machine_mode != FFS_MACH_GENE && machine_mode != FFS_MACH_EARLIEST))
+        (mach != FFS_MACH_GENE && mach != FFS_MACH_EARLIEST))
         return FFS_E_ARG;
+    if ((machine_mode & FFS_PLACE_INSERT) && order_mode != FFS_ORDER_STAGE) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "insertion placement needs the stage-by-stage order");
+        return FFS_E_ARG;
+    }
     return FFS_OK;
 }
 
@@ -248,7 +258,9 @@ int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y,
                 int32_t count, int64_t *obj, int64_t *tard, int32_t *cmax, int32_t *S, int32_t *Mo,
                 cudaStream_t st) {
     FFS_TRY(check_modes(order, mach));
-    if (count < 0 || (count > 0 && (!y || !obj)) || (mach == FFS_MACH_GENE && count > 0 && !x)) return FFS_E_ARG;
+    if (count < 0 || (count > 0 && (!y || !obj)) || ((mach & 1) == FFS_MACH_GENE && count > 0 && !x))
+        return FFS_E_ARG;
+    const bool ins = (mach & FFS_PLACE_INSERT) != 0;
     if (count == 0) return FFS_OK;
     FFS_TRY(sync_device(in));
     const TabHeader &h = in->hdr;
@@ -267,7 +279,7 @@ int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y,
     a.M0 = in->d_M0;
     a.status = in->d_status;
     a.err = in->d_err;
-    const int slots = smem_slots(h, false);
+    const int slots = smem_slots(h, false, ins);
     const int sms = num_sms();
     const NoArena plain;  // per-instance buffers outlive any service arena
     if (slots > 0) {
@@ -280,7 +292,7 @@ int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y,
         a.Hcap = slots;
         a.over_list = in->d_over;
         a.over_count = in->d_over_count;
-        const int per_sm = std::max(1, (228 * 1024) / (cta_smem_bytes(h, slots, false, false) + 1024));
+        const int per_sm = std::max(1, (228 * 1024) / (cta_smem_bytes(h, slots, false, false, ins) + 1024));
         const int grid = std::max(1, std::min((count + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * per_sm));
         FFS_CUDA(launch_decode(order, mach, false, a, h, grid, st));
         g_launches += 1;
@@ -290,7 +302,8 @@ int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y,
     }
     // Global-memory profiles: the whole bound per warp.
     const int grid = std::max(1, std::min((count + kWarpsPerBlock - 1) / kWarpsPerBlock, sms * 2));
-    FFS_TRY(ensure_scratch(&in->d_scratch, &in->d_scratch_cap, (size_t)grid * kWarpsPerBlock * h.H));
+    FFS_TRY(ensure_scratch(&in->d_scratch, &in->d_scratch_cap,
+                           (size_t)grid * kWarpsPerBlock * gwork_stride(h.H, h.maxo, ins)));
     a.gscratch = in->d_scratch;
     a.Hcap = h.H;
     g_launches += 1;
@@ -662,10 +675,11 @@ void pop_shape(ga_population *pp, ffs_instance *in, const ga_params *par, int si
     pp->side = side;
     pp->hdr = in->hdr;
     pp->NG = in->N * in->g;
-    pp->Hcap = smem_slots(pp->hdr, true);
+    const bool ins = (par->machine_mode & FFS_PLACE_INSERT) != 0;
+    pp->Hcap = smem_slots(pp->hdr, true, ins);
     const int P = pp->P;
     pp->grid_gen = std::max(1, std::min((P + kWarpsPerBlock - 1) / kWarpsPerBlock,
-                                        num_sms() * std::max(1, (228 * 1024) / (cta_smem_bytes(pp->hdr, pp->Hcap, true, false) + 1024))));
+                                        num_sms() * std::max(1, (228 * 1024) / (cta_smem_bytes(pp->hdr, pp->Hcap, true, false, ins) + 1024))));
     pp->grid_fb = std::max(1, std::min((P + kWarpsPerBlock - 1) / kWarpsPerBlock, num_sms() * 2));
 }
 
@@ -686,7 +700,8 @@ void pop_buffers(ga_population *pp, F &&f) {
     f(pp->err, (size_t)1);
     f(pp->dev, (size_t)1);
     f(pp->isl_done, nisl);
-    f(pp->scratch, (size_t)std::max(pp->grid_fb, pp->grid_gen) * kWarpsPerBlock * pp->hdr.H);
+    f(pp->scratch, (size_t)std::max(pp->grid_fb, pp->grid_gen) * kWarpsPerBlock *
+                       gwork_stride(pp->hdr.H, pp->hdr.maxo, (pp->par.machine_mode & FFS_PLACE_INSERT) != 0));
     f(pp->r_obj, (size_t)1); f(pp->r_tard, (size_t)1); f(pp->r_cm, (size_t)1);
     f(pp->r_S, (size_t)pp->NG); f(pp->r_M, (size_t)pp->NG);
     f(pp->r_over, (size_t)1); f(pp->r_cnt, (size_t)1);
@@ -953,7 +968,7 @@ int ffs_rt::ga_finish(ga_population *pp, ffs_result *best) {
     a.status = in->d_status;
     a.err = pp->err;
     const int order = pp->par.order_mode, mach = pp->par.machine_mode;
-    const int slots = smem_slots(h, false);
+    const int slots = smem_slots(h, false, (mach & FFS_PLACE_INSERT) != 0);
     if (slots > 0) {
         FFS_CUDA(cudaMemsetAsync(pp->r_cnt, 0, 4, pp->st));
         a.Hcap = slots;
@@ -1182,11 +1197,12 @@ extern "C" int ffs_decode_noalloc(ffs_instance *in, int32_t order_mode, int32_t 
                                   int64_t *tard, int32_t *cmax, void *stream) {
     if (!in) return FFS_E_ARG;
     FFS_TRY(check_modes(order_mode, machine_mode));
-    if (count < 0 || (count > 0 && (!y || !obj)) || (machine_mode == FFS_MACH_GENE && count > 0 && !x))
+    if (count < 0 || (count > 0 && (!y || !obj)) || ((machine_mode & 1) == FFS_MACH_GENE && count > 0 && !x))
         return FFS_E_ARG;
     if (count == 0) return FFS_OK;
     const TabHeader &h = in->hdr;
-    const size_t per_cta = (size_t)kWarpsPerBlock * (size_t)h.H * sizeof(uint16_t);
+    const size_t per_cta =
+        (size_t)kWarpsPerBlock * gwork_stride(h.H, h.maxo, (machine_mode & FFS_PLACE_INSERT) != 0) * sizeof(uint16_t);
     const size_t profile_bytes = kNoAllocBytes - kNoAllocProfileOff;
     if ((size_t)h.bytes > kNoAllocTableCap || per_cta > profile_bytes) {
         std::snprintf(g_last_error, sizeof(g_last_error),
@@ -1365,6 +1381,10 @@ int ga_batch_create(ffs_instance *const *insts, int32_t count, const ga_params *
             return FFS_E_ARG;
         }
     FFS_TRY(check_modes(par->order_mode, par->machine_mode));
+    if (par->machine_mode & FFS_PLACE_INSERT) {
+        std::snprintf(ffs_rt::g_last_error, sizeof(ffs_rt::g_last_error), "batched runs use append placement only");
+        return FFS_E_ARG;
+    }
     const int P = par->pop, I = par->island;
     if (P < 2 || P % 2 || I < 2 || I % 2 || P % I || par->tournament_k < 0 || par->tournament_k > 32 ||
         par->pc_den <= 0 || par->pm_den <= 0 || par->pc_num < 0 || par->pm_num < 0 || par->pc_num > par->pc_den ||

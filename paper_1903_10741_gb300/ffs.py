@@ -17,6 +17,7 @@ from . import build as _build
 FFS_OK = 0
 ORDER_TOPO, ORDER_STAGE = 0, 1
 MACH_GENE, MACH_EARLIEST = 0, 1
+PLACE_INSERT = 4  # or-ed into a machine mode: idle-gap insertion placement
 ST_FREE, ST_EXEC, ST_DONE, ST_FIXED = 0, 1, 2, 3
 
 _i32p = C.POINTER(C.c_int32)

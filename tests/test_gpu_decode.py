@@ -26,7 +26,7 @@ def compare(lib_i, orc_i, Y, X, order, mach, schedule=True, sample=None):
     torch = _torch()
     yd = torch.from_numpy(np.ascontiguousarray(Y)).cuda()
     xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
-    out = lib_i.decode(yd, xd if mach == ffs.MACH_GENE else None, order, mach, schedule=schedule)
+    out = lib_i.decode(yd, xd if (mach & 1) == ffs.MACH_GENE else None, order, mach, schedule=schedule)
     obj = out["obj"].cpu().numpy()
     idx = range(len(Y)) if sample is None else sample
     S = out["S"].cpu().numpy() if schedule else None
