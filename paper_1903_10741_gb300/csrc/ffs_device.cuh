@@ -198,6 +198,18 @@ __device__ __forceinline__ void commit_power(uint16_t *h, int &hw, int t, int e,
     hw = max(hw, e);
 }
 
+// commit_power for a profile whose every slot below the scan bound is initialised (a
+// shared-memory slice filled with Qmax up front): no untouched slots to blend in.
+__device__ __forceinline__ void commit_power_full(uint16_t *h, int t, int e, uint32_t q2, int lane) {
+    for (int b = (t & ~3) + 4 * lane; b < e; b += 128) {
+        const unsigned sub = range4(b, t, e);
+        uint2 w = *reinterpret_cast<const uint2 *>(h + b);
+        w.x -= q2 & halves(sub);
+        w.y -= q2 & halves(sub >> 2);
+        *reinterpret_cast<uint2 *>(h + b) = w;
+    }
+}
+
 // Marks slots [t, e) busy in a machine's occupancy bitmap; lane l takes word (t >> 5) + l
 // (+ 32 i), so no word has two writers.
 __device__ __forceinline__ void commit_busy(uint32_t *bm, int t, int e, int lane) {
@@ -214,12 +226,13 @@ __device__ __forceinline__ void commit_busy(uint32_t *bm, int t, int e, int lane
 // frees first is scanned first, another only if it could still start earlier.
 template <bool INS = false>
 __device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int t0, uint32_t q2, int os,
-                                                 int p, int lane, int &best_t, int &best_m,
+                                                 int p, int lane, int &best_t, int &best_m, uint32_t &best_q2,
                                                  const uint32_t *busy = nullptr, int words = 0) {
     const unsigned key = lane < os ? ((unsigned)t0 << 5) | (unsigned)lane : 0xFFFFFFFFu;
     const unsigned kmin = __reduce_min_sync(kFull, key);
     best_m = (int)(kmin & 31u);
-    best_t = earliest_start<INS>(h, hw, (int)(kmin >> 5), p, __shfl_sync(kFull, q2, best_m), INT_MAX, lane,
+    best_q2 = __shfl_sync(kFull, q2, best_m);
+    best_t = earliest_start<INS>(h, hw, (int)(kmin >> 5), p, best_q2, INT_MAX, lane,
                                  busy + (size_t)best_m * words, words);
     unsigned cand = __ballot_sync(kFull, lane < os && lane != best_m && t0 < best_t + (lane < best_m));
     while (cand) {
@@ -228,11 +241,12 @@ __device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int 
         const int tm = __shfl_sync(kFull, t0, m);
         const int lim = best_t + (m < best_m ? 1 : 0);
         if (tm >= lim) continue;
-        const int t = earliest_start<INS>(h, hw, tm, p, __shfl_sync(kFull, q2, m), lim, lane,
-                                          busy + (size_t)m * words, words);
+        const uint32_t qm = __shfl_sync(kFull, q2, m);
+        const int t = earliest_start<INS>(h, hw, tm, p, qm, lim, lane, busy + (size_t)m * words, words);
         if (t < lim) {
             best_t = t;
             best_m = m;
+            best_q2 = qm;
         }
     }
 }
@@ -279,7 +293,12 @@ __device__ __forceinline__ void earliest_machine_u(const uint16_t *h, int hw, in
 //
 // C[j] starts at the end of the job's frozen prefix, raised to R_j when the job still
 // has free ops, so every op becomes available at max(RS, C[j]).
-template <int ORDER, int MACH>
+//
+// FULL (shared-memory slices): the whole slice is filled first (the executing ops'
+// profile, then Qmax), so the scan bound is Hcap and a commit has nothing to blend in.
+// Otherwise (global profiles of the full bound) slots are initialised as the schedule
+// first reaches them (high-water mark hw).
+template <int ORDER, int MACH, bool FULL = false>
 __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *C, int32_t *mfree,
                                  int16_t *inv, int16_t *y, const int8_t *x, int32_t *S_out,
                                  int32_t *M_out, int lane) {
@@ -289,7 +308,16 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
     if (T.E0 > Hcap) return {0, 0, 1};  // executing ops alone outgrow the profile slice
     for (int j = lane; j < N; j += 32) C[j] = T.gcnt[j] > 0 ? max(T.C0[j], T.R[j]) : T.C0[j];
     for (int i = lane; i < T.E0; i += 32) h[i] = T.h0[i];
-    int hw = T.E0;
+    if (FULL) {  // slots E0 .. Hcap: full headroom (Hcap is a multiple of 8)
+        const uint16_t Qm = (uint16_t)T.Qmax;
+        for (int i = T.E0 + lane; i < min(Hcap, (T.E0 + 3) & ~3); i += 32) h[i] = Qm;
+        __syncwarp();
+        for (int b = ((T.E0 + 3) & ~3) + 4 * lane; b < Hcap; b += 128)
+            *reinterpret_cast<uint2 *>(h + b) = make_uint2(Q2, Q2);
+        __syncwarp();
+    }
+    int hw = FULL ? Hcap : T.E0;  // scan bound: every slot below it is initialised
+    int top = T.E0;               // end of the latest op placed (occupancy bits lie below it)
     // Insertion placement: occupancy bitmaps of the current stage's machines after the
     // profile slice (the caller sized it with profile_bytes(Hcap, maxo)).
     constexpr bool INS = mach_insert(MACH) && ORDER == kOrderStage;
@@ -338,9 +366,9 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             const int lo = T.soff[s], hi = T.soff[s + 1];
             if (lo == hi) continue;
             const int mo = T.moff[s], os = T.o[s];
-            if (INS) {  // every bit set so far lies below hw
+            if (INS) {  // every bit set so far lies below top
                 __syncwarp();
-                const int hwords = busy_words(hw);
+                const int hwords = busy_words(top);
                 for (int i = lane; i < os * hwords; i += 32) busy[(i / hwords) * words + i % hwords] = 0u;
                 __syncwarp();
             }
@@ -371,21 +399,25 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 }
                 const int est = max(cj - RS, 0);
                 int best_t, best_m;
+                uint32_t bq2;
                 if (mach_gene(MACH)) {
                     best_m = x[k];
                     if (mach_unrel(MACH)) p = __shfl_sync(kFull, p, best_m);
-                    best_t = earliest_start<INS>(h, hw, max(est, __shfl_sync(kFull, mf, best_m)), p,
-                                                 __shfl_sync(kFull, qo2, best_m), INT_MAX, lane,
-                                                 busy + (size_t)best_m * words, words);
+                    bq2 = __shfl_sync(kFull, qo2, best_m);
+                    best_t = earliest_start<INS>(h, hw, max(est, __shfl_sync(kFull, mf, best_m)), p, bq2, INT_MAX,
+                                                 lane, busy + (size_t)best_m * words, words);
                 } else if (mach_unrel(MACH)) {
                     earliest_machine_u<INS>(h, hw, max(est, mf), qo2, p, os, lane, best_t, best_m, p, busy, words);
+                    bq2 = __shfl_sync(kFull, qo2, best_m);
                 } else {
                     earliest_machine<INS>(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m,
-                                          busy, words);
+                                          bq2, busy, words);
                 }
                 const int e = best_t + p;
                 if (e > Hcap) return {0, 0, 1};
-                commit_power(h, hw, best_t, e, __shfl_sync(kFull, qo2, best_m), Q2, lane);
+                if (FULL) commit_power_full(h, best_t, e, bq2, lane);
+                else commit_power(h, hw, best_t, e, bq2, Q2, lane);
+                if (INS) top = max(top, e);
                 if (INS) commit_busy(busy + (size_t)best_m * words, best_t, e, lane);
                 else if (lane == best_m) mf = e;
                 if (lane == 0) {
@@ -440,11 +472,15 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             } else if (mach_unrel(MACH)) {
                 earliest_machine_u(h, hw, max(est, mf), q2, p, os, lane, best_t, best_m, p);
             } else {
-                earliest_machine(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m);
+                uint32_t bq2_unused;
+                earliest_machine(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m,
+                                 bq2_unused);
             }
             const int e = best_t + p;
             if (e > Hcap) return {0, 0, 1};
-            commit_power(h, hw, best_t, e, __shfl_sync(kFull, q2, best_m), Q2, lane);
+            const uint32_t bq2 = __shfl_sync(kFull, q2, best_m);
+            if (FULL) commit_power_full(h, best_t, e, bq2, lane);
+            else commit_power(h, hw, best_t, e, bq2, Q2, lane);
             __syncwarp();
             if (lane == 0) {
                 nxt[bestj] = (int16_t)(k + 1);

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_decode(DecodeArgs a) {
                 }
         }
         __syncwarp();
-        const DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x, S, Mo, lane);
+        const DecodeOut r = decode_warp<ORDER, MACH, !GPROF>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x, S, Mo, lane);
         if (lane == 0) {
             if (r.status == 1) {
                 if (GPROF) atomicOr(a.err, kErrOverflow);
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_init(GenArgs a) {
             if (mach_gene(MACH))
                 for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
         }
-        const DecodeOut r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x,
+        const DecodeOut r = decode_warp<ORDER, MACH, true>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x,
                                                      nullptr, nullptr, lane);
         if (lane == 0) {
             if (r.status == 1) a.over_list[atomicAdd(&a.dev->nover, 1)] = i;
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a
         }
         DecodeOut r{0, 0, 1};
         if (a.Hcap > 0)
-            r = decode_warp<ORDER, MACH>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
+            r = decode_warp<ORDER, MACH, true>(T, w.h, a.Hcap, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
         if (r.status == 1) {  // the schedule outgrew the shared slice: redo it in global memory
             for (int k = lane; k < K; k += 32) w.y[k] = yo[k];  // the decode reused w.y
             __syncwarp();
