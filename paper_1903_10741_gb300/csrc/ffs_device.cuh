@@ -234,6 +234,9 @@ __device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int 
     best_q2 = __shfl_sync(kFull, q2, best_m);
     best_t = earliest_start<INS>(h, hw, (int)(kmin >> 5), p, best_q2, INT_MAX, lane,
                                  busy + (size_t)best_m * words, words);
+    // if the first machine starts as soon as it frees, no machine can start earlier (every
+    // other one frees no sooner, and equal times lose to its lower index)
+    if (best_t == (int)(kmin >> 5)) return;
     unsigned cand = __ballot_sync(kFull, lane < os && lane != best_m && t0 < best_t + (lane < best_m));
     while (cand) {
         const int m = __ffs(cand) - 1;
@@ -267,6 +270,7 @@ __device__ __forceinline__ void earliest_machine_u(const uint16_t *h, int hw, in
     best_t = earliest_start<INS>(h, hw, __shfl_sync(kFull, t0, best_m), best_p, __shfl_sync(kFull, q2, best_m),
                                  INT_MAX, lane, busy + (size_t)best_m * words, words);
     int best_c = best_t + best_p;
+    if (best_c == (int)(kmin >> 5)) return;  // the completion bound itself: nothing beats it
     unsigned cand = __ballot_sync(kFull, lane < os && lane != best_m && c0 < best_c + (lane < best_m));
     while (cand) {
         const int m = __ffs(cand) - 1;
@@ -295,9 +299,8 @@ __device__ __forceinline__ void earliest_machine_u(const uint16_t *h, int hw, in
 // has free ops, so every op becomes available at max(RS, C[j]).
 //
 // FULL (shared-memory slices): the whole slice is filled first (the executing ops'
-// profile, then Qmax), so the scan bound is Hcap and a commit has nothing to blend in.
-// Otherwise (global profiles of the full bound) slots are initialised as the schedule
-// first reaches them (high-water mark hw).
+// profile, then Qmax), so a commit has nothing to blend in.  Otherwise (global profiles
+// of the full bound) slots are initialised as the schedule first reaches them.
 template <int ORDER, int MACH, bool FULL = false>
 __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *C, int32_t *mfree,
                                  int16_t *inv, int16_t *y, const int8_t *x, int32_t *S_out,
@@ -316,8 +319,9 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             *reinterpret_cast<uint2 *>(h + b) = make_uint2(Q2, Q2);
         __syncwarp();
     }
-    int hw = FULL ? Hcap : T.E0;  // scan bound: every slot below it is initialised
-    int top = T.E0;               // end of the latest op placed (occupancy bits lie below it)
+    // high-water mark: slots at or above it have never been drawn on (full headroom, and no
+    // occupancy bits); scans stop there
+    int hw = T.E0;
     // Insertion placement: occupancy bitmaps of the current stage's machines after the
     // profile slice (the caller sized it with profile_bytes(Hcap, maxo)).
     constexpr bool INS = mach_insert(MACH) && ORDER == kOrderStage;
@@ -366,9 +370,9 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             const int lo = T.soff[s], hi = T.soff[s + 1];
             if (lo == hi) continue;
             const int mo = T.moff[s], os = T.o[s];
-            if (INS) {  // every bit set so far lies below top
+            if (INS) {  // every bit set so far lies below hw
                 __syncwarp();
-                const int hwords = busy_words(top);
+                const int hwords = busy_words(hw);
                 for (int i = lane; i < os * hwords; i += 32) busy[(i / hwords) * words + i % hwords] = 0u;
                 __syncwarp();
             }
@@ -415,9 +419,12 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 }
                 const int e = best_t + p;
                 if (e > Hcap) return {0, 0, 1};
-                if (FULL) commit_power_full(h, best_t, e, bq2, lane);
-                else commit_power(h, hw, best_t, e, bq2, Q2, lane);
-                if (INS) top = max(top, e);
+                if (FULL) {
+                    commit_power_full(h, best_t, e, bq2, lane);
+                    hw = max(hw, e);
+                } else {
+                    commit_power(h, hw, best_t, e, bq2, Q2, lane);
+                }
                 if (INS) commit_busy(busy + (size_t)best_m * words, best_t, e, lane);
                 else if (lane == best_m) mf = e;
                 if (lane == 0) {
@@ -479,8 +486,12 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             const int e = best_t + p;
             if (e > Hcap) return {0, 0, 1};
             const uint32_t bq2 = __shfl_sync(kFull, q2, best_m);
-            if (FULL) commit_power_full(h, best_t, e, bq2, lane);
-            else commit_power(h, hw, best_t, e, bq2, Q2, lane);
+            if (FULL) {
+                commit_power_full(h, best_t, e, bq2, lane);
+                hw = max(hw, e);
+            } else {
+                commit_power(h, hw, best_t, e, bq2, Q2, lane);
+            }
             __syncwarp();
             if (lane == 0) {
                 nxt[bestj] = (int16_t)(k + 1);
