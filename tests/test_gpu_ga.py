@@ -123,3 +123,20 @@ def test_stale_population_rejected():
     with pytest.raises(ffs.FFSError) as e:
         pop.run(1)
     assert e.value.code == -7
+
+
+def test_service_sized_instance_sampled():
+    """The service workload's largest shape: 500 jobs, 10 stages of U{2..8} machines, p up
+    to 199 (K = 5000 genes), population 2048 after one generation; sampled rows of the
+    device population decode in the oracle to the objectives the GPU recorded."""
+    rng = np.random.default_rng(41)
+    prob = wl.random_instance(rng, 500, 10, 2, 8, 199, 5, 30, 55)
+    lib_i, orc_i = ffs.Instance(prob), oracle.Instance(prob)
+    pop = ffs.Population(lib_i, P=2048, island=64, seed=3)
+    pop.run(1, want_schedule=False)
+    d = pop.read()
+    assert d["gen"] == 1 and d["Y"].shape[1] == orc_i.K == 5000
+    for i in range(0, 2048, 409):
+        assert d["obj"][i] == orc_i.decode(d["Y"][i], d["X"][i])["obj"], i
+    for isl in range(0, 32, 11):
+        assert d["bobj"][isl] == orc_i.decode(d["bY"][isl], d["bX"][isl])["obj"], isl

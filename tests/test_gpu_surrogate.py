@@ -190,3 +190,24 @@ def test_screened_slots_keep_the_best_scored_offspring():
     orc_i = oracle.Instance(prob)
     for i in range(0, 256, 9):
         assert runs[0]["obj"][i] == orc_i.decode(runs[0]["Y"][i])["obj"]
+
+
+def test_forward_at_the_surrogate_workload_size():
+    """The surrogate workload's instance (200 jobs, 8 stages, K = 1600, Kpad = 1664, so the
+    first-layer GEMM runs with 128-wide tiles), 1024 candidates against the float64 oracle."""
+    torch = _torch()
+    prob = wl.surrogate_large(1)
+    lib_i, orc_i = ffs.Instance(prob), oracle.Instance(prob)
+    gj, gs = orc_i.gene_map()
+    ph, dh = mlp.gene_features(orc_i.p, orc_i.D, gj, gs)
+    rng = np.random.default_rng(3)
+    Y, _ = wl.random_chromosomes(rng, 1024, orc_i.K, orc_i.gene_machines())
+    params = mlp.init_params(orc_i.K, seed=3)
+    for k in params:
+        params[k] = params[k] + rng.normal(0, 0.02, params[k].shape)
+    sur = ffs.Surrogate(lib_i, max_batch=1024)
+    sur.set_params(sur.pack(params))
+    got = sur.predict(torch.from_numpy(Y).cuda()).cpu().numpy().astype(np.float64)
+    idx = np.arange(0, 1024, 37)
+    ref = mlp.forward(params, mlp.features(Y[idx], ph, dh, gs))[0]
+    assert _rel(got[idx], ref) < 0.03, _rel(got[idx], ref)
