@@ -404,9 +404,10 @@ int ffs_tensor_gemm(const void *A, const void *B, int32_t M, int32_t N, int32_t 
  *     requests overlap on the GPU; finished requests are retired as their streams drain,
  *     and their slots and memory go to the next requests;
  *   - keeps each instance's last population on the device and starts the instance's next
- *     request from it (ga_population_create_warm); kept populations are dropped, least
- *     recently used first, when an admission needs their memory, and the request then
- *     starts cold (ffs_request_info.warm = 0).
+ *     request from it (ga_population_create_warm); a kept population holds only its
+ *     chromosomes (2 x P x K x 3 bytes) and its generation counter.  Kept populations are
+ *     dropped, least recently used first, when an admission needs their memory, and the
+ *     request then starts cold (ffs_request_info.warm = 0).
  * Every request of an instance draws from Philox stream id ga.instance_id + (the number
  * of the instance's earlier requests in this service), so its result depends only on the
  * instance, the request and whether it started warm: not on the other requests, their

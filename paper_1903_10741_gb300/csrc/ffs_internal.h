@@ -190,6 +190,9 @@ int ga_finish(ga_population *pp, ffs_result *best);
 int population_footprint(ffs_instance *in, const ga_params *par, int64_t *bytes);
 // ga_population_create / ga_population_create_warm (prev may be null).
 int population_create(ffs_instance *in, const ga_params *par, ga_population *prev, ga_population **out);
+// Frees everything but the chromosomes (both buffers) and the generation counter: what a
+// warm start reads.  The population can then only be a warm start's source or destroyed.
+void population_trim(ga_population *pp);
 // One surrogate-assisted generation on `st` (ffs_surrogate.cu); with events, the fused
 // generation kernel is bracketed by ev0/ev1.  Kernels launched per generation:
 constexpr int kSurrogateFixedLaunches = 12, kSurrogateStepLaunches = 18;

@@ -864,6 +864,25 @@ int ffs_rt::population_create(ffs_instance *in, const ga_params *par, ga_populat
     return create_population(in, par, prev, out);
 }
 
+void ffs_rt::population_trim(ga_population *pp) {
+    if (pp->graph) cudaGraphExecDestroy(pp->graph);
+    if (pp->graph_sur) cudaGraphExecDestroy(pp->graph_sur);
+    pp->graph = pp->graph_sur = nullptr;
+    dfree(pp->d_blob);
+    for (int b = 0; b < 2; ++b) {
+        dfree(pp->obj[b]);
+        dfree(pp->fit[b]);
+    }
+    dfree(pp->bY); dfree(pp->bX); dfree(pp->bobj); dfree(pp->bfit);
+    dfree(pp->mY); dfree(pp->mX); dfree(pp->mobj); dfree(pp->mfit); dfree(pp->mw);
+    dfree(pp->over); dfree(pp->isl_done); dfree(pp->scratch);
+    dfree(pp->r_obj); dfree(pp->r_tard); dfree(pp->r_cm); dfree(pp->r_S); dfree(pp->r_M);
+    dfree(pp->r_over); dfree(pp->r_cnt);
+    dfree(pp->cand_Y); dfree(pp->cand_X); dfree(pp->cand_Yh); dfree(pp->cand_H1); dfree(pp->cand_H2);
+    dfree(pp->cand_out); dfree(pp->cand_new); dfree(pp->kept_obj);
+    pp->sur = nullptr;
+}
+
 extern "C" {
 
 int ga_population_create(ffs_instance *in, const ga_params *par, ga_population **out) {

@@ -341,8 +341,12 @@ void retire(ffs_service *s, Slot &slot, cudaError_t q) {
     InstState &is = *inst_state(s, r->inst);
     is.active = false;
     is.last_use = ++s->tick;
-    if (rc == FFS_OK) set_warm(s, &is, pop);
-    else ga_population_destroy(pop);
+    if (rc == FFS_OK) {
+        population_trim(pop);  // kept only as the next request's warm-start source
+        set_warm(s, &is, pop);
+    } else {
+        ga_population_destroy(pop);
+    }
     finish_request(s, r, rc, true);
 }
 

@@ -196,13 +196,20 @@ def test_service_memory_admission_and_footprint():
 
 
 def test_service_footprint_is_what_a_population_holds():
+    """While a request runs its population holds ga_population_footprint; once it is kept
+    as the instance's warm state, only the chromosomes (two buffers of int16 Y and int8 X)
+    and the generation counter stay, each block rounded to 256 bytes."""
     work = wl.service_small(seed=9, n_instances=1, n_requests=1)
     inst = ffs.Instance(work.problems[0])
     fp = ffs.footprint(inst, **GA)
+    K = inst.K
     svc = ffs.Service(max_active=2, memory_bytes=64 << 20, **GA)
     svc.wait(svc.submit(inst, None, 0, 3))
     st = svc.stats()
-    assert st["used_bytes"] == fp and st["warm"] == 1
+    r = lambda n: (n + 255) // 256 * 256
+    kept = 2 * r(GA["P"] * K * 2) + 2 * r(GA["P"] * K) + r(24) + r(4)
+    assert st["used_bytes"] == kept < fp and st["warm"] == 1
+    assert st["peak_bytes"] >= fp
     svc.close()
 
 
