@@ -269,6 +269,8 @@ def bench_ours(args):
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if args.cpu_all_cores:
+            line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -431,6 +433,53 @@ def bench_surrogate(args):
                    "plain_curve": plain[:: max(1, len(plain) // 12)],
                    "surrogate_curve": sur_curve[:: max(1, len(sur_curve) // 12)]},
     }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- static instance
+STATIC_WORKLOAD = ("static instance: 10 jobs, 3 stages with [2,3,2] identical machines, p U{1..20}, q U{1..10}, "
+                   "peak 60% of all-on power, releases 0; population 64 (one island), tournament 2, pc 0.8, pm 0.1; "
+                   "100 generations per step")
+
+
+def bench_static(args):
+    import torch
+
+    from paper_1903_10741_gb300 import ffs
+
+    torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+    stream = torch.cuda.current_stream()
+    prob = wl.static_small(1)
+    G, Ps = args.generations, 64
+    kw = dict(P=Ps, island=64, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE, seed=SEED, stream=stream)
+    for _ in range(args.warmup):
+        ffs.Population(ffs.Instance(prob), **kw).run(G, want_schedule=False)
+    total_ms, res = 0.0, None
+    for _ in range(args.steps):
+        inst = ffs.Instance(prob)
+        pop = ffs.Population(inst, **kw)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        res = pop.run(G, want_schedule=False)
+        e.record(stream)
+        e.synchronize()
+        total_ms += s.elapsed_time(e)
+    line = {
+        "metric": METRIC, "value": Ps * G * args.steps / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": STATIC_WORKLOAD, "generations_per_step": G, "best_objective": res["obj"],
+                   "timing": "CUDA events around ga_run (the GA wall time of one run)"},
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        ga = oracle.GA(oracle.Instance(prob), P=Ps, island=64, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE,
+                       seed=SEED).init().step(G)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": Ps * (G + 1) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"the whole oracle GA run ({G} generations) in {dt:.3f} s",
+                                "best_objective": int(ga.bobj.min())}
     print(json.dumps(line), flush=True)
 
 
@@ -691,6 +740,40 @@ def cpu_baseline(seconds: float) -> dict:
                       f"{dec} exact decodes in {dt:.1f} s"}
 
 
+def _oracle_decode_slice(args):
+    """Worker of the all-cores oracle baseline: decode rows [lo, hi) of the generation-0
+    population of the job's initial solve, repeatedly, for `seconds`."""
+    lo, hi, seconds = args
+    import oracle
+    dyn = wl.dynamic_medium(1)
+    inst = oracle.Instance(dyn.problem)
+    ga = oracle.GA(inst, P=P, island=ISLAND, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE, seed=SEED,
+                   instance_id=0).init()
+    rows = ga.Y[lo:hi, :ga.K].copy()
+    t0, n = time.perf_counter(), 0
+    while time.perf_counter() - t0 < seconds:
+        for y in rows:
+            inst.decode(y)
+            n += 1
+    return n, time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(seconds: float) -> dict:
+    """The same oracle decoder as os.cpu_count() independent processes, each on its own
+    slice of the initial solve's population (the paper's 1-core vs multi-core comparison).
+    Processes are spawned, never forked from a process that has used the GPU."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    bounds = [(P * i // cores, P * (i + 1) // cores, seconds) for i in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_decode_slice, bounds)
+    dec = sum(n for n, _ in res)
+    wall = max(t for _, t in res)
+    return {"value": dec / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{cores} spawned processes decoding disjoint slices of the initial solve's population "
+                      f"(population {P}) for about {seconds:.0f} s: {dec} exact decodes"}
+
+
 def bench_reference(args):
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
@@ -729,8 +812,10 @@ def main():
     ap.add_argument("--ref-generations", type=int, default=2, help="oracle generations per reference step")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-all-cores", action="store_true",
+                    help="also time the oracle as one process per host core on disjoint slices")
     ap.add_argument("--workload", choices=["dynamic", "batched", "surrogate", "service", "static-vs-reactive",
-                                           "unrelated", "insert"],
+                                           "unrelated", "insert", "static"],
                     default="dynamic",
                     help="dynamic: the headline rescheduling job; batched: 256 uneven instances; "
                          "surrogate: time-to-objective of the surrogate-assisted GA; service: Poisson "
@@ -765,6 +850,10 @@ def main():
         if args.generations == 500:
             args.generations = 1000
         bench_surrogate(args)
+    elif args.workload == "static":
+        if args.generations == 500:
+            args.generations = 100
+        bench_static(args)
     elif args.workload == "insert":
         bench_insert(args)
     elif args.workload == "unrelated":
