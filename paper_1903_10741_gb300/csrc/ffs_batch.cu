@@ -103,8 +103,10 @@ __device__ __forceinline__ void decode_into(const Tabs &T, const WarpPtrs &w, in
     __syncwarp();
 }
 
+// 128 registers: the whole register file for one CTA of 512 threads per SM (shared memory
+// allows one), set explicitly so that no variant spills.
 template <int ORDER, int MACH>
-__global__ void __launch_bounds__(512) k_batch(BatchArgs a) {
+__global__ void __maxnreg__(128) k_batch(BatchArgs a) {
     extern __shared__ __align__(128) char smem[];
     __shared__ long long s_red[32];
     __shared__ int s_over;
@@ -234,15 +236,9 @@ __global__ void __launch_bounds__(512) k_batch(BatchArgs a) {
             if (migrate) {
                 cluster.sync();  // every island's migrant is recorded
                 if (fits) {
-                    for (int isl = rank + warp * CS; isl < nisl; isl += W * CS) {
-                        const int srci = (isl + nisl - 1) % nisl, wslot = __ldcg(in->mw + isl);
-                        warp_copy_ind(in->Y[nx] + (size_t)wslot * K, in->X[nx] + (size_t)wslot * K,
-                                      in->mY + (size_t)srci * K, in->mX + (size_t)srci * K, K, lane);
-                        if (lane == 0) {
-                            in->obj[nx][wslot] = __ldcg(in->mobj + srci);
-                            in->fit[nx][wslot] = __ldcg(in->mfit + srci);
-                        }
-                    }
+                    for (int isl = rank + warp * CS; isl < nisl; isl += W * CS)
+                        migrate_edge(in->Y[nx], in->X[nx], in->obj[nx], in->fit[nx], in->mY, in->mX, in->mobj,
+                                     in->mfit, in->mw, isl, nisl, K, lane);
                 }
                 __threadfence();
             }

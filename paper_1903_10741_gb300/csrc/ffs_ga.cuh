@@ -230,8 +230,10 @@ __device__ __forceinline__ void make_initial(const Tabs &T, const WarpPtrs &w, u
 
 // ---------------------------------------------------------------- GA: island bookkeeping
 // Best (largest fitness, lowest index) and worst (smallest fitness, lowest index) of
-// fit[lo .. lo+n) with one warp; reads bypass L1 because other SMs wrote the values.
-__device__ __forceinline__ void warp_extremes(const int64_t *fit, int lo, int n, int lane, int &best, int &worst) {
+// fit[lo .. lo+n) with one warp, and the best's fitness; reads bypass L1 because other SMs
+// wrote the values.
+__device__ __forceinline__ void warp_extremes(const int64_t *fit, int lo, int n, int lane, int &best, int &worst,
+                                              long long &best_fit) {
     long long bf = LLONG_MIN, wf = LLONG_MAX;
     int bi = INT_MAX, wi = INT_MAX;
     for (int t = lane; t < n; t += 32) {
@@ -248,13 +250,39 @@ __device__ __forceinline__ void warp_extremes(const int64_t *fit, int lo, int n,
     }
     best = bi;
     worst = wi;
+    best_fit = bf;
 }
 
+__device__ __forceinline__ void warp_extremes(const int64_t *fit, int lo, int n, int lane, int &best, int &worst) {
+    long long bf;
+    warp_extremes(fit, lo, n, lane, best, worst, bf);
+}
+
+// Copies one individual (K genes of y and x) to one or two destinations.  Each lane loads
+// its share of a chunk of 32 kCopyU genes before it stores any of them, so a chunk costs
+// one round trip to L2 rather than one per 32 genes.
+constexpr int kCopyU = 4;
+
 __device__ __forceinline__ void warp_copy_ind(int16_t *yd, int8_t *xd, const int16_t *ys, const int8_t *xs, int K,
-                                              int lane) {
-    for (int k = lane; k < K; k += 32) {
-        yd[k] = __ldcg(ys + k);
-        xd[k] = __ldcg(xs + k);
+                                              int lane, int16_t *yd2 = nullptr, int8_t *xd2 = nullptr) {
+#pragma unroll 1
+    for (int k0 = lane; k0 < K; k0 += 32 * kCopyU) {
+        const int n = K - k0;  // genes left from this lane's first one
+        uint32_t v[kCopyU];    // y in the low halfword, x in bits 16..23
+#pragma unroll
+        for (int u = 0; u < kCopyU; ++u)
+            if (32 * u < n)
+                v[u] = (uint16_t)__ldcg(ys + k0 + 32 * u) | ((uint32_t)(uint8_t)__ldcg(xs + k0 + 32 * u) << 16);
+#pragma unroll
+        for (int u = 0; u < kCopyU; ++u)
+            if (32 * u < n) {
+                yd[k0 + 32 * u] = (int16_t)(v[u] & 0xFFFFu);
+                xd[k0 + 32 * u] = (int8_t)(v[u] >> 16);
+                if (yd2) {
+                    yd2[k0 + 32 * u] = (int16_t)(v[u] & 0xFFFFu);
+                    xd2[k0 + 32 * u] = (int8_t)(v[u] >> 16);
+                }
+            }
     }
 }
 
@@ -267,30 +295,59 @@ __device__ __forceinline__ void island_replace(int16_t *Y, int8_t *X, int64_t *o
                                                int32_t *mw, int lane) {
     const int lo = isl * I;
     int best, worst;
-    warp_extremes(fit, lo, I, lane, best, worst);
-    const long long fb = __ldcg(fit + best);
-    if (fb > bfit[isl]) {
-        warp_copy_ind(bY + (size_t)isl * K, bX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K, lane);
-        if (lane == 0) {
-            bobj[isl] = __ldcg(obj + best);
-            bfit[isl] = fb;
-        }
-    }
-    __syncwarp();
-    warp_copy_ind(Y + (size_t)worst * K, X + (size_t)worst * K, bY + (size_t)isl * K, bX + (size_t)isl * K, K, lane);
+    long long fb;
+    warp_extremes(fit, lo, I, lane, best, worst, fb);
+    const long long bf0 = bfit[isl];
+    const bool better = fb > bf0;
+    // the elite after the update: the best child if strictly fitter, else the kept one;
+    // it overwrites the worst child (and, when it is new, the island's best-ever record)
+    long long eobj = 0;
+    if (lane == 0) eobj = better ? __ldcg(obj + best) : bobj[isl];
+    const long long efit = better ? fb : bf0;
+    int16_t *bYi = bY + (size_t)isl * K;
+    int8_t *bXi = bX + (size_t)isl * K;
+    if (better)
+        warp_copy_ind(Y + (size_t)worst * K, X + (size_t)worst * K, Y + (size_t)best * K, X + (size_t)best * K, K,
+                      lane, bYi, bXi);
+    else
+        warp_copy_ind(Y + (size_t)worst * K, X + (size_t)worst * K, bYi, bXi, K, lane);
     if (lane == 0) {
-        obj[worst] = bobj[isl];
-        fit[worst] = bfit[isl];
+        if (better) {
+            bobj[isl] = eobj;
+            bfit[isl] = efit;
+        }
+        obj[worst] = eobj;
+        fit[worst] = efit;
     }
     __syncwarp();
     if (migrate) {
-        warp_extremes(fit, lo, I, lane, best, worst);
+        warp_extremes(fit, lo, I, lane, best, worst, fb);
+        long long mo = 0;
+        if (lane == 0) mo = __ldcg(obj + best);
         warp_copy_ind(mY + (size_t)isl * K, mX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K, lane);
         if (lane == 0) {
-            mobj[isl] = __ldcg(obj + best);
-            mfit[isl] = __ldcg(fit + best);
+            mobj[isl] = mo;
+            mfit[isl] = fb;
             mw[isl] = worst;
         }
+    }
+}
+
+// Edge e of the single migration ring, by one warp: island e's recorded worst slot <-
+// island e-1's migrant.
+__device__ __forceinline__ void migrate_edge(int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit, const int16_t *mY,
+                                             const int8_t *mX, const int64_t *mobj, const int64_t *mfit,
+                                             const int32_t *mw, int e, int nisl, int K, int lane) {
+    const int src = (e + nisl - 1) % nisl, wslot = __ldcg(mw + e);
+    long long o = 0, f = 0;
+    if (lane == 0) {
+        o = __ldcg(mobj + src);
+        f = __ldcg(mfit + src);
+    }
+    warp_copy_ind(Y + (size_t)wslot * K, X + (size_t)wslot * K, mY + (size_t)src * K, mX + (size_t)src * K, K, lane);
+    if (lane == 0) {
+        obj[wslot] = o;
+        fit[wslot] = f;
     }
 }
 
@@ -298,14 +355,8 @@ __device__ __forceinline__ void island_replace(int16_t *Y, int8_t *X, int64_t *o
 __device__ __forceinline__ void ring_migrate(int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit, const int16_t *mY,
                                              const int8_t *mX, const int64_t *mobj, const int64_t *mfit,
                                              const int32_t *mw, int nisl, int K, int lane) {
-    for (int d = 0; d < nisl; ++d) {
-        const int src = (d + nisl - 1) % nisl, wslot = __ldcg(mw + d);
-        warp_copy_ind(Y + (size_t)wslot * K, X + (size_t)wslot * K, mY + (size_t)src * K, mX + (size_t)src * K, K, lane);
-        if (lane == 0) {
-            obj[wslot] = __ldcg(mobj + src);
-            fit[wslot] = __ldcg(mfit + src);
-        }
-    }
+#pragma unroll 1
+    for (int d = 0; d < nisl; ++d) migrate_edge(Y, X, obj, fit, mY, mX, mobj, mfit, mw, d, nisl, K, lane);
 }
 
 }  // namespace edffs

@@ -160,9 +160,11 @@ __device__ void island_finish(const Args &a, int isl, int nx, int gen, int lane)
 // ---------------------------------------------------------------- GA: one generation
 // Selection -> paired crossover + correction -> mutation -> decode, one child per warp.
 // Each warp recomputes both parents of its pair from the counter-based stream, so the
-// children of a pair are built independently by two warps.
+// children of a pair are built independently by two warps.  An explicit cap of 128
+// registers (2 CTAs of 128 threads per SM are set by shared memory anyway) keeps every
+// variant free of spills.
 template <int ORDER, int MACH>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_generation(GenArgs a) {
+__global__ void __maxnreg__(128) k_ga_generation(GenArgs a) {
     extern __shared__ __align__(128) char smem[];
     char *tab = smem + 128;
     if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
