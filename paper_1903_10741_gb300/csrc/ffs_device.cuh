@@ -210,6 +210,29 @@ __device__ __forceinline__ void commit_power_full(uint16_t *h, int t, int e, uin
     }
 }
 
+// The common case of one op on a shared-memory profile whose slots at or beyond hw hold
+// full headroom: when [t, t+p) lies within one 128-slot step from t & ~3 and every slot of
+// it below hw has headroom q, q is drawn there from the words the check loaded (no second
+// read) and true is returned.  Otherwise nothing changes and false is returned.  The
+// caller ensures t + p <= Hcap.
+__device__ __forceinline__ bool place_first(uint16_t *h, int hw, int t, int p, uint32_t q2, uint32_t Q2, int lane) {
+    const int c = t & ~3, e = t + p, end = min(e, hw);
+    if (e - c > 128) return false;
+    const int b = c + 4 * lane;
+    uint2 w = make_uint2(Q2, Q2);  // slots at or beyond hw: full headroom
+    if (b < end) w = *reinterpret_cast<const uint2 *>(h + b);
+    const uint32_t dx = (w.x | 0x80008000u) - q2, dy = (w.y | 0x80008000u) - q2;
+    const unsigned good = ((dx >> 15) & 1u) | ((dx >> 30) & 2u) | ((dy >> 13) & 4u) | ((dy >> 28) & 8u);
+    if (__any_sync(kFull, (~good & range4(b, t, end)) != 0u)) return false;
+    const unsigned sub = range4(b, t, e);
+    if (sub) {
+        w.x -= q2 & halves(sub);
+        w.y -= q2 & halves(sub >> 2);
+        *reinterpret_cast<uint2 *>(h + b) = w;
+    }
+    return true;
+}
+
 // Marks slots [t, e) busy in a machine's occupancy bitmap; lane l takes word (t >> 5) + l
 // (+ 32 i), so no word has two writers.
 __device__ __forceinline__ void commit_busy(uint32_t *bm, int t, int e, int lane) {
@@ -404,22 +427,47 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 const int est = max(cj - RS, 0);
                 int best_t, best_m;
                 uint32_t bq2;
+                // fast path (identical machines, append placement, prefilled profile): the
+                // first candidate start is feasible and the op is drawn in the same step
+                constexpr bool kFast = FULL && !INS && !mach_unrel(MACH);
+                bool placed = false;
                 if (mach_gene(MACH)) {
                     best_m = x[k];
                     if (mach_unrel(MACH)) p = __shfl_sync(kFull, p, best_m);
                     bq2 = __shfl_sync(kFull, qo2, best_m);
-                    best_t = earliest_start<INS>(h, hw, max(est, __shfl_sync(kFull, mf, best_m)), p, bq2, INT_MAX,
-                                                 lane, busy + (size_t)best_m * words, words);
+                    const int t0 = max(est, __shfl_sync(kFull, mf, best_m));
+                    if (kFast && t0 + p <= Hcap && place_first(h, hw, t0, p, bq2, Q2, lane)) {
+                        best_t = t0;
+                        placed = true;
+                    } else {
+                        best_t = earliest_start<INS>(h, hw, t0, p, bq2, INT_MAX, lane, busy + (size_t)best_m * words,
+                                                     words);
+                    }
                 } else if (mach_unrel(MACH)) {
                     earliest_machine_u<INS>(h, hw, max(est, mf), qo2, p, os, lane, best_t, best_m, p, busy, words);
                     bq2 = __shfl_sync(kFull, qo2, best_m);
                 } else {
-                    earliest_machine<INS>(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m,
-                                          bq2, busy, words);
+                    const int tl = lane < os ? max(est, mf) : INT_MAX;
+                    if (kFast) {  // the machine that frees first (lowest index on ties)
+                        const unsigned key = lane < os ? ((unsigned)tl << 5) | (unsigned)lane : 0xFFFFFFFFu;
+                        const unsigned kmin = __reduce_min_sync(kFull, key);
+                        const int t0 = (int)(kmin >> 5);
+                        best_m = (int)(kmin & 31u);
+                        bq2 = __shfl_sync(kFull, q2, best_m);
+                        if (t0 + p <= Hcap && place_first(h, hw, t0, p, bq2, Q2, lane)) {
+                            best_t = t0;
+                            placed = true;
+                        }
+                    }
+                    if (!placed)
+                        earliest_machine<INS>(h, hw, tl, q2, os, p, lane, best_t, best_m, bq2, busy, words);
                 }
                 const int e = best_t + p;
-                if (e > Hcap) return {0, 0, 1};
-                if (FULL) {
+                if (placed) {
+                    hw = max(hw, e);
+                } else if (e > Hcap) {
+                    return {0, 0, 1};
+                } else if (FULL) {
                     commit_power_full(h, best_t, e, bq2, lane);
                     hw = max(hw, e);
                 } else {

@@ -35,7 +35,8 @@ __device__ __forceinline__ WarpPtrs warp_ptrs(char *tab, int blob_bytes, const T
 
 // ---------------------------------------------------------------- decode kernel
 template <int ORDER, int MACH, bool GPROF>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_decode(DecodeArgs a) {
+// At most 128 registers in this and the other per-warp kernels: no variant spills.
+__global__ void __maxnreg__(128) k_decode(DecodeArgs a) {
     extern __shared__ __align__(128) char smem[];
     char *tab = smem + 128;
     if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_decode(DecodeArgs a) {
 
 // ---------------------------------------------------------------- GA: generation 0
 template <int ORDER, int MACH>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_ga_init(GenArgs a) {
+__global__ void __maxnreg__(128) k_ga_init(GenArgs a) {
     extern __shared__ __align__(128) char smem[];
     char *tab = smem + 128;
     if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(kRemapThreads) k_warm_remap(WarmArgs a) {
 // generation's child); its model input (the within-stage rank features, BF16, zero padded
 // to Kpad) is written beside it.  Nothing is decoded here.
 template <int MACH>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_candidates(GenArgs a) {
+__global__ void __maxnreg__(128) k_candidates(GenArgs a) {
     extern __shared__ __align__(128) char smem[];
     char *tab = smem + 128;
     if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
