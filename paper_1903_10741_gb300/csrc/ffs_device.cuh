@@ -210,24 +210,35 @@ __device__ __forceinline__ void commit_power_full(uint16_t *h, int t, int e, uin
     }
 }
 
+// Halfword masks of the slots [lo, hi) among b .. b+3 (x: slots b, b+1; y: b+2, b+3).
+// PTX clamps a 64-bit shift amount at 64, so no range checks are needed.
+__device__ __forceinline__ uint2 slot_mask(int b, int lo, int hi) {
+    const uint32_t sl = (uint32_t)max(lo - b, 0) << 4, sh = (uint32_t)max(hi - b, 0) << 4;
+    uint64_t a, c;
+    asm("shl.b64 %0, %1, %2;" : "=l"(a) : "l"(~0ull), "r"(sl));
+    asm("shl.b64 %0, %1, %2;" : "=l"(c) : "l"(~0ull), "r"(sh));
+    const uint64_t m = a & ~c;
+    return make_uint2((uint32_t)m, (uint32_t)(m >> 32));
+}
+
 // The common case of one op on a shared-memory profile whose slots at or beyond hw hold
 // full headroom: when [t, t+p) lies within one 128-slot step from t & ~3 and every slot of
-// it below hw has headroom q, q is drawn there from the words the check loaded (no second
-// read) and true is returned.  Otherwise nothing changes and false is returned.  The
-// caller ensures t + p <= Hcap.
+// it has headroom q, q is drawn there from the words the check loaded (no second read) and
+// true is returned.  Otherwise nothing changes and false is returned.  Slots at or beyond
+// hw need no check, as q never exceeds the peak.  The caller ensures t + p <= Hcap.
 __device__ __forceinline__ bool place_first(uint16_t *h, int hw, int t, int p, uint32_t q2, uint32_t Q2, int lane) {
-    const int c = t & ~3, e = t + p, end = min(e, hw);
+    const int c = t & ~3, e = t + p;
     if (e - c > 128) return false;
     const int b = c + 4 * lane;
     uint2 w = make_uint2(Q2, Q2);  // slots at or beyond hw: full headroom
-    if (b < end) w = *reinterpret_cast<const uint2 *>(h + b);
-    const uint32_t dx = (w.x | 0x80008000u) - q2, dy = (w.y | 0x80008000u) - q2;
-    const unsigned good = ((dx >> 15) & 1u) | ((dx >> 30) & 2u) | ((dy >> 13) & 4u) | ((dy >> 28) & 8u);
-    if (__any_sync(kFull, (~good & range4(b, t, end)) != 0u)) return false;
-    const unsigned sub = range4(b, t, e);
-    if (sub) {
-        w.x -= q2 & halves(sub);
-        w.y -= q2 & halves(sub >> 2);
+    if (b < min(e, hw)) w = *reinterpret_cast<const uint2 *>(h + b);
+    const uint2 m = slot_mask(b, t, e);
+    // bit 15 of (h | 0x8000) - q is clear exactly where h < q (no borrow between halfwords)
+    const uint32_t vx = ~((w.x | 0x80008000u) - q2) & m.x, vy = ~((w.y | 0x80008000u) - q2) & m.y;
+    if (__any_sync(kFull, ((vx | vy) & 0x80008000u) != 0u)) return false;
+    if (m.x | m.y) {
+        w.x -= q2 & m.x;
+        w.y -= q2 & m.y;
         *reinterpret_cast<uint2 *>(h + b) = w;
     }
     return true;
@@ -401,7 +412,10 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             }
             // lane m < os: end of the last op on machine m past RS (with insertion: the end
             // of its frozen ops, before which it stays unavailable)
-            int mf = INT_MAX;
+            // (lanes past the stage's machines hold an availability no machine reaches, so
+            // their keys below lose without a lane test)
+            constexpr int kNever = 0x07FFFFFF;
+            int mf = kNever;
             uint32_t q2 = 0;
             if (lane < os) {
                 mf = T.mfree0[mo + lane] - RS;
@@ -449,7 +463,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 } else {
                     const int tl = lane < os ? max(est, mf) : INT_MAX;
                     if (kFast) {  // the machine that frees first (lowest index on ties)
-                        const unsigned key = lane < os ? ((unsigned)tl << 5) | (unsigned)lane : 0xFFFFFFFFu;
+                        const unsigned key = ((unsigned)max(est, mf) << 5) | (unsigned)lane;
                         const unsigned kmin = __reduce_min_sync(kFull, key);
                         const int t0 = (int)(kmin >> 5);
                         best_m = (int)(kmin & 31u);

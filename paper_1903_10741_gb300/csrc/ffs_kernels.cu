@@ -34,8 +34,8 @@ __device__ __forceinline__ WarpPtrs warp_ptrs(char *tab, int blob_bytes, const T
 }
 
 // ---------------------------------------------------------------- decode kernel
-template <int ORDER, int MACH, bool GPROF>
 // At most 128 registers in this and the other per-warp kernels: no variant spills.
+template <int ORDER, int MACH, bool GPROF>
 __global__ void __maxnreg__(128) k_decode(DecodeArgs a) {
     extern __shared__ __align__(128) char smem[];
     char *tab = smem + 128;
