@@ -378,27 +378,38 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
         }
     }
     __syncwarp();
-    for (int i = lane; i < K; i += 32)
-        if (inv[i] < 0) bad = true;
-    if (__any_sync(kFull, bad)) return {0, 0, 2};
+    if (ORDER != kOrderStage) {
+        for (int i = lane; i < K; i += 32)
+            if (inv[i] < 0) bad = true;
+        if (__any_sync(kFull, bad)) return {0, 0, 2};
+    }
 
     if (ORDER == kOrderStage) {
-        // Z: stage by stage, y descending.  Each stage's genes, in priority order, go to
-        // order[soff[s] ..) by a ballot-compaction pass over inv; y is no longer needed.
+        // Z: stage by stage, y descending.  One pass over inv in priority order sends each
+        // gene to order[next[s]++] of its stage s: lanes of a chunk with the same stage
+        // take consecutive places in lane order, and the group's last lane advances next[s]
+        // (kept in the mfree scratch, which stage order does not use).  y is no longer
+        // needed; a hole left in inv marks a chromosome that is no permutation.
         int16_t *order = y;
+        int32_t *next = mfree;
+        for (int s = lane; s < g; s += 32) next[s] = T.soff[s];
         __syncwarp();
-        for (int s = 0; s < g; ++s) {
-            int pos = T.soff[s];
-            for (int base = 0; base < K; base += 32) {
-                const int i = base + lane;
-                const int k = i < K ? inv[i] : -1;
-                const bool sel = k >= 0 && T.gstg[k] == s;
-                const unsigned mask = __ballot_sync(kFull, sel);
-                if (sel) order[pos + __popc(mask & ((1u << lane) - 1u))] = (int16_t)k;
-                pos += __popc(mask);
+        for (int base = 0; base < K; base += 32) {
+            const int i = base + lane;
+            const int k = i < K ? inv[i] : -1;
+            if (i < K && k < 0) bad = true;
+            const int s = k >= 0 ? (int)T.gstg[k] : -1;
+            const unsigned grp = __match_any_sync(kFull, s);
+            int at = 0;
+            if (k >= 0) at = next[s] + __popc(grp & ((1u << lane) - 1u));
+            __syncwarp();  // every lane has read next[s] before the group's last lane moves it
+            if (k >= 0) {
+                order[at] = (int16_t)k;
+                if (lane == 31 - __clz(grp)) next[s] = at + 1;
             }
+            __syncwarp();
         }
-        __syncwarp();
+        if (__any_sync(kFull, bad)) return {0, 0, 2};
         // Place the ops; the stage's machines live in lanes (availability, power).
         for (int s = 0; s < g; ++s) {
             const int lo = T.soff[s], hi = T.soff[s + 1];
