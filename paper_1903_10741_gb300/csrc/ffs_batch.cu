@@ -73,16 +73,16 @@ __device__ __forceinline__ void write_ind(int16_t *Y, int8_t *X, const WarpPtrs 
 }
 
 // Decodes the warp's chromosome (already written to row i of Y) into obj/fit slot i.  The
-// schedule is built in the warp's shared slice unless `gfirst`; one that outgrows the
-// slice is redone in the warp's global slice from the row in global memory (the decode
-// reuses w.y), and counted in *overflows.
+// schedule is built in the warp's shared slice (filled with full headroom first) unless
+// `gfirst`; one that outgrows the slice is redone in the warp's global slice from the row
+// in global memory (the decode reuses w.y), and counted in *overflows.
 template <int ORDER, int MACH>
 __device__ __forceinline__ void decode_into(const Tabs &T, const WarpPtrs &w, int Hcap, uint16_t *hg, int H,
                                             bool gfirst, const int16_t *Y, int64_t *obj, int64_t *fit,
                                             long long emax, int i, int32_t *err, int *overflows, int lane) {
     DecodeOut r{0, 0, 1};
     if (!gfirst) {
-        r = decode_warp<ORDER, MACH>(T, w.h, Hcap, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
+        r = decode_warp<ORDER, MACH, true>(T, w.h, Hcap, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
         if (r.status == 1) {
             if (lane == 0) atomicAdd(overflows, 1);
             const int16_t *row = Y + (size_t)i * T.K;
