@@ -111,25 +111,22 @@ struct DecodeOut {
     int status;      // 0 ok, 1 profile outgrew Hcap, 2 malformed chromosome
 };
 
-// 4-bit mask of slots b .. b+3 that fall in [lo, hi).
-__device__ __forceinline__ unsigned range4(int b, int lo, int hi) {
-    const int l = min(max(lo - b, 0), 4), h = min(max(hi - b, 0), 4);
-    return ((1u << h) - 1u) & ~((1u << l) - 1u);
-}
-
 // Expands bits 0/1 of m to the low/high halfword of a 32-bit word.
 __device__ __forceinline__ uint32_t halves(unsigned m) {
     return (m & 1u) * 0xFFFFu + (m & 2u) * 0x7FFF8000u;
 }
 
-// Earliest start r >= t0 (slots past RS) such that headroom h[r .. r+p) >= q everywhere.
-// Slots at or beyond the high-water mark hw were never touched and hold the full peak, so
-// only [r, min(r+p, hw)) needs checking.  Each lane reads 4 consecutive slots with one
-// 64-bit load (128 slots per step) and compares both halfwords of a word at once: with
-// headroom and q below 2^15, (h | 0x8000) - q keeps bit 15 set exactly when h >= q, and no
-// borrow crosses into the next halfword.  A ballot finds the last violating slot and the
-// candidate jumps past it.  Returns `limit` as soon as the answer cannot be below it.
-// Loads stay below hw <= Hcap (Hcap a multiple of 4); lanes past the window read slot 0.
+// Halfword masks of the slots [lo, hi) among b .. b+3 (x: slots b, b+1; y: b+2, b+3).
+// PTX clamps a 64-bit shift amount at 64, so no range checks are needed.
+__device__ __forceinline__ uint2 slot_mask(int b, int lo, int hi) {
+    const uint32_t sl = (uint32_t)max(lo - b, 0) << 4, sh = (uint32_t)max(hi - b, 0) << 4;
+    uint64_t a, c;
+    asm("shl.b64 %0, %1, %2;" : "=l"(a) : "l"(~0ull), "r"(sl));
+    asm("shl.b64 %0, %1, %2;" : "=l"(c) : "l"(~0ull), "r"(sh));
+    const uint64_t m = a & ~c;
+    return make_uint2((uint32_t)m, (uint32_t)(m >> 32));
+}
+
 // First slot >= t at which a machine is idle, from its occupancy bitmap (nw words): each
 // step the warp looks at 32 words (1024 slots).  At least 32 nw if there is none below.
 __device__ __forceinline__ int next_idle(const uint32_t *bm, int nw, int t, int lane) {
@@ -146,6 +143,14 @@ __device__ __forceinline__ int next_idle(const uint32_t *bm, int nw, int t, int 
     return t > 32 * nw ? t : 32 * nw;
 }
 
+// Earliest start r >= t0 (slots past RS) such that headroom h[r .. r+p) >= q everywhere.
+// Slots at or beyond the high-water mark hw were never touched and hold the full peak, so
+// only [r, min(r+p, hw)) needs checking.  Each lane reads 4 consecutive slots with one
+// 64-bit load (128 slots per step) and compares both halfwords of a word at once: with
+// headroom and q below 2^15, (h | 0x8000) - q keeps bit 15 set exactly when h >= q, and no
+// borrow crosses into the next halfword.  A ballot finds the last violating slot and the
+// candidate jumps past it.  Returns `limit` as soon as the answer cannot be below it.
+// Loads stay below hw <= Hcap (Hcap a multiple of 4); lanes past the window load nothing.
 // With INS, `bm` is the machine's occupancy bitmap (nw words; bit t: busy at slot t) and a
 // slot also violates when the machine is busy there; a candidate start that falls in a
 // busy stretch moves to the stretch's end directly.  Bits are only set below hw.
@@ -159,20 +164,26 @@ __device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0,
     int c = run & ~3;
     while (c < end) {
         const int b = c + 4 * lane;
-        const bool in = b < end;
-        const uint2 w = *reinterpret_cast<const uint2 *>(h + (in ? b : 0));
-        const uint32_t dx = (w.x | 0x80008000u) - q2, dy = (w.y | 0x80008000u) - q2;
-        const unsigned good = ((dx >> 15) & 1u) | ((dx >> 30) & 2u) | ((dy >> 13) & 4u) | ((dy >> 28) & 8u);
-        unsigned busy = 0u;
-        if (INS && in) busy = (bm[b >> 5] >> (b & 31)) & 0xFu;
-        const unsigned badm = in ? ((~good | busy) & range4(b, run, end)) : 0u;  // bit i: slot b + i violates
-        const unsigned vm = __ballot_sync(kFull, badm != 0);
+        uint2 w = make_uint2(0u, 0u);
+        if (b < end) w = *reinterpret_cast<const uint2 *>(h + b);
+        const uint2 m = slot_mask(b, run, end);  // empty for lanes past the window
+        // bit 15 of each halfword: the slot lacks headroom q (or, with INS, the machine is busy)
+        uint32_t vx = ~((w.x | 0x80008000u) - q2), vy = ~((w.y | 0x80008000u) - q2);
+        if (INS && b < end) {
+            const unsigned busy = (bm[b >> 5] >> (b & 31)) & 0xFu;
+            vx |= halves(busy);
+            vy |= halves(busy >> 2);
+        }
+        vx &= m.x & 0x80008000u;
+        vy &= m.y & 0x80008000u;
+        // the lane's last violating slot among its four
+        const int li = vy ? 2 + (int)(vy >> 31) : vx ? (int)(vx >> 31) : -1;
+        const unsigned vm = __ballot_sync(kFull, li >= 0);
         if (vm == 0) {
             c += 128;
         } else {
             const int l = 31 - __clz(vm);
-            const unsigned lm = __shfl_sync(kFull, badm, l);
-            run = c + 4 * l + (31 - __clz(lm)) + 1;  // one past the last violating slot
+            run = c + 4 * l + __shfl_sync(kFull, li, l) + 1;  // one past the last violating slot
             if (INS && run < limit) run = next_idle(bm, nw, run, lane);
             if (run >= limit) return limit;
             end = min(run + p, hw);
@@ -187,12 +198,11 @@ __device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0,
 __device__ __forceinline__ void commit_power(uint16_t *h, int &hw, int t, int e, uint32_t q2,
                                              uint32_t Q2, int lane) {
     for (int b = (min(t, hw) & ~3) + 4 * lane; b < e; b += 128) {
-        const unsigned keep = range4(b, 0, hw), sub = range4(b, t, e);
+        const uint2 keep = slot_mask(b, 0, hw), sub = slot_mask(b, t, e);
         uint2 w = make_uint2(0u, 0u);
-        if (keep) w = *reinterpret_cast<const uint2 *>(h + b);
-        const uint32_t kx = halves(keep), ky = halves(keep >> 2);
-        w.x = ((w.x & kx) | (Q2 & ~kx)) - (q2 & halves(sub));
-        w.y = ((w.y & ky) | (Q2 & ~ky)) - (q2 & halves(sub >> 2));
+        if (b < hw) w = *reinterpret_cast<const uint2 *>(h + b);
+        w.x = ((w.x & keep.x) | (Q2 & ~keep.x)) - (q2 & sub.x);
+        w.y = ((w.y & keep.y) | (Q2 & ~keep.y)) - (q2 & sub.y);
         *reinterpret_cast<uint2 *>(h + b) = w;
     }
     hw = max(hw, e);
@@ -202,23 +212,12 @@ __device__ __forceinline__ void commit_power(uint16_t *h, int &hw, int t, int e,
 // shared-memory slice filled with Qmax up front): no untouched slots to blend in.
 __device__ __forceinline__ void commit_power_full(uint16_t *h, int t, int e, uint32_t q2, int lane) {
     for (int b = (t & ~3) + 4 * lane; b < e; b += 128) {
-        const unsigned sub = range4(b, t, e);
+        const uint2 sub = slot_mask(b, t, e);
         uint2 w = *reinterpret_cast<const uint2 *>(h + b);
-        w.x -= q2 & halves(sub);
-        w.y -= q2 & halves(sub >> 2);
+        w.x -= q2 & sub.x;
+        w.y -= q2 & sub.y;
         *reinterpret_cast<uint2 *>(h + b) = w;
     }
-}
-
-// Halfword masks of the slots [lo, hi) among b .. b+3 (x: slots b, b+1; y: b+2, b+3).
-// PTX clamps a 64-bit shift amount at 64, so no range checks are needed.
-__device__ __forceinline__ uint2 slot_mask(int b, int lo, int hi) {
-    const uint32_t sl = (uint32_t)max(lo - b, 0) << 4, sh = (uint32_t)max(hi - b, 0) << 4;
-    uint64_t a, c;
-    asm("shl.b64 %0, %1, %2;" : "=l"(a) : "l"(~0ull), "r"(sl));
-    asm("shl.b64 %0, %1, %2;" : "=l"(c) : "l"(~0ull), "r"(sh));
-    const uint64_t m = a & ~c;
-    return make_uint2((uint32_t)m, (uint32_t)(m >> 32));
 }
 
 // The common case of one op on a shared-memory profile whose slots at or beyond hw hold
