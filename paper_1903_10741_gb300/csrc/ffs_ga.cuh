@@ -51,6 +51,35 @@ __device__ __forceinline__ void warp_best(long long &bf, int &bi) {
 }
 
 
+constexpr int kRowU = 4;
+
+// Copies a parent's y row (when ys is non-null) and the x row made of xa[0 .. cx) and
+// xb[cx .. K) (when `with_x`) from global into shared memory; each lane loads its values
+// of a chunk of 32 kRowU genes before it stores any.
+__device__ __forceinline__ void rows_to_smem(int16_t *yd, int8_t *xd, const int16_t *ys, const int8_t *xa,
+                                             const int8_t *xb, int cx, int K, bool with_x, int lane) {
+    for (int k0 = lane; k0 < K; k0 += 32 * kRowU) {
+        int16_t vy[kRowU];
+        int8_t vx[kRowU];
+#pragma unroll
+        for (int u = 0; u < kRowU; ++u) {
+            const int k = k0 + 32 * u;
+            if (k < K) {
+                if (ys) vy[u] = ys[k];
+                if (with_x) vx[u] = k < cx ? xa[k] : xb[k];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kRowU; ++u) {
+            const int k = k0 + 32 * u;
+            if (k < K) {
+                if (ys) yd[k] = vy[u];
+                if (with_x) xd[k] = vx[u];
+            }
+        }
+    }
+}
+
 // Parent population and operator settings of one generation.
 struct GASrc {
     const int16_t *Yc;   // [P][K] parents
@@ -76,27 +105,47 @@ __device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, con
     const int K = s.K, I = s.I;
     const int pp = i >> 1;
     int parent[2];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
+    // Entrant e of slot 2 pp + t's tournament (the 5-cell neighbourhood with tour_k = 0).
+    auto entrant = [&](int t, int e, long long &bf, int &bi) {
         const int slot = 2 * pp + t;
-        long long bf = LLONG_MIN;
-        int bi = INT_MAX;
         if (s.tour_k > 0) {
-            if (lane < s.tour_k) {
+            if (e < s.tour_k) {
                 const int lo = ((s.F > 1 ? slot % s.P : slot) / I) * I;  // the island of the slot the child is for
-                bi = lo + (int)below(draw(s.seed, kPSelect, s.iid, gen, (uint32_t)slot, (uint32_t)lane),
-                                     (uint32_t)I);
+                bi = lo + (int)below(draw(s.seed, kPSelect, s.iid, gen, (uint32_t)slot, (uint32_t)e), (uint32_t)I);
                 bf = s.fc[bi];
             }
-        } else if (lane < 5) {  // the cell and its N, S, W, E neighbours on the torus
+        } else if (e < 5) {  // the cell and its N, S, W, E neighbours on the torus
             const int sd = s.side, base = s.F > 1 ? slot % s.P : slot, r = base / sd, cc = base % sd;
-            const int rr = lane == 1 ? (r + sd - 1) % sd : lane == 2 ? (r + 1) % sd : r;
-            const int c2 = lane == 3 ? (cc + sd - 1) % sd : lane == 4 ? (cc + 1) % sd : cc;
+            const int rr = e == 1 ? (r + sd - 1) % sd : e == 2 ? (r + 1) % sd : r;
+            const int c2 = e == 3 ? (cc + sd - 1) % sd : e == 4 ? (cc + 1) % sd : cc;
             bi = rr * sd + c2;
             bf = s.fc[bi];
         }
-        warp_best(bf, bi);
-        parent[t] = bi;
+    };
+    if (s.tour_k <= 16) {  // both tournaments at once, one per half-warp
+        long long bf = LLONG_MIN;
+        int bi = INT_MAX;
+        entrant(lane >> 4, lane & 15, bf, bi);
+#pragma unroll
+        for (int off = 8; off; off >>= 1) {
+            const long long of = __shfl_xor_sync(kFull, bf, off);
+            const int oi = __shfl_xor_sync(kFull, bi, off);
+            if (fitter(of, oi, bf, bi)) {
+                bf = of;
+                bi = oi;
+            }
+        }
+        parent[0] = __shfl_sync(kFull, bi, 0);
+        parent[1] = __shfl_sync(kFull, bi, 16);
+    } else {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            long long bf = LLONG_MIN;
+            int bi = INT_MAX;
+            entrant(t, lane, bf, bi);
+            warp_best(bf, bi);
+            parent[t] = bi;
+        }
     }
     const uint4 rc = stream_block(s.seed, kPCross, s.iid, gen, (uint32_t)pp, 0);
     const bool cross = K >= 2 && (uint64_t)rc.x < s.pc_thr;
@@ -104,25 +153,38 @@ __device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, con
     const int second = (i & 1) ? parent[0] : parent[1];
     const int16_t *yf = s.Yc + (size_t)first * K, *yb = s.Yc + (size_t)second * K;
     if (!cross) {
-        for (int k = lane; k < K; k += 32) w.y[k] = yf[k];
-        if (mach_gene(MACH))
-            for (int k = lane; k < K; k += 32) w.x[k] = s.Xc[(size_t)first * K + k];
+        rows_to_smem(w.y, w.x, yf, s.Xc + (size_t)first * K, s.Xc + (size_t)first * K, K, K, mach_gene(MACH),
+                     lane);
     } else {
         const int cx = 1 + (int)below(rc.y, (uint32_t)(K - 1));
         const int cy = 1 + (int)below(rc.z, (uint32_t)(K - 1));
         const int nw = (K + 32) / 32;  // bitmap words covering values 0..K
         for (int q = lane; q < nw; q += 32) w.bits[q] = 0;
         __syncwarp();
-        for (int k = lane; k < cy; k += 32) {
-            const int v = yf[k];
-            w.y[k] = (int16_t)v;
-            atomicOr(&w.bits[v >> 5], 1u << (v & 31));
+        // Parent reads: each lane loads its values of a chunk of 32 kRowU genes before it
+        // uses any, so a chunk costs one round trip to L2.
+        for (int k0 = lane; k0 < cy; k0 += 32 * kRowU) {
+            int v[kRowU];
+#pragma unroll
+            for (int u = 0; u < kRowU; ++u) v[u] = k0 + 32 * u < cy ? yf[k0 + 32 * u] : 0;
+#pragma unroll
+            for (int u = 0; u < kRowU; ++u)
+                if (k0 + 32 * u < cy) {
+                    w.y[k0 + 32 * u] = (int16_t)v[u];
+                    atomicOr(&w.bits[v[u] >> 5], 1u << (v[u] & 31));
+                }
         }
         __syncwarp();
-        for (int k = cy + lane; k < K; k += 32) {  // tail values already in the head: duplicates
-            const int v = yb[k];
-            const bool dup = (w.bits[v >> 5] >> (v & 31)) & 1u;
-            w.y[k] = dup ? (int16_t)0 : (int16_t)v;
+        for (int k0 = cy + lane; k0 < K; k0 += 32 * kRowU) {  // tail values already in the head: duplicates
+            int v[kRowU];
+#pragma unroll
+            for (int u = 0; u < kRowU; ++u) v[u] = k0 + 32 * u < K ? yb[k0 + 32 * u] : 0;
+#pragma unroll
+            for (int u = 0; u < kRowU; ++u)
+                if (k0 + 32 * u < K) {
+                    const bool dup = (w.bits[v[u] >> 5] >> (v[u] & 31)) & 1u;
+                    w.y[k0 + 32 * u] = dup ? (int16_t)0 : (int16_t)v[u];
+                }
         }
         __syncwarp();
         for (int k = cy + lane; k < K; k += 32) {
@@ -167,8 +229,8 @@ __device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, con
             rank += __popc(bm);
         }
         if (mach_gene(MACH))
-            for (int k = lane; k < K; k += 32)
-                w.x[k] = k < cx ? s.Xc[(size_t)first * K + k] : s.Xc[(size_t)second * K + k];
+            rows_to_smem(nullptr, w.x, nullptr, s.Xc + (size_t)first * K, s.Xc + (size_t)second * K, cx, K, true,
+                         lane);
     }
     __syncwarp();
     const uint4 rm = stream_block(s.seed, kPMutate, s.iid, gen, (uint32_t)i, 0);
