@@ -321,22 +321,21 @@ __device__ __forceinline__ void warp_extremes(const int64_t *fit, int lo, int n,
 }
 
 // Copies one individual (K genes of y and x) to one or two destinations.  Each lane loads
-// its share of a chunk of 32 kCopyU genes before it stores any of them, so a chunk costs
-// one round trip to L2 rather than one per 32 genes.
-constexpr int kCopyU = 4;
-
+// its share of a chunk of 32 U genes before it stores any of them, so a chunk costs one
+// round trip to L2 rather than one per 32 genes.
+template <int U = 4>
 __device__ __forceinline__ void warp_copy_ind(int16_t *yd, int8_t *xd, const int16_t *ys, const int8_t *xs, int K,
                                               int lane, int16_t *yd2 = nullptr, int8_t *xd2 = nullptr) {
 #pragma unroll 1
-    for (int k0 = lane; k0 < K; k0 += 32 * kCopyU) {
+    for (int k0 = lane; k0 < K; k0 += 32 * U) {
         const int n = K - k0;  // genes left from this lane's first one
-        uint32_t v[kCopyU];    // y in the low halfword, x in bits 16..23
+        uint32_t v[U];         // y in the low halfword, x in bits 16..23
 #pragma unroll
-        for (int u = 0; u < kCopyU; ++u)
+        for (int u = 0; u < U; ++u)
             if (32 * u < n)
                 v[u] = (uint16_t)__ldcg(ys + k0 + 32 * u) | ((uint32_t)(uint8_t)__ldcg(xs + k0 + 32 * u) << 16);
 #pragma unroll
-        for (int u = 0; u < kCopyU; ++u)
+        for (int u = 0; u < U; ++u)
             if (32 * u < n) {
                 yd[k0 + 32 * u] = (int16_t)(v[u] & 0xFFFFu);
                 xd[k0 + 32 * u] = (int8_t)(v[u] >> 16);
@@ -350,7 +349,9 @@ __device__ __forceinline__ void warp_copy_ind(int16_t *yd, int8_t *xd, const int
 
 // Elitist replacement of island `isl` by one warp (Sec. 4.4): the best-ever individual is
 // updated if a child is strictly fitter, then overwrites the worst child.  With `migrate`,
-// the island's best and worst after replacement are recorded for the ring exchange.
+// the island's best and worst after replacement are recorded for the ring exchange.  U:
+// genes per lane per copy chunk.
+template <int U = 4>
 __device__ __forceinline__ void island_replace(int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit, int16_t *bY,
                                                int8_t *bX, int64_t *bobj, int64_t *bfit, int isl, int I, int K,
                                                bool migrate, int16_t *mY, int8_t *mX, int64_t *mobj, int64_t *mfit,
@@ -369,10 +370,10 @@ __device__ __forceinline__ void island_replace(int16_t *Y, int8_t *X, int64_t *o
     int16_t *bYi = bY + (size_t)isl * K;
     int8_t *bXi = bX + (size_t)isl * K;
     if (better)
-        warp_copy_ind(Y + (size_t)worst * K, X + (size_t)worst * K, Y + (size_t)best * K, X + (size_t)best * K, K,
-                      lane, bYi, bXi);
+        warp_copy_ind<U>(Y + (size_t)worst * K, X + (size_t)worst * K, Y + (size_t)best * K, X + (size_t)best * K,
+                         K, lane, bYi, bXi);
     else
-        warp_copy_ind(Y + (size_t)worst * K, X + (size_t)worst * K, bYi, bXi, K, lane);
+        warp_copy_ind<U>(Y + (size_t)worst * K, X + (size_t)worst * K, bYi, bXi, K, lane);
     if (lane == 0) {
         if (better) {
             bobj[isl] = eobj;
@@ -386,7 +387,8 @@ __device__ __forceinline__ void island_replace(int16_t *Y, int8_t *X, int64_t *o
         warp_extremes(fit, lo, I, lane, best, worst, fb);
         long long mo = 0;
         if (lane == 0) mo = __ldcg(obj + best);
-        warp_copy_ind(mY + (size_t)isl * K, mX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K, lane);
+        warp_copy_ind<U>(mY + (size_t)isl * K, mX + (size_t)isl * K, Y + (size_t)best * K, X + (size_t)best * K, K,
+                         lane);
         if (lane == 0) {
             mobj[isl] = mo;
             mfit[isl] = fb;
@@ -413,12 +415,34 @@ __device__ __forceinline__ void migrate_edge(int16_t *Y, int8_t *X, int64_t *obj
     }
 }
 
-// Single-ring migration by one warp: island d's recorded worst <- island d-1's migrant.
+// The whole single ring by one warp (island d's recorded worst slot <- island d-1's
+// migrant, every d): lane l first reads the slot and migrant record of island 32 c + l, so
+// each island then costs only the copy.
+template <int U = 4>
 __device__ __forceinline__ void ring_migrate(int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit, const int16_t *mY,
                                              const int8_t *mX, const int64_t *mobj, const int64_t *mfit,
                                              const int32_t *mw, int nisl, int K, int lane) {
+    for (int c = 0; c < nisl; c += 32) {
+        const int d = c + lane, src = (d + nisl - 1) % nisl;
+        int ws = 0;
+        long long o = 0, f = 0;
+        if (d < nisl) {
+            ws = __ldcg(mw + d);
+            o = __ldcg(mobj + src);
+            f = __ldcg(mfit + src);
+        }
+        const int n = min(32, nisl - c);
 #pragma unroll 1
-    for (int d = 0; d < nisl; ++d) migrate_edge(Y, X, obj, fit, mY, mX, mobj, mfit, mw, d, nisl, K, lane);
+        for (int l = 0; l < n; ++l) {
+            const int wslot = __shfl_sync(kFull, ws, l), sl = (c + l + nisl - 1) % nisl;
+            warp_copy_ind<U>(Y + (size_t)wslot * K, X + (size_t)wslot * K, mY + (size_t)sl * K, mX + (size_t)sl * K,
+                             K, lane);
+        }
+        if (d < nisl) {
+            obj[ws] = o;
+            fit[ws] = f;
+        }
+    }
 }
 
 }  // namespace edffs

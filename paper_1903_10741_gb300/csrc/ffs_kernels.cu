@@ -128,6 +128,10 @@ __global__ void __maxnreg__(128) k_ga_init(GenArgs a) {
 // last island to finish performs the single-ring migration (island i's worst <- island
 // i-1's best, from those records) and advances the generation counter.  Completion is
 // counted with atomics after a device-wide fence; nothing waits.
+// Copies in this tail lie on the critical path of a generation (the last island's last
+// warp runs them after every decode): 256 genes per chunk, one L2 round trip each.
+constexpr int kTailU = 8;
+
 template <typename Args>
 __device__ void island_finish(const Args &a, int isl, int nx, int gen, int lane) {
     __threadfence();
@@ -141,15 +145,15 @@ __device__ void island_finish(const Args &a, int isl, int nx, int gen, int lane)
     int8_t *X = a.X[nx];
     int64_t *obj = a.obj[nx], *fit = a.fit[nx];
     const bool migrate = a.migrate_every > 0 && gen % a.migrate_every == 0 && a.nisl > 1;
-    island_replace(Y, X, obj, fit, a.bY, a.bX, a.bobj, a.bfit, isl, a.I, K, migrate, a.mY, a.mX, a.mobj, a.mfit,
-                   a.mw, lane);
+    island_replace<kTailU>(Y, X, obj, fit, a.bY, a.bX, a.bobj, a.bfit, isl, a.I, K, migrate, a.mY, a.mX, a.mobj,
+                           a.mfit, a.mw, lane);
     if (lane == 0) a.isl_done[isl] = 0;
     __threadfence();
     if (lane == 0) ticket = atomicAdd(&a.dev->islands_done, 1);
     ticket = __shfl_sync(kFull, ticket, 0);
     if (ticket != a.nisl - 1) return;
     __threadfence();
-    if (migrate) ring_migrate(Y, X, obj, fit, a.mY, a.mX, a.mobj, a.mfit, a.mw, a.nisl, K, lane);
+    if (migrate) ring_migrate<kTailU>(Y, X, obj, fit, a.mY, a.mX, a.mobj, a.mfit, a.mw, a.nisl, K, lane);
     if (lane == 0) {
         a.dev->islands_done = 0;
         a.dev->nover = 0;
