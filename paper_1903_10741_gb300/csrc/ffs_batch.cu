@@ -110,6 +110,7 @@ __global__ void __maxnreg__(128) k_batch(BatchArgs a) {
     extern __shared__ __align__(128) char smem[];
     __shared__ long long s_red[32];
     __shared__ int s_over;
+    __shared__ int s_next;  // next of this CTA's children to build in the current generation
     cg::cluster_group cluster = cg::this_cluster();
     const int CS = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
     const int cid = blockIdx.x / CS, ncl = gridDim.x / CS;
@@ -146,7 +147,10 @@ __global__ void __maxnreg__(128) k_batch(BatchArgs a) {
         // Profiles go to shared memory first; if more than a quarter of this CTA's first
         // round of decodes for the instance outgrows the slice, the rest go straight to
         // global memory (schedules, and so results, are the same either way).
-        if (threadIdx.x == 0) s_over = 0;
+        if (threadIdx.x == 0) {
+            s_over = 0;
+            s_next = 0;
+        }
         __syncthreads();
         bool gfirst = Hcap == 0;
         bool probing = true;
@@ -215,15 +219,22 @@ __global__ void __maxnreg__(128) k_batch(BatchArgs a) {
             if (fits) {
                 const GASrc src{in->Y[cur], in->X[cur], in->fit[cur], P, I, K, a.tour_k, a.side,
                                 a.pc_thr, a.pm_thr, a.seed, in->iid, 1};
-                for (int isl = rank; isl < nisl; isl += CS)
-                    for (int c = warp; c < I; c += W) {
-                        const int i = isl * I + c;
-                        make_child<MACH>(T, w, src, i, g1, lane);
-                        write_ind(in->Y[nx], in->X[nx], w, i, K, gene, lane);
-                        decode_into<ORDER, MACH>(T, w, Hcap, hg, H, gfirst, in->Y[nx], in->obj[nx], in->fit[nx],
-                                                 emax, i, a.err, &s_over, lane);
-                    }
+                // children t = 0 .. per_round-1 of this CTA's islands (rank, rank + CS, ...), taken
+                // one at a time by whichever warp is free, so slow decodes do not pile up on one
+                // warp (a child's result depends only on its index)
+                for (;;) {
+                    int t = 0;
+                    if (lane == 0) t = atomicAdd(&s_next, 1);
+                    t = __shfl_sync(kFull, t, 0);
+                    if (t >= per_round) break;
+                    const int i = (rank + (t / I) * CS) * I + t % I;
+                    make_child<MACH>(T, w, src, i, g1, lane);
+                    write_ind(in->Y[nx], in->X[nx], w, i, K, gene, lane);
+                    decode_into<ORDER, MACH>(T, w, Hcap, hg, H, gfirst, in->Y[nx], in->obj[nx], in->fit[nx], emax,
+                                             i, a.err, &s_over, lane);
+                }
                 __syncthreads();
+                if (threadIdx.x == 0) s_next = 0;  // the next generation starts after another barrier
                 if (probing) {
                     gfirst = gfirst || 4 * s_over > per_round;
                     probing = false;
