@@ -223,24 +223,35 @@ __device__ __forceinline__ void commit_power_full(uint16_t *h, int t, int e, uin
 // The common case of one op on a shared-memory profile whose slots at or beyond hw hold
 // full headroom: when [t, t+p) lies within one 128-slot step from t & ~3 and every slot of
 // it has headroom q, q is drawn there from the words the check loaded (no second read) and
-// true is returned.  Otherwise nothing changes and false is returned.  Slots at or beyond
-// hw need no check, as q never exceeds the peak.  The caller ensures t + p <= Hcap.
-__device__ __forceinline__ bool place_first(uint16_t *h, int hw, int t, int p, uint32_t q2, uint32_t Q2, int lane) {
+// t is returned.  Otherwise nothing changes and the returned start is where the general
+// scan may resume: one past the last slot lacking headroom (the jump its own first step
+// would make), or t when the op spans more than one step.  Slots at or beyond hw need no
+// check, as q never exceeds the peak.  The caller ensures t + p <= Hcap.
+__device__ __forceinline__ int place_first(uint16_t *h, int hw, int t, int p, uint32_t q2, uint32_t Q2, int lane,
+                                           bool &placed) {
+    placed = false;
     const int c = t & ~3, e = t + p;
-    if (e - c > 128) return false;
+    if (e - c > 128) return t;
     const int b = c + 4 * lane;
     uint2 w = make_uint2(Q2, Q2);  // slots at or beyond hw: full headroom
     if (b < min(e, hw)) w = *reinterpret_cast<const uint2 *>(h + b);
     const uint2 m = slot_mask(b, t, e);
     // bit 15 of (h | 0x8000) - q is clear exactly where h < q (no borrow between halfwords)
-    const uint32_t vx = ~((w.x | 0x80008000u) - q2) & m.x, vy = ~((w.y | 0x80008000u) - q2) & m.y;
-    if (__any_sync(kFull, ((vx | vy) & 0x80008000u) != 0u)) return false;
+    const uint32_t vx = ~((w.x | 0x80008000u) - q2) & m.x & 0x80008000u;
+    const uint32_t vy = ~((w.y | 0x80008000u) - q2) & m.y & 0x80008000u;
+    const unsigned vm = __ballot_sync(kFull, (vx | vy) != 0u);
+    if (vm) {
+        const int l = 31 - __clz(vm);
+        const int li = vy ? 2 + (int)(vy >> 31) : (int)(vx >> 31);  // the lane's last violating slot
+        return c + 4 * l + __shfl_sync(kFull, li, l) + 1;
+    }
     if (m.x | m.y) {
         w.x -= q2 & m.x;
         w.y -= q2 & m.y;
         *reinterpret_cast<uint2 *>(h + b) = w;
     }
-    return true;
+    placed = true;
+    return t;
 }
 
 // Marks slots [t, e) busy in a machine's occupancy bitmap; lane l takes word (t >> 5) + l
@@ -257,15 +268,17 @@ __device__ __forceinline__ void commit_busy(uint32_t *bm, int t, int e, int lane
 // availability t0 (slots past RS; INT_MAX elsewhere) and power q2.  Returns the
 // lexicographic minimum of (earliest power-feasible start, machine): the machine that
 // frees first is scanned first, another only if it could still start earlier.
+// `from`: a start below which the first machine is already known to fail (its scan
+// resumes there).
 template <bool INS = false>
 __device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int t0, uint32_t q2, int os,
                                                  int p, int lane, int &best_t, int &best_m, uint32_t &best_q2,
-                                                 const uint32_t *busy = nullptr, int words = 0) {
+                                                 const uint32_t *busy = nullptr, int words = 0, int from = 0) {
     const unsigned key = lane < os ? ((unsigned)t0 << 5) | (unsigned)lane : 0xFFFFFFFFu;
     const unsigned kmin = __reduce_min_sync(kFull, key);
     best_m = (int)(kmin & 31u);
     best_q2 = __shfl_sync(kFull, q2, best_m);
-    best_t = earliest_start<INS>(h, hw, (int)(kmin >> 5), p, best_q2, INT_MAX, lane,
+    best_t = earliest_start<INS>(h, hw, max((int)(kmin >> 5), from), p, best_q2, INT_MAX, lane,
                                  busy + (size_t)best_m * words, words);
     // if the first machine starts as soon as it frees, no machine can start earlier (every
     // other one frees no sooner, and equal times lose to its lower index)
@@ -460,31 +473,30 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                     if (mach_unrel(MACH)) p = __shfl_sync(kFull, p, best_m);
                     bq2 = __shfl_sync(kFull, qo2, best_m);
                     const int t0 = max(est, __shfl_sync(kFull, mf, best_m));
-                    if (kFast && t0 + p <= Hcap && place_first(h, hw, t0, p, bq2, Q2, lane)) {
+                    int from = t0;
+                    if (kFast && t0 + p <= Hcap) from = place_first(h, hw, t0, p, bq2, Q2, lane, placed);
+                    if (placed)
                         best_t = t0;
-                        placed = true;
-                    } else {
-                        best_t = earliest_start<INS>(h, hw, t0, p, bq2, INT_MAX, lane, busy + (size_t)best_m * words,
+                    else
+                        best_t = earliest_start<INS>(h, hw, from, p, bq2, INT_MAX, lane, busy + (size_t)best_m * words,
                                                      words);
-                    }
                 } else if (mach_unrel(MACH)) {
                     earliest_machine_u<INS>(h, hw, max(est, mf), qo2, p, os, lane, best_t, best_m, p, busy, words);
                     bq2 = __shfl_sync(kFull, qo2, best_m);
                 } else {
                     const int tl = lane < os ? max(est, mf) : INT_MAX;
+                    int from = 0;
                     if (kFast) {  // the machine that frees first (lowest index on ties)
                         const unsigned key = ((unsigned)max(est, mf) << 5) | (unsigned)lane;
                         const unsigned kmin = __reduce_min_sync(kFull, key);
                         const int t0 = (int)(kmin >> 5);
                         best_m = (int)(kmin & 31u);
                         bq2 = __shfl_sync(kFull, q2, best_m);
-                        if (t0 + p <= Hcap && place_first(h, hw, t0, p, bq2, Q2, lane)) {
-                            best_t = t0;
-                            placed = true;
-                        }
+                        if (t0 + p <= Hcap) from = place_first(h, hw, t0, p, bq2, Q2, lane, placed);
+                        if (placed) best_t = t0;
                     }
                     if (!placed)
-                        earliest_machine<INS>(h, hw, tl, q2, os, p, lane, best_t, best_m, bq2, busy, words);
+                        earliest_machine<INS>(h, hw, tl, q2, os, p, lane, best_t, best_m, bq2, busy, words, from);
                 }
                 const int e = best_t + p;
                 if (placed) {
