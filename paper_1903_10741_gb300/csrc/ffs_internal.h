@@ -143,6 +143,7 @@ struct ga_population {
     int train_steps = 1;
     uint64_t screen_thr = (uint64_t)1 << 32;  // floor(screen probability * 2^32)
     cudaGraphExec_t graph_sur = nullptr;
+    cudaGraphExec_t graph_r = nullptr;      // kGraphGens generations, each launched as the previous one drains
     bool profiling = false;                 // eager launches with timed generation kernels
     std::vector<cudaEvent_t> ev;            // event pairs, reused across ga_run calls
     double prof_ms = 0.0;
@@ -152,6 +153,7 @@ struct ga_population {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         if (graph) cudaGraphExecDestroy(graph);
         if (graph_sur) cudaGraphExecDestroy(graph_sur);
+        if (graph_r) cudaGraphExecDestroy(graph_r);
         dfree(cand_Y);
         dfree(cand_X);
         dfree(cand_Yh);

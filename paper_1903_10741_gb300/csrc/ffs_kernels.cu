@@ -173,6 +173,12 @@ __global__ void __maxnreg__(128) k_ga_generation(GenArgs a) {
     extern __shared__ __align__(128) char smem[];
     char *tab = smem + 128;
     if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
+    // Launched as a programmatic dependent, the kernel got here (tables staged, which no
+    // generation changes) while the previous generation was draining: wait until it has
+    // completed and its writes are visible, then let the next generation be scheduled.
+    // Without such a launch both are no-ops.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const Tabs T = tabs_view(tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, true, false, nullptr, warp, mach_insert(MACH));
@@ -498,12 +504,22 @@ cudaError_t launch_ga_init(int order, int mach, const GenArgs &a, const TabHeade
 }
 
 cudaError_t launch_ga_generation(int order, int mach, const GenArgs &a, const TabHeader &h,
-                                 int grid, cudaStream_t st) {
+                                 int grid, cudaStream_t st, bool overlap) {
     const int smem = cta_smem_bytes(h, a.Hcap, true, false, mach_insert(mach));
     cudaError_t e = cudaSuccess;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kWarpsPerBlock * 32);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = overlap ? 1 : 0;
     FFS_DISPATCH({
         e = prepare(k_ga_generation<O_, M_>, smem);
-        if (e == cudaSuccess) k_ga_generation<O_, M_><<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
+        if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_ga_generation<O_, M_>, a);
     });
     return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -151,8 +151,11 @@ cudaError_t launch_decode(int order, int mach, bool global_profile, const Decode
                           const TabHeader &h, int grid, cudaStream_t st);
 cudaError_t launch_ga_init(int order, int mach, const GenArgs &a, const TabHeader &h, int grid,
                            cudaStream_t st);
+// overlap: launched as a programmatic dependent of the stream's previous kernel.
 cudaError_t launch_ga_generation(int order, int mach, const GenArgs &a, const TabHeader &h,
-                                 int grid, cudaStream_t st);
+                                 int grid, cudaStream_t st, bool overlap = false);
+// Generations per graph of generations launched back to back.
+constexpr int kGraphGens = 8;
 cudaError_t prepare_ga_generation(int order, int mach, const TabHeader &h, int Hcap);
 // Over-generation for the surrogate: P*F candidates (no decoding).
 cudaError_t launch_candidates(int mach, const GenArgs &a, const TabHeader &h, int grid, cudaStream_t st);

@@ -632,11 +632,16 @@ static void ga_fallback_args(ga_population *pp, DecodeArgs *d, bool ga_mode) {
 // One generation is one kernel: selection, crossover, mutation and decoding per child,
 // then (by the last warps to finish) elitist replacement, migration and the counter.
 // With timing events, the kernel is bracketed by ev0/ev1 on the population's stream.
-static int ga_enqueue_generation(ga_population *pp, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
+// With `overlap`, the kernel is launched as a programmatic dependent of the previous one on
+// the stream: its CTAs are scheduled while that kernel drains and stage their tables, then
+// wait until it has completed and its writes are visible.
+static int ga_enqueue_generation(ga_population *pp, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
+                                 bool overlap = false) {
     GenArgs a;
     ga_gen_args(pp, &a);
     if (ev0) FFS_CUDA(cudaEventRecord(ev0, pp->st));
-    FFS_CUDA(launch_ga_generation(pp->par.order_mode, pp->par.machine_mode, a, pp->hdr, pp->grid_gen, pp->st));
+    FFS_CUDA(launch_ga_generation(pp->par.order_mode, pp->par.machine_mode, a, pp->hdr, pp->grid_gen, pp->st,
+                                  overlap));
     if (ev1) FFS_CUDA(cudaEventRecord(ev1, pp->st));
     return FFS_OK;
 }
@@ -831,11 +836,22 @@ int create_population(ffs_instance *in, const ga_params *par, ga_population *pre
         rc = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
         const int erc = rc == FFS_OK ? ga_enqueue_generation(pp) : rc;
         const int ce = rc == FFS_OK ? cuda_rc(cudaStreamEndCapture(cap, &graph)) : rc;
-        pp->st = user;
-        cudaStreamDestroy(cap);
         rc = erc != FFS_OK ? erc : ce;
         if (rc == FFS_OK) rc = cuda_rc(cudaGraphInstantiate(&pp->graph, graph, 0));
         if (graph) cudaGraphDestroy(graph);
+        graph = nullptr;
+        // kGraphGens generations in one graph, each launched as a programmatic dependent of
+        // the one before, which hides the launch gap between generations
+        if (rc == FFS_OK) rc = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        int erc2 = FFS_OK;
+        for (int g = 0; rc == FFS_OK && erc2 == FFS_OK && g < kGraphGens; ++g)
+            erc2 = ga_enqueue_generation(pp, nullptr, nullptr, g > 0);
+        const int ce2 = rc == FFS_OK ? cuda_rc(cudaStreamEndCapture(cap, &graph)) : rc;
+        if (rc == FFS_OK) rc = erc2 != FFS_OK ? erc2 : ce2;
+        if (rc == FFS_OK) rc = cuda_rc(cudaGraphInstantiate(&pp->graph_r, graph, 0));
+        if (graph) cudaGraphDestroy(graph);
+        pp->st = user;
+        cudaStreamDestroy(cap);
     }
     const int sync_rc = cuda_rc(cudaStreamSynchronize(st));
     dfree(d_map);
@@ -867,7 +883,8 @@ int ffs_rt::population_create(ffs_instance *in, const ga_params *par, ga_populat
 void ffs_rt::population_trim(ga_population *pp) {
     if (pp->graph) cudaGraphExecDestroy(pp->graph);
     if (pp->graph_sur) cudaGraphExecDestroy(pp->graph_sur);
-    pp->graph = pp->graph_sur = nullptr;
+    if (pp->graph_r) cudaGraphExecDestroy(pp->graph_r);
+    pp->graph = pp->graph_sur = pp->graph_r = nullptr;
     dfree(pp->d_blob);
     for (int b = 0; b < 2; ++b) {
         dfree(pp->obj[b]);
@@ -949,7 +966,10 @@ int ffs_rt::ga_enqueue(ga_population *pp, int32_t generations) {
     }
     if (pp->profiling) return FFS_E_STATE;
     cudaGraphExec_t gx = pp->sur ? pp->graph_sur : pp->graph;
-    for (int i = 0; i < generations; ++i) FFS_CUDA(cudaGraphLaunch(gx, pp->st));
+    int i = 0;
+    if (!pp->sur && pp->graph_r)
+        for (; i + kGraphGens <= generations; i += kGraphGens) FFS_CUDA(cudaGraphLaunch(pp->graph_r, pp->st));
+    for (; i < generations; ++i) FFS_CUDA(cudaGraphLaunch(gx, pp->st));
     g_launches += per_gen * (unsigned long long)generations;
     return FFS_OK;
 }
