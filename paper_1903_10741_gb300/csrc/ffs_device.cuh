@@ -464,9 +464,9 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 const int est = max(cj - RS, 0);
                 int best_t, best_m;
                 uint32_t bq2;
-                // fast path (identical machines, append placement, prefilled profile): the
-                // first candidate start is feasible and the op is drawn in the same step
-                constexpr bool kFast = FULL && !INS && !mach_unrel(MACH);
+                // fast path (append placement, prefilled profile): the first candidate start
+                // is feasible and the op is drawn in the same step
+                constexpr bool kFast = FULL && !INS;
                 bool placed = false;
                 if (mach_gene(MACH)) {
                     best_m = x[k];
@@ -481,8 +481,25 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                         best_t = earliest_start<INS>(h, hw, from, p, bq2, INT_MAX, lane, busy + (size_t)best_m * words,
                                                      words);
                 } else if (mach_unrel(MACH)) {
-                    earliest_machine_u<INS>(h, hw, max(est, mf), qo2, p, os, lane, best_t, best_m, p, busy, words);
-                    bq2 = __shfl_sync(kFull, qo2, best_m);
+                    if (kFast) {  // the machine whose completion bound is lowest (lowest index on ties):
+                                  // starting as soon as it frees, nothing completes earlier
+                        const int tl = max(est, mf);
+                        const unsigned key =
+                            lane < os ? ((unsigned)(tl + p) << 5) | (unsigned)lane : 0xFFFFFFFFu;
+                        const unsigned kmin = __reduce_min_sync(kFull, key);
+                        best_m = (int)(kmin & 31u);
+                        const int t0 = __shfl_sync(kFull, tl, best_m), pb = __shfl_sync(kFull, p, best_m);
+                        bq2 = __shfl_sync(kFull, qo2, best_m);
+                        if (t0 + pb <= Hcap) place_first(h, hw, t0, pb, bq2, Q2, lane, placed);
+                        if (placed) {
+                            best_t = t0;
+                            p = pb;
+                        }
+                    }
+                    if (!placed) {
+                        earliest_machine_u<INS>(h, hw, max(est, mf), qo2, p, os, lane, best_t, best_m, p, busy, words);
+                        bq2 = __shfl_sync(kFull, qo2, best_m);
+                    }
                 } else {
                     const int tl = lane < os ? max(est, mf) : INT_MAX;
                     int from = 0;
