@@ -126,7 +126,8 @@ __global__ void __maxnreg__(128) k_ga_init(GenArgs a) {
 // the elitist replacement (Sec. 4.4: the island's best-ever individual overwrites its
 // worst child) and, at migration generations, records the island's best and worst; the
 // last island to finish performs the single-ring migration (island i's worst <- island
-// i-1's best, from those records) and advances the generation counter.  Completion is
+// i-1's best, from those records) and, at the last generation of a chain, advances the
+// generation counter (islands count themselves only then or to migrate).  Completion is
 // counted with atomics after a device-wide fence; nothing waits.
 // Copies in this tail lie on the critical path of a generation (the last island's last
 // warp runs them after every decode): 256 genes per chunk, one L2 round trip each.
@@ -148,6 +149,8 @@ __device__ void island_finish(const Args &a, int isl, int nx, int gen, int lane)
     island_replace<kTailU>(Y, X, obj, fit, a.bY, a.bX, a.bobj, a.bfit, isl, a.I, K, migrate, a.mY, a.mX, a.mobj,
                            a.mfit, a.mw, lane);
     if (lane == 0) a.isl_done[isl] = 0;
+    // within a chain the counter is left as it was; islands meet only to migrate
+    if (!a.publish && !migrate) return;
     __threadfence();
     if (lane == 0) ticket = atomicAdd(&a.dev->islands_done, 1);
     ticket = __shfl_sync(kFull, ticket, 0);
@@ -156,9 +159,11 @@ __device__ void island_finish(const Args &a, int isl, int nx, int gen, int lane)
     if (migrate) ring_migrate<kTailU>(Y, X, obj, fit, a.mY, a.mX, a.mobj, a.mfit, a.mw, a.nisl, K, lane);
     if (lane == 0) {
         a.dev->islands_done = 0;
-        a.dev->nover = 0;
-        __threadfence();
-        a.dev->gen = gen;
+        if (a.publish) {
+            a.dev->nover = 0;
+            __threadfence();
+            a.dev->gen = gen;
+        }
     }
 }
 
@@ -183,8 +188,9 @@ __global__ void __maxnreg__(128) k_ga_generation(GenArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, true, false, nullptr, warp, mach_insert(MACH));
     const int K = T.K, I = a.I;
-    const int cur = a.dev->gen & 1, nx = cur ^ 1;
-    const uint32_t gen = (uint32_t)a.dev->gen + 1;
+    const int g0 = a.dev->gen + a.gen_ofs;  // generations completed before this one
+    const int cur = g0 & 1, nx = cur ^ 1;
+    const uint32_t gen = (uint32_t)g0 + 1;
     const long long emax = a.dev->emax;
     const GASrc src{a.Y[cur], a.X[cur], a.fit[cur], a.P, a.I, K, a.tour_k, a.side, a.pc_thr, a.pm_thr, a.seed,
                     a.instance_id, 1};

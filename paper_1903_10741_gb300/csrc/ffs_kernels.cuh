@@ -46,6 +46,9 @@ struct GenArgs {
     int64_t *fit[2];
     GADev *dev;
     int P, I, K, tour_k, side;  // side: torus side for 5-neighbourhood selection
+    // Generation gen_ofs of a chain launched together (the counter is read as it stood when
+    // the chain began); only a chain's last generation (publish) advances the counter.
+    int gen_ofs, publish;
     uint64_t pc_thr, pm_thr;    // floor(p * 2^32)
     uint32_t instance_id;
     uint64_t seed;

@@ -592,6 +592,8 @@ void ffs_rt::ga_gen_args(ga_population *pp, GenArgs *a) {
     a->P = pp->P;
     a->I = pp->I;
     a->K = pp->K;
+    a->gen_ofs = 0;
+    a->publish = 1;
     a->H = pp->hdr.H;
     a->gscratch = pp->scratch;
     a->isl_done = pp->isl_done;
@@ -635,10 +637,14 @@ static void ga_fallback_args(ga_population *pp, DecodeArgs *d, bool ga_mode) {
 // With `overlap`, the kernel is launched as a programmatic dependent of the previous one on
 // the stream: its CTAs are scheduled while that kernel drains and stage their tables, then
 // wait until it has completed and its writes are visible.
+// In a chain of generations launched together, generation `ofs` reads the counter as it
+// stood when the chain began and only the last one (`publish`) advances it.
 static int ga_enqueue_generation(ga_population *pp, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr,
-                                 bool overlap = false) {
+                                 bool overlap = false, int ofs = 0, bool publish = true) {
     GenArgs a;
     ga_gen_args(pp, &a);
+    a.gen_ofs = ofs;
+    a.publish = publish ? 1 : 0;
     if (ev0) FFS_CUDA(cudaEventRecord(ev0, pp->st));
     FFS_CUDA(launch_ga_generation(pp->par.order_mode, pp->par.machine_mode, a, pp->hdr, pp->grid_gen, pp->st,
                                   overlap));
@@ -845,7 +851,7 @@ int create_population(ffs_instance *in, const ga_params *par, ga_population *pre
         if (rc == FFS_OK) rc = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
         int erc2 = FFS_OK;
         for (int g = 0; rc == FFS_OK && erc2 == FFS_OK && g < kGraphGens; ++g)
-            erc2 = ga_enqueue_generation(pp, nullptr, nullptr, g > 0);
+            erc2 = ga_enqueue_generation(pp, nullptr, nullptr, g > 0, g, g == kGraphGens - 1);
         const int ce2 = rc == FFS_OK ? cuda_rc(cudaStreamEndCapture(cap, &graph)) : rc;
         if (rc == FFS_OK) rc = erc2 != FFS_OK ? erc2 : ce2;
         if (rc == FFS_OK) rc = cuda_rc(cudaGraphInstantiate(&pp->graph_r, graph, 0));
