@@ -48,7 +48,7 @@ SLOTS_PER_DECODE = 64865.5
 # DRAM bytes (read + write) of one generation-kernel launch from the ncu capture of the
 # current kernel (dram__bytes_read.sum + dram__bytes_write.sum, initial solve); None once
 # the kernel changes until it is captured again.
-TRAFFIC_BYTES = 423936
+TRAFFIC_BYTES = 423680
 # INT32 issue ceiling: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (lane-ops/s).
 ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
