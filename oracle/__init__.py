@@ -90,6 +90,17 @@ def lib():
         L.orc_correct.argtypes = [C.c_int32, C.c_void_p]
         L.orc_crossover.argtypes = [C.c_int32] + [C.c_void_p] * 4 + [C.c_int32, C.c_int32] + [C.c_void_p] * 4
         L.orc_mutate.argtypes = [C.c_int32, _i32p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32]
+        L.orc_order.argtypes = [C.POINTER(_Inst), C.c_int32, C.c_void_p, C.c_void_p, _i32p]
+        _i64p = C.POINTER(C.c_int64)
+        L.orc_island_best_worst.argtypes = [_i64p, C.c_int32, C.c_int32, _i32p, _i32p]
+        L.orc_tournament.restype = C.c_int32
+        L.orc_tournament.argtypes = [_i64p, _i32p, C.c_int32]
+        L.orc_l5_cells.argtypes = [C.c_int32, C.c_int32, _i32p]
+        L.orc_select.restype = C.c_int32
+        L.orc_select.argtypes = [_i64p, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_int32, C.c_int32,
+                                 C.c_int32]
+        L.orc_island_replace.argtypes = [C.c_int32, C.c_int32, C.c_int32] + [C.c_void_p] * 8
+        L.orc_migrate.argtypes = [C.c_int32, C.c_int32, C.c_int32] + [C.c_void_p] * 4
         L.orc_ga_init.restype = C.c_int32
         L.orc_ga_init.argtypes = [C.POINTER(_Inst), C.POINTER(_GAParams), C.POINTER(_GAState)]
         L.orc_ga_init_from.restype = C.c_int32
@@ -213,6 +224,16 @@ class Instance:
         return dict(S=S, M=M, obj=int(ev.obj), tard=int(ev.tard), cmax=int(ev.cmax),
                     probes=int(ev.probes), span=int(ev.span), slots=int(ev.slots))
 
+    def order(self, y, order_mode=ORDER_STAGE, given=None) -> np.ndarray:
+        """Z of Alg. 1: the genes in the order the decoder assigns them."""
+        y = np.ascontiguousarray(y, dtype=np.int16)
+        K = self.K
+        gv = None if given is None else np.ascontiguousarray(given, dtype=np.int32)
+        out = np.zeros(max(K, 1), dtype=np.int32)
+        c = self._c()
+        lib().orc_order(C.byref(c), order_mode, _ptr(y), _ptr(gv), _p32(out))
+        return out[:K]
+
     def commit(self, S, M):
         """Make (S, M) the plan being executed."""
         self.S0 = np.ascontiguousarray(S, dtype=np.int32).copy()
@@ -276,6 +297,63 @@ def mutate(y, x, gene_o, xr, a, b):
     xr = np.ascontiguousarray(xr, dtype=np.uint32)
     lib().orc_mutate(len(y), _p32(go), _ptr(y), _ptr(x), _ptr(xr), int(a), int(b))
     return y, x
+
+
+# ------------------------------------------------------------------ GA operators (Sec. 4.4)
+
+def _i64(a):
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+def island_best_worst(fit, lo: int, hi: int):
+    """(best, worst) of fit[lo:hi]: largest / smallest fitness, lowest index among equals."""
+    f = _i64(fit)
+    b, w = C.c_int32(), C.c_int32()
+    lib().orc_island_best_worst(f.ctypes.data_as(C.POINTER(C.c_int64)), lo, hi, C.byref(b), C.byref(w))
+    return int(b.value), int(w.value)
+
+
+def tournament(fit, entrants) -> int:
+    """Winner among the entrant indices: largest fitness, ties to the lowest index."""
+    f = _i64(fit)
+    e = np.ascontiguousarray(entrants, dtype=np.int32)
+    return int(lib().orc_tournament(f.ctypes.data_as(C.POINTER(C.c_int64)), _p32(e), len(e)))
+
+
+def l5_cells(P: int, i: int):
+    """Cell i and its N, S, W, E neighbours on the sqrt(P) x sqrt(P) torus."""
+    out = np.zeros(5, np.int32)
+    lib().orc_l5_cells(P, i, _p32(out))
+    return out.tolist()
+
+
+def select(fit, P: int, I: int, tour_k: int, seed: int, instance: int, gen: int, slot: int) -> int:
+    """The parent the GA selects for `slot` at generation `gen`."""
+    f = _i64(fit)
+    return int(lib().orc_select(f.ctypes.data_as(C.POINTER(C.c_int64)), P, I, tour_k, seed, instance, gen, slot))
+
+
+def island_replace(cY, cX, cobj, cfit, lo: int, I: int, bY, bX, bobj: int, bfit: int):
+    """Elitist replacement of the island at slots lo..lo+I.  Returns the updated children
+    (Y, X, obj, fit) and best-ever record (bY, bX, bobj, bfit) as new arrays."""
+    cY = np.ascontiguousarray(cY, dtype=np.int16).copy()
+    cX = np.ascontiguousarray(cX, dtype=np.int8).copy()
+    cobj, cfit = _i64(cobj).copy(), _i64(cfit).copy()
+    bY = np.ascontiguousarray(bY, dtype=np.int16).copy()
+    bX = np.ascontiguousarray(bX, dtype=np.int8).copy()
+    bo, bf = np.array([bobj], np.int64), np.array([bfit], np.int64)
+    lib().orc_island_replace(cY.shape[1], lo, I, _ptr(cY), _ptr(cX), _ptr(cobj), _ptr(cfit), _ptr(bY), _ptr(bX),
+                             _ptr(bo), _ptr(bf))
+    return cY, cX, cobj, cfit, bY, bX, int(bo[0]), int(bf[0])
+
+
+def migrate(cY, cX, cobj, cfit, I: int):
+    """Single-ring migration over the islands of I slots; returns new arrays."""
+    cY = np.ascontiguousarray(cY, dtype=np.int16).copy()
+    cX = np.ascontiguousarray(cX, dtype=np.int8).copy()
+    cobj, cfit = _i64(cobj).copy(), _i64(cfit).copy()
+    lib().orc_migrate(cY.shape[1], I, len(cfit) // I, _ptr(cY), _ptr(cX), _ptr(cobj), _ptr(cfit))
+    return cY, cX, cobj, cfit
 
 
 # ------------------------------------------------------------------ GA

@@ -17,6 +17,9 @@
  *   - Brute force over all priority orders on tiny instances.
  *   - Fig. 11 crossover/correction and Fig. 12 mutation examples.
  *   - Table 11 objective arithmetic (Eq. 1).
+ *   - Hand-worked selection (tournament ties, the 5-cell torus), elitist replacement and
+ *     ring migration cases, the operator order of a generation, and the Z order of both
+ *     readings of Alg. 1 on the Sec. 4.3 example, position by position.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -182,6 +185,50 @@ static int32_t max32(int32_t a, int32_t b) { return a > b ? a : b; }
 
 /* ---------------------------------------------------------------- decoder */
 
+/* Z, the assignment order of the K free ops (Alg. 1), into order[0..K):
+ *   ORDER_TOPO  -- repeatedly the next unassigned free op of some job: among those heads,
+ *                  the one with the largest y (y values are distinct).
+ *   ORDER_STAGE -- stage s = 0..g-1 in turn, each stage's free ops by y descending.
+ *   ORDER_GIVEN -- `given` as it is.
+ * gene_at[j*g+s] is the gene of op (j, s), or -1 for a frozen op. */
+static void fill_order(int32_t N, int32_t g, int32_t K, const int32_t *gstg, const int32_t *gene_at,
+                       int32_t order_mode, const int16_t *y, const int32_t *given, int32_t *order)
+{
+    if (order_mode == ORDER_TOPO) {
+        int32_t *head = (int32_t *)calloc((size_t)N + 1, sizeof(int32_t)); /* next stage of j */
+        for (int32_t j = 0; j < N; j++) {
+            head[j] = 0;
+            while (head[j] < g && gene_at[j * g + head[j]] < 0) head[j]++;
+        }
+        for (int32_t n = 0; n < K; n++) {
+            int32_t bestj = -1, besty = -1;
+            for (int32_t j = 0; j < N; j++) {
+                if (head[j] >= g) continue;
+                int32_t k = gene_at[j * g + head[j]];
+                if (y[k] > besty) { besty = y[k]; bestj = j; }
+            }
+            order[n] = gene_at[bestj * g + head[bestj]];
+            head[bestj]++;
+        }
+        free(head);
+    } else if (order_mode == ORDER_STAGE) {
+        int32_t n = 0;
+        for (int32_t s = 0; s < g; s++) {
+            int32_t first = n;
+            for (int32_t k = 0; k < K; k++)
+                if (gstg[k] == s) order[n++] = k;
+            /* insertion sort of this stage's genes by y, descending */
+            for (int32_t a = first + 1; a < n; a++) {
+                int32_t v = order[a], b = a - 1;
+                while (b >= first && y[order[b]] < y[v]) { order[b + 1] = order[b]; b--; }
+                order[b + 1] = v;
+            }
+        }
+    } else {
+        for (int32_t n = 0; n < K; n++) order[n] = given[n];
+    }
+}
+
 /*
  * Decode one chromosome (Sec. 4.3, Alg. 1 and Alg. 2) into a schedule and its objective.
  *
@@ -302,40 +349,7 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
     int32_t *gene_at = (int32_t *)malloc(sizeof(int32_t) * (size_t)N * (size_t)g);
     for (int32_t i = 0; i < N * g; i++) gene_at[i] = -1;
     for (int32_t k = 0; k < K; k++) gene_at[gjob[k] * g + gstg[k]] = k;
-
-    if (order_mode == ORDER_TOPO) {
-        int32_t *head = (int32_t *)calloc((size_t)N, sizeof(int32_t)); /* next stage of j */
-        for (int32_t j = 0; j < N; j++) {
-            head[j] = 0;
-            while (head[j] < g && gene_at[j * g + head[j]] < 0) head[j]++;
-        }
-        for (int32_t n = 0; n < K; n++) {
-            int32_t bestj = -1, besty = -1;
-            for (int32_t j = 0; j < N; j++) {
-                if (head[j] >= g) continue;
-                int32_t k = gene_at[j * g + head[j]];
-                if (y[k] > besty) { besty = y[k]; bestj = j; }
-            }
-            order[n] = gene_at[bestj * g + head[bestj]];
-            head[bestj]++;
-        }
-        free(head);
-    } else if (order_mode == ORDER_STAGE) {
-        int32_t n = 0;
-        for (int32_t s = 0; s < g; s++) {
-            int32_t first = n;
-            for (int32_t k = 0; k < K; k++)
-                if (gstg[k] == s) order[n++] = k;
-            /* insertion sort of this stage's genes by y, descending */
-            for (int32_t a = first + 1; a < n; a++) {
-                int32_t v = order[a], b = a - 1;
-                while (b >= first && y[order[b]] < y[v]) { order[b + 1] = order[b]; b--; }
-                order[b + 1] = v;
-            }
-        }
-    } else {
-        for (int32_t n = 0; n < K; n++) order[n] = given[n];
-    }
+    fill_order(N, g, K, gstg, gene_at, order_mode, y, given, order);
 
     /* ---- Alg. 2: assign in Z order */
     int32_t *placed = (int32_t *)calloc((size_t)K + 1, sizeof(int32_t));
@@ -405,6 +419,22 @@ int32_t orc_decode(const orc_inst *in, int32_t order_mode, int32_t mach_mode,
     free(placed); free(order); free(gene_at); free(Qt); free(mfree); free(C); free(busy);
     free(moff); free(gjob); free(gstg);
     return ev->err;
+}
+
+/* The assignment order Z that orc_decode uses for chromosome y (Alg. 1): order_out[n] is
+ * the gene placed n-th.  y must be a permutation of 1..K (not checked here). */
+void orc_order(const orc_inst *in, int32_t order_mode, const int16_t *y, const int32_t *given,
+               int32_t *order_out)
+{
+    const int32_t N = in->N, g = in->g, K = orc_gene_count(in);
+    int32_t *gjob = (int32_t *)calloc((size_t)K + 1, sizeof(int32_t));
+    int32_t *gstg = (int32_t *)calloc((size_t)K + 1, sizeof(int32_t));
+    orc_gene_map(in, gjob, gstg);
+    int32_t *gene_at = (int32_t *)malloc(sizeof(int32_t) * (size_t)N * (size_t)g);
+    for (int32_t i = 0; i < N * g; i++) gene_at[i] = -1;
+    for (int32_t k = 0; k < K; k++) gene_at[gjob[k] * g + gstg[k]] = k;
+    fill_order(N, g, K, gstg, gene_at, order_mode, y, given, order_out);
+    free(gene_at); free(gjob); free(gstg);
 }
 
 /* Objective of Eq. (1) from per-job completion times (Table 11 arithmetic). */
@@ -526,8 +556,9 @@ static int64_t fitness(int64_t emax, int64_t obj)
     return emax - obj > 0 ? emax - obj : 0;
 }
 
-static void island_best_worst(const int64_t *fit, int32_t lo, int32_t hi, int32_t *best,
-                              int32_t *worst)
+/* Best (largest fitness) and worst (smallest fitness) of fit[lo..hi), each the lowest
+ * index among equals. */
+void orc_island_best_worst(const int64_t *fit, int32_t lo, int32_t hi, int32_t *best, int32_t *worst)
 {
     int32_t b = lo, w = lo;
     for (int32_t i = lo + 1; i < hi; i++) {
@@ -536,6 +567,104 @@ static void island_best_worst(const int64_t *fit, int32_t lo, int32_t hi, int32_
     }
     *best = b;
     *worst = w;
+}
+
+/* Winner among the n entrants cand[0..n) (population indices, repeats allowed): the
+ * largest fitness, ties to the lowest index (Sec. 4.4 selection). */
+int32_t orc_tournament(const int64_t *fit, const int32_t *cand, int32_t n)
+{
+    int32_t best = -1;
+    for (int32_t t = 0; t < n; t++) {
+        int32_t c = cand[t];
+        if (best < 0 || fit[c] > fit[best] || (fit[c] == fit[best] && c < best))
+            best = c;
+    }
+    return best;
+}
+
+/* The 5-cell neighbourhood of cell i on the side x side torus of the population grid
+ * (Sec. 4.4, Fig. 9: the cell, then N, S, W, E), side * side = P, cells row-major. */
+void orc_l5_cells(int32_t P, int32_t i, int32_t out[5])
+{
+    int32_t side = 1;
+    while (side * side < P) side++;
+    int32_t r = i / side, c = i % side;
+    out[0] = i;
+    out[1] = ((r + side - 1) % side) * side + c;
+    out[2] = ((r + 1) % side) * side + c;
+    out[3] = r * side + (c + side - 1) % side;
+    out[4] = r * side + (c + 1) % side;
+}
+
+/* Parent of population slot i at generation gen: with tour_k > 0 the winner of k entrants
+ * drawn uniformly from the slot's island (entrant t = island start + floor(u_t * I / 2^32),
+ * u_t = draw t of the selection stream of slot i); with tour_k = 0 the winner of the
+ * slot's 5-cell torus neighbourhood. */
+int32_t orc_select(const int64_t *fit, int32_t P, int32_t I, int32_t tour_k, uint64_t seed,
+                   int32_t iid, int32_t gen, int32_t i)
+{
+    int32_t cand[64];
+    int32_t n;
+    if (tour_k > 0) {
+        int32_t lo = (i / I) * I;
+        n = tour_k < 64 ? tour_k : 64;
+        for (int32_t t = 0; t < n; t++)
+            cand[t] = lo + (int32_t)below(orc_draw(seed, P_SELECT, (uint32_t)iid, (uint32_t)gen, (uint32_t)i,
+                                                   (uint32_t)t), (uint32_t)I);
+    } else {
+        orc_l5_cells(P, i, cand);
+        n = 5;
+    }
+    return orc_tournament(fit, cand, n);
+}
+
+/* Elitist replacement of one island (Sec. 4.4): the children cY/cX/cobj/cfit of slots
+ * lo..lo+I; b* is the island's best-ever record.  If the best child (lowest index among
+ * equals) is strictly fitter than the record, it becomes the record; then the record
+ * overwrites the worst child (lowest index among equals). */
+void orc_island_replace(int32_t K, int32_t lo, int32_t I, int16_t *cY, int8_t *cX, int64_t *cobj,
+                        int64_t *cfit, int16_t *bY, int8_t *bX, int64_t *bobj, int64_t *bfit)
+{
+    int32_t b, w;
+    orc_island_best_worst(cfit, lo, lo + I, &b, &w);
+    if (cfit[b] > *bfit) {
+        memcpy(bY, cY + (size_t)b * K, sizeof(int16_t) * (size_t)K);
+        memcpy(bX, cX + (size_t)b * K, (size_t)K);
+        *bobj = cobj[b];
+        *bfit = cfit[b];
+    }
+    memcpy(cY + (size_t)w * K, bY, sizeof(int16_t) * (size_t)K);
+    memcpy(cX + (size_t)w * K, bX, (size_t)K);
+    cobj[w] = *bobj;
+    cfit[w] = *bfit;
+}
+
+/* Single-ring migration over nisl islands of I slots (Sec. 4.4): from a snapshot of every
+ * island's best and worst (after replacement), island i's worst slot takes island
+ * (i - 1 mod nisl)'s best individual. */
+void orc_migrate(int32_t K, int32_t I, int32_t nisl, int16_t *cY, int8_t *cX, int64_t *cobj, int64_t *cfit)
+{
+    int32_t *bi = (int32_t *)calloc((size_t)nisl, sizeof(int32_t));
+    int32_t *wi = (int32_t *)calloc((size_t)nisl, sizeof(int32_t));
+    int16_t *mY = (int16_t *)calloc((size_t)nisl * K, sizeof(int16_t));
+    int8_t *mX = (int8_t *)calloc((size_t)nisl * K, 1);
+    int64_t *mo = (int64_t *)calloc((size_t)nisl, sizeof(int64_t));
+    int64_t *mf = (int64_t *)calloc((size_t)nisl, sizeof(int64_t));
+    for (int32_t isl = 0; isl < nisl; isl++) {
+        orc_island_best_worst(cfit, isl * I, isl * I + I, &bi[isl], &wi[isl]);
+        memcpy(mY + (size_t)isl * K, cY + (size_t)bi[isl] * K, sizeof(int16_t) * (size_t)K);
+        memcpy(mX + (size_t)isl * K, cX + (size_t)bi[isl] * K, (size_t)K);
+        mo[isl] = cobj[bi[isl]];
+        mf[isl] = cfit[bi[isl]];
+    }
+    for (int32_t isl = 0; isl < nisl; isl++) {
+        int32_t src = (isl + nisl - 1) % nisl, w = wi[isl];
+        memcpy(cY + (size_t)w * K, mY + (size_t)src * K, sizeof(int16_t) * (size_t)K);
+        memcpy(cX + (size_t)w * K, mX + (size_t)src * K, (size_t)K);
+        cobj[w] = mo[src];
+        cfit[w] = mf[src];
+    }
+    free(bi); free(wi); free(mY); free(mX); free(mo); free(mf);
 }
 
 /* Generation-0 bookkeeping over the rows already in st->Y / st->X: decode every row,
@@ -555,7 +684,7 @@ int32_t orc_ga_init_from(const orc_inst *in, const orc_ga_params *par, orc_ga_st
     for (int32_t i = 0; i < P; i++) st->fit[i] = fitness(e, st->obj[i]);
     for (int32_t isl = 0; isl < P / I; isl++) {
         int32_t b, w;
-        island_best_worst(st->fit, isl * I, isl * I + I, &b, &w);
+        orc_island_best_worst(st->fit, isl * I, isl * I + I, &b, &w);
         memcpy(st->bY + (size_t)isl * K, st->Y + (size_t)b * K, sizeof(int16_t) * (size_t)K);
         memcpy(st->bX + (size_t)isl * K, st->X + (size_t)b * K, (size_t)K);
         st->bobj[isl] = st->obj[b];
@@ -614,29 +743,8 @@ int32_t orc_ga_step(const orc_inst *in, const orc_ga_params *par, orc_ga_state *
 
     /* selection: one parent per slot */
     int32_t *parent = (int32_t *)calloc((size_t)P, sizeof(int32_t));
-    for (int32_t i = 0; i < P; i++) {
-        int32_t best = -1;
-        if (par->tour_k > 0) {
-            int32_t lo = (i / I) * I;
-            for (int32_t t = 0; t < par->tour_k; t++) {
-                int32_t c = lo + (int32_t)below(orc_draw(seed, P_SELECT, iid, gen, i, t), I);
-                if (best < 0 || st->fit[c] > st->fit[best] || (st->fit[c] == st->fit[best] && c < best))
-                    best = c;
-            }
-        } else {
-            int32_t side = 1;
-            while (side * side < P) side++;
-            int32_t r = i / side, c = i % side;
-            int32_t cand[5] = { i, ((r + side - 1) % side) * side + c, ((r + 1) % side) * side + c,
-                                r * side + (c + side - 1) % side, r * side + (c + 1) % side };
-            for (int32_t t = 0; t < 5; t++) {
-                int32_t v = cand[t];
-                if (best < 0 || st->fit[v] > st->fit[best] || (st->fit[v] == st->fit[best] && v < best))
-                    best = v;
-            }
-        }
-        parent[i] = best;
-    }
+    for (int32_t i = 0; i < P; i++)
+        parent[i] = orc_select(st->fit, P, I, par->tour_k, seed, iid, gen, i);
 
     /* crossover on neighbouring pairs, then mutation of each child */
     int16_t *cY = (int16_t *)calloc((size_t)P * K + 1, sizeof(int16_t));
@@ -685,45 +793,13 @@ int32_t orc_ga_step(const orc_inst *in, const orc_ga_params *par, orc_ga_state *
     }
 
     /* elitist replacement: the island's best-ever overwrites its worst child */
-    for (int32_t isl = 0; isl < nisl; isl++) {
-        int32_t b, w;
-        island_best_worst(cfit, isl * I, isl * I + I, &b, &w);
-        if (cfit[b] > st->bfit[isl]) {
-            memcpy(st->bY + (size_t)isl * K, cY + (size_t)b * K, sizeof(int16_t) * (size_t)K);
-            memcpy(st->bX + (size_t)isl * K, cX + (size_t)b * K, (size_t)K);
-            st->bobj[isl] = cobj[b];
-            st->bfit[isl] = cfit[b];
-        }
-        memcpy(cY + (size_t)w * K, st->bY + (size_t)isl * K, sizeof(int16_t) * (size_t)K);
-        memcpy(cX + (size_t)w * K, st->bX + (size_t)isl * K, (size_t)K);
-        cobj[w] = st->bobj[isl];
-        cfit[w] = st->bfit[isl];
-    }
+    for (int32_t isl = 0; isl < nisl; isl++)
+        orc_island_replace(K, isl * I, I, cY, cX, cobj, cfit, st->bY + (size_t)isl * K, st->bX + (size_t)isl * K,
+                           &st->bobj[isl], &st->bfit[isl]);
 
     /* single-ring migration: island i's worst <- island (i-1)'s best, from a snapshot */
-    if (par->migrate_every > 0 && gen % par->migrate_every == 0 && nisl > 1) {
-        int32_t *bi = (int32_t *)calloc((size_t)nisl, sizeof(int32_t));
-        int32_t *wi = (int32_t *)calloc((size_t)nisl, sizeof(int32_t));
-        int16_t *mY = (int16_t *)calloc((size_t)nisl * K, sizeof(int16_t));
-        int8_t *mX = (int8_t *)calloc((size_t)nisl * K, 1);
-        int64_t *mo = (int64_t *)calloc((size_t)nisl, sizeof(int64_t));
-        int64_t *mf = (int64_t *)calloc((size_t)nisl, sizeof(int64_t));
-        for (int32_t isl = 0; isl < nisl; isl++) {
-            island_best_worst(cfit, isl * I, isl * I + I, &bi[isl], &wi[isl]);
-            memcpy(mY + (size_t)isl * K, cY + (size_t)bi[isl] * K, sizeof(int16_t) * (size_t)K);
-            memcpy(mX + (size_t)isl * K, cX + (size_t)bi[isl] * K, (size_t)K);
-            mo[isl] = cobj[bi[isl]];
-            mf[isl] = cfit[bi[isl]];
-        }
-        for (int32_t isl = 0; isl < nisl; isl++) {
-            int32_t src = (isl + nisl - 1) % nisl, w = wi[isl];
-            memcpy(cY + (size_t)w * K, mY + (size_t)src * K, sizeof(int16_t) * (size_t)K);
-            memcpy(cX + (size_t)w * K, mX + (size_t)src * K, (size_t)K);
-            cobj[w] = mo[src];
-            cfit[w] = mf[src];
-        }
-        free(bi); free(wi); free(mY); free(mX); free(mo); free(mf);
-    }
+    if (par->migrate_every > 0 && gen % par->migrate_every == 0 && nisl > 1)
+        orc_migrate(K, I, nisl, cY, cX, cobj, cfit);
 
     memcpy(st->Y, cY, sizeof(int16_t) * (size_t)P * K);
     memcpy(st->X, cX, (size_t)P * K);

@@ -108,6 +108,47 @@ def test_worked_example_topological_reading():
     check_invariants(inst, r["S"], r["M"], obj=r["obj"], tard=r["tard"], cmax=r["cmax"])
 
 
+def _ops(order, gj, gs):
+    return [(int(gj[k]), int(gs[k])) for k in order]
+
+
+def test_worked_example_topological_order_itself():
+    """The Z order of the topological reading on the Sec. 4.3 example, worked by hand.
+
+    Free ops and their y (printed Y): (2,1)4 (2,2)2 | (3,1)10 (3,2)6 | (4,2)12 | (5,1)9
+    (5,2)3 | (6,0)8 (6,1)13 (6,2)11 | (7,0)1 (7,1)5 (7,2)7.  Taking, each time, the ready job
+    head with the largest y:
+      heads 4,10,12,9,8,1  -> (4,2);   heads 4,10,9,8,1 -> (3,1);   heads 4,6,9,8,1 -> (5,1);
+      heads 4,6,3,8,1      -> (6,0);   heads 4,6,3,13,1 -> (6,1);   heads 4,6,3,11,1 -> (6,2);
+      heads 4,6,3,1        -> (3,2);   heads 4,3,1      -> (2,1);   heads 2,3,1      -> (5,2);
+      heads 2,1            -> (2,2);   then (7,0), (7,1), (7,2).
+    The printed Z agrees at positions 1-3 and 8-13 (nine of 13).  It lists (3,2) fourth, before
+    the ready head (6,0) with the larger y, which no y rule gives; with (3,2) set aside the
+    two orders are the same sequence.
+    """
+    ex, inst = _worked_example()
+    y, x, given, gj, gs = _example_genes(ex, inst)
+    got = _ops(inst.order(y, ORDER_TOPO), gj, gs)
+    want = [(4, 2), (3, 1), (5, 1), (6, 0), (6, 1), (6, 2), (3, 2), (2, 1), (5, 2), (2, 2), (7, 0), (7, 1), (7, 2)]
+    assert got == want
+    printed = _ops(inst.order(y, ORDER_GIVEN, given=given), gj, gs)
+    Z = ex["Z_printed"]
+    assert [Z[j][s] for j, s in printed] == list(range(1, 14))  # ORDER_GIVEN is the printed Z
+    agree = [n + 1 for n in range(13) if got[n] == printed[n]]
+    assert agree == [1, 2, 3, 8, 9, 10, 11, 12, 13]
+    assert [op for op in got if op != (3, 2)] == [op for op in printed if op != (3, 2)]
+
+
+def test_worked_example_stage_order_itself():
+    """The stage-by-stage order on the Sec. 4.3 example, by hand: stage 0 by y descending is
+    (6,0)8, (7,0)1; stage 1 is (6,1)13, (3,1)10, (5,1)9, (7,1)5, (2,1)4; stage 2 is (4,2)12,
+    (6,2)11, (7,2)7, (3,2)6, (5,2)3, (2,2)2."""
+    ex, inst = _worked_example()
+    y, x, given, gj, gs = _example_genes(ex, inst)
+    assert _ops(inst.order(y, ORDER_STAGE), gj, gs) == [
+        (6, 0), (7, 0), (6, 1), (3, 1), (5, 1), (7, 1), (2, 1), (4, 2), (6, 2), (7, 2), (3, 2), (5, 2), (2, 2)]
+
+
 # ------------------------------------------------------------------ objective
 
 @pytest.mark.parametrize("wt,tard,cmax,obj", [
@@ -355,6 +396,142 @@ def test_mutation_never_keeps_machine():
         assert (xm != x).all()
         seen.add(tuple(xm.tolist()))
     assert len(seen) == 4
+
+
+# ------------------------------------------------------------------ selection, replacement, migration
+
+def test_tournament_ties_to_lower_index():
+    """Sec. 4.4 selection: the entrant with the larger fitness wins; equal fitness goes to
+    the lower population index, whatever the entrants' order.  With fit = [5, 7, 7, 3, 7]:
+    k=2 {2,1} -> 1 (7 = 7, 1 < 2); {0,3} -> 0 (5 > 3); {4,4} -> 4; k=3 {4,2,0} -> 2;
+    {3,3,0} -> 0; {1,3,4} -> 1; all-equal fitness {3,1,2} -> 1."""
+    fit = [5, 7, 7, 3, 7]
+    assert oracle.tournament(fit, [2, 1]) == 1
+    assert oracle.tournament(fit, [1, 2]) == 1
+    assert oracle.tournament(fit, [0, 3]) == 0
+    assert oracle.tournament(fit, [4, 4]) == 4
+    assert oracle.tournament(fit, [4, 2, 0]) == 2
+    assert oracle.tournament(fit, [3, 3, 0]) == 0
+    assert oracle.tournament(fit, [1, 3, 4]) == 1
+    assert oracle.tournament([9, 9, 9, 9], [3, 1, 2]) == 1
+
+
+def test_l5_torus_cells():
+    """The 5-cell neighbourhood (Sec. 4.4, Fig. 9) on the 4 x 4 torus, cells row-major
+    (r = i // 4, c = i % 4), listed as the cell, N, S, W, E:
+      cell 0  (0,0): N (3,0)=12, S (1,0)=4,  W (0,3)=3,  E (0,1)=1
+      cell 6  (1,2): N (0,2)=2,  S (2,2)=10, W (1,1)=5,  E (1,3)=7
+      cell 7  (1,3): N (0,3)=3,  S (2,3)=11, W (1,2)=6,  E (1,0)=4
+      cell 15 (3,3): N (2,3)=11, S (0,3)=3,  W (3,2)=14, E (3,0)=12
+    and on the 3 x 3 torus the centre cell 4: 1, 7, 3, 5."""
+    assert oracle.l5_cells(16, 0) == [0, 12, 4, 3, 1]
+    assert oracle.l5_cells(16, 6) == [6, 2, 10, 5, 7]
+    assert oracle.l5_cells(16, 7) == [7, 3, 11, 6, 4]
+    assert oracle.l5_cells(16, 15) == [15, 11, 3, 14, 12]
+    assert oracle.l5_cells(9, 4) == [4, 1, 7, 3, 5]
+
+
+def test_select_l5_picks_the_fittest_neighbour():
+    """With tournament size 0 the parent of a slot is the fittest of its five cells: on the
+    4 x 4 torus, slot 6 with fitness 50 at cell 7 (its E neighbour) and 40 elsewhere in the
+    neighbourhood takes 7; slot 0 with equal fitness at 12 (N) and 1 (E) takes 1; cell 9,
+    outside slot 6's neighbourhood, never wins it."""
+    fit = np.full(16, 40, np.int64)
+    fit[7], fit[9] = 50, 99
+    assert oracle.select(fit, 16, 16, 0, 1, 0, 1, 6) == 7
+    fit = np.zeros(16, np.int64)
+    fit[12] = fit[1] = 8
+    assert oracle.select(fit, 16, 16, 0, 1, 0, 1, 0) == 1
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_select_tournament_draws(k):
+    """Entrant t of slot i is island start + floor(u_t * I / 2^32), u_t = draw t of slot i's
+    selection stream (purpose 3; the stream itself is pinned above).  Islands of 8 in a
+    population of 32: with equal fitness the winner is the smallest entrant; with distinct
+    fitness (larger for larger index) the largest; entrants never leave the slot's island."""
+    P, I, seed, gen = 32, 8, 77, 5
+    flat = np.zeros(P, np.int64)
+    rising = np.arange(P, dtype=np.int64)
+    for i in range(P):
+        lo = (i // I) * I
+        ent = [lo + (oracle.draw(seed, 3, 2, gen, i, t) * I >> 32) for t in range(k)]
+        assert all(lo <= e < lo + I for e in ent)
+        assert oracle.select(flat, P, I, k, seed, 2, gen, i) == min(ent)
+        assert oracle.select(rising, P, I, k, seed, 2, gen, i) == max(ent)
+
+
+def _marked_rows(n, K):
+    """Row r holds y = [10 r + 1, 10 r + 2, ...] and x = [r, r, ...], so every copy is traceable."""
+    Y = np.array([[10 * r + 1 + c for c in range(K)] for r in range(n)], np.int16)
+    X = np.array([[r] * K for r in range(n)], np.int8)
+    return Y, X
+
+
+def test_island_replace_strict_improvement():
+    """Elitist replacement (Sec. 4.4) of the second island (slots 4..7) of two, K = 3.
+    Children's fitness 10, 30, 30, 5 (slots 4-7), objectives 90, 70, 70, 95; record fitness 20.
+    The best child is slot 5 (30; slot 6 ties and loses on index), strictly fitter than 20,
+    so the record becomes slot 5's row (y 51 52 53, obj 70, fit 30); then the record
+    overwrites the worst child, slot 7 (fitness 5).  Island 0 is untouched."""
+    Y, X = _marked_rows(8, 3)
+    obj = np.array([1, 2, 3, 4, 90, 70, 70, 95], np.int64)
+    fit = np.array([9, 9, 9, 9, 10, 30, 30, 5], np.int64)
+    bY, bX = np.array([7, 7, 7], np.int16), np.array([1, 1, 1], np.int8)
+    cY, cX, cobj, cfit, nbY, nbX, bo, bf = oracle.island_replace(Y, X, obj, fit, 4, 4, bY, bX, 80, 20)
+    assert (bo, bf) == (70, 30) and nbY.tolist() == [51, 52, 53] and nbX.tolist() == [5, 5, 5]
+    assert cY[7].tolist() == [51, 52, 53] and cX[7].tolist() == [5, 5, 5]
+    assert cobj[7] == 70 and cfit[7] == 30
+    assert np.array_equal(cY[:7], Y[:7]) and np.array_equal(cobj[:7], obj[:7]) and np.array_equal(cfit[:7], fit[:7])
+
+
+def test_island_replace_tie_keeps_record_and_worst_tie_lowest():
+    """Same island; the record has fitness 30 and the best child only equals it, so the
+    record stays (y 7 7 7, obj 80).  Children's fitness 10, 5, 30, 5: the worst is slot 5
+    (5; slot 7 ties and loses on index), and it takes the record."""
+    Y, X = _marked_rows(8, 3)
+    obj = np.array([1, 2, 3, 4, 90, 95, 70, 95], np.int64)
+    fit = np.array([9, 9, 9, 9, 10, 5, 30, 5], np.int64)
+    bY, bX = np.array([7, 7, 7], np.int16), np.array([1, 1, 1], np.int8)
+    cY, cX, cobj, cfit, nbY, nbX, bo, bf = oracle.island_replace(Y, X, obj, fit, 4, 4, bY, bX, 80, 30)
+    assert (bo, bf) == (80, 30) and nbY.tolist() == [7, 7, 7]
+    assert cY[5].tolist() == [7, 7, 7] and cX[5].tolist() == [1, 1, 1] and cobj[5] == 80 and cfit[5] == 30
+    assert cY[7].tolist() == Y[7].tolist() and cfit[7] == 5
+
+
+def test_migrate_ring_from_snapshot():
+    """Single-ring migration (Sec. 4.4) over three islands of two, K = 2, rows marked by slot.
+    Fitness 3 3 | 8 2 | 5 9: bests are slots 0, 2, 5 and worsts 0, 3, 4 (island 0 ties: slot
+    0 is both).  Island i's worst takes island i-1's best as it was before any copy:
+      slot 0 <- slot 5 (y 51 52, obj 105, fit 9);  slot 3 <- slot 0 (y 1 2, obj 100, fit 3);
+      slot 4 <- slot 2 (y 21 22, obj 102, fit 8).
+    Copying in place, island 1 would have received slot 5's row through slot 0, and a ring
+    turning the other way would put slot 2's row into slot 0."""
+    Y, X = _marked_rows(6, 2)
+    obj = np.arange(100, 106, dtype=np.int64)
+    fit = np.array([3, 3, 8, 2, 5, 9], np.int64)
+    cY, cX, cobj, cfit = oracle.migrate(Y, X, obj, fit, 2)
+    assert cY.tolist() == [[51, 52], [11, 12], [21, 22], [1, 2], [21, 22], [51, 52]]
+    assert cX[:, 0].tolist() == [5, 1, 2, 0, 2, 5]
+    assert cobj.tolist() == [105, 101, 102, 100, 102, 105]
+    assert cfit.tolist() == [9, 3, 8, 3, 8, 9]
+
+
+def test_ga_migrants_are_post_replacement_bests():
+    """Operator order of a generation: replacement, then migration.  After replacement each
+    island's fittest member is its best-ever record (fitness bfit); migration then copies it
+    into the next island.  So after every migration generation island i holds a member with
+    fitness bfit[i-1]; migrating before replacement would move only the best child, whose
+    fitness falls short of the record in most generations."""
+    prob = wl.static_small(4)
+    ga = oracle.GA(oracle.Instance(prob), P=64, island=8, tour_k=2, migrate_every=1, seed=9).init()
+    nisl = 8
+    for _ in range(25):
+        ga.step()
+        for i in range(nisl):
+            members = ga.fit[8 * i:8 * i + 8]
+            assert ga.bfit[(i - 1) % nisl] in members, (ga.gen, i)
+            assert members.max() >= ga.bfit[i]
 
 
 # ------------------------------------------------------------------ GA properties
