@@ -274,6 +274,15 @@ int ffs_surrogate_gradients(ffs_surrogate *sur, const int16_t *y, const int64_t 
  * *loss (before the step) if not NULL. */
 int ffs_surrogate_train(ffs_surrogate *sur, const int16_t *y, const int64_t *obj, int32_t count, float lr,
                         float *loss);
+/* For verification (not in the paper): copies to host the first `rows` rows of the
+ * surrogate's last forward pass over its own batch -- the one made by ffs_surrogate_predict
+ * (with count <= max_batch), ffs_surrogate_gradients or ffs_surrogate_train: the stored
+ * hidden activations h1, h2 host [rows][256] as BF16 bit patterns, the outputs host [rows]
+ * FP32 and, after a gradient or training call, the normalised targets t host [rows] FP32.
+ * Any pointer may be NULL.  rows <= the batch rows (FFS_E_ARG beyond); synchronises. */
+int ffs_surrogate_read_activations(ffs_surrogate *sur, int32_t rows, uint16_t *h1, uint16_t *h2, float *out,
+                                   float *t);
+
 /* Surrogate-assisted generations for a population of the same instance: each generation
  * builds `oversample` candidates per slot with the Sec. 4.4 operators and scores them all.
  * A slot whose first candidate is a parent's plain copy keeps it, as a plain generation
@@ -292,21 +301,24 @@ int ga_population_attach_surrogate(ga_population *pop, ffs_surrogate *sur, int32
 int ffs_surrogate_pretrain(ffs_surrogate *sur, ga_population *pop, int32_t steps, float lr, float *loss);
 
 /* Allocation-free variant of ffs_decode, for callers that cannot allocate device memory:
- * code that runs while a CUDA stream is being captured (cudaMalloc is not permitted
- * there), hosts that fix the process's device memory at start-up, and real-time loops
- * that must not wait on the allocator.  The paper has no counterpart; it is a deployment
- * aid.  Arguments and results are those of ffs_decode.  It allocates nothing: its scratch
- * (error word, instance tables, per-warp power profiles) is one 16 MiB device array
- * inside the library, reserved on every GPU that loads it until the process exits.
+ * hosts that fix the process's device memory at start-up and hand each library a budget
+ * it may not grow, frameworks whose own caching allocator owns the device memory, and
+ * real-time loops that must not wait on the allocator (cudaMalloc can block, and
+ * cudaFree synchronises the whole device).  The paper has no counterpart; it is a
+ * deployment aid.  Arguments and results are those of ffs_decode; the caller still
+ * provides the chromosomes and the output arrays.  It allocates nothing: its scratch (error
+ * word, instance tables, per-warp power profiles) is one 16 MiB device array inside the
+ * library, reserved on every GPU that loads it until the process exits.
  *   - Limits: instance tables up to 1 MiB, and 4 warps' profiles (4 * 2 bytes per slot of
  *     ffs_info.horizon) within the remaining ~15 MiB; beyond them it returns FFS_E_ARG
  *     and ffs_last_error() explains.  ffs_decode has no such limit.
  *   - The first call on each device looks up the array's device address; make that
  *     first call before any stream capture begins.
- *   - Every call shares the one array: calls whose work overlaps on the GPU (other
- *     streams, other threads) race and must be serialised by the caller.
- *   - Synchronous: returns after `stream` has finished, with FFS_E_DEVICE if a row was
- *     not a permutation of 1..K. */
+ *   - Every call shares the one array, which keeps the last call's contents (the error
+ *     word is cleared at each call): calls whose work overlaps on the GPU (other streams,
+ *     other threads) race and must be serialised by the caller.
+ *   - Synchronous: copies the tables from host memory, waits for `stream` to finish and
+ *     returns FFS_E_DEVICE if a row was not a permutation of 1..K. */
 int ffs_decode_noalloc(ffs_instance *inst, int32_t order_mode, int32_t machine_mode,
                        const int16_t *y, const int8_t *x, int32_t count,
                        int64_t *obj, int64_t *tard, int32_t *cmax, void *stream);
@@ -477,6 +489,23 @@ int ffs_service_wait(ffs_service *svc, int64_t ticket, int32_t timeout_ms, ffs_r
 int ffs_service_forget(ffs_service *svc, ffs_instance *inst);
 
 int ffs_service_stats_read(ffs_service *svc, ffs_service_stats *stats);
+
+/* Failure injection, for tests of the library's bounded device waits (not in the paper;
+ * not for production use).  Process-wide; mode is an or of:
+ *   FFS_INJECT_TABLE_COPY  every later ffs_decode launch skips the copy of the instance
+ *                          tables into shared memory, so each CTA's bounded wait for them
+ *                          runs out (a short limit: no copy is in flight), the CTA records
+ *                          a timeout and returns, and ffs_decode_check reports
+ *                          FFS_E_TIMEOUT;
+ *   FFS_INJECT_GEMM_LOADS  every later ffs_tensor_gemm launch issues no operand loads, so
+ *                          the tensor-core issuer's bounded wait runs out (short limit, no
+ *                          copy in flight), the CTA frees its tensor memory and the call
+ *                          reports FFS_E_TIMEOUT.
+ * FFS_INJECT_NONE restores normal operation.  FFS_E_ARG for unknown bits. */
+#define FFS_INJECT_NONE        0
+#define FFS_INJECT_TABLE_COPY  1
+#define FFS_INJECT_GEMM_LOADS  2
+int ffs_debug_inject(int32_t mode);
 
 /* Number of kernels this library has launched in the process so far (graph replays count
  * each kernel node).  For benchmark accounting. */

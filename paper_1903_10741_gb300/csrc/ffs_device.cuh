@@ -64,18 +64,24 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// Iterations of the bounded wait for the instance tables.
+constexpr int kStageWaitIters = 1 << 22;
+
 // Copies the instance blob (16-byte aligned, size a multiple of 16) into shared memory
 // with cp.async.bulk completing on an mbarrier.  Every thread waits with an iteration
-// limit; on timeout the error word gets kErrTimeout and false is returned.
+// limit; on timeout the error word gets kErrTimeout and false is returned.  With `skip`
+// (failure injection for tests) nothing is copied and nothing arrives, so the wait runs
+// out with no copy in flight.
 __device__ __forceinline__ bool stage_tables(char *dst, const char *src, int bytes,
-                                             uint64_t *mbar, int32_t *err) {
+                                             uint64_t *mbar, int32_t *err, bool skip = false,
+                                             int iters = kStageWaitIters) {
     const uint32_t bar = smem_u32(mbar);
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !skip) {
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                      : "memory");
         constexpr int kChunk = 16384;
@@ -89,7 +95,7 @@ __device__ __forceinline__ bool stage_tables(char *dst, const char *src, int byt
         }
     }
     bool done = false;
-    for (int it = 0; it < (1 << 22) && !done; ++it) {
+    for (int it = 0; it < iters && !done; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

@@ -39,7 +39,9 @@ template <int ORDER, int MACH, bool GPROF>
 __global__ void __maxnreg__(128) k_decode(DecodeArgs a) {
     extern __shared__ __align__(128) char smem[];
     char *tab = smem + 128;
-    if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
+    if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err, a.inject_skip != 0,
+                      a.wait_iters > 0 ? a.wait_iters : kStageWaitIters))
+        return;
     const Tabs T = tabs_view(tab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const WarpPtrs w = warp_ptrs(tab, a.blob_bytes, T, a.Hcap, false, GPROF, a.gscratch, warp, mach_insert(MACH));

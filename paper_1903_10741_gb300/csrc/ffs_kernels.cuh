@@ -32,6 +32,9 @@ struct DecodeArgs {
     int32_t *over_list;         // shared-profile variant: chromosomes that overflowed
     int32_t *over_count;
     int32_t *err;
+    // failure injection for tests: skip the table copy and wait only this many iterations
+    // (0: the default limit); no copy is then in flight when the wait runs out
+    int inject_skip, wait_iters;
 };
 
 struct GenArgs {

@@ -21,6 +21,7 @@
 #include "ffs_internal.h"
 #include "ffs_kernels.cuh"
 #include "ffs_layout.h"
+#include "ffs_mlp.cuh"
 
 using namespace edffs;
 using namespace ffs_rt;
@@ -254,6 +255,10 @@ int check_modes(int32_t order_mode, int32_t machine_mode) {
     return FFS_OK;
 }
 
+// Failure injection for tests (ffs_debug_inject): decode launches skip the table copy.
+std::atomic<int> g_inject_table_copy{0};
+constexpr int kInjectWaitIters = 1 << 12;
+
 int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y, const int8_t *x,
                 int32_t count, int64_t *obj, int64_t *tard, int32_t *cmax, int32_t *S, int32_t *Mo,
                 cudaStream_t st) {
@@ -279,6 +284,10 @@ int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y,
     a.M0 = in->d_M0;
     a.status = in->d_status;
     a.err = in->d_err;
+    if (g_inject_table_copy.load()) {
+        a.inject_skip = 1;
+        a.wait_iters = kInjectWaitIters;
+    }
     const int slots = smem_slots(h, false, ins);
     const int sms = num_sms();
     const NoArena plain;  // per-instance buffers outlive any service arena
@@ -1105,6 +1114,13 @@ int ga_profile_read(ga_population *pp, double *kernel_ms, int64_t *launches) {
 
 const char *ffs_last_error(void) { return g_last_error; }
 
+int ffs_debug_inject(int32_t mode) {
+    if (mode & ~(FFS_INJECT_TABLE_COPY | FFS_INJECT_GEMM_LOADS)) return FFS_E_ARG;
+    g_inject_table_copy.store((mode & FFS_INJECT_TABLE_COPY) ? 1 : 0);
+    mlp_gemm_inject_skip_loads((mode & FFS_INJECT_GEMM_LOADS) != 0);
+    return FFS_OK;
+}
+
 int ffs_kernel_launches(uint64_t *count) {
     if (!count) return FFS_E_ARG;
     *count = g_launches.load();
@@ -1197,10 +1213,10 @@ int ga_restore(ga_population *pp, const void *buf, size_t len) {
 
 // ====================================================================== allocation-free decode
 //
-// Some callers cannot allocate device memory: code running inside a CUDA stream capture,
-// where cudaMalloc is not permitted; hosts that hand the library a fixed memory budget and
-// forbid growth after start-up; and real-time loops that must not block on the
-// allocator.  ffs_decode_noalloc serves them.  It runs the global-profile decode kernel
+// Some callers cannot allocate device memory: hosts that hand the library a fixed memory
+// budget and forbid growth after start-up, frameworks whose own caching allocator owns the
+// device memory, and real-time loops that must not block on the allocator (cudaMalloc can
+// block; cudaFree synchronises the device).  ffs_decode_noalloc serves them.  It runs the global-profile decode kernel
 // with every piece of scratch it needs placed in one file-scope device array, so it
 // allocates nothing.
 //

@@ -278,6 +278,19 @@ int ffs_surrogate_train(ffs_surrogate *s, const int16_t *y, const int64_t *obj, 
     return FFS_OK;
 }
 
+int ffs_surrogate_read_activations(ffs_surrogate *s, int32_t rows, uint16_t *h1, uint16_t *h2, float *out,
+                                   float *t) {
+    if (!s || rows < 0 || rows > s->rows_cap) return FFS_E_ARG;
+    FFS_CUDA(cudaStreamSynchronize(s->st));
+    FFS_TRY(ffs_rt::surrogate_status());
+    const size_t n = (size_t)rows * s->H;
+    if (h1) FFS_CUDA(cudaMemcpy(h1, s->H1, 2 * n, cudaMemcpyDeviceToHost));
+    if (h2) FFS_CUDA(cudaMemcpy(h2, s->H2, 2 * n, cudaMemcpyDeviceToHost));
+    if (out) FFS_CUDA(cudaMemcpy(out, s->out, 4 * (size_t)rows, cudaMemcpyDeviceToHost));
+    if (t) FFS_CUDA(cudaMemcpy(t, s->t, 4 * (size_t)rows, cudaMemcpyDeviceToHost));
+    return FFS_OK;
+}
+
 int ffs_tensor_gemm(const void *A, const void *B, int32_t M, int32_t N, int32_t K, const float *bias, void *C,
                     int32_t relu_bf16, int32_t synchronous, void *stream) {
     if (!A || !B || !C || (relu_bf16 && !bias)) return FFS_E_ARG;

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "ffs_device.cuh"
@@ -34,6 +35,10 @@ constexpr int kStages = 4;
 constexpr int kThreads = 128;
 constexpr int kABytes = kTM * kTK * 2;
 constexpr int kWaitIters = 1 << 24;
+// Failure injection for tests: operand loads skipped, and this short wait limit (nothing
+// is then in flight when a wait runs out).
+constexpr int kInjectWaitIters = 1 << 12;
+std::atomic<int> g_inject_skip_loads{0};
 
 __device__ int32_t g_gemm_err;  // sticky kErrTimeout from any GEMM launch
 
@@ -45,8 +50,8 @@ struct Smem {
     static constexpr int kBytes = 1024 + kRing + 8 * (2 * kStages + 1) + 16;
 };
 
-__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < kWaitIters; ++it) {
+__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity, int iters) {
+    for (int it = 0; it < iters; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -98,7 +103,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     k_umma(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, int K, void *C, int ldc,
-           const float *__restrict__ bias) {
+           const float *__restrict__ bias, int skip_loads, int iters) {
     using L = Smem<BN>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -137,9 +142,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
             int kb = 0;
-            for (; kb < nk; ++kb) {
+            for (; kb < nk && !skip_loads; ++kb) {
                 const int s = kb % kStages;
-                if (kb >= kStages && !wait_parity(empty0 + 8 * s, ((kb / kStages) & 1) ^ 1)) {
+                if (kb >= kStages && !wait_parity(empty0 + 8 * s, ((kb / kStages) & 1) ^ 1, iters)) {
                     ctr[0] = 1;
                     break;
                 }
@@ -160,7 +165,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int kb = 0;
             for (; kb < nk; ++kb) {
                 const int s = kb % kStages;
-                if (!wait_parity(full0 + 8 * s, (kb / kStages) & 1)) {
+                if (!wait_parity(full0 + 8 * s, (kb / kStages) & 1, iters)) {
                     ctr[0] = 1;
                     break;
                 }
@@ -189,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     }
 
-    const bool ok = wait_parity(done, 0) && !ctr[0];
+    const bool ok = wait_parity(done, 0, iters) && !ctr[0];
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (__all_sync(kFull, ok)) {
         const int row = m0 + 32 * warp + lane;
@@ -226,7 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (threadIdx.x == 0 && (!ok || ctr[0])) {
         atomicOr(&g_gemm_err, kErrTimeout);
         // copies issued but never consumed may still be landing: wait for them (bounded)
-        for (int kb = ctr[2]; kb < ctr[1]; ++kb) wait_parity(full0 + 8 * (kb % kStages), (kb / kStages) & 1);
+        for (int kb = ctr[2]; kb < ctr[1]; ++kb) wait_parity(full0 + 8 * (kb % kStages), (kb / kStages) & 1, iters);
     }
     __syncthreads();
     if (warp == 0) {
@@ -277,7 +282,9 @@ cudaError_t launch(const CUtensorMap &a, const CUtensorMap &b, int M, int N, int
         attr = cudaFuncSetAttribute(k_umma<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<BN>::kBytes);
     });
     if (attr != cudaSuccess) return attr;
-    k_umma<BN, EPI><<<dim3(N / BN, M / kTM), kThreads, Smem<BN>::kBytes, st>>>(a, b, K, C, ldc, bias);
+    const int skip = g_inject_skip_loads.load();
+    k_umma<BN, EPI><<<dim3(N / BN, M / kTM), kThreads, Smem<BN>::kBytes, st>>>(a, b, K, C, ldc, bias, skip,
+                                                                               skip ? kInjectWaitIters : kWaitIters);
     return cudaGetLastError();
 }
 
@@ -300,6 +307,8 @@ cudaError_t mlp_gemm(int epi, const __nv_bfloat16 *A, const __nv_bfloat16 *B, in
     return epi == kEpiF32 ? launch<128, kEpiF32>(ma, mb, M, N, K, C, ldc, bias, st)
                           : launch<128, kEpiBiasReluBf16>(ma, mb, M, N, K, C, ldc, bias, st);
 }
+
+void mlp_gemm_inject_skip_loads(bool on) { g_inject_skip_loads.store(on ? 1 : 0); }
 
 int32_t mlp_gemm_take_error() {
     int32_t e = 0;

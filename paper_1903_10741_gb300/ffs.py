@@ -19,6 +19,8 @@ ORDER_TOPO, ORDER_STAGE = 0, 1
 MACH_GENE, MACH_EARLIEST = 0, 1
 PLACE_INSERT = 4  # or-ed into a machine mode: idle-gap insertion placement
 ST_FREE, ST_EXEC, ST_DONE, ST_FIXED = 0, 1, 2, 3
+E_TIMEOUT = -5
+INJECT_NONE, INJECT_TABLE_COPY, INJECT_GEMM_LOADS = 0, 1, 2  # ffs_debug_inject (tests only)
 
 _i32p = C.POINTER(C.c_int32)
 _lib = None
@@ -139,6 +141,9 @@ _SIGS = {
     "ffs_surrogate_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ffs_surrogate_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "ffs_surrogate_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p]),
+    "ffs_debug_inject": (C.c_int, [C.c_int32]),
+    "ffs_surrogate_read_activations": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                                 C.c_void_p]),
     "ga_population_attach_surrogate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_int32, C.c_int32]),
     "ffs_surrogate_pretrain": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p]),
     "ga_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(GAParams_c), C.POINTER(C.c_void_p)]),
@@ -153,6 +158,11 @@ _SIGS = {
     "ga_set_profiling": (C.c_int, [C.c_void_p, C.c_int32]),
     "ga_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
+
+
+def debug_inject(mode: int):
+    """Failure injection for tests of the bounded device waits (``ffs_debug_inject``)."""
+    _check(lib().ffs_debug_inject(int(mode)), "ffs_debug_inject")
 
 
 def kernel_launches() -> int:
@@ -304,8 +314,9 @@ class Instance:
     def decode_noalloc(self, y, x=None, order_mode=ORDER_STAGE, mach_mode=MACH_EARLIEST, stream=None):
         """Decodes like ``decode`` through ``ffs_decode_noalloc``: the library uses only its
         fixed internal device scratch, never allocating, for callers that cannot allocate
-        (for instance while a CUDA graph is being captured).  The output tensors are
-        allocated here, by the caller's side.  Synchronous."""
+        (a fixed device-memory budget, a framework allocator that owns the memory, loops
+        that must not wait on the allocator).  The output tensors are allocated here, on
+        the caller's side.  Synchronous."""
         import torch
         count = int(y.shape[0]) if y.dim() == 2 else 1
         obj = torch.empty(count, dtype=torch.int64, device=y.device)
@@ -585,6 +596,20 @@ class Surrogate:
         _check(lib().ffs_surrogate_train(self._h, _dptr(y), _dptr(obj), int(y.shape[0]), float(lr),
                                          C.addressof(loss)), "ffs_surrogate_train")
         return float(loss.value)
+
+    def activations(self, rows: int) -> dict:
+        """Stored activations of the last forward pass over the surrogate's own batch: h1, h2
+        [rows, 256] (BF16 values as float64), out and t [rows] (float64)."""
+        h1 = np.zeros((rows, self.H), np.uint16)
+        h2 = np.zeros((rows, self.H), np.uint16)
+        out = np.zeros(rows, np.float32)
+        t = np.zeros(rows, np.float32)
+        _check(lib().ffs_surrogate_read_activations(self._h, int(rows), h1.ctypes.data, h2.ctypes.data,
+                                                    out.ctypes.data, t.ctypes.data), "ffs_surrogate_read_activations")
+
+        def widen(b):
+            return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        return dict(h1=widen(h1), h2=widen(h2), out=out.astype(np.float64), t=t.astype(np.float64))
 
 
 class Service:

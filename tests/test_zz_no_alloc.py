@@ -1,15 +1,17 @@
 """The allocation-free decode entry point, ffs_decode_noalloc.
 
-It exists for callers that may not allocate device memory (inside a CUDA graph capture,
-under a fixed up-front memory budget, in loops that must not wait on the allocator); it
-keeps all of its scratch in one fixed device array inside the library.  Its results must
-equal ffs_decode's exactly (integer arithmetic), call after call, since every call reuses
-the same array.  This file is collected last so that a failure here cannot stop the other
-GPU tests from running first.
+It exists for callers that may not allocate device memory (a fixed device-memory budget
+set at start-up, a framework allocator that owns the memory, loops that must not wait on
+the allocator); it keeps all of its scratch in one fixed device array inside the library.
+Its results must equal the oracle's and ffs_decode's exactly (integer arithmetic), call
+after call, since every call reuses the same array; and after its first call on a device
+it must not change the device's free memory.  This file is collected last so that a
+failure here cannot stop the other GPU tests from running first.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1903_10741_gb300 import ffs
 from paper_1903_10741_gb300 import workloads as wl
 
@@ -32,6 +34,7 @@ def test_noalloc_matches_decode_twice(mode):
     torch = _torch()
     dyn = wl.dynamic_medium(2)
     inst = ffs.Instance(dyn.problem)
+    orc = oracle.Instance(dyn.problem)
     rng = np.random.default_rng(17)
     gj, gs = inst.genes()
     machines = dyn.problem.o[gs]
@@ -45,11 +48,17 @@ def test_noalloc_matches_decode_twice(mode):
         _same(want, got)
         got_again = inst.decode_noalloc(y, x, *mode)  # the array keeps the last call's data
         _same(want, got_again)
+        for i in range(0, 257, 16):  # a sample of rows against the oracle itself
+            r = orc.decode(Y[i], X[i], *mode)
+            assert (int(got["obj"][i]), int(got["tard"][i]), int(got["cmax"][i])) == (r["obj"], r["tard"], r["cmax"])
         if call == 0:
             out = inst.decode(y[:1], x[:1] if x is not None else None, *mode, schedule=True)
-            inst.commit(out["S"][0].cpu().numpy(), out["M"][0].cpu().numpy())
+            S, M = out["S"][0].cpu().numpy(), out["M"][0].cpu().numpy()
+            inst.commit(S, M)
+            orc.commit(S, M)
             t_now, arr = dyn.events[0]
             inst.reschedule(arr, t_now)
+            orc.reschedule(arr, t_now)
             gj, gs = inst.genes()
             machines = dyn.problem.o[gs]
     assert (inst.status() == ffs.ST_EXEC).any()
@@ -67,3 +76,35 @@ def test_noalloc_rejects_oversized_instance():
         inst.decode_noalloc(y)
     assert e.value.code == -1
     assert "limit" in ffs.lib().ffs_last_error().decode()
+
+
+def test_noalloc_leaves_device_memory_unchanged():
+    """After the first call on the device (which looks up the array's address), further
+    calls into preallocated outputs leave the device's free memory exactly as it was."""
+    torch = _torch()
+    import ctypes as C
+    dyn = wl.dynamic_medium(3)
+    inst = ffs.Instance(dyn.problem)
+    rng = np.random.default_rng(5)
+    Y, _ = wl.random_chromosomes(rng, 300, inst.K, dyn.problem.o[inst.genes()[1]])
+    y = torch.from_numpy(Y).cuda()
+    want = inst.decode(y)
+    obj = torch.empty(300, dtype=torch.int64, device="cuda")
+    tard = torch.empty(300, dtype=torch.int64, device="cuda")
+    cmax = torch.empty(300, dtype=torch.int32, device="cuda")
+    L = ffs.lib()
+
+    def call():
+        rc = L.ffs_decode_noalloc(inst.handle, ffs.ORDER_STAGE, ffs.MACH_EARLIEST, C.c_void_p(y.data_ptr()), None,
+                                  300, C.c_void_p(obj.data_ptr()), C.c_void_p(tard.data_ptr()),
+                                  C.c_void_p(cmax.data_ptr()), None)
+        assert rc == 0, rc
+
+    call()
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        call()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    _same(want, {"obj": obj, "tard": tard, "cmax": cmax})
