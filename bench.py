@@ -40,17 +40,26 @@ WORKLOAD = ("dynamic rescheduling, plain GA: 50 initial jobs, 5 stages x U{2..4}
             "p U{1..99}, q U{5..30} kW, peak 55% of all-on power; events at t=100,250,400 adding 10 jobs "
             "(due = arrival + U[1.2,2.0] x work); complete reschedule at each event; population 1024 "
             "(16 islands of 64), tournament 2, pc 0.8, pm 0.1, migration every 10; 500 generations per solve")
-# Algorithmic work of one exact decode on this job: per-instant power checks (Eq. 7) over
-# every machine of the op's stage plus profile updates (Eq. 8), averaged by the oracle over
-# its own GA trajectory of this job (python -m oracle.work_per_decode --generations 500
-# --every 50: 53232 / 62226 / 68630 / 75374 for the four solves, mean 64865).
+# Algorithmic work of one exact decode on this job (python -m oracle.work_per_decode
+# --generations 500 --every 50, the oracle's own GA trajectory of this job): per-instant
+# power checks (Eq. 7) over every machine of the op's stage plus profile updates (Eq. 8),
+# 53232 / 62226 / 68630 / 75374 for the four solves, mean 64865.5; and the stage-by-stage
+# sort, sum over stages of n_s ceil(log2 n_s) compares: 1500 / 1710 / 2126 / 2409, mean 1936.25.
 SLOTS_PER_DECODE = 64865.5
+SORT_PER_DECODE = 1936.25
 # DRAM bytes (read + write) of one generation-kernel launch from the ncu capture of the
 # current kernel (dram__bytes_read.sum + dram__bytes_write.sum, initial solve); None once
 # the kernel changes until it is captured again.
-TRAFFIC_BYTES = 423680
-# INT32 issue ceiling: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz (lane-ops/s).
-ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+TRAFFIC_BYTES = None
+
+
+def work_per_decode() -> float:
+    return SLOTS_PER_DECODE + SORT_PER_DECODE
+
+
+def alu_peak_tops(sms: int, mhz: float) -> float:
+    """INT32 issue ceiling: SMs x 4 schedulers x 32 lanes x clock, in 10^12 lane-ops/s."""
+    return sms * 128 * mhz * 1e6 / 1e12
 
 
 def _env_int(name, default):
@@ -137,15 +146,17 @@ def input_bytes(dyn) -> int:
     return b
 
 
-def run_job(ffs, inst, dyn, generations: int, stream, profile: bool, out_stats: dict):
-    """Initial solve + one solve per event on `inst`; returns exact decodes performed."""
+def run_job(ffs, inst, dyn, generations: int, stream, profile, out_stats: dict):
+    """Initial solve + one solve per event on `inst`; returns exact decodes performed.
+    profile: 0 untimed graph replays, 1 eager launches with the fused kernel timed, 2 graph
+    replays each timed (see ga_set_profiling)."""
     decodes = 0
     d2h = 0
     for solve in range(len(dyn.events) + 1):
         pop = ffs.Population(inst, P=P, island=ISLAND, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE,
                              seed=SEED, instance_id=solve, stream=stream)
         if profile:
-            pop.set_profiling(True)
+            pop.set_profiling(int(profile))
         res = pop.run(generations)
         if profile:
             ms, n = pop.profile()
@@ -160,10 +171,6 @@ def run_job(ffs, inst, dyn, generations: int, stream, profile: bool, out_stats: 
             inst.reschedule(arr, t_now)
     out_stats["d2h"] = d2h
     return decodes
-
-
-def slots_per_decode() -> float:
-    return SLOTS_PER_DECODE
 
 
 # ----------------------------------------------------------------------------- ours
@@ -217,19 +224,25 @@ def bench_ours(args):
         dist.barrier()
     tot_decodes, max_s = aggregate(dist if world > 1 else None, float(decodes), total_ms / 1e3, dev)
 
-    # Roofline pass: the same job again, each generation launched directly with a CUDA event
-    # pair around the fused generation kernel on the population's stream.
-    prof, prof_ms, prof_dec = {}, 0.0, 0
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        inst = ffs.Instance(dyn.problem)
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record(stream)
-        prof_dec += run_job(ffs, inst, dyn, G, stream, True, prof)
-        e.record(stream)
-        e.synchronize()
-        prof_ms += s.elapsed_time(e)
-        inst.close()
+    # Roofline passes: the same job again, (a) in the timed run's own launch mode -- graph
+    # replays of 8 chained generations, each replay bracketed by CUDA events on the
+    # population's stream -- and (b) with every generation launched directly and the fused
+    # kernel alone bracketed (no overlap between generations).
+    def timed_pass(mode, jobs):
+        st_, ms_, dec_ = {}, 0.0, 0
+        for k in range(jobs):
+            flush.fill_(float(k))
+            inst = ffs.Instance(dyn.problem)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            dec_ += run_job(ffs, inst, dyn, G, stream, mode, st_)
+            e.record(stream)
+            e.synchronize()
+            ms_ += s.elapsed_time(e)
+            inst.close()
+        return st_, ms_, dec_
+    prof, prof_ms, prof_dec = timed_pass(2, args.steps)
+    eager, eager_ms, eager_dec = timed_pass(1, min(args.steps, 3))
 
     # end to end through the public API: host arrays in, host schedules out, per step
     e2e_s, e2e_dec, e2e_stats = 0.0, 0, {}
@@ -244,8 +257,12 @@ def bench_ours(args):
         inst.close()
     e2e_tot, e2e_max = aggregate(dist if world > 1 else None, float(e2e_dec), e2e_s, dev)
 
-    avg_launch_s = prof["kernel_ms"] / prof["kernel_launches"] / 1e3
-    achieved = slots_per_decode() * P / avg_launch_s / 1e12
+    avg_launch_s = prof["kernel_ms"] / prof["kernel_launches"] / 1e3   # per generation, graph mode
+    eager_launch_s = eager["kernel_ms"] / eager["kernel_launches"] / 1e3
+    achieved = work_per_decode() * P / avg_launch_s / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    alu_peak = alu_peak_tops(sms, mhz)
     line = {
         "metric": METRIC, "value": tot_decodes / max_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
@@ -256,18 +273,29 @@ def bench_ours(args):
                    "wall_s": t_wall, "best_objectives_last_step": stats["best_obj"][-(len(dyn.events) + 1):],
                    "launch": "eager" if args.eager else ("captured CUDA graphs of 8 generations, each generation launched as a "
                                                          "programmatic dependent of the one before"),
-                   "profiled_pass_value": prof_dec / (prof_ms / 1e3)},
+                   "profiled_pass_value": prof_dec / (prof_ms / 1e3),
+                   "eager_pass_value": eager_dec / (eager_ms / 1e3)},
         "e2e": {"value": e2e_tot / e2e_max, "unit": UNIT, "h2d_bytes_per_step": input_bytes(dyn),
                 "d2h_bytes_per_step": e2e_stats["d2h"]},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "fused selection/crossover/mutation/decode generation kernel",
-                     "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s", "frac": achieved / ALU_PEAK_TOPS,
+                     "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
+                     "peak_basis": f"{sms} SMs x 4 schedulers x 32 INT32 lanes x {mhz:.0f} MHz (median sampled SM "
+                                   "clock in the timed region), derived",
                      "traffic": TRAFFIC_BYTES, "avg_launch_us": avg_launch_s * 1e6,
-                     "timing": f"CUDA events around each of {prof['kernel_launches']} launches in a profiled pass of "
-                               f"{args.steps} jobs",
-                     "work_per_launch": f"{slots_per_decode():.0f} slot checks/decode x {P} decodes"},
+                     "timing": f"CUDA events around each graph replay (8 chained generations, the timed run's launch "
+                               f"mode) in a pass of {args.steps} jobs: {prof['kernel_launches']} generations",
+                     "eager_kernel_us": eager_launch_s * 1e6,
+                     "eager_timing": f"CUDA events around the fused kernel alone, each generation launched directly, "
+                                     f"{eager['kernel_launches']} launches",
+                     "work_per_launch": f"{work_per_decode():.0f} INT32 ops/decode ({SLOTS_PER_DECODE:.0f} power-slot "
+                                        f"checks and updates + {SORT_PER_DECODE:.0f} sort compares) x {P} decodes"},
         "clocks": clk,
     }
+    if rank == 0 and not args.no_tto:
+        # the metric's second half: time-to-objective of the surrogate-assisted GA against
+        # the plain GA on the surrogate workload (200 jobs x 8 stages, population 4096)
+        line["time_to_objective"] = time_to_objective(ffs, torch, stream)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         if args.cpu_all_cores:
@@ -342,6 +370,8 @@ def bench_batched(args):
     decodes = count * 512 * G * args.steps
     kinfo = [i.info() for i in insts]
     avg_launch_s = total_ms / args.steps / 1e3
+    alu_peak = alu_peak_tops(torch.cuda.get_device_properties(local).multi_processor_count,
+                             clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0)
     achieved = BATCH_SLOTS_PER_DECODE * count * 512 * G / avg_launch_s / 1e12 if BATCH_SLOTS_PER_DECODE else None
     line = {
         "metric": METRIC, "value": decodes / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -353,8 +383,8 @@ def bench_batched(args):
                    "l2": "flushed between steps (256 MiB write)"},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "kernel": "persistent batched GA kernel", "achieved": achieved,
-                     "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                     "frac": achieved / ALU_PEAK_TOPS if achieved else None, "traffic": None,
+                     "peak": alu_peak, "unit": "Tops/s",
+                     "frac": achieved / alu_peak if achieved else None, "traffic": None,
                      "avg_launch_us": avg_launch_s * 1e6,
                      "work_per_launch": f"{BATCH_SLOTS_PER_DECODE} slot checks/decode x {count * 512 * G} decodes"},
         "clocks": clk,
@@ -364,10 +394,112 @@ def bench_batched(args):
 
 # ----------------------------------------------------------------------------- surrogate
 SUR_WORKLOAD = ("surrogate-assisted GA: 200 jobs, 8 stages, machines U{2..6}, p U{1..99}, q U{5..50} kW, peak 50%; "
-                "population 4096 (islands of 64); the plain GA runs G generations, the surrogate GA over-generates F "
-                "candidates per slot, scores them with the BF16 MLP (256-256-1); a screened offspring slot keeps its "
-                "best-scored offspring, the others the plain child; kept children are decoded exactly and train the "
-                "model online; time until its best total tardiness is within 0.5% of the plain GA's final value")
+                "population 4096 (64 islands of 64), tournament 2, pc 0.8, pm 0.1, migration every 10; the plain GA "
+                "runs 1000 generations and its final best total tardiness is the target; each surrogate arm "
+                "over-generates F candidates per slot, scores them with the BF16 MLP (256-256-1, trained online by Adam "
+                "on the kept children's exact decodes) and decodes exactly only the kept ones; time-to-objective = wall "
+                "seconds until the arm's best total tardiness is within 0.5% of the target (checked every 20 generations)")
+# Surrogate arms: the configuration as stated (8x over-generation, the top 12.5% of each island's
+# pool decoded exactly), the same rule with parent copies kept at the plain GA's rate and only
+# offspring ranked, the best per-slot screening found earlier, and -- as a diagnostic, not a
+# surrogate -- the stated rule ranked by exact objectives (every candidate decoded), which
+# bounds what the rule itself can give.  cap: generations as a multiple of the plain run's.
+SUR_ARMS = {
+    "island_top_12.5pct_of_8x": dict(oversample=8, keep=1, screen=1.0, train_steps=1, lr=1e-3, pretrain_steps=50,
+                                     cap=1.0),
+    "island_top_offspring_12.5pct_of_8x": dict(oversample=8, keep=2, screen=1.0, train_steps=1, lr=1e-3,
+                                               pretrain_steps=50, cap=1.0),
+    "slot_screen_F2_p0.5": dict(oversample=2, keep=0, screen=0.5, train_steps=2, lr=1e-3, pretrain_steps=50, cap=2.0),
+    "diagnostic_exact_scores_island_top_12.5pct_of_8x": dict(oversample=8, keep=1, screen=1.0, train_steps=0, lr=1e-3,
+                                                             pretrain_steps=0, cap=1.0, exact=True),
+}
+
+
+def time_to_objective(ffs, torch, stream, G=1000, chunk=20, cap_factor=2.0, arms=None, profile_gens=20):
+    """Plain GA vs surrogate-assisted arms on the surrogate workload: the plain GA's final
+    best total tardiness after G generations is the target; each arm's wall time and
+    generations until its best is within 0.5 % of it; both at equal generation counts; and
+    the per-generation time split of each arm (profiled eager pass of profile_gens)."""
+    arms = SUR_ARMS if arms is None else arms
+    prob = wl.surrogate_large(1)
+    Ps = 4096
+    kw = dict(P=Ps, island=64, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE, seed=SEED, stream=stream)
+    ffs.Population(ffs.Instance(prob), **kw).run(2, want_schedule=False)  # kernels loaded, limits set
+
+    def run_arm(arm, cap, target):
+        inst = ffs.Instance(prob)
+        pop = ffs.Population(inst, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if arm is not None:
+            sur = ffs.Surrogate(inst, max_batch=Ps, seed=SEED)
+            if arm.get("exact"):
+                sur.score_exactly(True)
+            pop.attach_surrogate(sur, oversample=arm["oversample"], lr=arm["lr"], train_steps=arm["train_steps"],
+                                 screen=arm["screen"], pretrain_steps=arm["pretrain_steps"], keep=arm["keep"])
+        curve, reached = [], None
+        for g in range(0, cap, chunk):
+            n = min(chunk, cap - g)
+            r = pop.run(n, want_schedule=False)
+            el = time.perf_counter() - t0
+            curve.append((g + n, round(el, 4), r["tard"], r["obj"]))
+            if target is not None and reached is None and r["tard"] <= target * 1.005:
+                reached = (g + n, el)
+                break
+        return curve, reached
+
+    def split(arm, gens):
+        inst = ffs.Instance(prob)
+        pop = ffs.Population(inst, **kw)
+        if arm is not None:
+            sur = ffs.Surrogate(inst, max_batch=Ps, seed=SEED)
+            if arm.get("exact"):
+                sur.score_exactly(True)
+            pop.attach_surrogate(sur, oversample=arm["oversample"], lr=arm["lr"], train_steps=arm["train_steps"],
+                                 screen=arm["screen"], pretrain_steps=0, keep=arm["keep"])
+        pop.set_profiling(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pop.run(gens, want_schedule=False)
+        wall = (time.perf_counter() - t0) / gens * 1e3
+        if arm is None:
+            ms, n = pop.profile()
+            return {"exact_decode": ms / n, "wall_ms_per_generation": wall}
+        ph = pop.profile_phases()
+        out = {k: v / gens for k, v in ph.items()}
+        out["wall_ms_per_generation"] = wall
+        return out
+
+    plain, _ = run_arm(None, G, None)
+    target = plain[-1][2]
+    plain_hit = next(c for c in plain if c[2] <= target * 1.005)
+    rec = {"workload": SUR_WORKLOAD, "target_total_tardiness": target, "tolerance": 0.005,
+           "plain": {"generations": G, "wall_s": plain[-1][1], "generations_to_target": plain_hit[0],
+                     "time_to_target_s": plain_hit[1], "final_objective": plain[-1][3],
+                     "ms_per_generation": plain[-1][1] / G * 1e3, "curve": plain[::5]}}
+    plain_at = {c[0]: c[2] for c in plain}
+    best = None
+    for name, arm in arms.items():
+        curve, reached = run_arm(arm, int(arm.get("cap", cap_factor) * G), target)
+        same = [(c[0], c[2], plain_at[c[0]]) for c in curve if c[0] in plain_at]
+        rec[name] = {"config": arm, "reached": reached is not None,
+                     "generations_to_target": reached[0] if reached else None,
+                     "time_to_target_s": reached[1] if reached else None,
+                     "generations_run": curve[-1][0], "wall_s": curve[-1][1],
+                     "ms_per_generation": curve[-1][1] / curve[-1][0] * 1e3,
+                     "speedup_vs_plain_time_to_target": (plain_hit[1] / reached[1]) if reached else None,
+                     "tardiness_at_equal_generations": same[::5] + ([same[-1]] if same else []),
+                     "curve": curve[::5]}
+        if reached and not arm.get("exact") and (best is None or reached[1] < rec[best]["time_to_target_s"]):
+            best = name
+    if profile_gens:
+        rec["time_split_ms_per_generation"] = {"plain": split(None, profile_gens)}
+        for name, arm in arms.items():
+            rec["time_split_ms_per_generation"][name] = split(arm, profile_gens)
+    rec["target_met_by"] = [n for n in arms if rec[n]["reached"] and rec[n]["time_to_target_s"] < plain_hit[1]
+                            and not arms[n].get("exact")]
+    rec["fastest_surrogate_arm"] = best
+    return rec
 
 
 def bench_surrogate(args):
@@ -377,62 +509,20 @@ def bench_surrogate(args):
 
     torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
     stream = torch.cuda.current_stream()
-    prob = wl.surrogate_large(1)
-    G, P, chunk = args.generations, 4096, args.chunk
-    kw = dict(P=P, island=64, tour_k=TOUR_K, pc=PC, pm=PM, migrate_every=MIGRATE, seed=SEED, stream=stream)
-
-    def plain_run():
-        inst = ffs.Instance(prob)
-        pop = ffs.Population(inst, **kw)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        curve = []
-        for g in range(0, G, chunk):
-            r = pop.run(min(chunk, G - g), want_schedule=False)
-            curve.append((g + min(chunk, G - g), time.perf_counter() - t0, r["tard"], r["obj"]))
-        return curve
-
-    def surrogate_run(target_tard, cap):
-        inst = ffs.Instance(prob)
-        pop = ffs.Population(inst, **kw)
-        sur = ffs.Surrogate(inst, max_batch=P, seed=SEED)
-        pop.attach_surrogate(sur, oversample=args.oversample, lr=args.lr, train_steps=args.train_steps, screen=args.screen,
-                             pretrain_steps=args.pretrain_steps)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        curve, reached = [], None
-        for g in range(0, cap, chunk):
-            r = pop.run(min(chunk, cap - g), want_schedule=False)
-            el = time.perf_counter() - t0
-            curve.append((g + min(chunk, cap - g), el, r["tard"], r["obj"]))
-            if reached is None and r["tard"] <= target_tard * 1.005:
-                reached = (g + min(chunk, cap - g), el)
-                break
-        return curve, reached
-
-    for _ in range(args.warmup):  # compile paths, caches
-        inst = ffs.Instance(prob)
-        ffs.Population(inst, **kw).run(2, want_schedule=False)
-    plain = plain_run()
-    target = plain[-1][2]
-    sur_curve, reached = surrogate_run(target, args.surrogate_cap or 2 * G)
-    # the plain GA's own time to the same target (first chunk at or below it)
-    plain_to_target = next((c for c in plain if c[2] <= target * 1.005), plain[-1])
+    G = args.generations
+    arms = SUR_ARMS
+    if args.sur_arm:  # a single arm given on the command line
+        arms = {"custom": dict(oversample=args.oversample, keep=args.keep, screen=args.screen,
+                               train_steps=args.train_steps, lr=args.lr, pretrain_steps=args.pretrain_steps)}
+    rec = time_to_objective(ffs, torch, stream, G=G, chunk=args.chunk,
+                            cap_factor=(args.surrogate_cap / G) if args.surrogate_cap else 2.0, arms=arms)
+    fastest = rec["fastest_surrogate_arm"]
     line = {
         "metric": "time-to-objective, surrogate vs plain GA", "unit": "s", "higher_is_better": False,
-        "value": reached[1] if reached else None, "n_gpus": 1, "dtype": "int32 decode / bf16 surrogate",
-        "data": "synthetic",
-        "config": {"workload": SUR_WORKLOAD, "generations_plain": G, "chunk": chunk, "lr": args.lr,
-                   "oversample": args.oversample, "screen": args.screen,
-                   "train_steps_per_generation": args.train_steps, "pretrain_steps": args.pretrain_steps,
-                   "target_total_tardiness": target, "plain_final_objective": plain[-1][3],
-                   "plain_time_s": plain[-1][1], "plain_time_to_target_s": plain_to_target[1],
-                   "plain_generations_to_target": plain_to_target[0],
-                   "surrogate_generations_to_target": reached[0] if reached else None,
-                   "speedup_vs_plain_full_run": (plain[-1][1] / reached[1]) if reached else None,
-                   "plain_decodes_per_s": P * G / plain[-1][1],
-                   "plain_curve": plain[:: max(1, len(plain) // 12)],
-                   "surrogate_curve": sur_curve[:: max(1, len(sur_curve) // 12)]},
+        "value": rec[fastest]["time_to_target_s"] if fastest else None, "n_gpus": 1,
+        "dtype": "int32 decode / bf16 surrogate", "data": "synthetic",
+        "config": {"workload": SUR_WORKLOAD, "generations_plain": G, "chunk": args.chunk},
+        "time_to_objective": rec,
     }
     print(json.dumps(line), flush=True)
 
@@ -833,6 +923,11 @@ def main():
     ap.add_argument("--oversample", type=int, default=2, help="surrogate candidates per population slot")
     ap.add_argument("--screen", type=float, default=0.5, help="fraction of offspring slots that take the surrogate's pick")
     ap.add_argument("--pretrain-steps", type=int, default=50, help="surrogate Adam steps on generation 0")
+    ap.add_argument("--keep", type=int, default=0, help="surrogate keep rule: 0 per-slot screening, 1 island top")
+    ap.add_argument("--sur-arm", action="store_true",
+                    help="surrogate workload: run only the arm given by --oversample/--keep/--screen/...")
+    ap.add_argument("--no-tto", action="store_true",
+                    help="default workload: skip the time-to-objective record of the surrogate workload")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--tune-generations", type=int, default=3)
     ap.add_argument("--batch-mapping", default="",

@@ -295,6 +295,38 @@ int ffs_surrogate_read_activations(ffs_surrogate *sur, int32_t rows, uint16_t *h
 int ga_population_attach_surrogate(ga_population *pop, ffs_surrogate *sur, int32_t oversample, float lr,
                                    int32_t train_steps, int32_t screen_permille);
 
+/* Keep rule of surrogate-assisted generations (after ga_population_attach_surrogate):
+ *   FFS_KEEP_SLOT    (default) per-slot screening as described above;
+ *   FFS_KEEP_ISLAND  each island ranks all oversample x island candidates of its slots by
+ *                    the surrogate's score (ties to the lower candidate row, an undefined
+ *                    score last) and keeps the best `island` of them, 1/oversample of the
+ *                    pool -- with oversample 8 the top 12.5 % -- in candidate-row order,
+ *                    one per slot; screen_permille is then unused.  Ranking within each
+ *                    island keeps one island's candidates from crowding out another's.
+ *   FFS_KEEP_ISLAND_OFFSPRING  as FFS_KEEP_ISLAND, except that a slot whose first candidate
+ *                    is a parent's plain copy keeps that copy (the plain GA's copy rate) and
+ *                    only offspring (crossover or mutation applied) compete for the island's
+ *                    other places.
+ * Island rules require oversample x island <= 4096 (FFS_E_ARG otherwise).  With a constant
+ * score they keep every slot's first candidate, which is the plain generation's child. */
+#define FFS_KEEP_SLOT    0
+#define FFS_KEEP_ISLAND  1
+#define FFS_KEEP_ISLAND_OFFSPRING  2
+int ga_population_surrogate_keep(ga_population *pop, int32_t rule);
+
+/* Diagnostic (not in the paper): with on != 0 the surrogate scores candidates by their exact
+ * objectives (every candidate decoded) instead of the network -- a perfect model, to
+ * measure what a keep rule itself gives.  Such generations are launched directly rather
+ * than replayed from a graph; training still runs as configured. */
+int ffs_surrogate_score_exactly(ffs_surrogate *sur, int32_t on);
+
+/* For verification (not in the paper): host copies of the last surrogate-assisted
+ * generation's candidates -- Y, X [P * oversample][K] (row f P + j is candidate f of slot
+ * j), their scores [P * oversample] -- and, under an island rule, the row kept for each
+ * slot, keep [P].  Any pointer may be NULL.  FFS_E_ARG without an attached surrogate or
+ * before the first such generation's buffers exist; synchronises. */
+int ga_population_read_candidates(ga_population *pop, int16_t *Y, int8_t *X, float *score, int32_t *keep);
+
 /* `steps` Adam steps on the population's current members and their exact objectives (for
  * example generation 0, before surrogate-assisted generations begin); host *loss after
  * the last step's forward pass if not NULL. */
@@ -380,15 +412,26 @@ int ga_checkpoint(ga_population *pop, void *buf, size_t *len);
  * population was created. */
 int ga_restore(ga_population *pop, const void *buf, size_t len);
 
-/* Switches ga_run between replaying the captured generation graph (enable = 0, default)
- * and launching each generation's kernels directly with a CUDA event pair on the
- * population's stream around the fused selection/crossover/mutation/decode kernel, whose
- * durations are summed.  Results are identical in both modes.  Resets the sums. */
+/* Measurement modes of ga_run.  enable = 0 (default): replays of the captured generation
+ * graphs, untimed.  enable = 1: each generation's kernels are launched directly, with a
+ * CUDA event pair on the population's stream around the fused
+ * selection/crossover/mutation/decode kernel, whose durations are summed.  enable = 2: the
+ * same graph replays as mode 0 (chains of 8 generations, each launched as a programmatic
+ * dependent of the one before), each replay bracketed by an event pair; the summed
+ * durations cover the generations in the launch mode ga_run normally uses.  Results are
+ * identical in every mode.  Resets the sums; FFS_E_ARG for other values. */
 int ga_set_profiling(ga_population *pop, int32_t enable);
 
-/* Summed duration (milliseconds) and launch count of the fused generation kernel measured
- * since profiling was enabled. */
+/* Summed duration (milliseconds) and number of generations measured since profiling was
+ * enabled (mode 1: of the fused generation kernel's launches; mode 2: of the graph replays). */
 int ga_profile_read(ga_population *pop, double *kernel_ms, int64_t *launches);
+
+/* Summed durations (milliseconds) of the phases of surrogate-assisted generations run in
+ * profiling mode since it was enabled: ms[0] over-generation of the candidates, ms[1]
+ * scoring by the surrogate, ms[2] the keep rule (island ranking; 0 for per-slot screening,
+ * which runs inside the next phase), ms[3] selection of the kept children, exact decoding
+ * and replacement, ms[4] training. */
+int ga_profile_read_phases(ga_population *pop, double *ms);
 
 /* The surrogate's dense contraction, exposed for verification (not in the paper):
  * C = A . B^T with A [M][K] and B [N][K] row-major BF16 device matrices, accumulated in

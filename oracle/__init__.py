@@ -101,6 +101,9 @@ def lib():
                                  C.c_int32]
         L.orc_island_replace.argtypes = [C.c_int32, C.c_int32, C.c_int32] + [C.c_void_p] * 8
         L.orc_migrate.argtypes = [C.c_int32, C.c_int32, C.c_int32] + [C.c_void_p] * 4
+        L.orc_candidates.restype = C.c_int32
+        L.orc_candidates.argtypes = [C.POINTER(_Inst), C.POINTER(_GAParams), C.POINTER(_GAState), C.c_int32,
+                                     C.c_void_p, C.c_void_p, C.c_void_p]
         L.orc_ga_init.restype = C.c_int32
         L.orc_ga_init.argtypes = [C.POINTER(_Inst), C.POINTER(_GAParams), C.POINTER(_GAState)]
         L.orc_ga_init_from.restype = C.c_int32
@@ -410,6 +413,18 @@ class GA:
             if rc:
                 raise RuntimeError(f"oracle GA step failed ({rc})")
         return self
+
+    def candidates(self, F: int):
+        """The P*F offspring the next generation would build, F per slot (row f P + j is
+        candidate f of slot j; F = 1 gives the children of `step`), and whether crossover or
+        mutation changed each row."""
+        P, K = self.Y.shape[0], self.K
+        cY = np.zeros((P * F, max(K, 1)), np.int16)
+        cX = np.zeros((P * F, max(K, 1)), np.int8)
+        cnew = np.zeros(P * F, np.uint8)
+        lib().orc_candidates(C.byref(self._ic()), C.byref(self.par), C.byref(self.st), int(F), cY.ctypes.data,
+                             cX.ctypes.data, cnew.ctypes.data)
+        return cY[:, :K], cX[:, :K], cnew
 
     @property
     def gen(self):

@@ -596,26 +596,33 @@ void orc_l5_cells(int32_t P, int32_t i, int32_t out[5])
     out[4] = r * side + (c + 1) % side;
 }
 
-/* Parent of population slot i at generation gen: with tour_k > 0 the winner of k entrants
- * drawn uniformly from the slot's island (entrant t = island start + floor(u_t * I / 2^32),
- * u_t = draw t of the selection stream of slot i); with tour_k = 0 the winner of the
- * slot's 5-cell torus neighbourhood. */
-int32_t orc_select(const int64_t *fit, int32_t P, int32_t I, int32_t tour_k, uint64_t seed,
-                   int32_t iid, int32_t gen, int32_t i)
+/* Parent drawn with the selection stream of row `v` from the island (or torus
+ * neighbourhood) of population slot `home`: with tour_k > 0 the winner of k entrants drawn
+ * uniformly from the island (entrant t = island start + floor(u_t * I / 2^32), u_t = draw t
+ * of row v's selection stream); with tour_k = 0 the winner of the 5-cell neighbourhood. */
+static int32_t select_parent(const int64_t *fit, int32_t P, int32_t I, int32_t tour_k, uint64_t seed,
+                             int32_t iid, int32_t gen, int32_t v, int32_t home)
 {
     int32_t cand[64];
     int32_t n;
     if (tour_k > 0) {
-        int32_t lo = (i / I) * I;
+        int32_t lo = (home / I) * I;
         n = tour_k < 64 ? tour_k : 64;
         for (int32_t t = 0; t < n; t++)
-            cand[t] = lo + (int32_t)below(orc_draw(seed, P_SELECT, (uint32_t)iid, (uint32_t)gen, (uint32_t)i,
+            cand[t] = lo + (int32_t)below(orc_draw(seed, P_SELECT, (uint32_t)iid, (uint32_t)gen, (uint32_t)v,
                                                    (uint32_t)t), (uint32_t)I);
     } else {
-        orc_l5_cells(P, i, cand);
+        orc_l5_cells(P, home, cand);
         n = 5;
     }
     return orc_tournament(fit, cand, n);
+}
+
+/* Parent of population slot i at generation gen (Sec. 4.4 selection). */
+int32_t orc_select(const int64_t *fit, int32_t P, int32_t I, int32_t tour_k, uint64_t seed,
+                   int32_t iid, int32_t gen, int32_t i)
+{
+    return select_parent(fit, P, I, tour_k, seed, iid, gen, i, i);
 }
 
 /* Elitist replacement of one island (Sec. 4.4): the children cY/cX/cobj/cfit of slots
@@ -725,11 +732,18 @@ int32_t orc_ga_init(const orc_inst *in, const orc_ga_params *par, orc_ga_state *
     return orc_ga_init_from(in, par, st);
 }
 
-/* One generation (Sec. 4.4): selection -> paired crossover + correction -> mutation ->
- * decode -> elitist replacement per island -> ring migration every `migrate_every`. */
-int32_t orc_ga_step(const orc_inst *in, const orc_ga_params *par, orc_ga_state *st)
+/* The offspring of generation st->gen + 1 built from the population st with the Sec. 4.4
+ * operators, F per slot (F > 1: candidates of a surrogate-assisted generation, not in the
+ * paper): row v = f P + j is candidate f of slot j.  Row v's parent comes from slot j's
+ * island (or torus neighbourhood) with row v's selection stream; rows 2q and 2q+1 are the
+ * two children of pair q (crossover stream of pair q: head of the first parent, corrected
+ * tail of the second); row v is then mutated with its own mutation stream.  With F = 1 the
+ * rows are the children of orc_ga_step.  cnew (may be NULL) gets 1 for a row that
+ * crossover or mutation changed from a parent's copy. */
+int32_t orc_candidates(const orc_inst *in, const orc_ga_params *par, const orc_ga_state *st, int32_t F,
+                       int16_t *cY, int8_t *cX, uint8_t *cnew)
 {
-    const int32_t P = par->P, K = st->K, I = par->I, nisl = P / I;
+    const int32_t P = par->P, K = st->K, I = par->I, R = P * F;
     const int32_t gen = st->gen + 1;
     const uint64_t seed = par->seed;
     const int32_t iid = par->instance_id;
@@ -741,18 +755,14 @@ int32_t orc_ga_step(const orc_inst *in, const orc_ga_params *par, orc_ga_state *
     orc_gene_map(in, gjob, gstg);
     for (int32_t k = 0; k < K; k++) gene_o[k] = in->o[gstg[k]];
 
-    /* selection: one parent per slot */
-    int32_t *parent = (int32_t *)calloc((size_t)P, sizeof(int32_t));
-    for (int32_t i = 0; i < P; i++)
-        parent[i] = orc_select(st->fit, P, I, par->tour_k, seed, iid, gen, i);
+    /* selection: one parent per row */
+    int32_t *parent = (int32_t *)calloc((size_t)R, sizeof(int32_t));
+    for (int32_t v = 0; v < R; v++)
+        parent[v] = select_parent(st->fit, P, I, par->tour_k, seed, iid, gen, v, v % P);
 
-    /* crossover on neighbouring pairs, then mutation of each child */
-    int16_t *cY = (int16_t *)calloc((size_t)P * K + 1, sizeof(int16_t));
-    int8_t *cX = (int8_t *)calloc((size_t)P * K + 1, 1);
-    int64_t *cobj = (int64_t *)calloc((size_t)P, sizeof(int64_t));
-    int64_t *cfit = (int64_t *)calloc((size_t)P, sizeof(int64_t));
+    /* crossover on neighbouring pairs, then mutation of each row */
     uint32_t *xr = (uint32_t *)calloc((size_t)K + 1, sizeof(uint32_t));
-    for (int32_t pp = 0; pp < P / 2; pp++) {
+    for (int32_t pp = 0; pp < R / 2; pp++) {
         int32_t a = parent[2 * pp], b = parent[2 * pp + 1];
         int16_t *y0 = cY + (size_t)(2 * pp) * K, *y1 = cY + (size_t)(2 * pp + 1) * K;
         int8_t *x0 = cX + (size_t)(2 * pp) * K, *x1 = cX + (size_t)(2 * pp + 1) * K;
@@ -769,8 +779,9 @@ int32_t orc_ga_step(const orc_inst *in, const orc_ga_params *par, orc_ga_state *
             memcpy(x0, st->X + (size_t)a * K, (size_t)K);
             memcpy(x1, st->X + (size_t)b * K, (size_t)K);
         }
+        if (cnew) cnew[2 * pp] = cnew[2 * pp + 1] = (uint8_t)cross;
     }
-    for (int32_t i = 0; i < P; i++) {
+    for (int32_t i = 0; i < R; i++) {
         if (!chance(orc_draw(seed, P_MUTATE, iid, gen, i, 0), par->pm_num, par->pm_den))
             continue;
         int32_t ma = 0, mb = 0;
@@ -783,7 +794,25 @@ int32_t orc_ga_step(const orc_inst *in, const orc_ga_params *par, orc_ga_state *
             xr[k] = gene_o[k] >= 2
                 ? below(orc_draw(seed, P_MUTATE, iid, gen, i, 3 + k), (uint32_t)gene_o[k] - 1) : 0;
         orc_mutate(K, gene_o, cY + (size_t)i * K, gene_mode ? cX + (size_t)i * K : NULL, xr, ma, mb);
+        if (cnew) cnew[i] = 1;
     }
+    free(parent); free(xr); free(gstg); free(gjob); free(gene_o);
+    return 0;
+}
+
+/* One generation (Sec. 4.4): selection -> paired crossover + correction -> mutation ->
+ * decode -> elitist replacement per island -> ring migration every `migrate_every`. */
+int32_t orc_ga_step(const orc_inst *in, const orc_ga_params *par, orc_ga_state *st)
+{
+    const int32_t P = par->P, K = st->K, I = par->I, nisl = P / I;
+    const int32_t gen = st->gen + 1;
+
+    /* selection, crossover on neighbouring pairs, mutation */
+    int16_t *cY = (int16_t *)calloc((size_t)P * K + 1, sizeof(int16_t));
+    int8_t *cX = (int8_t *)calloc((size_t)P * K + 1, 1);
+    int64_t *cobj = (int64_t *)calloc((size_t)P, sizeof(int64_t));
+    int64_t *cfit = (int64_t *)calloc((size_t)P, sizeof(int64_t));
+    orc_candidates(in, par, st, 1, cY, cX, NULL);
 
     /* fitness of the children */
     int32_t rc = 0;
@@ -807,7 +836,6 @@ int32_t orc_ga_step(const orc_inst *in, const orc_ga_params *par, orc_ga_state *
     memcpy(st->fit, cfit, sizeof(int64_t) * (size_t)P);
     st->gen = gen;
 
-    free(parent); free(cY); free(cX); free(cobj); free(cfit); free(xr);
-    free(gstg); free(gjob); free(gene_o);
+    free(cY); free(cX); free(cobj); free(cfit);
     return rc;
 }

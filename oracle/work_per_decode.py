@@ -6,7 +6,9 @@ rescheduling events) in the oracle GA and, every `--every` generations, decodes 
 population to average the oracle's `slots` count: for every op, over every machine tried,
 (earliest feasible start - earliest availability + p), plus p for the profile update.
 That is the number of per-instant power checks (Eq. 7) and updates (Eq. 8) an exact
-evaluation performs.  Prints one JSON line.
+evaluation performs.  The stage-by-stage order adds a sort of each stage's free ops by
+priority: sum over stages of n_s * ceil(log2 n_s) comparisons (n_s free ops at stage s),
+a property of the instance at each rescheduling point.  Prints one JSON line.
 
     python -m oracle.work_per_decode --generations 500 --every 50
     python -m oracle.work_per_decode --workload batched --samples 8
@@ -75,15 +77,21 @@ def main():
                 ga.step()
         y, x, _ = ga.best()
         r = inst.decode(y, x)
+        _, gs = inst.gene_map()
+        n_s = np.bincount(gs, minlength=inst.g)
+        sort = int(sum(int(n) * int(np.ceil(np.log2(n))) for n in n_s if n > 1))
         per_solve.append(dict(K=ga.K, N=inst.N, rs=inst.RS, slots_mean=float(np.mean(samples)),
-                              slots_first=samples[0], slots_last=samples[-1], best_obj=r["obj"]))
+                              slots_first=samples[0], slots_last=samples[-1], sort_compares=sort,
+                              best_obj=r["obj"]))
         inst.commit(r["S"], r["M"])
         if solve < len(dyn.events):
             t_now, arr = dyn.events[solve]
             inst.reschedule(arr, t_now)
     mean = float(np.mean([p["slots_mean"] for p in per_solve]))
+    sort = float(np.mean([p["sort_compares"] for p in per_solve]))
     print(json.dumps(dict(workload="dynamic_medium(seed=1)", pop=a.pop, generations=a.generations,
-                          every=a.every, slots_per_decode=mean, per_solve=per_solve)))
+                          every=a.every, slots_per_decode=mean, sort_compares_per_decode=sort,
+                          work_per_decode=mean + sort, per_solve=per_solve)))
 
 
 if __name__ == "__main__":

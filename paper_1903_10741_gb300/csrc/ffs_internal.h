@@ -142,9 +142,14 @@ struct ga_population {
     int64_t *kept_obj = nullptr;
     int train_steps = 1;
     uint64_t screen_thr = (uint64_t)1 << 32;  // floor(screen probability * 2^32)
+    int keep_rule = 0;                      // FFS_KEEP_SLOT or FFS_KEEP_ISLAND
+    int32_t *cand_keep = nullptr;           // [P] kept candidate of each slot (island rule)
+    std::vector<cudaEvent_t> ev_sur;        // profiling: phase events of surrogate generations
+    double phase_ms[5] = {0, 0, 0, 0, 0};   // candidates, scoring, keep rule, exact decode, training
     cudaGraphExec_t graph_sur = nullptr;
     cudaGraphExec_t graph_r = nullptr;      // kGraphGens generations, each launched as the previous one drains
-    bool profiling = false;                 // eager launches with timed generation kernels
+    int profiling = 0;                      // 1: eager launches with timed generation kernels;
+                                            // 2: graph replays, each bracketed by events
     std::vector<cudaEvent_t> ev;            // event pairs, reused across ga_run calls
     double prof_ms = 0.0;
     int64_t prof_launches = 0;
@@ -162,6 +167,8 @@ struct ga_population {
         dfree(cand_out);
         dfree(cand_new);
         dfree(kept_obj);
+        dfree(cand_keep);
+        for (cudaEvent_t e : ev_sur) cudaEventDestroy(e);
         dfree(d_blob);
         for (int b = 0; b < 2; ++b) {
             dfree(Y[b]);
@@ -184,8 +191,10 @@ int sync_device(ffs_instance *in);
 int decode_impl(ffs_instance *in, int32_t order, int32_t mach, const int16_t *y, const int8_t *x, int32_t count,
                 int64_t *obj, int64_t *tard, int32_t *cmax, int32_t *S, int32_t *Mo, cudaStream_t st);
 void ga_gen_args(ga_population *pp, edffs::GenArgs *a);
-// Enqueues `generations` generations on the population's stream without waiting.
-int ga_enqueue(ga_population *pp, int32_t generations);
+// Enqueues `generations` generations on the population's stream without waiting.  In
+// profiling mode 2 each graph replay is bracketed by an event pair (pp->ev) and *timed
+// gets the number of pairs.
+int ga_enqueue(ga_population *pp, int32_t generations, int *timed = nullptr);
 // Waits for the population's stream, then decodes, commits and returns the best-ever schedule.
 int ga_finish(ga_population *pp, ffs_result *best);
 // Device bytes a population of `in` with `par` holds (each buffer rounded to kArenaAlign).
@@ -198,10 +207,16 @@ void population_trim(ga_population *pp);
 // One surrogate-assisted generation on `st` (ffs_surrogate.cu); with events, the fused
 // generation kernel is bracketed by ev0/ev1.  Kernels launched per generation:
 constexpr int kSurrogateFixedLaunches = 12, kSurrogateStepLaunches = 18;
+// ... plus one with the island keep rule.
+int surrogate_launches_per_generation(const ga_population *pp);
+// The attached surrogate scores candidates by their exact objectives (a diagnostic); such
+// generations are launched directly, not from a captured graph.
+bool surrogate_is_exact(const ga_population *pp);
 // FFS_E_TIMEOUT if a tensor-core GEMM recorded a wait timeout since the last call (and
 // clears it).  Synchronous.
 int surrogate_status();
-int surrogate_enqueue_generation(ga_population *pp, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
+int surrogate_enqueue_generation(ga_population *pp, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
+                                 cudaEvent_t *phase = nullptr);
 // Raises the shared-memory limits of the kernels a surrogate generation launches, so that
 // the generation can be captured.
 int prepare_surrogate_kernels(ga_population *pp);

@@ -200,6 +200,13 @@ __global__ void __maxnreg__(128) k_ga_generation(GenArgs a) {
     for (int i = blockIdx.x * kWarpsPerBlock + warp; i < a.P; i += gridDim.x * kWarpsPerBlock) {
         if (!a.cand_Y) {
             make_child<MACH>(T, w, src, i, gen, lane);
+        } else if (a.cand_keep) {  // island top rule: the candidate chosen for this slot
+            const size_t c = (size_t)__ldg(a.cand_keep + i);
+            for (int k = lane; k < K; k += 32) w.y[k] = a.cand_Y[c * K + k];
+            if (mach_gene(MACH))
+                for (int k = lane; k < K; k += 32) w.x[k] = a.cand_X[c * K + k];
+            for (int k = lane; k < a.Kpad; k += 32) a.kept_Yh[(size_t)i * a.Kpad + k] = a.cand_Yh[c * a.Kpad + k];
+            __syncwarp();
         } else {
             // surrogate-assisted: the slot's first candidate decides, as a plain generation
             // would, between a parent's plain copy (kept as it is) and an offspring; a
@@ -353,6 +360,86 @@ __global__ void __maxnreg__(128) k_candidates(GenArgs a) {
             for (int k = lane; k < K; k += 32) xo[k] = w.x[k];
         }
         stage_rank_row(w.y, K, a.Kpad, T.gstg, T.soff, T.g, w.inv, a.cand_Yh + (size_t)c * a.Kpad, lane);
+    }
+}
+
+// ---------------------------------------------------------------- surrogate: island top rule
+// One CTA per island: its n = F I candidate rows get 64-bit keys (score made orderable as
+// an unsigned integer, an undefined score ranking last | row), a bitonic sort in shared
+// memory puts the I best first, and a block-wide prefix over the kept flags in row order
+// gives each kept row its slot.  With is_new (offspring only), a slot whose first candidate
+// is a parent's plain copy keeps that copy (the plain GA's copy rate), other copies rank
+// last, and the offspring fill the remaining places by score.
+constexpr int kTopThreads = 1024;
+
+__device__ __forceinline__ uint32_t orderable(float f) {
+    if (isnan(f)) return 0xFFFFFFFFu;
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void __launch_bounds__(kTopThreads) k_island_top(const float *__restrict__ score,
+                                                             const uint8_t *__restrict__ is_new, int P, int F, int I,
+                                                             int32_t *__restrict__ keep) {
+    __shared__ unsigned long long key[kTopMax];
+    __shared__ uint8_t kept[kTopMax];
+    __shared__ int wsum[kTopThreads / 32];
+    const int lo = blockIdx.x * I, n = F * I;
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int l = threadIdx.x; l < m; l += blockDim.x) {  // local row l = f I + (j - lo)
+        if (l < n) {
+            const int f = l / I, j = lo + l % I;
+            const size_t row = (size_t)f * P + j;
+            unsigned hi = orderable(score[row]);
+            if (is_new && !is_new[row]) hi = f == 0 ? 0u : 0xFFFFFFFFu;  // a copy slot keeps its copy; other copies last
+            key[l] = ((unsigned long long)hi << 32) | (unsigned)l;
+        } else {
+            key[l] = ~0ull;  // padding sorts last
+        }
+        if (l < n) kept[l] = 0;
+    }
+    __syncthreads();
+    for (int size = 2; size <= m; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < m / 2; t += blockDim.x) {
+                const int a = 2 * t - (t & (stride - 1)), b = a + stride;
+                const bool up = (a & size) == 0;
+                const unsigned long long ka = key[a], kb = key[b];
+                if ((ka > kb) == up) {
+                    key[a] = kb;
+                    key[b] = ka;
+                }
+            }
+            __syncthreads();
+        }
+    for (int r = threadIdx.x; r < I; r += blockDim.x) kept[(int)(key[r] & 0xFFFFFFFFu)] = 1;
+    __syncthreads();
+    // slot of each kept row: the number of kept rows before it, in row order (chunks of
+    // blockDim rows, a warp-shuffle scan within each warp, then across warps)
+    int base = 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        const int l = c0 + threadIdx.x;
+        const int v = l < n ? kept[l] : 0;
+        int inc = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(kFull, inc, off);
+            if (lane >= off) inc += u;
+        }
+        if (lane == 31) wsum[wid] = inc;
+        __syncthreads();
+        int before = base;
+        for (int q = 0; q < wid; ++q) before += wsum[q];
+        if (v) {
+            const int f = l / I, j = lo + l % I;
+            keep[lo + before + inc - 1] = f * P + j;
+        }
+        int tot = 0;
+        for (int q = 0; q < nw; ++q) tot += wsum[q];
+        __syncthreads();
+        base += tot;
     }
 }
 
@@ -561,6 +648,13 @@ cudaError_t launch_warm_remap(const WarmArgs &a, cudaStream_t st) {
     if (a.Ko > kMaxK || a.K > kMaxK) return cudaErrorInvalidValue;
     const int grid = a.P < 1216 ? a.P : 1216;
     k_warm_remap<<<grid, kRemapThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_island_top(const float *score, const uint8_t *is_new, int P, int F, int I, int32_t *keep,
+                              cudaStream_t st) {
+    if (F < 1 || I < 1 || P % I || F * I > kTopMax) return cudaErrorInvalidValue;
+    k_island_top<<<P / I, kTopThreads, 0, st>>>(score, is_new, P, F, I, keep);
     return cudaGetLastError();
 }
 

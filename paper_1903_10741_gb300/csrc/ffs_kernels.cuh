@@ -78,6 +78,7 @@ struct GenArgs {
     uint16_t *kept_Yh;          // [P][Kpad] inputs of the kept candidates, for training
     int64_t *kept_obj;          // [P] their exact objectives (before replacement)
     uint64_t screen_thr;        // an offspring slot takes the model's pick iff its draw < this
+    const int32_t *cand_keep;   // [P] candidate kept for each slot (island top rule), or null
     int warm;                   // generation 0 decodes the rows already in Y[0] / X[0]
 };
 
@@ -167,6 +168,14 @@ cudaError_t prepare_ga_generation(int order, int mach, const TabHeader &h, int H
 cudaError_t launch_candidates(int mach, const GenArgs &a, const TabHeader &h, int grid, cudaStream_t st);
 cudaError_t prepare_candidates(int mach, const TabHeader &h);
 cudaError_t launch_warm_remap(const WarmArgs &a, cudaStream_t st);
+// Island top rule of surrogate screening: of the F * I candidates of each island (candidate
+// f of slot j is row f P + j), the I best-scored (lowest score, ties to the lower row; an
+// undefined score ranks last) are kept, and slot lo + r takes the r-th kept row in row
+// order.  With is_new (offspring only): slots whose first candidate is a parent's plain
+// copy keep it, and only offspring compete for the other places.  F * I <= kTopMax.
+constexpr int kTopMax = 4096;
+cudaError_t launch_island_top(const float *score, const uint8_t *is_new, int P, int F, int I, int32_t *keep,
+                              cudaStream_t st);
 cudaError_t launch_emax(const ReplArgs &a, cudaStream_t st);
 cudaError_t launch_replace(const ReplArgs &a, cudaStream_t st);
 

@@ -183,6 +183,11 @@ __global__ void k_adam(float *p, const float *g, float *m, float *v, size_t n, f
     p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
 }
 
+__global__ void k_obj_to_score(const int64_t *__restrict__ obj, int n, float *score) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) score[i] = (float)obj[i];
+}
+
 unsigned blocks(size_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -247,6 +252,11 @@ cudaError_t mlp_backward_hidden(const float *dh1, const __nv_bfloat16 *h1, int r
 cudaError_t mlp_grad_w1(const float *G, int Kpad, const float *ph, const float *dh, int H, int K, float *gW1,
                         cudaStream_t st) {
     k_grad_w1<<<blocks((size_t)H * K, 256), 256, 0, st>>>(G, Kpad, ph, dh, H, K, gW1);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_obj_to_score(const int64_t *obj, int n, float *score, cudaStream_t st) {
+    k_obj_to_score<<<blocks(n, 256), 256, 0, st>>>(obj, n, score);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,8 @@ cudaError_t mlp_gemm(int epi, const __nv_bfloat16 *A, const __nv_bfloat16 *B, in
 // Error bits (kErrTimeout) that GEMM launches recorded since the last call, and clears
 // them.  Synchronous.
 int32_t mlp_gemm_take_error();
+// score[i] = obj[i] as FP32 (exact scoring of candidates, a diagnostic).
+cudaError_t mlp_obj_to_score(const int64_t *obj, int n, float *score, cudaStream_t st);
 // Failure injection for tests: GEMM launches issue no operand loads (see ffs_debug_inject).
 void mlp_gemm_inject_skip_loads(bool on);
 cudaError_t mlp_rowdot(const __nv_bfloat16 *h2, const __nv_bfloat16 *w3, const float *b3, int rows, int H, float *out,

@@ -911,7 +911,7 @@ void ffs_rt::population_trim(ga_population *pp) {
     dfree(pp->r_obj); dfree(pp->r_tard); dfree(pp->r_cm); dfree(pp->r_S); dfree(pp->r_M);
     dfree(pp->r_over); dfree(pp->r_cnt);
     dfree(pp->cand_Y); dfree(pp->cand_X); dfree(pp->cand_Yh); dfree(pp->cand_H1); dfree(pp->cand_H2);
-    dfree(pp->cand_out); dfree(pp->cand_new); dfree(pp->kept_obj);
+    dfree(pp->cand_out); dfree(pp->cand_new); dfree(pp->kept_obj); dfree(pp->cand_keep);
     pp->sur = nullptr;
 }
 
@@ -959,13 +959,13 @@ int ga_population_read(ga_population *pp, int16_t *Y, int8_t *X, int64_t *obj, i
 
 }  // extern "C"
 
-int ffs_rt::ga_enqueue(ga_population *pp, int32_t generations) {
+int ffs_rt::ga_enqueue(ga_population *pp, int32_t generations, int *timed) {
     if (!pp || generations < 0) return FFS_E_ARG;
+    if (timed) *timed = 0;
     ffs_instance *in = pp->inst;
     if (pp->version != in->version) return FFS_E_STATE;
-    const unsigned long long per_gen =
-        pp->sur ? (unsigned long long)(kSurrogateFixedLaunches + kSurrogateStepLaunches * pp->train_steps) : 1;
-    if (pp->sur && !pp->graph_sur && !pp->profiling) {  // capture the surrogate generation once
+    const unsigned long long per_gen = pp->sur ? (unsigned long long)surrogate_launches_per_generation(pp) : 1;
+    if (pp->sur && !pp->graph_sur && pp->profiling != 1 && !surrogate_is_exact(pp)) {  // capture once
         FFS_TRY(prepare_surrogate_kernels(pp));
         cudaStream_t cap = nullptr;
         FFS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -979,13 +979,37 @@ int ffs_rt::ga_enqueue(ga_population *pp, int32_t generations) {
         if (g) cudaGraphDestroy(g);
         if (rc != FFS_OK) return rc;
     }
-    if (pp->profiling) return FFS_E_STATE;
+    if (pp->profiling == 1) return FFS_E_STATE;
+    if (surrogate_is_exact(pp)) {  // decodes every candidate: launched directly
+        FFS_TRY(prepare_surrogate_kernels(pp));
+        for (int i = 0; i < generations; ++i) FFS_TRY(surrogate_enqueue_generation(pp, pp->st, nullptr, nullptr));
+        g_launches += per_gen * (unsigned long long)generations;
+        return FFS_OK;
+    }
     cudaGraphExec_t gx = pp->sur ? pp->graph_sur : pp->graph;
-    int i = 0;
+    // profiling mode 2: events around every replay, in the launch mode of ga_run itself
+    const bool time_it = pp->profiling == 2 && timed;
+    const int pairs = time_it ? (pp->sur || !pp->graph_r ? generations
+                                                          : generations / kGraphGens + generations % kGraphGens)
+                              : 0;
+    while ((int)pp->ev.size() < 2 * pairs) {
+        cudaEvent_t e;
+        FFS_CUDA(cudaEventCreate(&e));
+        pp->ev.push_back(e);
+    }
+    int i = 0, q = 0;
+    auto replay = [&](cudaGraphExec_t g) {
+        if (time_it) FFS_CUDA(cudaEventRecord(pp->ev[2 * q], pp->st));
+        FFS_CUDA(cudaGraphLaunch(g, pp->st));
+        if (time_it) FFS_CUDA(cudaEventRecord(pp->ev[2 * q + 1], pp->st));
+        ++q;
+        return FFS_OK;
+    };
     if (!pp->sur && pp->graph_r)
-        for (; i + kGraphGens <= generations; i += kGraphGens) FFS_CUDA(cudaGraphLaunch(pp->graph_r, pp->st));
-    for (; i < generations; ++i) FFS_CUDA(cudaGraphLaunch(gx, pp->st));
+        for (; i + kGraphGens <= generations; i += kGraphGens) FFS_TRY(replay(pp->graph_r));
+    for (; i < generations; ++i) FFS_TRY(replay(gx));
     g_launches += per_gen * (unsigned long long)generations;
+    if (time_it) *timed = q;
     return FFS_OK;
 }
 
@@ -1069,21 +1093,35 @@ extern "C" {
 int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
     if (!pp || generations < 0) return FFS_E_ARG;
     if (pp->version != pp->inst->version) return FFS_E_STATE;
-    if (!pp->profiling) {
-        FFS_TRY(ga_enqueue(pp, generations));
-        return ga_finish(pp, best);
+    if (pp->profiling != 1) {
+        int timed = 0;
+        FFS_TRY(ga_enqueue(pp, generations, &timed));
+        const int rc = ga_finish(pp, best);  // synchronises the stream first
+        for (int q = 0; q < timed; ++q) {
+            float ms = 0.f;
+            FFS_CUDA(cudaEventElapsedTime(&ms, pp->ev[2 * q], pp->ev[2 * q + 1]));
+            pp->prof_ms += ms;
+        }
+        if (timed) pp->prof_launches += generations;
+        return rc;
     }
-    // profiling: every generation launched eagerly between two events
-    const unsigned long long per_gen =
-        pp->sur ? (unsigned long long)(kSurrogateFixedLaunches + kSurrogateStepLaunches * pp->train_steps) : 1;
+    // profiling: every generation launched eagerly between two events (surrogate generations:
+    // six events bracketing their phases)
+    const unsigned long long per_gen = pp->sur ? (unsigned long long)surrogate_launches_per_generation(pp) : 1;
     if (pp->sur) FFS_TRY(prepare_surrogate_kernels(pp));
     while ((int)pp->ev.size() < 2 * generations) {
         cudaEvent_t e;
         FFS_CUDA(cudaEventCreate(&e));
         pp->ev.push_back(e);
     }
+    while (pp->sur && (int)pp->ev_sur.size() < 6 * generations) {
+        cudaEvent_t e;
+        FFS_CUDA(cudaEventCreate(&e));
+        pp->ev_sur.push_back(e);
+    }
     for (int i = 0; i < generations; ++i) {
-        if (pp->sur) FFS_TRY(surrogate_enqueue_generation(pp, pp->st, pp->ev[2 * i], pp->ev[2 * i + 1]));
+        if (pp->sur)
+            FFS_TRY(surrogate_enqueue_generation(pp, pp->st, pp->ev[2 * i], pp->ev[2 * i + 1], &pp->ev_sur[6 * i]));
         else FFS_TRY(ga_enqueue_generation(pp, pp->ev[2 * i], pp->ev[2 * i + 1]));
     }
     g_launches += per_gen * (unsigned long long)generations;
@@ -1092,6 +1130,10 @@ int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
         float ms = 0.f;
         FFS_CUDA(cudaEventElapsedTime(&ms, pp->ev[2 * i], pp->ev[2 * i + 1]));
         pp->prof_ms += ms;
+        for (int q = 0; pp->sur && q < 5; ++q) {
+            FFS_CUDA(cudaEventElapsedTime(&ms, pp->ev_sur[6 * i + q], pp->ev_sur[6 * i + q + 1]));
+            pp->phase_ms[q] += ms;
+        }
     }
     pp->prof_launches += generations;
     return ga_finish(pp, best);
@@ -1099,9 +1141,17 @@ int ga_run(ga_population *pp, int32_t generations, ffs_result *best) {
 
 int ga_set_profiling(ga_population *pp, int32_t enable) {
     if (!pp) return FFS_E_ARG;
-    pp->profiling = enable != 0;
+    if (enable < 0 || enable > 2) return FFS_E_ARG;
+    pp->profiling = enable;
     pp->prof_ms = 0.0;
     pp->prof_launches = 0;
+    for (double &v : pp->phase_ms) v = 0.0;
+    return FFS_OK;
+}
+
+int ga_profile_read_phases(ga_population *pp, double *ms) {
+    if (!pp || !ms) return FFS_E_ARG;
+    for (int q = 0; q < 5; ++q) ms[q] = pp->phase_ms[q];
     return FFS_OK;
 }
 

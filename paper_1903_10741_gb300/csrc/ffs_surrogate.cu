@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -41,8 +42,13 @@ struct ffs_surrogate {
     __nv_bfloat16 *Yh = nullptr, *YhT = nullptr, *H1 = nullptr, *H2 = nullptr, *dz2b = nullptr, *dz2T = nullptr,
                   *H1T = nullptr, *dz1b = nullptr, *dz1T = nullptr;
     float *out = nullptr, *t = nullptr, *dout = nullptr, *dz2 = nullptr, *dh1 = nullptr, *dz1 = nullptr, *G = nullptr;
+    // diagnostic: candidates scored by their exact objective instead of the network
+    int exact = 0;
+    int64_t *cand_obj = nullptr;
+    size_t cand_obj_cap = 0;
 
     ~ffs_surrogate() {
+        dfree(cand_obj);
         dfree(params); dfree(grads); dfree(m); dfree(v); dfree(step); dfree(ph); dfree(dh); dfree(gstg); dfree(soff);
         dfree(V); dfree(W2b); dfree(W2Tb); dfree(w3b);
         dfree(Yh); dfree(YhT); dfree(H1); dfree(H2); dfree(dz2b); dfree(dz2T); dfree(H1T); dfree(dz1b); dfree(dz1T);
@@ -327,6 +333,8 @@ int ga_population_attach_surrogate(ga_population *pp, ffs_surrogate *s, int32_t 
             return FFS_E_NOMEM;
     }
     if (!pp->kept_obj && dalloc(&pp->kept_obj, (size_t)pp->P) != cudaSuccess) return FFS_E_NOMEM;
+    if (!pp->cand_keep && dalloc(&pp->cand_keep, (size_t)pp->P) != cudaSuccess) return FFS_E_NOMEM;
+    if (pp->keep_rule != FFS_KEEP_SLOT && oversample * pp->I > kTopMax) return FFS_E_ARG;
     pp->sur = s;
     pp->F = oversample;
     pp->lr = lr;
@@ -336,6 +344,40 @@ int ga_population_attach_surrogate(ga_population *pp, ffs_surrogate *s, int32_t 
         cudaGraphExecDestroy(pp->graph_sur);
         pp->graph_sur = nullptr;
     }
+    return FFS_OK;
+}
+
+int ffs_surrogate_score_exactly(ffs_surrogate *s, int32_t on) {
+    if (!s) return FFS_E_ARG;
+    s->exact = on != 0;
+    return FFS_OK;
+}
+
+int ga_population_surrogate_keep(ga_population *pp, int32_t rule) {
+    if (!pp || !pp->sur || (rule != FFS_KEEP_SLOT && rule != FFS_KEEP_ISLAND && rule != FFS_KEEP_ISLAND_OFFSPRING))
+        return FFS_E_ARG;
+    if (rule != FFS_KEEP_SLOT && pp->F * pp->I > kTopMax) {
+        std::snprintf(ffs_rt::g_last_error, sizeof(ffs_rt::g_last_error),
+                      "island keep rule: oversample x island = %d candidates per island, limit %d", pp->F * pp->I,
+                      kTopMax);
+        return FFS_E_ARG;
+    }
+    if (pp->keep_rule != rule && pp->graph_sur) {
+        cudaGraphExecDestroy(pp->graph_sur);
+        pp->graph_sur = nullptr;
+    }
+    pp->keep_rule = rule;
+    return FFS_OK;
+}
+
+int ga_population_read_candidates(ga_population *pp, int16_t *Y, int8_t *X, float *score, int32_t *keep) {
+    if (!pp || !pp->sur || !pp->cand_Y) return FFS_E_ARG;
+    FFS_CUDA(cudaStreamSynchronize(pp->st));
+    const size_t C = (size_t)pp->P * pp->F;
+    if (Y) FFS_CUDA(cudaMemcpy(Y, pp->cand_Y, 2 * C * pp->K, cudaMemcpyDeviceToHost));
+    if (X) FFS_CUDA(cudaMemcpy(X, pp->cand_X, C * pp->K, cudaMemcpyDeviceToHost));
+    if (score) FFS_CUDA(cudaMemcpy(score, pp->cand_out, 4 * C, cudaMemcpyDeviceToHost));
+    if (keep) FFS_CUDA(cudaMemcpy(keep, pp->cand_keep, 4 * (size_t)pp->P, cudaMemcpyDeviceToHost));
     return FFS_OK;
 }
 
@@ -364,7 +406,19 @@ int ffs_rt::surrogate_status() { return mlp_gemm_take_error() ? FFS_E_TIMEOUT : 
 
 // One surrogate-assisted generation: candidates, their scores, the fused select + decode +
 // replacement kernel, then one training step on the kept children's exact objectives.
-int ffs_rt::surrogate_enqueue_generation(ga_population *pp, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+int ffs_rt::surrogate_launches_per_generation(const ga_population *pp) {
+    // exact scoring replaces the 7 launches of weight sync and forward pass with up to two
+    // decode launches and one conversion
+    return kSurrogateFixedLaunches + kSurrogateStepLaunches * pp->train_steps +
+           (pp->keep_rule != FFS_KEEP_SLOT ? 1 : 0) - (pp->sur->exact ? 4 : 0);
+}
+
+bool ffs_rt::surrogate_is_exact(const ga_population *pp) { return pp->sur && pp->sur->exact; }
+
+// With `phase` (six events), the phases are bracketed: candidates, scoring, keep rule,
+// exact decode with replacement, training.
+int ffs_rt::surrogate_enqueue_generation(ga_population *pp, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1,
+                                         cudaEvent_t *phase) {
     ffs_surrogate *s = pp->sur;
     GenArgs a;
     ga_gen_args(pp, &a);
@@ -380,21 +434,43 @@ int ffs_rt::surrogate_enqueue_generation(ga_population *pp, cudaStream_t st, cud
     a.screen_thr = pp->screen_thr;
     const int C = pp->P * pp->F;
     const int grid_c = std::max(1, std::min((C + kWarpsPerBlock - 1) / kWarpsPerBlock, num_sms() * 8));
+    auto mark = [&](int q) { return phase ? cuda_rc(cudaEventRecord(phase[q], st)) : FFS_OK; };
+    FFS_TRY(mark(0));
     FFS_CUDA(launch_candidates(pp->par.machine_mode, a, pp->hdr, grid_c, st));
-    FFS_TRY(sync_weights(s, st));
-    FFS_TRY(forward(s, reinterpret_cast<const __nv_bfloat16 *>(pp->cand_Yh), C,
-                    reinterpret_cast<__nv_bfloat16 *>(pp->cand_H1), reinterpret_cast<__nv_bfloat16 *>(pp->cand_H2),
-                    pp->cand_out, st));
+    FFS_TRY(mark(1));
+    if (s->exact) {  // diagnostic: a perfect model, every candidate decoded exactly
+        if ((size_t)C > s->cand_obj_cap) {
+            dfree(s->cand_obj);
+            FFS_CUDA(dalloc(&s->cand_obj, (size_t)C));
+            s->cand_obj_cap = (size_t)C;
+        }
+        FFS_TRY(decode_impl(pp->inst, pp->par.order_mode, pp->par.machine_mode, pp->cand_Y, pp->cand_X, C, s->cand_obj,
+                            nullptr, nullptr, nullptr, nullptr, st));
+        FFS_CUDA(mlp_obj_to_score(s->cand_obj, C, pp->cand_out, st));
+    } else {
+        FFS_TRY(sync_weights(s, st));
+        FFS_TRY(forward(s, reinterpret_cast<const __nv_bfloat16 *>(pp->cand_Yh), C,
+                        reinterpret_cast<__nv_bfloat16 *>(pp->cand_H1),
+                        reinterpret_cast<__nv_bfloat16 *>(pp->cand_H2), pp->cand_out, st));
+    }
+    FFS_TRY(mark(2));
+    if (pp->keep_rule != FFS_KEEP_SLOT) {
+        FFS_CUDA(launch_island_top(pp->cand_out, pp->keep_rule == FFS_KEEP_ISLAND_OFFSPRING ? pp->cand_new : nullptr,
+                                   pp->P, pp->F, pp->I, pp->cand_keep, st));
+        a.cand_keep = pp->cand_keep;
+    }
+    FFS_TRY(mark(3));
     if (ev0) FFS_CUDA(cudaEventRecord(ev0, st));
     FFS_CUDA(launch_ga_generation(pp->par.order_mode, pp->par.machine_mode, a, pp->hdr, pp->grid_gen, st));
     if (ev1) FFS_CUDA(cudaEventRecord(ev1, st));
+    FFS_TRY(mark(4));
     // training steps on the kept children (inputs gathered into s->Yh, objectives in kept_obj)
     for (int step = 0; step < pp->train_steps; ++step) {
         if (step) FFS_TRY(sync_weights(s, st));
         FFS_TRY(forward(s, s->Yh, pp->P, s->H1, s->H2, s->out, st));
         FFS_TRY(backward(s, pp->kept_obj, pp->P, pp->P, true, pp->lr, st));
     }
-    return FFS_OK;
+    return mark(5);
 }
 
 int ffs_rt::prepare_surrogate_kernels(ga_population *pp) {

@@ -21,6 +21,7 @@ PLACE_INSERT = 4  # or-ed into a machine mode: idle-gap insertion placement
 ST_FREE, ST_EXEC, ST_DONE, ST_FIXED = 0, 1, 2, 3
 E_TIMEOUT = -5
 INJECT_NONE, INJECT_TABLE_COPY, INJECT_GEMM_LOADS = 0, 1, 2  # ffs_debug_inject (tests only)
+KEEP_SLOT, KEEP_ISLAND, KEEP_ISLAND_OFFSPRING = 0, 1, 2  # keep rules of surrogate-assisted generations
 
 _i32p = C.POINTER(C.c_int32)
 _lib = None
@@ -142,6 +143,10 @@ _SIGS = {
     "ffs_surrogate_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "ffs_surrogate_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p]),
     "ffs_debug_inject": (C.c_int, [C.c_int32]),
+    "ga_population_surrogate_keep": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ffs_surrogate_score_exactly": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ga_profile_read_phases": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ga_population_read_candidates": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ffs_surrogate_read_activations": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                                  C.c_void_p]),
     "ga_population_attach_surrogate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_int32, C.c_int32]),
@@ -416,9 +421,11 @@ class Population:
         return d
 
     def attach_surrogate(self, sur, oversample: int = 8, lr: float = 1e-3, train_steps: int = 1,
-                         pretrain_steps: int = 0, screen: float = 1.0):
+                         pretrain_steps: int = 0, screen: float = 1.0, keep: int = KEEP_SLOT):
         """Surrogate-assisted generations from now on (None detaches); optionally first
-        trains the surrogate on the current population."""
+        trains the surrogate on the current population.  ``keep``: KEEP_SLOT (per-slot
+        screening with probability ``screen``) or KEEP_ISLAND (each island keeps the
+        best-scored 1/oversample of its candidates)."""
         if sur is not None and pretrain_steps > 0:
             loss = C.c_float()
             _check(lib().ffs_surrogate_pretrain(sur._h, self._h, int(pretrain_steps), float(lr), C.addressof(loss)),
@@ -426,10 +433,26 @@ class Population:
         _check(lib().ga_population_attach_surrogate(self._h, sur._h if sur is not None else None, int(oversample),
                                                     float(lr), int(train_steps), int(round(screen * 1000))),
                "ga_population_attach_surrogate")
+        if sur is not None:
+            _check(lib().ga_population_surrogate_keep(self._h, int(keep)), "ga_population_surrogate_keep")
         self._sur = sur
 
-    def set_profiling(self, enable: bool):
-        _check(lib().ga_set_profiling(self._h, 1 if enable else 0), "ga_set_profiling")
+    def candidates(self, oversample: int) -> dict:
+        """The last surrogate-assisted generation's candidates (Y, X [P*F, K]), their scores
+        and, under KEEP_ISLAND, the row kept for each slot."""
+        n = self.P * oversample
+        d = dict(Y=np.zeros((n, self.K), np.int16), X=np.zeros((n, self.K), np.int8),
+                 score=np.zeros(n, np.float32), keep=np.zeros(self.P, np.int32))
+        _check(lib().ga_population_read_candidates(self._h, d["Y"].ctypes.data, d["X"].ctypes.data,
+                                                   d["score"].ctypes.data, d["keep"].ctypes.data),
+               "ga_population_read_candidates")
+        return d
+
+    def set_profiling(self, enable):
+        """False/0: untimed graph replays; True/1: eager launches, the fused kernel timed;
+        2: graph replays (the normal launch mode), each replay timed."""
+        mode = 1 if enable is True else (0 if enable is False else int(enable))
+        _check(lib().ga_set_profiling(self._h, mode), "ga_set_profiling")
 
     def profile(self):
         """(summed milliseconds, launches) of the fused generation kernel while profiling."""
@@ -437,6 +460,12 @@ class Population:
         n = C.c_int64()
         _check(lib().ga_profile_read(self._h, C.byref(ms), C.byref(n)), "ga_profile_read")
         return float(ms.value), int(n.value)
+
+    def profile_phases(self) -> dict:
+        """Summed milliseconds of the phases of surrogate-assisted generations while profiling."""
+        ms = np.zeros(5, np.float64)
+        _check(lib().ga_profile_read_phases(self._h, ms.ctypes.data), "ga_profile_read_phases")
+        return dict(zip(("candidates", "scoring", "keep_rule", "exact_decode", "training"), ms.tolist()))
 
     def checkpoint(self) -> bytes:
         n = C.c_size_t(0)
@@ -596,6 +625,10 @@ class Surrogate:
         _check(lib().ffs_surrogate_train(self._h, _dptr(y), _dptr(obj), int(y.shape[0]), float(lr),
                                          C.addressof(loss)), "ffs_surrogate_train")
         return float(loss.value)
+
+    def score_exactly(self, on: bool = True):
+        """Diagnostic: score candidates by their exact objectives (a perfect model)."""
+        _check(lib().ffs_surrogate_score_exactly(self._h, 1 if on else 0), "ffs_surrogate_score_exactly")
 
     def activations(self, rows: int) -> dict:
         """Stored activations of the last forward pass over the surrogate's own batch: h1, h2

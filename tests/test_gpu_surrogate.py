@@ -275,3 +275,76 @@ def test_forward_at_the_surrogate_workload_size():
     got = sur.predict(torch.from_numpy(Y).cuda()).cpu().numpy().astype(np.float64)
     out, _, _ = _check_forward(sur, orc_i, Y, params)
     assert np.array_equal(got, out)
+
+
+# ------------------------------------------------------------------ island keep rule
+
+@pytest.mark.parametrize("rule", [ffs.KEEP_ISLAND, ffs.KEEP_ISLAND_OFFSPRING])
+def test_island_keep_with_constant_scores_equals_plain_run(rule):
+    """With every parameter zero the model scores every candidate alike, an island rule
+    then keeps each slot's first candidate -- the plain generation's child -- and with no
+    training the run is the plain run bit for bit (machine genes compared too)."""
+    prob = wl.random_instance(np.random.default_rng(14), 22, 4, 2, 4, 50, 5, 30, 50)
+    kw = dict(P=256, island=64, seed=9, mach_mode=ffs.MACH_GENE)
+    plain = ffs.Population(ffs.Instance(prob), **kw)
+    plain.run(7, want_schedule=False)
+    inst = ffs.Instance(prob)
+    pop = ffs.Population(inst, **kw)
+    sur = ffs.Surrogate(inst, max_batch=256, seed=3)
+    sur.set_params(np.zeros(sur.n_params, np.float32))
+    pop.attach_surrogate(sur, oversample=8, lr=1e-3, train_steps=0, keep=rule)
+    pop.run(7, want_schedule=False)
+    a, b = plain.read(), pop.read()
+    for k in ("Y", "X", "obj", "fit", "bY", "bobj"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_island_keep_ranks_each_island():
+    """One generation under the island rule (8 candidates per slot, islands of 64): the
+    candidates equal the oracle's offspring of the same parents bit for bit; each island
+    keeps exactly its 64 best-scored rows (ties to the lower row), in row order; and every
+    slot but the island's replaced one holds its kept candidate, exactly decoded."""
+    prob = wl.random_instance(np.random.default_rng(15), 24, 4, 2, 4, 50, 5, 30, 50)
+    P, I, F = 256, 64, 8
+    inst = ffs.Instance(prob)
+    pop = ffs.Population(inst, P=P, island=I, seed=11)
+    sur = ffs.Surrogate(inst, max_batch=P, seed=5)
+    pop.attach_surrogate(sur, oversample=F, lr=1e-3, train_steps=1, keep=ffs.KEEP_ISLAND)
+    pop.run(2, want_schedule=False)
+    before = pop.read()
+    orc_i = oracle.Instance(prob)
+    ga = oracle.GA(orc_i, P=P, island=I, seed=11)
+    ga.Y[:, :ga.K], ga.X[:, :ga.K], ga.fit[:] = before["Y"], before["X"], before["fit"]
+    ga.st.gen = before["gen"]
+    want_Y, _, _ = ga.candidates(F)
+    pop.run(1, want_schedule=False)
+    c = pop.candidates(F)
+    assert np.array_equal(c["Y"], want_Y)
+    after = pop.read()
+    for isl in range(P // I):
+        rows = np.array([f * P + j for f in range(F) for j in range(isl * I, (isl + 1) * I)])
+        s = c["score"][rows].astype(np.float64)
+        s = np.where(np.isnan(s), np.inf, s)
+        best = rows[np.lexsort((rows, s))[:I]]
+        assert np.array_equal(c["keep"][isl * I:(isl + 1) * I], np.sort(best))
+        held = (after["Y"][isl * I:(isl + 1) * I] == c["Y"][c["keep"][isl * I:(isl + 1) * I]]).all(axis=1)
+        assert held.sum() >= I - 1
+    for i in range(0, P, 7):
+        assert after["obj"][i] == orc_i.decode(after["Y"][i])["obj"]
+
+
+def test_exact_scores_rank_by_the_objective():
+    """The diagnostic exact scoring: every candidate's score is its exact objective (the
+    oracle's decode of the candidate row), so the island rule keeps the truly best rows."""
+    prob = wl.random_instance(np.random.default_rng(16), 20, 4, 2, 4, 50, 5, 30, 50)
+    P, I, F = 256, 64, 4
+    inst = ffs.Instance(prob)
+    pop = ffs.Population(inst, P=P, island=I, seed=2)
+    sur = ffs.Surrogate(inst, max_batch=P, seed=2)
+    sur.score_exactly(True)
+    pop.attach_surrogate(sur, oversample=F, lr=1e-3, train_steps=0, keep=ffs.KEEP_ISLAND)
+    pop.run(3, want_schedule=False)
+    c = pop.candidates(F)
+    orc_i = oracle.Instance(prob)
+    for r in range(0, P * F, 13):
+        assert c["score"][r] == np.float32(orc_i.decode(c["Y"][r])["obj"])

@@ -534,6 +534,24 @@ def test_ga_migrants_are_post_replacement_bests():
             assert members.max() >= ga.bfit[i]
 
 
+def test_candidates_with_one_per_slot_are_the_generation_children():
+    """With one candidate per slot the offspring rows are exactly the children a generation
+    builds before decoding; with F per slot, candidate 0 of every slot is that child, and
+    every row is a permutation of 1..K."""
+    prob = wl.static_small(5)
+    ga = oracle.GA(oracle.Instance(prob), P=64, island=16, tour_k=2, migrate_every=0, seed=4, mach_mode=MACH_GENE)
+    ga.init().step(3)
+    cY, cX, _ = ga.candidates(1)
+    cY8, cX8, new8 = ga.candidates(8)
+    assert np.array_equal(cY8[:64], cY) and np.array_equal(cX8[:64], cX)
+    assert all(sorted(r.tolist()) == list(range(1, ga.K + 1)) for r in cY8)
+    ga.step()
+    # the children after replacement: all but one slot per island (the record's) are cY
+    same = (ga.Y[:, :ga.K] == cY).all(axis=1)
+    assert same.reshape(4, 16).sum(axis=1).min() >= 15
+    assert 0.5 < new8.mean() < 1.0  # crossover 0.8, mutation 0.1
+
+
 # ------------------------------------------------------------------ GA properties
 
 def test_ga_population_stays_valid_and_elitist():
