@@ -226,21 +226,21 @@ __device__ __forceinline__ void commit_power_full(uint16_t *h, int t, int e, uin
     }
 }
 
-// The common case of one op on a shared-memory profile whose slots at or beyond hw hold
-// full headroom: when [t, t+p) lies within one 128-slot step from t & ~3 and every slot of
-// it has headroom q, q is drawn there from the words the check loaded (no second read) and
-// t is returned.  Otherwise nothing changes and the returned start is where the general
-// scan may resume: one past the last slot lacking headroom (the jump its own first step
-// would make), or t when the op spans more than one step.  Slots at or beyond hw need no
-// check, as q never exceeds the peak.  The caller ensures t + p <= Hcap.
-__device__ __forceinline__ int place_first(uint16_t *h, int hw, int t, int p, uint32_t q2, uint32_t Q2, int lane,
-                                           bool &placed) {
+// The common case of one op on a shared-memory profile prefilled with full headroom up to
+// its end: when [t, t+p) lies within one 128-slot step from t & ~3 and every slot of it has
+// headroom q, q is drawn there from the words the check loaded (no second read) and t is
+// returned.  Otherwise nothing changes and the returned start is where the general scan
+// may resume: one past the last slot lacking headroom (the jump its own first step would
+// make), or t when the op spans more than one step.  Only lanes whose four slots start
+// below t + p load and store.  The caller ensures t + p <= Hcap.
+__device__ __forceinline__ int place_first(uint16_t *h, int t, int p, uint32_t q2, int lane, bool &placed) {
     placed = false;
     const int c = t & ~3, e = t + p;
     if (e - c > 128) return t;
     const int b = c + 4 * lane;
-    uint2 w = make_uint2(Q2, Q2);  // slots at or beyond hw: full headroom
-    if (b < min(e, hw)) w = *reinterpret_cast<const uint2 *>(h + b);
+    const bool mine = b < e;
+    uint2 w = make_uint2(0u, 0u);  // lanes past the window: no slot in it
+    if (mine) w = *reinterpret_cast<const uint2 *>(h + b);
     const uint2 m = slot_mask(b, t, e);
     // bit 15 of (h | 0x8000) - q is clear exactly where h < q (no borrow between halfwords)
     const uint32_t vx = ~((w.x | 0x80008000u) - q2) & m.x & 0x80008000u;
@@ -251,7 +251,7 @@ __device__ __forceinline__ int place_first(uint16_t *h, int hw, int t, int p, ui
         const int li = vy ? 2 + (int)(vy >> 31) : (int)(vx >> 31);  // the lane's last violating slot
         return c + 4 * l + __shfl_sync(kFull, li, l) + 1;
     }
-    if (m.x | m.y) {
+    if (mine) {
         w.x -= q2 & m.x;
         w.y -= q2 & m.y;
         *reinterpret_cast<uint2 *>(h + b) = w;
@@ -347,8 +347,8 @@ __device__ __forceinline__ void earliest_machine_u(const uint16_t *h, int hw, in
 // scratch copy.  Schedule output (S_out/M_out, [N*g]) is written for free ops only when
 // non-null.
 //
-// C[j] starts at the end of the job's frozen prefix, raised to R_j when the job still
-// has free ops, so every op becomes available at max(RS, C[j]).
+// C[j] (kept relative to RS) starts at the end of the job's frozen prefix, raised to R_j
+// when the job still has free ops, so every op becomes available at RS + max(0, C[j]).
 //
 // FULL (shared-memory slices): the whole slice is filled first (the executing ops'
 // profile, then Qmax), so a commit has nothing to blend in.  Otherwise (global profiles
@@ -361,7 +361,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
     const uint32_t Q2 = (uint32_t)T.Qmax * 0x10001u;
 
     if (T.E0 > Hcap) return {0, 0, 1};  // executing ops alone outgrow the profile slice
-    for (int j = lane; j < N; j += 32) C[j] = T.gcnt[j] > 0 ? max(T.C0[j], T.R[j]) : T.C0[j];
+    for (int j = lane; j < N; j += 32) C[j] = (T.gcnt[j] > 0 ? max(T.C0[j], T.R[j]) : T.C0[j]) - RS;
     for (int i = lane; i < T.E0; i += 32) h[i] = T.h0[i];
     if (FULL) {  // slots E0 .. Hcap: full headroom (Hcap is a multiple of 8)
         const uint16_t Qm = (uint16_t)T.Qmax;
@@ -467,7 +467,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                     p = (int)(pq & 0xFFFFu);
                     qo2 = (pq >> 16) * 0x10001u;
                 }
-                const int est = max(cj - RS, 0);
+                const int est = max(cj, 0);
                 int best_t, best_m;
                 uint32_t bq2;
                 // fast path (append placement, prefilled profile): the first candidate start
@@ -480,7 +480,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                     bq2 = __shfl_sync(kFull, qo2, best_m);
                     const int t0 = max(est, __shfl_sync(kFull, mf, best_m));
                     int from = t0;
-                    if (kFast && t0 + p <= Hcap) from = place_first(h, hw, t0, p, bq2, Q2, lane, placed);
+                    if (kFast && t0 + p <= Hcap) from = place_first(h, t0, p, bq2, lane, placed);
                     if (placed)
                         best_t = t0;
                     else
@@ -496,7 +496,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                         best_m = (int)(kmin & 31u);
                         const int t0 = __shfl_sync(kFull, tl, best_m), pb = __shfl_sync(kFull, p, best_m);
                         bq2 = __shfl_sync(kFull, qo2, best_m);
-                        if (t0 + pb <= Hcap) place_first(h, hw, t0, pb, bq2, Q2, lane, placed);
+                        if (t0 + pb <= Hcap) place_first(h, t0, pb, bq2, lane, placed);
                         if (placed) {
                             best_t = t0;
                             p = pb;
@@ -515,7 +515,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                         const int t0 = (int)(kmin >> 5);
                         best_m = (int)(kmin & 31u);
                         bq2 = __shfl_sync(kFull, q2, best_m);
-                        if (t0 + p <= Hcap) from = place_first(h, hw, t0, p, bq2, Q2, lane, placed);
+                        if (t0 + p <= Hcap) from = place_first(h, t0, p, bq2, lane, placed);
                         if (placed) best_t = t0;
                     }
                     if (!placed)
@@ -535,7 +535,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 if (INS) commit_busy(busy + (size_t)best_m * words, best_t, e, lane);
                 else if (lane == best_m) mf = e;
                 if (lane == 0) {
-                    C[j] = e + RS;
+                    C[j] = e;
                     if (S_out) {
                         S_out[j * g + s] = best_t + RS;
                         M_out[j * g + s] = best_m;
@@ -576,7 +576,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 p = (int)(pq & 0xFFFFu);
                 q2 = (pq >> 16) * 0x10001u;
             }
-            const int est = max(C[j] - RS, 0);
+            const int est = max(C[j], 0);
             int best_t, best_m;
             if (mach_gene(MACH)) {
                 best_m = x[k];
@@ -603,7 +603,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             if (lane == 0) {
                 nxt[bestj] = (int16_t)(k + 1);
                 mfree[mo + best_m] = e + RS;
-                C[j] = e + RS;
+                C[j] = e;
                 if (S_out) {
                     S_out[j * g + s] = best_t + RS;
                     M_out[j * g + s] = best_m;
@@ -617,7 +617,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
     long long tard = 0;
     int cmax = 0;
     for (int j = lane; j < N; j += 32) {
-        const int cj = C[j];
+        const int cj = C[j] + RS;
         const long long d = (long long)cj - T.D[j];
         if (d > 0) tard += d;
         cmax = max(cmax, cj);
