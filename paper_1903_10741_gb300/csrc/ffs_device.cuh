@@ -428,6 +428,101 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             __syncwarp();
         }
         if (__any_sync(kFull, bad)) return {0, 0, 2};
+        // Identical machines, earliest start, prefilled profile (the common case): a
+        // software pipeline.  While op n's window is loaded, checked and voted on, the
+        // machine of op n+1 is chosen as if op n were placed at its first candidate start
+        // (the one-step case, which most ops take); when op n needs the general search
+        // instead, op n+1 is chosen again from the true machine state.  The statements
+        // are ordered so that op n's load and op n+1's reduction are in flight together.
+        if (MACH == kMachEarliest && FULL) {
+            for (int s = 0; s < g; ++s) {
+                const int lo = T.soff[s], hi = T.soff[s + 1];
+                if (lo == hi) continue;
+                const int mo = T.moff[s], os = T.o[s];
+                constexpr int kNever = 0x07FFFFFF;
+                int mf = kNever;
+                uint32_t q2 = 0;
+                if (lane < os) {
+                    mf = T.mfree0[mo + lane] - RS;
+                    q2 = (uint32_t)T.q[mo + lane] * 0x10001u;
+                }
+                int k = order[lo];
+                uint2 gr = T.grec[k];
+                int est = max(C[gr.x & 0xFFFFu], 0);
+                int kn = order[min(lo + 1, hi - 1)];
+                uint2 grn = T.grec[kn];
+                int cjn = C[grn.x & 0xFFFFu];
+                // op n's machine (the one that frees first, lowest index on ties) and start
+                unsigned kmin = __reduce_min_sync(kFull, ((unsigned)max(est, mf) << 5) | (unsigned)lane);
+                int ct = (int)(kmin >> 5), cm = (int)(kmin & 31u);
+                uint32_t cq = __shfl_sync(kFull, q2, cm);
+                for (int n = lo; n < hi; ++n) {
+                    const int j = (int)(gr.x & 0xFFFFu), p = (int)(gr.y & 0xFFFFu);
+                    const int e = ct + p, c = ct & ~3, b = c + 4 * lane;
+                    const bool one = e <= Hcap && e - c <= 128;  // one 128-slot step suffices
+                    const bool mine = one && b < e;
+                    uint2 w = make_uint2(0u, 0u);
+                    if (mine) w = *reinterpret_cast<const uint2 *>(h + b);  // op n's window
+                    // op n+1 as if op n is placed at ct on machine cm
+                    const int estn = max(cjn, 0);
+                    const int mfs = lane == cm ? e : mf;
+                    const unsigned kminn = __reduce_min_sync(kFull, ((unsigned)max(estn, mfs) << 5) | (unsigned)lane);
+                    const int kn2 = order[min(n + 2, hi - 1)];
+                    const uint2 grn2 = T.grec[kn2];
+                    const uint2 m = slot_mask(b, ct, e);
+                    int nt = (int)(kminn >> 5), nm = (int)(kminn & 31u);
+                    uint32_t nq = __shfl_sync(kFull, q2, nm);
+                    const uint32_t vx = ~((w.x | 0x80008000u) - cq) & m.x & 0x80008000u;
+                    const uint32_t vy = ~((w.y | 0x80008000u) - cq) & m.y & 0x80008000u;
+                    const unsigned vm = __ballot_sync(kFull, (vx | vy) != 0u);
+                    const int cjn2 = C[grn2.x & 0xFFFFu];
+                    int best_t = ct, best_m = cm, ee = e;
+                    if (one && vm == 0u) {  // placed at ct: draw q from the loaded words
+                        if (mine) {
+                            w.x -= cq & m.x;
+                            w.y -= cq & m.y;
+                            *reinterpret_cast<uint2 *>(h + b) = w;
+                        }
+                        mf = mfs;
+                    } else {  // the general search, resuming past the last violating slot
+                        int from = ct;
+                        if (one) {
+                            const int l = 31 - __clz(vm);
+                            const int li = vy ? 2 + (int)(vy >> 31) : (int)(vx >> 31);
+                            from = c + 4 * l + __shfl_sync(kFull, li, l) + 1;
+                        }
+                        uint32_t bq2;
+                        earliest_machine(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m, bq2,
+                                         nullptr, 0, from);
+                        ee = best_t + p;
+                        if (ee > Hcap) return {0, 0, 1};
+                        commit_power_full(h, best_t, ee, bq2, lane);
+                        if (lane == best_m) mf = ee;
+                        // op n+1 from the true machine state
+                        const unsigned kr = __reduce_min_sync(kFull, ((unsigned)max(estn, mf) << 5) | (unsigned)lane);
+                        nt = (int)(kr >> 5);
+                        nm = (int)(kr & 31u);
+                        nq = __shfl_sync(kFull, q2, nm);
+                    }
+                    hw = max(hw, ee);
+                    if (lane == 0) {
+                        C[j] = ee;
+                        if (S_out) {
+                            S_out[j * g + s] = best_t + RS;
+                            M_out[j * g + s] = best_m;
+                        }
+                    }
+                    __syncwarp();
+                    gr = grn;
+                    est = estn;
+                    ct = nt;
+                    cm = nm;
+                    cq = nq;
+                    grn = grn2;
+                    cjn = cjn2;
+                }
+            }
+        } else
         // Place the ops; the stage's machines live in lanes (availability, power).
         for (int s = 0; s < g; ++s) {
             const int lo = T.soff[s], hi = T.soff[s + 1];
