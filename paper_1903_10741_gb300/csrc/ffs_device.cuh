@@ -456,6 +456,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 unsigned kmin = __reduce_min_sync(kFull, ((unsigned)max(est, mf) << 5) | (unsigned)lane);
                 int ct = (int)(kmin >> 5), cm = (int)(kmin & 31u);
                 uint32_t cq = __shfl_sync(kFull, q2, cm);
+#pragma unroll 2
                 for (int n = lo; n < hi; ++n) {
                     const int j = (int)(gr.x & 0xFFFFu), p = (int)(gr.y & 0xFFFFu);
                     const int e = ct + p, c = ct & ~3, b = c + 4 * lane;
@@ -505,12 +506,10 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                         nq = __shfl_sync(kFull, q2, nm);
                     }
                     hw = max(hw, ee);
-                    if (lane == 0) {
-                        C[j] = ee;
-                        if (S_out) {
-                            S_out[j * g + s] = best_t + RS;
-                            M_out[j * g + s] = best_m;
-                        }
+                    C[j] = ee;  // every lane stores the same value
+                    if (S_out && lane == 0) {
+                        S_out[j * g + s] = best_t + RS;
+                        M_out[j * g + s] = best_m;
                     }
                     __syncwarp();
                     gr = grn;
