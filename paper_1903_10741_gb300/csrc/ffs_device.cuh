@@ -306,6 +306,33 @@ __device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int 
     }
 }
 
+// earliest_machine when the machine that frees first is already known (m0 with start t0m
+// and power q0, the lexicographic minimum of (availability, machine)) and its scan may
+// resume at `from`.
+__device__ __forceinline__ void earliest_machine_from(const uint16_t *h, int hw, int t0, uint32_t q2, int os, int p,
+                                                      int lane, int m0, int t0m, uint32_t q0, int from, int &best_t,
+                                                      int &best_m, uint32_t &best_q2) {
+    best_m = m0;
+    best_q2 = q0;
+    best_t = earliest_start(h, hw, max(t0m, from), p, q0, INT_MAX, lane);
+    if (best_t == t0m) return;  // as in earliest_machine: nothing starts earlier
+    unsigned cand = __ballot_sync(kFull, lane < os && lane != best_m && t0 < best_t + (lane < best_m));
+    while (cand) {
+        const int m = __ffs(cand) - 1;
+        cand &= cand - 1;
+        const int tm = __shfl_sync(kFull, t0, m);
+        const int lim = best_t + (m < best_m ? 1 : 0);
+        if (tm >= lim) continue;
+        const uint32_t qm = __shfl_sync(kFull, q2, m);
+        const int t = earliest_start(h, hw, tm, p, qm, lim, lane);
+        if (t < lim) {
+            best_t = t;
+            best_m = m;
+            best_q2 = qm;
+        }
+    }
+}
+
 // Unrelated machines: lane m < os holds its machine's availability t0, power q2 and the
 // op's processing time p on it.  Returns the lexicographic minimum of (earliest completion
 // of a power-feasible start, machine) and that machine's p.  The machine whose completion
@@ -456,7 +483,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 unsigned kmin = __reduce_min_sync(kFull, ((unsigned)max(est, mf) << 5) | (unsigned)lane);
                 int ct = (int)(kmin >> 5), cm = (int)(kmin & 31u);
                 uint32_t cq = __shfl_sync(kFull, q2, cm);
-#pragma unroll 2
+#pragma unroll 4
                 for (int n = lo; n < hi; ++n) {
                     const int j = (int)(gr.x & 0xFFFFu), p = (int)(gr.y & 0xFFFFu);
                     const int e = ct + p, c = ct & ~3, b = c + 4 * lane;
@@ -493,8 +520,8 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                             from = c + 4 * l + __shfl_sync(kFull, li, l) + 1;
                         }
                         uint32_t bq2;
-                        earliest_machine(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, best_t, best_m, bq2,
-                                         nullptr, 0, from);
+                        earliest_machine_from(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, cm, ct, cq,
+                                              from, best_t, best_m, bq2);
                         ee = best_t + p;
                         if (ee > Hcap) return {0, 0, 1};
                         commit_power_full(h, best_t, ee, bq2, lane);
