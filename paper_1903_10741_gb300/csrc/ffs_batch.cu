@@ -82,7 +82,8 @@ __device__ __forceinline__ void decode_into(const Tabs &T, const WarpPtrs &w, in
                                             long long emax, int i, int32_t *err, int *overflows, int lane) {
     DecodeOut r{0, 0, 1};
     if (!gfirst) {
-        r = decode_warp<ORDER, MACH, true>(T, w.h, Hcap, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
+        // many warps per scheduler here: the plain placement loop (fewer instructions per op)
+        r = decode_warp<ORDER, MACH, true, false>(T, w.h, Hcap, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
         if (r.status == 1) {
             if (lane == 0) atomicAdd(overflows, 1);
             const int16_t *row = Y + (size_t)i * T.K;

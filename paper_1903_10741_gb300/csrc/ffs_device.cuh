@@ -380,7 +380,10 @@ __device__ __forceinline__ void earliest_machine_u(const uint16_t *h, int hw, in
 // FULL (shared-memory slices): the whole slice is filled first (the executing ops'
 // profile, then Qmax), so a commit has nothing to blend in.  Otherwise (global profiles
 // of the full bound) slots are initialised as the schedule first reaches them.
-template <int ORDER, int MACH, bool FULL = false>
+// PIPE selects the software-pipelined placement loop for identical machines (for kernels
+// whose schedulers hold few warps, bound by each warp's dependency chain); without it the
+// loop does less work per op (for kernels bound by issue slots).
+template <int ORDER, int MACH, bool FULL = false, bool PIPE = true>
 __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *C, int32_t *mfree,
                                  int16_t *inv, int16_t *y, const int8_t *x, int32_t *S_out,
                                  int32_t *M_out, int lane) {
@@ -461,7 +464,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
         // (the one-step case, which most ops take); when op n needs the general search
         // instead, op n+1 is chosen again from the true machine state.  The statements
         // are ordered so that op n's load and op n+1's reduction are in flight together.
-        if (MACH == kMachEarliest && FULL) {
+        if (MACH == kMachEarliest && FULL && PIPE) {
             for (int s = 0; s < g; ++s) {
                 const int lo = T.soff[s], hi = T.soff[s + 1];
                 if (lo == hi) continue;
