@@ -50,7 +50,7 @@ SORT_PER_DECODE = 1936.25
 # DRAM bytes (read + write) of one generation-kernel launch from the ncu capture of the
 # current kernel (dram__bytes_read.sum + dram__bytes_write.sum, initial solve); None once
 # the kernel changes until it is captured again.
-TRAFFIC_BYTES = None
+TRAFFIC_BYTES = 428544
 
 
 def work_per_decode() -> float:
@@ -737,6 +737,47 @@ SVC_WORKLOAD = ("rescheduling service: 16 instances (N U{50..500}, g U{5..10}, m
                 "instance's last population, 200 generations per request")
 
 
+def run_service(ffs, work, G, ga_kw, max_active, memory_gb, local):
+    """Submits `work`'s requests at their arrival times to a fresh service over fresh
+    instances, waits for all of them; returns latency percentiles and throughput."""
+    insts = [ffs.Instance(p) for p in work.problems]
+    svc = ffs.Service(max_active=max_active, memory_bytes=int(memory_gb * (1 << 30)), **ga_kw)
+    launches0 = ffs.kernel_launches()
+    t0 = time.perf_counter()
+    tickets = []
+    for r in work.requests:
+        dt = t0 + r.at - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(svc.submit(insts[r.instance], r.arrivals, r.t_now, G))
+    infos = [svc.wait(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    stats = svc.stats()
+    svc.close()
+    lat = sorted((i["done_ns"] - i["submit_ns"]) / 1e6 for i in infos)
+    queue = sorted((i["admit_ns"] - i["submit_ns"]) / 1e6 for i in infos)
+    run = sorted((i["done_ns"] - i["admit_ns"]) / 1e6 for i in infos)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(round(q / 100 * (len(v) - 1))))]
+
+    P_ = ga_kw["P"]
+    return {"requests": len(infos), "genes": [min(i.K for i in insts), max(i.K for i in insts)],
+            "arrival_window_s": work.requests[-1].at,
+            "offered_rate_per_s": len(infos) / max(work.requests[-1].at, 1e-9), "wall_s": wall,
+            "requests_per_s": len(infos) / wall,
+            "decodes": sum(P_ * (i["generations"] + 1) + 1 for i in infos),
+            "p50_latency_ms": pct(lat, 50), "p99_latency_ms": pct(lat, 99),
+            "p50_queue_ms": pct(queue, 50), "p99_queue_ms": pct(queue, 99),
+            "p50_run_ms": pct(run, 50), "p99_run_ms": pct(run, 99),
+            "warm_starts": sum(i["warm"] for i in infos), "peak_memory_bytes": stats["peak_bytes"],
+            "failed": stats["failed"], "launches": ffs.kernel_launches() - launches0,
+            "d2h": sum(8 * i["n_ops"] + 20 for i in infos),
+            "h2d": sum(np.asarray(a, np.int32).nbytes for p in work.problems for a in (p.o, p.p, p.q, p.R, p.D))
+            + sum(r.arrivals.p.nbytes + r.arrivals.R.nbytes + r.arrivals.D.nbytes
+                  for r in work.requests if r.arrivals is not None)}
+
+
 def bench_service(args):
     import torch
 
@@ -754,53 +795,43 @@ def bench_service(args):
         svc.wait(t, schedule=False)
     svc.close()
 
-    work = wl.service(seed=1, n_requests=args.service_requests, rate=args.rate)
-    insts = [ffs.Instance(p) for p in work.problems]
-    h2d = sum(np.asarray(a, np.int32).nbytes for p in work.problems for a in (p.o, p.p, p.q, p.R, p.D))
-    h2d += sum(r.arrivals.p.nbytes + r.arrivals.R.nbytes + r.arrivals.D.nbytes
-               for r in work.requests if r.arrivals is not None)
-    svc = ffs.Service(max_active=args.max_active, memory_bytes=int(args.service_memory_gb * (1 << 30)), **ga_kw)
     clocks = ClockSampler(local)
     clocks.start()
-    launches0 = ffs.kernel_launches()
-    t0 = time.perf_counter()
-    tickets = []
-    for r in work.requests:
-        dt = t0 + r.at - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        tickets.append(svc.submit(insts[r.instance], r.arrivals, r.t_now, G))
-    infos = [svc.wait(t) for t in tickets]
-    wall = time.perf_counter() - t0
-    launches = ffs.kernel_launches() - launches0
+    # (1) the stated arrival rate (50/s): far above what one GPU completes at these sizes,
+    # so it measures the capacity (requests completed per second under a full queue)
+    burst = run_service(ffs, wl.service(seed=1, n_requests=args.service_requests, rate=args.rate), G, ga_kw,
+                        args.max_active, args.service_memory_gb, local)
+    capacity = burst["requests_per_s"]
+    # (2) at offered rates the GPU sustains, over `service_seconds` of Poisson arrivals
+    sustained = []
+    for frac in ([0.5, 1.0] if args.service_seconds > 0 else []):
+        rate = frac * capacity
+        n = max(4, int(np.ceil(args.service_seconds * rate)))
+        rec = run_service(ffs, wl.service(seed=1, n_requests=n, rate=rate), G, ga_kw, args.max_active,
+                          args.service_memory_gb, local)
+        rec["fraction_of_capacity"] = frac
+        sustained.append(rec)
     clk = clocks.stop()
-    stats = svc.stats()
-    svc.close()
-    lat = sorted((i["done_ns"] - i["submit_ns"]) / 1e6 for i in infos)
-    queue = sorted((i["admit_ns"] - i["submit_ns"]) / 1e6 for i in infos)
-    run = sorted((i["done_ns"] - i["admit_ns"]) / 1e6 for i in infos)
-
-    def pct(v, q):
-        return v[min(len(v) - 1, int(round(q / 100 * (len(v) - 1))))]
-
-    decodes = sum(Ps * (i["generations"] + 1) + 1 for i in infos)
-    d2h = sum(8 * i["n_ops"] + 20 for i in infos)
     line = {
-        "metric": METRIC, "value": decodes / wall, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": args.warmup,
-        "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int32", "data": "synthetic",
-        "config": {"workload": SVC_WORKLOAD, "requests": len(infos), "offered_rate_per_s": args.rate,
-                   "arrival_window_s": work.requests[-1].at, "generations_per_request": G,
+        "metric": METRIC, "value": burst["decodes"] / burst["wall_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": args.warmup, "ms_per_step": burst["wall_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": SVC_WORKLOAD, "requests": burst["requests"], "offered_rate_per_s": args.rate,
+                   "arrival_window_s": burst["arrival_window_s"], "generations_per_request": G,
                    "max_active": args.max_active, "service_memory_gb": args.service_memory_gb,
-                   "genes": [min(i.K for i in insts), max(i.K for i in insts)]},
-        "service": {"p50_latency_ms": pct(lat, 50), "p99_latency_ms": pct(lat, 99),
-                    "p50_queue_ms": pct(queue, 50), "p99_queue_ms": pct(queue, 99),
-                    "p50_run_ms": pct(run, 50), "p99_run_ms": pct(run, 99),
-                    "requests_per_s": len(infos) / wall, "warm_starts": sum(i["warm"] for i in infos),
-                    "peak_memory_bytes": stats["peak_bytes"], "failed": stats["failed"]},
-        "e2e": {"value": decodes / wall, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "genes": burst["genes"], "sustained_arrivals_s": args.service_seconds},
+        "service": {k: burst[k] for k in ("p50_latency_ms", "p99_latency_ms", "p50_queue_ms", "p99_queue_ms",
+                                           "p50_run_ms", "p99_run_ms", "requests_per_s", "warm_starts",
+                                           "peak_memory_bytes", "failed")},
+        "capacity_rps": capacity,
+        "sustained_rates": [{k: r[k] for k in ("fraction_of_capacity", "offered_rate_per_s", "requests",
+                                               "arrival_window_s", "requests_per_s", "p50_latency_ms",
+                                               "p99_latency_ms", "p50_queue_ms", "p99_queue_ms", "p50_run_ms",
+                                               "p99_run_ms", "warm_starts", "failed")} for r in sustained],
+        "e2e": {"value": burst["decodes"] / burst["wall_s"], "unit": UNIT, "h2d_bytes_per_step": burst["h2d"],
+                "d2h_bytes_per_step": burst["d2h"],
                 "note": "the whole run is end to end: host arrays in, host schedules out, through ffs_service_*"},
-        "gpu_launches": launches,
+        "gpu_launches": burst["launches"],
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
@@ -912,6 +943,8 @@ def main():
                          "surrogate: time-to-objective of the surrogate-assisted GA; service: Poisson "
                          "rescheduling requests through the continuous-batching service")
     ap.add_argument("--service-requests", type=int, default=48)
+    ap.add_argument("--service-seconds", type=float, default=60.0,
+                    help="service: seconds of Poisson arrivals at 0.5x and 1x the measured capacity (0: skip)")
     ap.add_argument("--svr-seeds", type=int, default=20, help="instances per ratio (static-vs-reactive)")
     ap.add_argument("--rate", type=float, default=50.0, help="service request arrival rate (1/s)")
     ap.add_argument("--max-active", type=int, default=8, help="service requests on the device at once")
