@@ -91,7 +91,7 @@ __device__ __forceinline__ void decode_into(const Tabs &T, const WarpPtrs &w, in
             __syncwarp();
         }
     }
-    if (r.status == 1) r = decode_warp<ORDER, MACH>(T, hg, H, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
+    if (r.status == 1) r = decode_warp<ORDER, MACH, false, false>(T, hg, H, w.C, w.mfree, w.inv, w.y, w.x, nullptr, nullptr, lane);
     if (lane == 0) {
         if (r.status != 0) {
             atomicOr(err, r.status == 2 ? kErrBadChromosome : kErrOverflow);

@@ -199,23 +199,8 @@ __device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0,
     return run;
 }
 
-// Draws q on [t, e) and extends the touched region to e (untouched slots read as Qmax).
-// Slots in [t, e) hold at least q, so the halfword subtraction never borrows.
-__device__ __forceinline__ void commit_power(uint16_t *h, int &hw, int t, int e, uint32_t q2,
-                                             uint32_t Q2, int lane) {
-    for (int b = (min(t, hw) & ~3) + 4 * lane; b < e; b += 128) {
-        const uint2 keep = slot_mask(b, 0, hw), sub = slot_mask(b, t, e);
-        uint2 w = make_uint2(0u, 0u);
-        if (b < hw) w = *reinterpret_cast<const uint2 *>(h + b);
-        w.x = ((w.x & keep.x) | (Q2 & ~keep.x)) - (q2 & sub.x);
-        w.y = ((w.y & keep.y) | (Q2 & ~keep.y)) - (q2 & sub.y);
-        *reinterpret_cast<uint2 *>(h + b) = w;
-    }
-    hw = max(hw, e);
-}
-
-// commit_power for a profile whose every slot below the scan bound is initialised (a
-// shared-memory slice filled with Qmax up front): no untouched slots to blend in.
+// Draws q on [t, e) of a profile initialised there.  Slots in [t, e) hold at least q, so
+// the halfword subtraction never borrows.
 __device__ __forceinline__ void commit_power_full(uint16_t *h, int t, int e, uint32_t q2, int lane) {
     for (int b = (t & ~3) + 4 * lane; b < e; b += 128) {
         const uint2 sub = slot_mask(b, t, e);
@@ -226,10 +211,24 @@ __device__ __forceinline__ void commit_power_full(uint16_t *h, int t, int e, uin
     }
 }
 
-// The common case of one op on a shared-memory profile prefilled with full headroom up to
-// its end: when [t, t+p) lies within one 128-slot step from t & ~3 and every slot of it has
-// headroom q, q is drawn there from the words the check loaded (no second read) and t is
-// returned.  Otherwise nothing changes and the returned start is where the general scan
+// Profiles filled on demand: slots below the fill mark fl (a multiple of 4) are
+// initialised, the rest not yet.  Advances fl past e in 256-slot steps, writing full
+// headroom (each lane 2 x 4 slots a step, below Hcap).  Every lane then sees every slot
+// below the new mark.
+__device__ __forceinline__ void fill_to(uint16_t *h, int &fl, int e, int Hcap, uint32_t Q2, int lane) {
+    if (fl >= e) return;
+    do {
+        const int b = fl + 4 * lane;
+        if (b < Hcap) *reinterpret_cast<uint2 *>(h + b) = make_uint2(Q2, Q2);
+        if (b + 128 < Hcap) *reinterpret_cast<uint2 *>(h + b + 128) = make_uint2(Q2, Q2);
+        fl += 256;
+    } while (fl < e);
+    __syncwarp();
+}
+
+// The common case of one op on a profile initialised up to the op's end: when [t, t+p)
+// lies within one 128-slot step from t & ~3 and every slot of it has headroom q, q is
+// drawn there from the words the check loaded (no second read) and t is returned.  Otherwise nothing changes and the returned start is where the general scan
 // may resume: one past the last slot lacking headroom (the jump its own first step would
 // make), or t when the op spans more than one step.  Only lanes whose four slots start
 // below t + p load and store.  The caller ensures t + p <= Hcap.
@@ -378,8 +377,10 @@ __device__ __forceinline__ void earliest_machine_u(const uint16_t *h, int hw, in
 // when the job still has free ops, so every op becomes available at RS + max(0, C[j]).
 //
 // FULL (shared-memory slices): the whole slice is filled first (the executing ops'
-// profile, then Qmax), so a commit has nothing to blend in.  Otherwise (global profiles
-// of the full bound) slots are initialised as the schedule first reaches them.
+// profile, then Qmax).  Otherwise (global profiles of the full bound, too large to fill per
+// decode) a fill mark runs ahead of every op's window and commit, so a decode initialises
+// only the slots its schedule reaches.  Either way scans, the one-step check and commits
+// read only initialised slots.
 // PIPE selects the software-pipelined placement loop for identical machines (for kernels
 // whose schedulers hold few warps, bound by each warp's dependency chain); without it the
 // loop does less work per op (for kernels bound by issue slots).
@@ -393,13 +394,18 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
     if (T.E0 > Hcap) return {0, 0, 1};  // executing ops alone outgrow the profile slice
     for (int j = lane; j < N; j += 32) C[j] = (T.gcnt[j] > 0 ? max(T.C0[j], T.R[j]) : T.C0[j]) - RS;
     for (int i = lane; i < T.E0; i += 32) h[i] = T.h0[i];
-    if (FULL) {  // slots E0 .. Hcap: full headroom (Hcap is a multiple of 8)
+    int fl = Hcap;  // fill mark: slots below it are initialised
+    {                // slots E0 .. Hcap (a multiple of 8) or up to the mark: full headroom
         const uint16_t Qm = (uint16_t)T.Qmax;
         for (int i = T.E0 + lane; i < min(Hcap, (T.E0 + 3) & ~3); i += 32) h[i] = Qm;
         __syncwarp();
-        for (int b = ((T.E0 + 3) & ~3) + 4 * lane; b < Hcap; b += 128)
-            *reinterpret_cast<uint2 *>(h + b) = make_uint2(Q2, Q2);
-        __syncwarp();
+        if (FULL) {
+            for (int b = ((T.E0 + 3) & ~3) + 4 * lane; b < Hcap; b += 128)
+                *reinterpret_cast<uint2 *>(h + b) = make_uint2(Q2, Q2);
+            __syncwarp();
+        } else {
+            fl = min(Hcap, (T.E0 + 3) & ~3);
+        }
     }
     // high-water mark: slots at or above it have never been drawn on (full headroom, and no
     // occupancy bits); scans stop there
@@ -464,7 +470,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
         // (the one-step case, which most ops take); when op n needs the general search
         // instead, op n+1 is chosen again from the true machine state.  The statements
         // are ordered so that op n's load and op n+1's reduction are in flight together.
-        if (MACH == kMachEarliest && FULL && PIPE) {
+        if (MACH == kMachEarliest && PIPE) {
             for (int s = 0; s < g; ++s) {
                 const int lo = T.soff[s], hi = T.soff[s + 1];
                 if (lo == hi) continue;
@@ -491,6 +497,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                     const int j = (int)(gr.x & 0xFFFFu), p = (int)(gr.y & 0xFFFFu);
                     const int e = ct + p, c = ct & ~3, b = c + 4 * lane;
                     const bool one = e <= Hcap && e - c <= 128;  // one 128-slot step suffices
+                    if (!FULL && one) fill_to(h, fl, e, Hcap, Q2, lane);
                     const bool mine = one && b < e;
                     uint2 w = make_uint2(0u, 0u);
                     if (mine) w = *reinterpret_cast<const uint2 *>(h + b);  // op n's window
@@ -527,6 +534,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                                               from, best_t, best_m, bq2);
                         ee = best_t + p;
                         if (ee > Hcap) return {0, 0, 1};
+                        if (!FULL) fill_to(h, fl, ee, Hcap, Q2, lane);
                         commit_power_full(h, best_t, ee, bq2, lane);
                         if (lane == best_m) mf = ee;
                         // op n+1 from the true machine state
@@ -594,9 +602,9 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 const int est = max(cj, 0);
                 int best_t, best_m;
                 uint32_t bq2;
-                // fast path (append placement, prefilled profile): the first candidate start
-                // is feasible and the op is drawn in the same step
-                constexpr bool kFast = FULL && !INS;
+                // fast path (append placement): the first candidate start is feasible and
+                // the op is drawn in the same step
+                constexpr bool kFast = !INS;
                 bool placed = false;
                 if (mach_gene(MACH)) {
                     best_m = x[k];
@@ -604,7 +612,10 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                     bq2 = __shfl_sync(kFull, qo2, best_m);
                     const int t0 = max(est, __shfl_sync(kFull, mf, best_m));
                     int from = t0;
-                    if (kFast && t0 + p <= Hcap) from = place_first(h, t0, p, bq2, lane, placed);
+                    if (kFast && t0 + p <= Hcap) {
+                        if (!FULL) fill_to(h, fl, t0 + p, Hcap, Q2, lane);
+                        from = place_first(h, t0, p, bq2, lane, placed);
+                    }
                     if (placed)
                         best_t = t0;
                     else
@@ -620,7 +631,10 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                         best_m = (int)(kmin & 31u);
                         const int t0 = __shfl_sync(kFull, tl, best_m), pb = __shfl_sync(kFull, p, best_m);
                         bq2 = __shfl_sync(kFull, qo2, best_m);
-                        if (t0 + pb <= Hcap) place_first(h, t0, pb, bq2, lane, placed);
+                        if (t0 + pb <= Hcap) {
+                            if (!FULL) fill_to(h, fl, t0 + pb, Hcap, Q2, lane);
+                            place_first(h, t0, pb, bq2, lane, placed);
+                        }
                         if (placed) {
                             best_t = t0;
                             p = pb;
@@ -639,7 +653,10 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                         const int t0 = (int)(kmin >> 5);
                         best_m = (int)(kmin & 31u);
                         bq2 = __shfl_sync(kFull, q2, best_m);
-                        if (t0 + p <= Hcap) from = place_first(h, t0, p, bq2, lane, placed);
+                        if (t0 + p <= Hcap) {
+                            if (!FULL) fill_to(h, fl, t0 + p, Hcap, Q2, lane);
+                            from = place_first(h, t0, p, bq2, lane, placed);
+                        }
                         if (placed) best_t = t0;
                     }
                     if (!placed)
@@ -650,11 +667,10 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                     hw = max(hw, e);
                 } else if (e > Hcap) {
                     return {0, 0, 1};
-                } else if (FULL) {
+                } else {
+                    if (!FULL) fill_to(h, fl, e, Hcap, Q2, lane);
                     commit_power_full(h, best_t, e, bq2, lane);
                     hw = max(hw, e);
-                } else {
-                    commit_power(h, hw, best_t, e, bq2, Q2, lane);
                 }
                 if (INS) commit_busy(busy + (size_t)best_m * words, best_t, e, lane);
                 else if (lane == best_m) mf = e;
@@ -717,12 +733,9 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             const int e = best_t + p;
             if (e > Hcap) return {0, 0, 1};
             const uint32_t bq2 = __shfl_sync(kFull, q2, best_m);
-            if (FULL) {
-                commit_power_full(h, best_t, e, bq2, lane);
-                hw = max(hw, e);
-            } else {
-                commit_power(h, hw, best_t, e, bq2, Q2, lane);
-            }
+            if (!FULL) fill_to(h, fl, e, Hcap, Q2, lane);
+            commit_power_full(h, best_t, e, bq2, lane);
+            hw = max(hw, e);
             __syncwarp();
             if (lane == 0) {
                 nxt[bestj] = (int16_t)(k + 1);
