@@ -1,7 +1,8 @@
 // ffs_batch.cu -- many independent rescheduling instances in one persistent launch.
 //
 // The launch is a grid of thread-block clusters.  A cluster owns one instance at a time
-// (instances are dealt to clusters largest first); CTA r of the cluster owns islands
+// and takes the next one from a queue (instances sorted largest first) when it is done;
+// CTA r of the cluster owns islands
 // r, r + CS, ... of that instance.  Each CTA stages the instance's tables into its shared
 // memory with a bulk copy and runs every requested generation for its islands: children
 // (one warp each, several per warp), then elitist replacement per island.  Islands only
@@ -112,9 +113,9 @@ __global__ void __maxnreg__(128) k_batch(BatchArgs a) {
     __shared__ long long s_red[32];
     __shared__ int s_over;
     __shared__ int s_next;  // next of this CTA's children to build in the current generation
+    __shared__ int s_item;  // rank 0: the instance its cluster took from the queue
     cg::cluster_group cluster = cg::this_cluster();
     const int CS = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
-    const int cid = blockIdx.x / CS, ncl = gridDim.x / CS;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
     char *tab = smem + 128;
     const int W = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -129,7 +130,16 @@ __global__ void __maxnreg__(128) k_batch(BatchArgs a) {
     const bool gene = mach_gene(MACH);
     // Every CTA of a cluster follows the same control flow, so the cluster barriers below
     // are reached by all of them.
-    for (int item = cid; item < a.count; item += ncl) {
+    for (;;) {
+        // rank 0 takes the cluster's next instance; every CTA reads it after the barrier
+        // (and rank 0 overwrites it only after the barrier that ends the instance)
+        if (rank == 0 && threadIdx.x == 0) s_item = atomicAdd(a.next, 1);
+        cluster.sync();
+        const int item = *cluster.map_shared_rank(&s_item, 0);
+        if (item >= a.count) {
+            cluster.sync();  // rank 0's shared memory stays until every CTA has read it
+            break;
+        }
         BatchInst *in = a.inst + a.order[item];
         const int K = in->K, nisl = in->nisl, H = in->H;
         const bool staged = stage_again(tab, in->blob, in->blob_bytes, mbar, phase, a.err);

@@ -135,7 +135,7 @@ struct BatchArgs {
     BatchInst *inst;
     int count;
     const int32_t *order;       // instances, largest work first
-    int32_t *next;              // unused (instances are dealt to clusters statically)
+    int32_t *next;              // instance queue head: zeroed before each launch
     int generations;
     int P, I, tour_k, side, migrate_every;
     uint64_t pc_thr, pm_thr, seed;

@@ -1464,6 +1464,7 @@ BatchArgs batch_args(ga_batch *b, int generations) {
 // Enqueues one persistent launch: reset the work queue, then every instance runs
 // `generations` generations (after generation 0 where it has not run yet).
 int batch_enqueue(ga_batch *b, int generations, cudaStream_t st) {
+    FFS_CUDA(cudaMemsetAsync(b->d_next, 0, sizeof(int32_t), st));
     FFS_CUDA(launch_batch(b->par.order_mode, b->par.machine_mode, batch_args(b, generations), b->grid, b->warps,
                           b->cluster, st));
     g_launches += 1;
