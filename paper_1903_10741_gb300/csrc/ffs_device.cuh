@@ -149,9 +149,71 @@ __device__ __forceinline__ int next_idle(const uint32_t *bm, int nw, int t, int 
     return t > 32 * nw ? t : 32 * nw;
 }
 
+// Earliest start r >= t0 (slots past RS) such that headroom h[r .. r+p) >= q everywhere,
+// slots at or beyond hw counting as full headroom (append placement, no occupancy).
+// State: the candidate r, with [r, v) known to have headroom q.  Each step loads the 128
+// slots from v & ~3 (4 per lane, below hw), marks the slots of [v, hw) lacking headroom,
+// and then either confirms r (its clean run reaches p slots, or hw), or takes the first
+// start right after a marked slot whose clean run reaches p.  Failing both, the start of
+// the clean run that reaches the window's end becomes the candidate (v moves to that end),
+// or the window's end itself when its last slot is marked.  Returns `limit` as soon as the
+// answer cannot be below it.  Loads stay below hw <= Hcap (Hcap a multiple of 4).
+__device__ __forceinline__ int earliest_start_win(const uint16_t *h, int hw, int t0, int p, uint32_t q2,
+                                                  int limit, int lane) {
+    int r = t0, v = t0;
+    for (;;) {
+        if (r >= limit) return limit;
+        if (v >= hw || v - r >= p) return r;
+        const int c = v & ~3, b = c + 4 * lane, wend = c + 128;
+        const bool fin = wend >= hw;  // slots past the window are full headroom
+        uint2 w = make_uint2(0u, 0u);
+        if (b < hw) w = *reinterpret_cast<const uint2 *>(h + b);
+        const uint32_t vx = ~((w.x | 0x80008000u) - q2), vy = ~((w.y | 0x80008000u) - q2);
+        // bit k: slot b + k lacks headroom q; only slots of [v, hw) count
+        unsigned nib = ((vx >> 15) & 1u) | ((vx >> 30) & 2u) | ((vy >> 13) & 4u) | ((vy >> 28) & 8u);
+        nib &= (0xFu << min(max(v - b, 0), 4)) & ~(0xFu << min(max(hw - b, 0), 4));
+        const unsigned anyv = __ballot_sync(kFull, nib != 0u);
+        if (anyv == 0u) {  // r's run reaches the window's end
+            if (fin) return r;
+            v = wend;
+            continue;
+        }
+        const int fvl = nib ? b + __ffs(nib) - 1 : INT_MAX;  // the lane's first marked slot
+        const int fv = __shfl_sync(kFull, fvl, __ffs(anyv) - 1);
+        if (fv - r >= p) return r;
+        // r fails: starts right after marked slots (a clean slot whose predecessor is marked)
+        const unsigned b3 = __ballot_sync(kFull, (nib & 8u) != 0u);
+        const unsigned later = anyv & ~((2u << lane) - 1u);  // lanes above this one with one
+        const int nfv = __shfl_sync(kFull, fvl, later ? __ffs(later) - 1 : 0);
+        const int tail = fin ? INT_MAX : wend;  // where unknown slots begin
+        const unsigned pv = (nib << 1) | (lane ? (b3 >> (lane - 1)) & 1u : 0u);
+        const unsigned st = pv & ~nib & 0xFu;
+        int best = INT_MAX, cont = INT_MAX;
+        int nv = later ? nfv : tail;  // next marked slot above the one considered
+#pragma unroll
+        for (int k = 3; k >= 0; --k) {
+            if ((nib >> k) & 1u) {
+                nv = b + k;
+            } else if ((st >> k) & 1u) {
+                if (nv - (b + k) >= p) best = b + k;
+                else if (nv == tail) cont = b + k;
+            }
+        }
+        const unsigned fb = __ballot_sync(kFull, best != INT_MAX);
+        if (fb) {
+            const int rr = __shfl_sync(kFull, best, __ffs(fb) - 1);
+            return rr < limit ? rr : limit;
+        }
+        const unsigned cb = __ballot_sync(kFull, cont != INT_MAX);
+        r = cb ? __shfl_sync(kFull, cont, __ffs(cb) - 1) : wend;
+        v = wend;
+    }
+}
+
 // Earliest start r >= t0 (slots past RS) such that headroom h[r .. r+p) >= q everywhere.
-// Slots at or beyond the high-water mark hw were never touched and hold the full peak, so
-// only [r, min(r+p, hw)) needs checking.  Each lane reads 4 consecutive slots with one
+// Append placement takes the window form above.  With insertion: slots at or beyond the
+// high-water mark hw were never touched and hold the full peak, so only
+// [r, min(r+p, hw)) needs checking.  Each lane reads 4 consecutive slots with one
 // 64-bit load (128 slots per step) and compares both halfwords of a word at once: with
 // headroom and q below 2^15, (h | 0x8000) - q keeps bit 15 set exactly when h >= q, and no
 // borrow crosses into the next halfword.  A ballot finds the last violating slot and the
@@ -163,6 +225,7 @@ __device__ __forceinline__ int next_idle(const uint32_t *bm, int nw, int t, int 
 template <bool INS = false>
 __device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0, int p, uint32_t q2,
                                               int limit, int lane, const uint32_t *bm = nullptr, int nw = 0) {
+    if (!INS) return earliest_start_win(h, hw, t0, p, q2, limit, lane);
     int run = t0;
     if (INS && run < limit) run = next_idle(bm, nw, run, lane);
     if (run >= limit) return limit;
