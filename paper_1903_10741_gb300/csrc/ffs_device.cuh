@@ -178,13 +178,13 @@ __device__ __forceinline__ int earliest_start_win(const uint16_t *h, int hw, int
             v = wend;
             continue;
         }
+        const unsigned b3 = __ballot_sync(kFull, (nib & 8u) != 0u);
         const int fvl = nib ? b + __ffs(nib) - 1 : INT_MAX;  // the lane's first marked slot
+        const unsigned later = anyv & ~((2u << lane) - 1u);  // lanes above this one with one
+        const int nfv = __shfl_sync(kFull, fvl, later ? __ffs(later) - 1 : 0);
         const int fv = __shfl_sync(kFull, fvl, __ffs(anyv) - 1);
         if (fv - r >= p) return r;
         // r fails: starts right after marked slots (a clean slot whose predecessor is marked)
-        const unsigned b3 = __ballot_sync(kFull, (nib & 8u) != 0u);
-        const unsigned later = anyv & ~((2u << lane) - 1u);  // lanes above this one with one
-        const int nfv = __shfl_sync(kFull, fvl, later ? __ffs(later) - 1 : 0);
         const int tail = fin ? INT_MAX : wend;  // where unknown slots begin
         const unsigned pv = (nib << 1) | (lane ? (b3 >> (lane - 1)) & 1u : 0u);
         const unsigned st = pv & ~nib & 0xFu;
@@ -211,9 +211,9 @@ __device__ __forceinline__ int earliest_start_win(const uint16_t *h, int hw, int
 }
 
 // Earliest start r >= t0 (slots past RS) such that headroom h[r .. r+p) >= q everywhere.
-// Append placement takes the window form above.  With insertion: slots at or beyond the
-// high-water mark hw were never touched and hold the full peak, so only
-// [r, min(r+p, hw)) needs checking.  Each lane reads 4 consecutive slots with one
+// Append placement takes the window form above unless WIN is off.  Otherwise (the jump
+// scan): slots at or beyond the high-water mark hw were never touched and hold the full
+// peak, so only [r, min(r+p, hw)) needs checking.  Each lane reads 4 consecutive slots with one
 // 64-bit load (128 slots per step) and compares both halfwords of a word at once: with
 // headroom and q below 2^15, (h | 0x8000) - q keeps bit 15 set exactly when h >= q, and no
 // borrow crosses into the next halfword.  A ballot finds the last violating slot and the
@@ -222,10 +222,10 @@ __device__ __forceinline__ int earliest_start_win(const uint16_t *h, int hw, int
 // With INS, `bm` is the machine's occupancy bitmap (nw words; bit t: busy at slot t) and a
 // slot also violates when the machine is busy there; a candidate start that falls in a
 // busy stretch moves to the stretch's end directly.  Bits are only set below hw.
-template <bool INS = false>
+template <bool INS = false, bool WIN = true>
 __device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0, int p, uint32_t q2,
                                               int limit, int lane, const uint32_t *bm = nullptr, int nw = 0) {
-    if (!INS) return earliest_start_win(h, hw, t0, p, q2, limit, lane);
+    if (!INS && WIN) return earliest_start_win(h, hw, t0, p, q2, limit, lane);
     int run = t0;
     if (INS && run < limit) run = next_idle(bm, nw, run, lane);
     if (run >= limit) return limit;
@@ -371,12 +371,13 @@ __device__ __forceinline__ void earliest_machine(const uint16_t *h, int hw, int 
 // earliest_machine when the machine that frees first is already known (m0 with start t0m
 // and power q0, the lexicographic minimum of (availability, machine)) and its scan may
 // resume at `from`.
+template <bool WIN = true>
 __device__ __forceinline__ void earliest_machine_from(const uint16_t *h, int hw, int t0, uint32_t q2, int os, int p,
                                                       int lane, int m0, int t0m, uint32_t q0, int from, int &best_t,
                                                       int &best_m, uint32_t &best_q2) {
     best_m = m0;
     best_q2 = q0;
-    best_t = earliest_start(h, hw, max(t0m, from), p, q0, INT_MAX, lane);
+    best_t = earliest_start<false, WIN>(h, hw, max(t0m, from), p, q0, INT_MAX, lane);
     if (best_t == t0m) return;  // as in earliest_machine: nothing starts earlier
     unsigned cand = __ballot_sync(kFull, lane < os && lane != best_m && t0 < best_t + (lane < best_m));
     while (cand) {
@@ -386,7 +387,7 @@ __device__ __forceinline__ void earliest_machine_from(const uint16_t *h, int hw,
         const int lim = best_t + (m < best_m ? 1 : 0);
         if (tm >= lim) continue;
         const uint32_t qm = __shfl_sync(kFull, q2, m);
-        const int t = earliest_start(h, hw, tm, p, qm, lim, lane);
+        const int t = earliest_start<false, WIN>(h, hw, tm, p, qm, lim, lane);
         if (t < lim) {
             best_t = t;
             best_m = m;
@@ -593,8 +594,9 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                             from = c + 4 * l + __shfl_sync(kFull, li, l) + 1;
                         }
                         uint32_t bq2;
-                        earliest_machine_from(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, cm, ct, cq,
-                                              from, best_t, best_m, bq2);
+                        // (few warps per scheduler: the jump scan, whose steps are shorter)
+                        earliest_machine_from<false>(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, cm,
+                                                     ct, cq, from, best_t, best_m, bq2);
                         ee = best_t + p;
                         if (ee > Hcap) return {0, 0, 1};
                         if (!FULL) fill_to(h, fl, ee, Hcap, Q2, lane);
