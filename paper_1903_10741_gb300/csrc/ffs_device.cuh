@@ -396,6 +396,43 @@ __device__ __forceinline__ void earliest_machine_from(const uint16_t *h, int hw,
     }
 }
 
+// One op of the stage-order loop on a profile initialised up to Hcap, after the one-step
+// check of its first candidate failed: the general search from the machine that frees
+// first (m0, starting at t0m with power q0), resuming at `from`, and the draw.  mf (the
+// lane's machine availability) and hw follow.  Returns the op's end, or -1 when it would
+// outgrow the slice.
+__device__ __forceinline__ int place_general(uint16_t *h, int &hw, int Hcap, int est, int &mf, uint32_t q2, int os,
+                                             int p, int lane, int m0, int t0m, uint32_t q0, int from, int &bt,
+                                             int &bm) {
+    uint32_t bq2;
+    earliest_machine_from<false>(h, hw, lane < os ? max(est, mf) : INT_MAX, q2, os, p, lane, m0, t0m, q0, from, bt,
+                                 bm, bq2);
+    const int e = bt + p;
+    if (e > Hcap) return -1;
+    commit_power_full(h, bt, e, bq2, lane);
+    if (lane == bm) mf = e;
+    hw = max(hw, e);
+    return e;
+}
+
+// One op from the true machine state: the machine that frees first (lowest index on
+// ties), its one-step check and draw, else the general search.  As place_general.
+__device__ __forceinline__ int place_single(uint16_t *h, int &hw, int Hcap, int est, int &mf, uint32_t q2, int os,
+                                            int p, int lane, int &bt, int &bm) {
+    const unsigned k = __reduce_min_sync(kFull, ((unsigned)max(est, mf) << 5) | (unsigned)lane);
+    const int t0 = (int)(k >> 5), m0 = (int)(k & 31u);
+    const uint32_t q0 = __shfl_sync(kFull, q2, m0);
+    bool placed = false;
+    int from = t0;
+    if (t0 + p <= Hcap) from = place_first(h, t0, p, q0, lane, placed);
+    if (!placed) return place_general(h, hw, Hcap, est, mf, q2, os, p, lane, m0, t0, q0, from, bt, bm);
+    bt = t0;
+    bm = m0;
+    if (lane == m0) mf = t0 + p;
+    hw = max(hw, t0 + p);
+    return t0 + p;
+}
+
 // Unrelated machines: lane m < os holds its machine's availability t0, power q2 and the
 // op's processing time p on it.  Returns the lexicographic minimum of (earliest completion
 // of a power-feasible start, machine) and that machine's p.  The machine whose completion
@@ -528,8 +565,158 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             __syncwarp();
         }
         if (__any_sync(kFull, bad)) return {0, 0, 2};
-        // Identical machines, earliest start, prefilled profile (the common case): a
-        // software pipeline.  While op n's window is loaded, checked and voted on, the
+        // Identical machines, earliest start, prefilled shared-memory profile (the common
+        // case): ops are placed two at a time.  Op A's machine and first candidate start
+        // are known on entry; op B's are chosen as if A were placed there, and op C's (the
+        // next pair's A) as if both were.  Both windows are loaded before either is drawn
+        // on, B's with A's draw subtracted where the two overlap, so the two checks, and
+        // the reductions of the next choices, are in flight together.  Most pairs pass both
+        // one-step checks; otherwise A (and then B) take the general search from the true
+        // machine state, and C's machine is chosen again.
+        if (MACH == kMachEarliest && PIPE && FULL) {
+            for (int s = 0; s < g; ++s) {
+                const int lo = T.soff[s], hi = T.soff[s + 1];
+                if (lo == hi) continue;
+                const int mo = T.moff[s], os = T.o[s];
+                constexpr int kNever = 0x07FFFFFF;  // lanes past the stage's machines never win
+                int mf = kNever;
+                uint32_t q2 = 0;
+                if (lane < os) {
+                    mf = T.mfree0[mo + lane] - RS;
+                    q2 = (uint32_t)T.q[mo + lane] * 0x10001u;
+                }
+                uint2 grA = T.grec[order[lo]];
+                int estA = max(C[grA.x & 0xFFFFu], 0);
+                uint2 grB = T.grec[order[min(lo + 1, hi - 1)]];
+                int cjB = C[grB.x & 0xFFFFu];
+                uint2 grC = T.grec[order[min(lo + 2, hi - 1)]];
+                int cjC = C[grC.x & 0xFFFFu];
+                const unsigned k0 = __reduce_min_sync(kFull, ((unsigned)max(estA, mf) << 5) | (unsigned)lane);
+                int ctA = (int)(k0 >> 5), cmA = (int)(k0 & 31u);
+                uint32_t cqA = __shfl_sync(kFull, q2, cmA);
+                int n = lo;
+#pragma unroll 2
+                for (; n + 1 < hi; n += 2) {
+                    const int jA = (int)(grA.x & 0xFFFFu), pA = (int)(grA.y & 0xFFFFu);
+                    const int jB = (int)(grB.x & 0xFFFFu), pB = (int)(grB.y & 0xFFFFu);
+                    const int eA = ctA + pA, cA = ctA & ~3, bA = cA + 4 * lane;
+                    const bool oneA = eA <= Hcap && eA - cA <= 128, mineA = oneA && bA < eA;
+                    uint2 wA = make_uint2(0u, 0u);
+                    if (mineA) wA = *reinterpret_cast<const uint2 *>(h + bA);
+                    // B as if A is placed at ctA on machine cmA
+                    const int estB = max(cjB, 0);
+                    const int mfA = lane == cmA ? eA : mf;
+                    const unsigned kB = __reduce_min_sync(kFull, ((unsigned)max(estB, mfA) << 5) | (unsigned)lane);
+                    const uint2 grD = T.grec[order[min(n + 3, hi - 1)]];
+                    const uint2 grE = T.grec[order[min(n + 4, hi - 1)]];
+                    const int ctB = (int)(kB >> 5), cmB = (int)(kB & 31u);
+                    const uint32_t cqB = __shfl_sync(kFull, q2, cmB);
+                    const int eB = ctB + pB, cB = ctB & ~3, bB = cB + 4 * lane;
+                    const bool oneB = eB <= Hcap && eB - cB <= 128, mineB = oneB && bB < eB;
+                    uint2 wB = make_uint2(0u, 0u);
+                    if (mineB) wB = *reinterpret_cast<const uint2 *>(h + bB);
+                    // C as if A and B are both placed
+                    const int estC = max(cjC, 0);
+                    const int mfB = lane == cmB ? eB : mfA;
+                    const unsigned kC = __reduce_min_sync(kFull, ((unsigned)max(estC, mfB) << 5) | (unsigned)lane);
+                    const int cjD = C[grD.x & 0xFFFFu], cjE = C[grE.x & 0xFFFFu];
+                    const uint2 mA = slot_mask(bA, ctA, eA);
+                    const uint32_t vxA = ~((wA.x | 0x80008000u) - cqA) & mA.x & 0x80008000u;
+                    const uint32_t vyA = ~((wA.y | 0x80008000u) - cqA) & mA.y & 0x80008000u;
+                    // B's words after A's draw (borrows, where A does not fit, are never used)
+                    const uint2 oB = slot_mask(bB, ctA, eA);
+                    wB.x -= cqA & oB.x;
+                    wB.y -= cqA & oB.y;
+                    const uint2 mB = slot_mask(bB, ctB, eB);
+                    const uint32_t vxB = ~((wB.x | 0x80008000u) - cqB) & mB.x & 0x80008000u;
+                    const uint32_t vyB = ~((wB.y | 0x80008000u) - cqB) & mB.y & 0x80008000u;
+                    const unsigned vmA = __ballot_sync(kFull, (vxA | vyA) != 0u);
+                    const unsigned vmB = __ballot_sync(kFull, (vxB | vyB) != 0u);
+                    int ctC = (int)(kC >> 5), cmC = (int)(kC & 31u);
+                    uint32_t cqC = __shfl_sync(kFull, q2, cmC);
+                    int tA = ctA, tB = ctB, mAo = cmA, mBo = cmB, eeA = eA, eeB = eB;
+                    const bool okA = oneA && vmA == 0u;
+                    if (okA && oneB && vmB == 0u) {  // both placed: A's words, then B's (which include A's draw)
+                        if (mineA) {
+                            wA.x -= cqA & mA.x;
+                            wA.y -= cqA & mA.y;
+                            *reinterpret_cast<uint2 *>(h + bA) = wA;
+                        }
+                        if (mineB) {
+                            wB.x -= cqB & mB.x;
+                            wB.y -= cqB & mB.y;
+                            *reinterpret_cast<uint2 *>(h + bB) = wB;
+                        }
+                        mf = mfB;
+                        hw = max(hw, max(eA, eB));
+                    } else {
+                        if (okA) {  // A placed; B searched from the machine already chosen for it
+                            if (mineA) {
+                                wA.x -= cqA & mA.x;
+                                wA.y -= cqA & mA.y;
+                                *reinterpret_cast<uint2 *>(h + bA) = wA;
+                            }
+                            mf = mfA;
+                            hw = max(hw, eA);
+                            int from = ctB;
+                            if (oneB) {  // past B's last slot short of headroom
+                                const int l = 31 - __clz(vmB);
+                                const int li = vyB ? 2 + (int)(vyB >> 31) : (int)(vxB >> 31);
+                                from = cB + 4 * l + __shfl_sync(kFull, li, l) + 1;
+                            }
+                            eeB = place_general(h, hw, Hcap, estB, mf, q2, os, pB, lane, cmB, ctB, cqB, from, tB, mBo);
+                        } else {  // A searched, then B from the true machine state
+                            int from = ctA;
+                            if (oneA) {
+                                const int l = 31 - __clz(vmA);
+                                const int li = vyA ? 2 + (int)(vyA >> 31) : (int)(vxA >> 31);
+                                from = cA + 4 * l + __shfl_sync(kFull, li, l) + 1;
+                            }
+                            eeA = place_general(h, hw, Hcap, estA, mf, q2, os, pA, lane, cmA, ctA, cqA, from, tA, mAo);
+                            if (eeA < 0) return {0, 0, 1};
+                            eeB = place_single(h, hw, Hcap, estB, mf, q2, os, pB, lane, tB, mBo);
+                        }
+                        if (eeB < 0) return {0, 0, 1};
+                        const unsigned kr = __reduce_min_sync(kFull, ((unsigned)max(estC, mf) << 5) | (unsigned)lane);
+                        ctC = (int)(kr >> 5);
+                        cmC = (int)(kr & 31u);
+                        cqC = __shfl_sync(kFull, q2, cmC);
+                    }
+                    C[jA] = eeA;  // every lane stores the same values
+                    C[jB] = eeB;
+                    if (S_out && lane == 0) {
+                        S_out[jA * g + s] = tA + RS;
+                        M_out[jA * g + s] = mAo;
+                        S_out[jB * g + s] = tB + RS;
+                        M_out[jB * g + s] = mBo;
+                    }
+                    __syncwarp();
+                    grA = grC;
+                    estA = estC;
+                    ctA = ctC;
+                    cmA = cmC;
+                    cqA = cqC;
+                    grB = grD;
+                    cjB = cjD;
+                    grC = grE;
+                    cjC = cjE;
+                }
+                if (n < hi) {  // the last op of a stage with an odd count
+                    const int jA = (int)(grA.x & 0xFFFFu);
+                    int tA, mAo;
+                    const int e = place_single(h, hw, Hcap, estA, mf, q2, os, (int)(grA.y & 0xFFFFu), lane, tA, mAo);
+                    if (e < 0) return {0, 0, 1};
+                    C[jA] = e;
+                    if (S_out && lane == 0) {
+                        S_out[jA * g + s] = tA + RS;
+                        M_out[jA * g + s] = mAo;
+                    }
+                    __syncwarp();
+                }
+            }
+        } else
+        // Identical machines, earliest start, profile filled on demand: a software
+        // pipeline.  While op n's window is loaded, checked and voted on, the
         // machine of op n+1 is chosen as if op n were placed at its first candidate start
         // (the one-step case, which most ops take); when op n needs the general search
         // instead, op n+1 is chosen again from the true machine state.  The statements
