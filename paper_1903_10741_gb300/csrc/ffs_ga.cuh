@@ -325,7 +325,8 @@ __device__ __forceinline__ void warp_extremes(const int64_t *fit, int lo, int n,
 // round trip to L2 rather than one per 32 genes.
 template <int U = 4>
 __device__ __forceinline__ void warp_copy_ind(int16_t *yd, int8_t *xd, const int16_t *ys, const int8_t *xs, int K,
-                                              int lane, int16_t *yd2 = nullptr, int8_t *xd2 = nullptr) {
+                                              int lane, int16_t *yd2 = nullptr, int8_t *xd2 = nullptr,
+                                              int16_t *yd3 = nullptr, int8_t *xd3 = nullptr) {
 #pragma unroll 1
     for (int k0 = lane; k0 < K; k0 += 32 * U) {
         const int n = K - k0;  // genes left from this lane's first one
@@ -343,20 +344,146 @@ __device__ __forceinline__ void warp_copy_ind(int16_t *yd, int8_t *xd, const int
                     yd2[k0 + 32 * u] = (int16_t)(v[u] & 0xFFFFu);
                     xd2[k0 + 32 * u] = (int8_t)(v[u] >> 16);
                 }
+                if (yd3) {
+                    yd3[k0 + 32 * u] = (int16_t)(v[u] & 0xFFFFu);
+                    xd3[k0 + 32 * u] = (int8_t)(v[u] >> 16);
+                }
             }
     }
+}
+
+// Two independent copies (src -> dst, src2 -> dst2, rows that do not overlap) in the same
+// chunks: every lane loads its share of both before storing any.
+template <int U = 4>
+__device__ __forceinline__ void warp_copy_two(int16_t *yd, int8_t *xd, const int16_t *ys, const int8_t *xs,
+                                              int16_t *yd2, int8_t *xd2, const int16_t *ys2, const int8_t *xs2,
+                                              int K, int lane) {
+#pragma unroll 1
+    for (int k0 = lane; k0 < K; k0 += 32 * U) {
+        const int n = K - k0;
+        uint32_t v[U], w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (32 * u < n) {
+                v[u] = (uint16_t)__ldcg(ys + k0 + 32 * u) | ((uint32_t)(uint8_t)__ldcg(xs + k0 + 32 * u) << 16);
+                w[u] = (uint16_t)__ldcg(ys2 + k0 + 32 * u) | ((uint32_t)(uint8_t)__ldcg(xs2 + k0 + 32 * u) << 16);
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (32 * u < n) {
+                yd[k0 + 32 * u] = (int16_t)(v[u] & 0xFFFFu);
+                xd[k0 + 32 * u] = (int8_t)(v[u] >> 16);
+                yd2[k0 + 32 * u] = (int16_t)(w[u] & 0xFFFFu);
+                xd2[k0 + 32 * u] = (int8_t)(w[u] >> 16);
+            }
+    }
+}
+
+// Best (largest fitness, lowest index) and worst (smallest fitness, lowest index) of an
+// island of at most 64 held in registers: lane l has slots l (f0, o0) and l + 32 (f1, o1),
+// lanes past the island LLONG_MIN / LLONG_MAX-free placeholders excluded by `h0`, `h1`.
+// Returns the indices (island-relative) and the best's fitness and objective.
+__device__ __forceinline__ void reg_extremes(long long f0, long long o0, bool h0, long long f1, long long o1, bool h1,
+                                             int lane, int &best, int &worst, long long &bfit, long long &bobj) {
+    long long bf = LLONG_MIN, wf = LLONG_MAX;
+    int bi = INT_MAX, wi = INT_MAX;
+    if (h0) { bf = f0; bi = lane; wf = f0; wi = lane; }
+    if (h1) {
+        if (fitter(f1, lane + 32, bf, bi)) { bf = f1; bi = lane + 32; }
+        if (f1 < wf) { wf = f1; wi = lane + 32; }
+    }
+    warp_best(bf, bi);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const long long of = __shfl_xor_sync(kFull, wf, off);
+        const int oi = __shfl_xor_sync(kFull, wi, off);
+        if (of < wf || (of == wf && oi < wi)) { wf = of; wi = oi; }
+    }
+    best = bi;
+    worst = wi;
+    bfit = bf;
+    // the best's objective from the lane that holds it
+    const long long mine = (bi >> 5) ? o1 : o0;
+    bobj = __shfl_sync(kFull, mine, bi & 31);
 }
 
 // Elitist replacement of island `isl` by one warp (Sec. 4.4): the best-ever individual is
 // updated if a child is strictly fitter, then overwrites the worst child.  With `migrate`,
 // the island's best and worst after replacement are recorded for the ring exchange.  U:
-// genes per lane per copy chunk.
-template <int U = 4>
+// genes per lane per copy chunk.  With REG (kernels with registers to spare), islands of
+// up to 64 are read once (fitness, objectives and the best-ever record in one round trip)
+// and the state after replacement is derived in registers.
+template <int U = 4, bool REG = false>
 __device__ __forceinline__ void island_replace(int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit, int16_t *bY,
                                                int8_t *bX, int64_t *bobj, int64_t *bfit, int isl, int I, int K,
                                                bool migrate, int16_t *mY, int8_t *mX, int64_t *mobj, int64_t *mfit,
                                                int32_t *mw, int lane) {
     const int lo = isl * I;
+    int16_t *bYi = bY + (size_t)isl * K;
+    int8_t *bXi = bX + (size_t)isl * K;
+    if (REG && I <= 64) {
+        const bool h0 = lane < I, h1 = lane + 32 < I;
+        long long f0 = 0, f1 = 0, o0 = 0, o1 = 0;
+        if (h0) {
+            f0 = __ldcg(fit + lo + lane);
+            o0 = __ldcg(obj + lo + lane);
+        }
+        if (h1) {
+            f1 = __ldcg(fit + lo + lane + 32);
+            o1 = __ldcg(obj + lo + lane + 32);
+        }
+        const long long bf0 = __ldcg(bfit + isl), bo0 = __ldcg(bobj + isl);
+        int best, worst;
+        long long fb, ob;
+        reg_extremes(f0, o0, h0, f1, o1, h1, lane, best, worst, fb, ob);
+        const bool better = fb > bf0;
+        const long long eobj = better ? ob : bo0, efit = better ? fb : bf0;
+        const int16_t *ys = better ? Y + (size_t)(lo + best) * K : bYi;
+        const int8_t *xs = better ? X + (size_t)(lo + best) * K : bXi;
+        int16_t *yw = Y + (size_t)(lo + worst) * K;
+        int8_t *xw = X + (size_t)(lo + worst) * K;
+        // the island after replacement: the worst slot holds the elite, whose fitness is at
+        // least every child's, so its best is the lower of `worst` and `best` when the two
+        // fitnesses tie, else `worst`; its worst is the least of the other slots, unless
+        // none is below the elite
+        const int b2 = efit == fb ? min(worst, best) : worst;
+        const bool same = b2 == worst || better;  // the migrant's row is the elite's
+        if (migrate) {
+            long long wf = LLONG_MAX;
+            int wi = INT_MAX;
+            if (h0 && lane != worst) { wf = f0; wi = lane; }
+            if (h1 && lane + 32 != worst && f1 < wf) { wf = f1; wi = lane + 32; }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                const long long of = __shfl_xor_sync(kFull, wf, off);
+                const int oi = __shfl_xor_sync(kFull, wi, off);
+                if (of < wf || (of == wf && oi < wi)) { wf = of; wi = oi; }
+            }
+            const int w2 = wf < efit || (wf == efit && wi < worst) ? wi : worst;
+            if (lane == 0) {
+                mobj[isl] = b2 == worst ? eobj : ob;
+                mfit[isl] = efit;
+                mw[isl] = lo + w2;
+            }
+        }
+        if (lane == 0) {
+            if (better) {
+                bobj[isl] = eobj;
+                bfit[isl] = efit;
+            }
+            obj[lo + worst] = eobj;
+            fit[lo + worst] = efit;
+        }
+        if (better)
+            warp_copy_ind<U>(yw, xw, ys, xs, K, lane, bYi, bXi);
+        else
+            warp_copy_ind<U>(yw, xw, ys, xs, K, lane);
+        if (migrate)  // the migrant: the elite's row, or a child tied with it at a lower index
+            warp_copy_ind<U>(mY + (size_t)isl * K, mX + (size_t)isl * K, same ? ys : Y + (size_t)(lo + b2) * K,
+                             same ? xs : X + (size_t)(lo + b2) * K, K, lane);
+        __syncwarp();
+        return;
+    }
     int best, worst;
     long long fb;
     warp_extremes(fit, lo, I, lane, best, worst, fb);
@@ -367,8 +494,6 @@ __device__ __forceinline__ void island_replace(int16_t *Y, int8_t *X, int64_t *o
     long long eobj = 0;
     if (lane == 0) eobj = better ? __ldcg(obj + best) : bobj[isl];
     const long long efit = better ? fb : bf0;
-    int16_t *bYi = bY + (size_t)isl * K;
-    int8_t *bXi = bX + (size_t)isl * K;
     if (better)
         warp_copy_ind<U>(Y + (size_t)worst * K, X + (size_t)worst * K, Y + (size_t)best * K, X + (size_t)best * K,
                          K, lane, bYi, bXi);

@@ -148,7 +148,7 @@ __device__ void island_finish(const Args &a, int isl, int nx, int gen, int lane)
     int8_t *X = a.X[nx];
     int64_t *obj = a.obj[nx], *fit = a.fit[nx];
     const bool migrate = a.migrate_every > 0 && gen % a.migrate_every == 0 && a.nisl > 1;
-    island_replace<kTailU>(Y, X, obj, fit, a.bY, a.bX, a.bobj, a.bfit, isl, a.I, K, migrate, a.mY, a.mX, a.mobj,
+    island_replace<kTailU, true>(Y, X, obj, fit, a.bY, a.bX, a.bobj, a.bfit, isl, a.I, K, migrate, a.mY, a.mX, a.mobj,
                            a.mfit, a.mw, lane);
     if (lane == 0) a.isl_done[isl] = 0;
     // within a chain the counter is left as it was; islands meet only to migrate
@@ -172,11 +172,11 @@ __device__ void island_finish(const Args &a, int isl, int nx, int gen, int lane)
 // ---------------------------------------------------------------- GA: one generation
 // Selection -> paired crossover + correction -> mutation -> decode, one child per warp.
 // Each warp recomputes both parents of its pair from the counter-based stream, so the
-// children of a pair are built independently by two warps.  An explicit cap of 128
-// registers (2 CTAs of 128 threads per SM are set by shared memory anyway) keeps every
-// variant free of spills.
+// children of a pair are built independently by two warps.  An explicit cap of 168
+// registers keeps every variant free of spills; shared memory sets 2 CTAs of 128 threads
+// per SM anyway, which the register file holds at that cap.
 template <int ORDER, int MACH>
-__global__ void __maxnreg__(128) k_ga_generation(GenArgs a) {
+__global__ void __maxnreg__(168) k_ga_generation(GenArgs a) {
     extern __shared__ __align__(128) char smem[];
     char *tab = smem + 128;
     if (!stage_tables(tab, a.blob, a.blob_bytes, reinterpret_cast<uint64_t *>(smem), a.err)) return;
