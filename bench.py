@@ -50,7 +50,7 @@ SORT_PER_DECODE = 1936.25
 # DRAM bytes (read + write) of one generation-kernel launch from the ncu capture of the
 # current kernel (dram__bytes_read.sum + dram__bytes_write.sum, initial solve); None once
 # the kernel changes until it is captured again.
-TRAFFIC_BYTES = 428544
+TRAFFIC_BYTES = 440320
 
 
 def work_per_decode() -> float:

@@ -11,6 +11,10 @@
 namespace edffs {
 
 constexpr unsigned kFull = 0xffffffffu;
+// Ops placed per step of the stage-order loop on prefilled shared-memory profiles (2
+// measured fastest on the dynamic job: 15.36 M decodes/s, against 14.17 M with 3 and
+// 13.31 M with 4).
+constexpr int kPlaceGroup = 2;
 constexpr int kOrderTopo = 0, kOrderStage = 1;
 constexpr int kMachGene = 0, kMachEarliest = 1;
 // Kernel-side machine modes add the unrelated-machine variants (per-gene p and q per
@@ -566,14 +570,19 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
         }
         if (__any_sync(kFull, bad)) return {0, 0, 2};
         // Identical machines, earliest start, prefilled shared-memory profile (the common
-        // case): ops are placed two at a time.  Op A's machine and first candidate start
-        // are known on entry; op B's are chosen as if A were placed there, and op C's (the
-        // next pair's A) as if both were.  Both windows are loaded before either is drawn
-        // on, B's with A's draw subtracted where the two overlap, so the two checks, and
-        // the reductions of the next choices, are in flight together.  Most pairs pass both
-        // one-step checks; otherwise A (and then B) take the general search from the true
-        // machine state, and C's machine is chosen again.
+        // case): ops are placed G = kPlaceGroup at a time.  The group's first op's machine
+        // and first candidate start are known on entry; each later op's are chosen (one
+        // reduction) as if the ops before it in the group were placed at theirs, and the
+        // next group's first op's as if all were.  Every window of the group is loaded
+        // before any is drawn on, each with the earlier ops' draws subtracted where they
+        // overlap, so the one-step checks and the reductions are in flight together.  When
+        // every check passes the words are stored in order (a later op's words include the
+        // earlier draws).  Otherwise the ops before the first failure are placed as checked,
+        // the failing one takes the general search from its machine, past its last slot
+        // short of headroom, and the rest are placed one at a time from the true machine
+        // state; the next group's first machine is then chosen again.
         if (MACH == kMachEarliest && PIPE && FULL) {
+            constexpr int G = kPlaceGroup;
             for (int s = 0; s < g; ++s) {
                 const int lo = T.soff[s], hi = T.soff[s + 1];
                 if (lo == hi) continue;
@@ -585,133 +594,162 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                     mf = T.mfree0[mo + lane] - RS;
                     q2 = (uint32_t)T.q[mo + lane] * 0x10001u;
                 }
-                uint2 grA = T.grec[order[lo]];
-                int estA = max(C[grA.x & 0xFFFFu], 0);
-                uint2 grB = T.grec[order[min(lo + 1, hi - 1)]];
-                int cjB = C[grB.x & 0xFFFFu];
-                uint2 grC = T.grec[order[min(lo + 2, hi - 1)]];
-                int cjC = C[grC.x & 0xFFFFu];
-                const unsigned k0 = __reduce_min_sync(kFull, ((unsigned)max(estA, mf) << 5) | (unsigned)lane);
-                int ctA = (int)(k0 >> 5), cmA = (int)(k0 & 31u);
-                uint32_t cqA = __shfl_sync(kFull, q2, cmA);
+                // records of ops n .. n+G (this group and the next group's first op), and the
+                // job completions before them
+                uint2 gr[G + 1];
+                int cj[G + 1];
+#pragma unroll
+                for (int u = 0; u <= G; ++u) {
+                    gr[u] = T.grec[order[min(lo + u, hi - 1)]];
+                    cj[u] = C[gr[u].x & 0xFFFFu];
+                }
+                int est0 = max(cj[0], 0);
+                const unsigned k0 = __reduce_min_sync(kFull, ((unsigned)max(est0, mf) << 5) | (unsigned)lane);
+                int ct0 = (int)(k0 >> 5), cm0 = (int)(k0 & 31u);
+                uint32_t cq0 = __shfl_sync(kFull, q2, cm0);
                 int n = lo;
 #pragma unroll 2
-                for (; n + 1 < hi; n += 2) {
-                    const int jA = (int)(grA.x & 0xFFFFu), pA = (int)(grA.y & 0xFFFFu);
-                    const int jB = (int)(grB.x & 0xFFFFu), pB = (int)(grB.y & 0xFFFFu);
-                    const int eA = ctA + pA, cA = ctA & ~3, bA = cA + 4 * lane;
-                    const bool oneA = eA <= Hcap && eA - cA <= 128, mineA = oneA && bA < eA;
-                    uint2 wA = make_uint2(0u, 0u);
-                    if (mineA) wA = *reinterpret_cast<const uint2 *>(h + bA);
-                    // B as if A is placed at ctA on machine cmA
-                    const int estB = max(cjB, 0);
-                    const int mfA = lane == cmA ? eA : mf;
-                    const unsigned kB = __reduce_min_sync(kFull, ((unsigned)max(estB, mfA) << 5) | (unsigned)lane);
-                    const uint2 grD = T.grec[order[min(n + 3, hi - 1)]];
-                    const uint2 grE = T.grec[order[min(n + 4, hi - 1)]];
-                    const int ctB = (int)(kB >> 5), cmB = (int)(kB & 31u);
-                    const uint32_t cqB = __shfl_sync(kFull, q2, cmB);
-                    const int eB = ctB + pB, cB = ctB & ~3, bB = cB + 4 * lane;
-                    const bool oneB = eB <= Hcap && eB - cB <= 128, mineB = oneB && bB < eB;
-                    uint2 wB = make_uint2(0u, 0u);
-                    if (mineB) wB = *reinterpret_cast<const uint2 *>(h + bB);
-                    // C as if A and B are both placed
-                    const int estC = max(cjC, 0);
-                    const int mfB = lane == cmB ? eB : mfA;
-                    const unsigned kC = __reduce_min_sync(kFull, ((unsigned)max(estC, mfB) << 5) | (unsigned)lane);
-                    const int cjD = C[grD.x & 0xFFFFu], cjE = C[grE.x & 0xFFFFu];
-                    const uint2 mA = slot_mask(bA, ctA, eA);
-                    const uint32_t vxA = ~((wA.x | 0x80008000u) - cqA) & mA.x & 0x80008000u;
-                    const uint32_t vyA = ~((wA.y | 0x80008000u) - cqA) & mA.y & 0x80008000u;
-                    // B's words after A's draw (borrows, where A does not fit, are never used)
-                    const uint2 oB = slot_mask(bB, ctA, eA);
-                    wB.x -= cqA & oB.x;
-                    wB.y -= cqA & oB.y;
-                    const uint2 mB = slot_mask(bB, ctB, eB);
-                    const uint32_t vxB = ~((wB.x | 0x80008000u) - cqB) & mB.x & 0x80008000u;
-                    const uint32_t vyB = ~((wB.y | 0x80008000u) - cqB) & mB.y & 0x80008000u;
-                    const unsigned vmA = __ballot_sync(kFull, (vxA | vyA) != 0u);
-                    const unsigned vmB = __ballot_sync(kFull, (vxB | vyB) != 0u);
-                    int ctC = (int)(kC >> 5), cmC = (int)(kC & 31u);
-                    uint32_t cqC = __shfl_sync(kFull, q2, cmC);
-                    int tA = ctA, tB = ctB, mAo = cmA, mBo = cmB, eeA = eA, eeB = eB;
-                    const bool okA = oneA && vmA == 0u;
-                    if (okA && oneB && vmB == 0u) {  // both placed: A's words, then B's (which include A's draw)
-                        if (mineA) {
-                            wA.x -= cqA & mA.x;
-                            wA.y -= cqA & mA.y;
-                            *reinterpret_cast<uint2 *>(h + bA) = wA;
+                for (; n + G - 1 < hi; n += G) {
+                    int ct[G + 1], cm[G + 1], est[G + 1], e[G], cc[G], b[G], p[G], jj[G];
+                    uint32_t cq[G + 1];
+                    bool one[G], mine[G];
+                    uint2 w[G], gn[G];
+                    ct[0] = ct0;
+                    cm[0] = cm0;
+                    cq[0] = cq0;
+                    est[0] = est0;
+                    int mfc = mf;  // the machines as if ops 0 .. u of the group are placed
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+                        jj[u] = (int)(gr[u].x & 0xFFFFu);
+                        p[u] = (int)(gr[u].y & 0xFFFFu);
+                        e[u] = ct[u] + p[u];
+                        cc[u] = ct[u] & ~3;
+                        b[u] = cc[u] + 4 * lane;
+                        one[u] = e[u] <= Hcap && e[u] - cc[u] <= 128;
+                        mine[u] = one[u] && b[u] < e[u];
+                        w[u] = make_uint2(0u, 0u);
+                        if (mine[u]) w[u] = *reinterpret_cast<const uint2 *>(h + b[u]);
+                        mfc = lane == cm[u] ? e[u] : mfc;
+                        est[u + 1] = max(cj[u + 1], 0);
+                        const unsigned k = __reduce_min_sync(kFull, ((unsigned)max(est[u + 1], mfc) << 5) | (unsigned)lane);
+                        gn[u] = T.grec[order[min(n + G + 1 + u, hi - 1)]];
+                        ct[u + 1] = (int)(k >> 5);
+                        cm[u + 1] = (int)(k & 31u);
+                        cq[u + 1] = __shfl_sync(kFull, q2, cm[u + 1]);
+                    }
+                    int cjn[G];
+#pragma unroll
+                    for (int u = 0; u < G; ++u) cjn[u] = C[gn[u].x & 0xFFFFu];
+                    uint2 m[G];
+                    uint32_t vx[G], vy[G];
+                    unsigned vm[G];
+                    bool all = true;
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+#pragma unroll
+                        for (int v = 0; v < u; ++v) {  // earlier ops' draws where they overlap
+                            const uint2 o = slot_mask(b[u], ct[v], e[v]);
+                            w[u].x -= cq[v] & o.x;
+                            w[u].y -= cq[v] & o.y;
                         }
-                        if (mineB) {
-                            wB.x -= cqB & mB.x;
-                            wB.y -= cqB & mB.y;
-                            *reinterpret_cast<uint2 *>(h + bB) = wB;
+                        m[u] = slot_mask(b[u], ct[u], e[u]);
+                        vx[u] = ~((w[u].x | 0x80008000u) - cq[u]) & m[u].x & 0x80008000u;
+                        vy[u] = ~((w[u].y | 0x80008000u) - cq[u]) & m[u].y & 0x80008000u;
+                        vm[u] = __ballot_sync(kFull, (vx[u] | vy[u]) != 0u);
+                        all = all && one[u] && vm[u] == 0u;
+                    }
+                    int tt[G], mm[G], ee[G];
+                    if (all) {  // every op placed: their words in order (later ones include earlier draws)
+#pragma unroll
+                        for (int u = 0; u < G; ++u) {
+                            if (mine[u]) {
+                                w[u].x -= cq[u] & m[u].x;
+                                w[u].y -= cq[u] & m[u].y;
+                                *reinterpret_cast<uint2 *>(h + b[u]) = w[u];
+                            }
+                            tt[u] = ct[u];
+                            mm[u] = cm[u];
+                            ee[u] = e[u];
+                            hw = max(hw, e[u]);
                         }
-                        mf = mfB;
-                        hw = max(hw, max(eA, eB));
+                        mf = mfc;
                     } else {
-                        if (okA) {  // A placed; B searched from the machine already chosen for it
-                            if (mineA) {
-                                wA.x -= cqA & mA.x;
-                                wA.y -= cqA & mA.y;
-                                *reinterpret_cast<uint2 *>(h + bA) = wA;
+                        // ops before the first failure placed as checked; the first failure
+                        // searched from its machine, past its last slot short of headroom;
+                        // the rest one at a time from the true machine state
+                        bool placed = true;
+#pragma unroll
+                        for (int u = 0; u < G; ++u) {
+                            if (placed && one[u] && vm[u] == 0u) {
+                                if (mine[u]) {
+                                    w[u].x -= cq[u] & m[u].x;
+                                    w[u].y -= cq[u] & m[u].y;
+                                    *reinterpret_cast<uint2 *>(h + b[u]) = w[u];
+                                }
+                                if (lane == cm[u]) mf = e[u];
+                                hw = max(hw, e[u]);
+                                tt[u] = ct[u];
+                                mm[u] = cm[u];
+                                ee[u] = e[u];
+                            } else if (placed) {
+                                int from = ct[u];
+                                if (one[u]) {
+                                    const int l = 31 - __clz(vm[u]);
+                                    const int li = vy[u] ? 2 + (int)(vy[u] >> 31) : (int)(vx[u] >> 31);
+                                    from = cc[u] + 4 * l + __shfl_sync(kFull, li, l) + 1;
+                                }
+                                ee[u] = place_general(h, hw, Hcap, est[u], mf, q2, os, p[u], lane, cm[u], ct[u], cq[u],
+                                                      from, tt[u], mm[u]);
+                                if (ee[u] < 0) return {0, 0, 1};
+                                placed = false;
+                            } else {
+                                ee[u] = place_single(h, hw, Hcap, est[u], mf, q2, os, p[u], lane, tt[u], mm[u]);
+                                if (ee[u] < 0) return {0, 0, 1};
                             }
-                            mf = mfA;
-                            hw = max(hw, eA);
-                            int from = ctB;
-                            if (oneB) {  // past B's last slot short of headroom
-                                const int l = 31 - __clz(vmB);
-                                const int li = vyB ? 2 + (int)(vyB >> 31) : (int)(vxB >> 31);
-                                from = cB + 4 * l + __shfl_sync(kFull, li, l) + 1;
-                            }
-                            eeB = place_general(h, hw, Hcap, estB, mf, q2, os, pB, lane, cmB, ctB, cqB, from, tB, mBo);
-                        } else {  // A searched, then B from the true machine state
-                            int from = ctA;
-                            if (oneA) {
-                                const int l = 31 - __clz(vmA);
-                                const int li = vyA ? 2 + (int)(vyA >> 31) : (int)(vxA >> 31);
-                                from = cA + 4 * l + __shfl_sync(kFull, li, l) + 1;
-                            }
-                            eeA = place_general(h, hw, Hcap, estA, mf, q2, os, pA, lane, cmA, ctA, cqA, from, tA, mAo);
-                            if (eeA < 0) return {0, 0, 1};
-                            eeB = place_single(h, hw, Hcap, estB, mf, q2, os, pB, lane, tB, mBo);
                         }
-                        if (eeB < 0) return {0, 0, 1};
-                        const unsigned kr = __reduce_min_sync(kFull, ((unsigned)max(estC, mf) << 5) | (unsigned)lane);
-                        ctC = (int)(kr >> 5);
-                        cmC = (int)(kr & 31u);
-                        cqC = __shfl_sync(kFull, q2, cmC);
+                        const unsigned kr = __reduce_min_sync(kFull, ((unsigned)max(est[G], mf) << 5) | (unsigned)lane);
+                        ct[G] = (int)(kr >> 5);
+                        cm[G] = (int)(kr & 31u);
+                        cq[G] = __shfl_sync(kFull, q2, cm[G]);
                     }
-                    C[jA] = eeA;  // every lane stores the same values
-                    C[jB] = eeB;
+#pragma unroll
+                    for (int u = 0; u < G; ++u) C[jj[u]] = ee[u];  // every lane stores the same values
                     if (S_out && lane == 0) {
-                        S_out[jA * g + s] = tA + RS;
-                        M_out[jA * g + s] = mAo;
-                        S_out[jB * g + s] = tB + RS;
-                        M_out[jB * g + s] = mBo;
+#pragma unroll
+                        for (int u = 0; u < G; ++u) {
+                            S_out[jj[u] * g + s] = tt[u] + RS;
+                            M_out[jj[u] * g + s] = mm[u];
+                        }
                     }
                     __syncwarp();
-                    grA = grC;
-                    estA = estC;
-                    ctA = ctC;
-                    cmA = cmC;
-                    cqA = cqC;
-                    grB = grD;
-                    cjB = cjD;
-                    grC = grE;
-                    cjC = cjE;
+                    gr[0] = gr[G];
+                    est0 = est[G];
+                    ct0 = ct[G];
+                    cm0 = cm[G];
+                    cq0 = cq[G];
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+                        gr[u + 1] = gn[u];
+                        cj[u + 1] = cjn[u];
+                    }
                 }
-                if (n < hi) {  // the last op of a stage with an odd count
-                    const int jA = (int)(grA.x & 0xFFFFu);
-                    int tA, mAo;
-                    const int e = place_single(h, hw, Hcap, estA, mf, q2, os, (int)(grA.y & 0xFFFFu), lane, tA, mAo);
-                    if (e < 0) return {0, 0, 1};
-                    C[jA] = e;
-                    if (S_out && lane == 0) {
-                        S_out[jA * g + s] = tA + RS;
-                        M_out[jA * g + s] = mAo;
+                // the stage's last ops when its count is not a multiple of G
+#pragma unroll
+                for (int u = 0; u + 1 < G; ++u) {
+                    if (n + u < hi) {
+                        const int ju = (int)(gr[u].x & 0xFFFFu);
+                        int tu, mu;
+                        const int e1 = place_single(h, hw, Hcap, u ? max(cj[u], 0) : est0, mf, q2, os,
+                                                    (int)(gr[u].y & 0xFFFFu), lane, tu, mu);
+                        if (e1 < 0) return {0, 0, 1};
+                        C[ju] = e1;
+                        if (S_out && lane == 0) {
+                            S_out[ju * g + s] = tu + RS;
+                            M_out[ju * g + s] = mu;
+                        }
+                        __syncwarp();
                     }
-                    __syncwarp();
                 }
             }
         } else
