@@ -45,6 +45,7 @@ extern "C" {
 #define FFS_E_ADMISSION  -6   /* the service cannot admit the request                    */
 #define FFS_E_STATE      -7   /* call not valid in the handle's current state            */
 #define FFS_E_DEVICE     -8   /* a kernel reported an internal error (bad chromosome, overflow) */
+#define FFS_E_STOPPED    -9   /* a batched run ended early on a stop request (ga_batch_stop)  */
 
 /* ---- decoding modes (Sec. 4.3) */
 #define FFS_ORDER_TOPO      0  /* Alg. 1: largest y among the next free op of every job   */
@@ -222,6 +223,19 @@ int ga_batch_destroy(ga_batch *batch);
  * array of `count` results, caller-allocated, start/machine optional), each instance's
  * best-ever schedule is decoded, returned and committed to its instance. */
 int ga_batch_run(ga_batch *batch, int32_t generations, ffs_result *best);
+
+/* Asks a ga_batch_run in progress on `batch` (called from another host thread) to end
+ * early, for a caller that must take the GPU back before a long persistent launch would
+ * finish (a deadline, a shutdown).  The paper has no counterpart.  The request is one word
+ * of host-mapped memory that each cluster of the launch reads at the start of every
+ * generation; a cluster that sees it finishes no further generation and takes no further
+ * instance.  Every instance is therefore left after a whole number of generations, in the
+ * state a run of exactly that many generations gives (ga_batch_read returns each one's
+ * count; instances may differ).  The run then returns FFS_E_STOPPED without decoding best
+ * schedules.  A request made while no run is in progress, or one that arrives after every
+ * cluster has finished, has no effect: each ga_batch_run clears it when it starts, and
+ * ga_batch_tune's trials do not read it.  FFS_E_ARG for a NULL batch. */
+int ga_batch_stop(ga_batch *batch);
 
 /* As ga_population_read, for instance `index` of the batch. */
 int ga_batch_read(ga_batch *batch, int32_t index, int16_t *Y, int8_t *X, int64_t *obj, int64_t *fit,

@@ -114,6 +114,7 @@ __global__ void __maxnreg__(128) k_batch(BatchArgs a) {
     __shared__ int s_over;
     __shared__ int s_next;  // next of this CTA's children to build in the current generation
     __shared__ int s_item;  // rank 0: the instance its cluster took from the queue
+    __shared__ int s_stop[2];  // rank 0: the stop word as read at a generation's start (by parity)
     cg::cluster_group cluster = cg::this_cluster();
     const int CS = (int)cluster.num_blocks(), rank = (int)cluster.block_rank();
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
@@ -223,7 +224,16 @@ __global__ void __maxnreg__(128) k_batch(BatchArgs a) {
             __syncthreads();
         }
 
+        bool stopped = false;
         for (int step = 0; step < a.generations; ++step) {
+            if (a.stop) {  // a stop request ends the cluster at this generation boundary
+                if (rank == 0 && threadIdx.x == 0) s_stop[step & 1] = *a.stop != 0;
+                cluster.sync();  // every CTA acts on rank 0's reading
+                if (*cluster.map_shared_rank(&s_stop[step & 1], 0)) {
+                    stopped = true;
+                    break;
+                }
+            }
             const int cur = gen & 1, nx = cur ^ 1;
             const uint32_t g1 = (uint32_t)gen + 1;
             const bool migrate = a.migrate_every > 0 && (int)g1 % a.migrate_every == 0 && nisl > 1;
@@ -271,8 +281,10 @@ __global__ void __maxnreg__(128) k_batch(BatchArgs a) {
         if (rank == 0 && threadIdx.x == 0) {
             in->gen = gen;
             in->emax = emax;
+            if (stopped) *a.stop = 2;
         }
         cluster.sync();
+        if (stopped) break;  // no further instance (the whole cluster decided alike)
     }
 }
 

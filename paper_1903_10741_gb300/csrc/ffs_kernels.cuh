@@ -143,6 +143,9 @@ struct BatchArgs {
     uint16_t *gscratch;         // Hmax slots per (CTA, warp)
     int Hmax;
     int32_t *err;
+    // host-mapped stop word: nonzero asks the launch to end at a generation boundary; a
+    // cluster that ends early sets it to 2
+    volatile int32_t *stop;
 };
 
 cudaError_t prepare_batch(int order, int mach, int smem_bytes);

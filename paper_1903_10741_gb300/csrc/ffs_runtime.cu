@@ -335,6 +335,7 @@ const char *ffs_strerror(int code) {
         case FFS_E_ADMISSION: return "request not admitted";
         case FFS_E_STATE: return "call not valid in the current state";
         case FFS_E_DEVICE: return "kernel reported an error";
+        case FFS_E_STOPPED: return "batched run stopped early on request";
         default: return "unknown status";
     }
 }
@@ -1380,9 +1381,13 @@ struct ga_batch {
     cudaGraphExec_t graph = nullptr;
     int graph_gens = -1;
     float tuned_ms = 0.f;
+    // stop word in host-mapped memory (ga_batch_stop writes 1; a launch that ended early 2)
+    volatile int32_t *stop_host = nullptr;
+    int32_t *stop_dev = nullptr;
 
     ~ga_batch() {
         if (graph) cudaGraphExecDestroy(graph);
+        if (stop_host) cudaFreeHost(const_cast<int32_t *>(stop_host));
         dfree(arena);
         dfree(shadow);
         dfree(d_inst);
@@ -1439,7 +1444,8 @@ int batch_config(ga_batch *b, int warps, int smem, int cluster) {
     return FFS_OK;
 }
 
-BatchArgs batch_args(ga_batch *b, int generations) {
+// stoppable: the launch reads the stop word (runs); generation 0 and tuner trials do not.
+BatchArgs batch_args(ga_batch *b, int generations, bool stoppable) {
     BatchArgs a{};
     a.inst = b->d_inst;
     a.count = b->count;
@@ -1458,14 +1464,15 @@ BatchArgs batch_args(ga_batch *b, int generations) {
     a.gscratch = b->gscratch;
     a.Hmax = b->Hmax;
     a.err = b->d_err;
+    a.stop = stoppable ? b->stop_dev : nullptr;
     return a;
 }
 
 // Enqueues one persistent launch: reset the work queue, then every instance runs
 // `generations` generations (after generation 0 where it has not run yet).
-int batch_enqueue(ga_batch *b, int generations, cudaStream_t st) {
+int batch_enqueue(ga_batch *b, int generations, cudaStream_t st, bool stoppable = false) {
     FFS_CUDA(cudaMemsetAsync(b->d_next, 0, sizeof(int32_t), st));
-    FFS_CUDA(launch_batch(b->par.order_mode, b->par.machine_mode, batch_args(b, generations), b->grid, b->warps,
+    FFS_CUDA(launch_batch(b->par.order_mode, b->par.machine_mode, batch_args(b, generations, stoppable), b->grid, b->warps,
                           b->cluster, st));
     g_launches += 1;
     return FFS_OK;
@@ -1542,6 +1549,16 @@ int ga_batch_create(ffs_instance *const *insts, int32_t count, const ga_params *
         dalloc(&b->d_order, (size_t)count) != cudaSuccess || dalloc(&b->d_next, 1) != cudaSuccess ||
         dalloc(&b->d_err, 1) != cudaSuccess)
         return fail(FFS_E_NOMEM);
+    {
+        void *hp = nullptr;
+        if (cudaHostAlloc(&hp, sizeof(int32_t), cudaHostAllocMapped) != cudaSuccess) return fail(FFS_E_NOMEM);
+        b->stop_host = static_cast<volatile int32_t *>(hp);
+        *b->stop_host = 0;
+        void *dp = nullptr;
+        const int mrc = cuda_rc(cudaHostGetDevicePointer(&dp, hp, 0));
+        if (mrc != FFS_OK) return fail(mrc);
+        b->stop_dev = static_cast<int32_t *>(dp);
+    }
     b->h_inst.resize(count);
     std::vector<std::pair<long long, int>> work(count);
     int rc = FFS_OK;
@@ -1614,6 +1631,12 @@ int ga_batch_destroy(ga_batch *b) {
     return FFS_OK;
 }
 
+int ga_batch_stop(ga_batch *b) {
+    if (!b || !b->stop_host) return FFS_E_ARG;
+    *b->stop_host = 1;
+    return FFS_OK;
+}
+
 int ga_batch_set_config(ga_batch *b, const ga_batch_config *cfg) {
     if (!b || !cfg) return FFS_E_ARG;
     return batch_config(b, cfg->warps_per_cta, cfg->smem_bytes, cfg->cluster > 0 ? cfg->cluster : b->cluster);
@@ -1640,7 +1663,7 @@ int ga_batch_run(ga_batch *b, int32_t generations, ffs_result *best) {
         FFS_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
         int rc = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        if (rc == FFS_OK) rc = batch_enqueue(b, generations, cap);
+        if (rc == FFS_OK) rc = batch_enqueue(b, generations, cap, true);
         const int ce = cuda_rc(cudaStreamEndCapture(cap, &g));
         cudaStreamDestroy(cap);
         if (rc == FFS_OK) rc = ce;
@@ -1650,9 +1673,11 @@ int ga_batch_run(ga_batch *b, int32_t generations, ffs_result *best) {
         b->graph_gens = generations;
         g_launches -= 1;  // counted at replay
     }
+    *b->stop_host = 0;  // a request made before this run has no effect on it
     FFS_CUDA(cudaGraphLaunch(b->graph, b->st));
     g_launches += 1;
     FFS_TRY(batch_check(b));
+    if (*b->stop_host == 2) return FFS_E_STOPPED;
     if (!best) return FFS_OK;
     // best-ever island of every instance, decoded and committed
     for (int i = 0; i < b->count; ++i) {

@@ -20,6 +20,7 @@ MACH_GENE, MACH_EARLIEST = 0, 1
 PLACE_INSERT = 4  # or-ed into a machine mode: idle-gap insertion placement
 ST_FREE, ST_EXEC, ST_DONE, ST_FIXED = 0, 1, 2, 3
 E_TIMEOUT = -5
+E_STOPPED = -9  # a batched run ended early on ga_batch_stop
 INJECT_NONE, INJECT_TABLE_COPY, INJECT_GEMM_LOADS = 0, 1, 2  # ffs_debug_inject (tests only)
 KEEP_SLOT, KEEP_ISLAND, KEEP_ISLAND_OFFSPRING = 0, 1, 2  # keep rules of surrogate-assisted generations
 
@@ -154,6 +155,7 @@ _SIGS = {
     "ga_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(GAParams_c), C.POINTER(C.c_void_p)]),
     "ga_batch_destroy": (C.c_int, [C.c_void_p]),
     "ga_batch_run": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "ga_batch_stop": (C.c_int, [C.c_void_p]),
     "ga_batch_read": (C.c_int, [C.c_void_p, C.c_int32] + [C.c_void_p] * 10),
     "ga_batch_tune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "ga_batch_get_config": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -506,6 +508,11 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def stop(self):
+        """Asks a run in progress (in another thread) to end at a generation boundary; that
+        run then raises FFSError with code E_STOPPED."""
+        _check(lib().ga_batch_stop(self._h), "ga_batch_stop")
 
     def run(self, generations: int, results: bool = False):
         if not results:

@@ -115,3 +115,51 @@ def test_batched_workload_shape_sampled():
         single = ffs.Population(inst, instance_id=i, **kw)
         single.run(3, want_schedule=False)
         _same(batch.read(i), single.read(), False)
+
+
+def test_stop_request_ends_a_run_at_generation_boundaries():
+    """ga_batch_stop from another thread ends a long persistent run early; every instance is
+    left after a whole number of generations, equal to its own single run of that many, and
+    the batch runs on normally afterwards.  A request made while no run is in progress is
+    cleared by the next run."""
+    import threading
+    import time
+
+    probs = _problems(12, 21)
+    kw = dict(P=64, island=16, tour_k=2, pc=(4, 5), pm=(1, 5), migrate_every=3, seed=9)
+    batch = ffs.Batch([ffs.Instance(p) for p in probs], instance_id=300, **kw)
+    batch.stop()  # no run in progress: the next run clears it
+    batch.run(2)
+    assert all(batch.read(i)["gen"] == 2 for i in range(len(probs)))
+
+    G = 200000  # far longer than the test waits
+    box = {}
+
+    def worker():
+        try:
+            batch.run(G)
+            box["rc"] = ffs.FFS_OK
+        except ffs.FFSError as e:
+            box["rc"] = e.code
+
+    th = threading.Thread(target=worker)
+    t0 = time.perf_counter()
+    th.start()
+    time.sleep(0.3)
+    batch.stop()
+    th.join(timeout=120)
+    assert not th.is_alive()
+    assert box["rc"] == ffs.E_STOPPED
+    assert time.perf_counter() - t0 < 60
+    gens = [batch.read(i)["gen"] for i in range(len(probs))]
+    assert all(2 < g < 2 + G for g in gens), gens
+    for i, p in enumerate(probs):
+        single = ffs.Population(ffs.Instance(p), instance_id=300 + i, **kw)
+        single.run(gens[i], want_schedule=False)
+        _same(batch.read(i), single.read(), False)
+    # the next run starts from each instance's own generation
+    batch.run(3)
+    for i, p in enumerate(probs):
+        single = ffs.Population(ffs.Instance(p), instance_id=300 + i, **kw)
+        single.run(gens[i] + 3, want_schedule=False)
+        _same(batch.read(i), single.read(), False)
