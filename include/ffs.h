@@ -502,7 +502,7 @@ typedef struct {
     int32_t state;            /* FFS_REQ_*                                                */
     int32_t status;           /* FFS_OK, or the failed request's error code             */
     int32_t warm;             /* 1 if generation 0 came from the instance's last population */
-    int32_t generations;
+    int32_t generations;      /* generations run: as requested, fewer if it was stopped     */
     int64_t submit_ns, admit_ns, done_ns;  /* steady-clock times (ns) of the three events  */
     int64_t footprint;        /* device bytes of the request's population                */
     int32_t n_ops;            /* N * g of the instance after this request's arrivals      */
@@ -540,6 +540,22 @@ int ffs_service_submit(ffs_service *svc, ffs_instance *inst, const ffs_arrivals 
  * FFS_E_ARG for an unknown ticket. */
 int ffs_service_wait(ffs_service *svc, int64_t ticket, int32_t timeout_ms, ffs_request_info *info,
                      ffs_result *best);
+
+/* Ends a request early, for a caller whose request has gone stale (a newer event for the
+ * instance) or who needs an answer now; the paper has no counterpart.  The worker enqueues
+ * an admitted request's generations 64 at a time, and checks for a stop between chunks:
+ *   - an admitted request ends after the chunk in flight and finishes FFS_REQ_DONE with
+ *     the best schedule found so far (committed to its instance, and its population kept
+ *     for the instance's next request, as for a full run); info.generations then says how
+ *     many generations ran, and the result equals a request for exactly that many;
+ *   - a queued request whose rescheduling has not yet been applied is dropped without
+ *     touching its instance and finishes FFS_REQ_FAILED with status FFS_E_STOPPED (it
+ *     does not count as one of the instance's requests for stream ids);
+ *   - a queued request whose rescheduling was already applied (it waited for memory) is
+ *     admitted and ends after generation 0.
+ * Results of a stopped request depend on when the stop arrived.  FFS_OK for a finished
+ * request (no effect), FFS_E_ARG for an unknown ticket. */
+int ffs_service_stop_request(ffs_service *svc, int64_t ticket);
 
 /* Drops the instance's kept population and its request count.  FFS_E_STATE while a
  * request of the instance is queued or active. */

@@ -136,14 +136,23 @@ struct Request {
     ffs_result res{};
     std::vector<int32_t> S, M;
     std::string err_text;
+    bool stop = false;              // ffs_service_stop_request was called (under mu)
 };
 
 struct Slot {
     cudaStream_t st = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t done = nullptr;     // recorded after the chunk of generations in flight
     Request *req = nullptr;
     ga_population *pop = nullptr;
+    int run = 0, left = 0;          // generations enqueued so far; still to enqueue
 };
+
+// Generations enqueued at a time for an admitted request: the worker enqueues the next
+// chunk when one completes, so a stop request takes effect within a chunk.  A multiple of
+// the 8-generation graphs, so the launches are those of one ga_run.
+constexpr int kChunk = 64;
+
+bool stop_requested(ffs_service *s, const Request *r);
 
 struct InstState {
     ga_population *warm = nullptr;  // last population, kept on the device (worker only)
@@ -177,6 +186,11 @@ struct ffs_service {
 };
 
 namespace {
+
+bool stop_requested(ffs_service *s, const Request *r) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    return r->stop;
+}
 
 // Records the end of a request (under the lock) and wakes waiters.
 void finish_request(ffs_service *s, Request *r, int rc, bool was_active) {
@@ -310,7 +324,9 @@ AdmitResult admit(ffs_service *s, Slot &slot, Request *r) {
         r->info.admit_ns = now_ns();
         s->active++;
     }
-    int rc = ga_enqueue(pop, r->generations);
+    // a request stopped while it waited runs no generation past generation 0
+    const int first = stop_requested(s, r) ? 0 : std::min(r->generations, kChunk);
+    int rc = ga_enqueue(pop, first);
     if (rc == FFS_OK) rc = cuda_rc(cudaEventRecord(slot.done, slot.st));
     if (rc != FFS_OK) {
         cudaStreamSynchronize(slot.st);
@@ -321,15 +337,17 @@ AdmitResult admit(ffs_service *s, Slot &slot, Request *r) {
     }
     slot.req = r;
     slot.pop = pop;
+    slot.run = first;
+    slot.left = stop_requested(s, r) ? 0 : r->generations - first;
     return kAdmitted;
 }
 
-void retire(ffs_service *s, Slot &slot, cudaError_t q) {
+void retire(ffs_service *s, Slot &slot, int rc) {
     Request *r = slot.req;
     ga_population *pop = slot.pop;
+    r->info.generations = slot.run;
     slot.req = nullptr;
     slot.pop = nullptr;
-    int rc = q == cudaSuccess ? FFS_OK : cuda_rc(q);
     if (rc == FFS_OK) {
         r->S.assign((size_t)pop->NG, 0);
         r->M.assign((size_t)pop->NG, 0);
@@ -373,13 +391,46 @@ void worker_main(ffs_service *s) {
             auto it = s->insts.find(in);
             if (it != s->insts.end() && it->second.pending == 0) s->insts.erase(it);
         }
-        // retire
+        // next chunks, or retire
         for (Slot &sl : s->slots) {
             if (!sl.req) continue;
             const cudaError_t q = cudaEventQuery(sl.done);
             if (q == cudaErrorNotReady) continue;
-            retire(s, sl, q);
+            int rc = q == cudaSuccess ? FFS_OK : cuda_rc(q);
+            if (rc == FFS_OK && sl.left > 0 && !stop_requested(s, sl.req)) {
+                const int n = std::min(sl.left, kChunk);
+                rc = ga_enqueue(sl.pop, n);
+                if (rc == FFS_OK) rc = cuda_rc(cudaEventRecord(sl.done, sl.st));
+                if (rc == FFS_OK) {
+                    sl.left -= n;
+                    sl.run += n;
+                    progress = true;
+                    continue;
+                }
+                cudaStreamSynchronize(sl.st);
+            }
+            retire(s, sl, rc);
             progress = true;
+        }
+        // queued requests stopped before their rescheduling was applied end unchanged
+        {
+            std::vector<Request *> gone;
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                for (auto it = s->queue.begin(); it != s->queue.end();) {
+                    if ((*it)->stop && !(*it)->prepared) {
+                        gone.push_back(*it);
+                        it = s->queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+            }
+            for (Request *r : gone) {
+                std::snprintf(g_last_error, sizeof(g_last_error), "request stopped before it was admitted");
+                finish_request(s, r, FFS_E_STOPPED, false);
+                progress = true;
+            }
         }
         // admit, first come first served
         std::vector<Request *> cand;
@@ -569,6 +620,18 @@ int ffs_service_wait(ffs_service *s, int64_t ticket, int32_t timeout_ms, ffs_req
         if (best->start) std::memcpy(best->start, r->S.data(), 4 * r->S.size());
         if (best->machine) std::memcpy(best->machine, r->M.data(), 4 * r->M.size());
     }
+    return FFS_OK;
+}
+
+int ffs_service_stop_request(ffs_service *s, int64_t ticket) {
+    if (!s) return FFS_E_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return FFS_E_ARG;
+        it->second->stop = true;
+    }
+    s->cv_work.notify_all();
     return FFS_OK;
 }
 

@@ -129,6 +129,7 @@ _SIGS = {
                                      C.POINTER(C.c_int64)]),
     "ffs_service_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(RequestInfo_c), C.POINTER(Result_c)]),
     "ffs_service_forget": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ffs_service_stop_request": (C.c_int, [C.c_void_p, C.c_int64]),
     "ffs_service_stats_read": (C.c_int, [C.c_void_p, C.POINTER(ServiceStats_c)]),
     "ga_run": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Result_c)]),
     "ga_population_read": (C.c_int, [C.c_void_p] + [C.c_void_p] * 10),
@@ -709,6 +710,10 @@ class Service:
         if schedule:
             out.update(S=S[:i.n_ops], M=M[:i.n_ops])
         return out
+
+    def stop(self, ticket: int):
+        """Ends a request early (ffs_service_stop_request)."""
+        _check(lib().ffs_service_stop_request(self._h, int(ticket)), "ffs_service_stop_request")
 
     def forget(self, inst: Instance):
         _check(lib().ffs_service_forget(self._h, inst.handle), "ffs_service_forget")

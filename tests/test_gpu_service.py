@@ -243,3 +243,40 @@ def test_service_bad_request_fails_alone():
         svc.wait(b)
     assert svc.wait(c)["warm"] == 1
     svc.close()
+
+
+def test_service_stop_request_ends_requests_early():
+    """A long admitted request stopped mid-run finishes with the best schedule of the
+    generations it ran, equal to a request of exactly that many; a queued request of the
+    same instance stopped before its rescheduling was applied ends with FFS_E_STOPPED and
+    leaves the instance alone, so the next request equals the direct calls without it.
+    A multi-chunk request that is not stopped equals its direct run too."""
+    rng = np.random.default_rng(12)
+    prob = wl.random_instance(rng, 30, 4, 1, 3, 40, 5, 20, 55)
+    arr = wl.random_arrivals(rng, 4, 4, 60, 40)
+    inst = ffs.Instance(prob)
+    svc = ffs.Service(max_active=2, memory_bytes=1 << 30, **GA)
+    big = 10 ** 6
+    t1 = svc.submit(inst, None, 0, big)
+    t2 = svc.submit(inst, arr, 60, 50)  # waits behind t1 (same instance)
+    time.sleep(0.3)
+    svc.stop(t2)
+    with pytest.raises(ffs.FFSError) as e:
+        svc.wait(t2, timeout_ms=60000)
+    assert e.value.code == ffs.E_STOPPED
+    svc.stop(t1)
+    r1 = svc.wait(t1, timeout_ms=60000)
+    assert r1["state"] == 2 and r1["status"] == 0 and 0 < r1["generations"] < big
+    t3 = svc.submit(inst, arr, 60, 150)  # three chunks, not stopped
+    r3 = svc.wait(t3, timeout_ms=60000)
+    assert r3["generations"] == 150 and r3["warm"] == 1
+    svc.close()
+    # the direct calls: a solve of r1's generation count, then the warm request
+    ref = ffs.Instance(prob)
+    pop = ffs.Population(ref, **GA, instance_id=0)
+    d1 = pop.run(r1["generations"])
+    assert r1["obj"] == d1["obj"] and np.array_equal(r1["S"], d1["S"].ravel())
+    ref.reschedule(arr, 60)
+    warm = ffs.Population(ref, **GA, instance_id=1, prev=pop)
+    d3 = warm.run(150)
+    assert r3["obj"] == d3["obj"] and np.array_equal(r3["S"], d3["S"].ravel())
