@@ -563,6 +563,16 @@ int ffs_service_forget(ffs_service *svc, ffs_instance *inst);
 
 int ffs_service_stats_read(ffs_service *svc, ffs_service_stats *stats);
 
+/* Bounds-checked builds, for tests (the paper has no counterpart; compute-sanitizer is not
+ * available where the library is tested).  A library built with FFS_CHECKED checks the
+ * device indices of the decoder's shared-memory profile windows, schedule records and job
+ * completion times, its stage-order list, and the crossover's bitmap and missing-value
+ * list: an index outside its buffer is counted and replaced by 0, so nothing is accessed
+ * out of range and control flow does not change.  *count = the indices found out of range
+ * since the last call (the count is then cleared).  An ordinary build checks nothing: it
+ * sets *count = 0 and returns FFS_E_STATE. */
+int ffs_debug_bounds_faults(uint32_t *count);
+
 /* Failure injection, for tests of the library's bounded device waits (not in the paper;
  * not for production use).  Process-wide; mode is an or of:
  *   FFS_INJECT_TABLE_COPY  every later ffs_decode launch skips the copy of the instance

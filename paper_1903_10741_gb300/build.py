@@ -18,6 +18,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libffs.so")
+# The bounds-checked variant (FFS_CHECKED): device indices into shared and global buffers
+# are checked, counted and clamped instead of used out of range; for tests, not for speed.
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
 
@@ -38,10 +41,10 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -50,16 +53,20 @@ def flags(extra=()):
                    "--expt-relaxed-constexpr", *extra]
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(), checked: bool = False) -> str:
+    out_dir = BUILD_CHECKED if checked else BUILD
+    lib_path = os.path.join(out_dir, "libffs.so")
+    if checked:
+        extra = tuple(extra) + ("-DFFS_CHECKED",)
     with _lock:
-        if not force and up_to_date():
-            return LIB
-        os.makedirs(BUILD, exist_ok=True)
+        if not force and up_to_date(lib_path):
+            return lib_path
+        os.makedirs(out_dir, exist_ok=True)
         nv = nvcc()
         srcs = _sources()
 
         def compile_one(src):
-            obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+            obj = os.path.join(out_dir, os.path.basename(src) + ".o")
             cmd = [nv, *flags(extra), "-c", src, "-o", obj]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
@@ -70,12 +77,12 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
 
         with cf.ThreadPoolExecutor(max_workers=max(1, len(srcs))) as ex:
             objs = list(ex.map(compile_one, srcs))
-        tmp = LIB + f".tmp{os.getpid()}"
+        tmp = lib_path + f".tmp{os.getpid()}"
         r = subprocess.run([nv, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc link failed:\n{r.stderr}")
-        os.replace(tmp, LIB)
-        return LIB
+        os.replace(tmp, lib_path)
+        return lib_path
 
 
 if __name__ == "__main__":

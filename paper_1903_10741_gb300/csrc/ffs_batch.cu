@@ -311,6 +311,10 @@ cudaError_t with_kernel(int order, int mach, Fn fn) {
 
 }  // namespace
 
+#ifdef FFS_CHECKED
+unsigned int bounds_faults_batch() { return bounds_faults_take(); }
+#endif
+
 cudaError_t prepare_batch(int order, int mach, int smem_bytes) {
     return with_kernel(order, mach, [&](auto kernel, int v) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

@@ -27,6 +27,31 @@ __host__ __device__ constexpr bool mach_unrel(int m) { return (m & 2) != 0; }
 __host__ __device__ constexpr bool mach_insert(int m) { return (m & kPlaceInsert) != 0; }
 
 
+// ---------------------------------------------------------------- bounds-checked builds
+// With FFS_CHECKED, an index into a shared- or global-memory buffer that falls outside
+// [0, n) is counted (per translation unit; bounds_faults_take reads and clears the count)
+// and replaced by 0, so the access stays inside the buffer and control flow, which is
+// warp-uniform, does not change.  Ordinary builds use the index as it is.
+#ifdef FFS_CHECKED
+static __device__ unsigned int g_bounds_faults;
+__device__ __forceinline__ int checked_ix(int i, int n) {
+    if ((unsigned)i >= (unsigned)n) {
+        atomicAdd(&g_bounds_faults, 1u);
+        return 0;
+    }
+    return i;
+}
+static inline unsigned int bounds_faults_take() {
+    unsigned int v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_faults, sizeof v) != cudaSuccess) return ~0u;
+    if (cudaMemcpyToSymbol(g_bounds_faults, &z, sizeof z) != cudaSuccess) return ~0u;
+    return v;
+}
+#define FFS_IX(i, n) ::edffs::checked_ix((i), (n))
+#else
+#define FFS_IX(i, n) (i)
+#endif
+
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror & Shaw, SC'11: ten rounds of the 4x32 Philox S-box with
 // multipliers 0xD2511F53 / 0xCD9E8D57 and Weyl key increments 0x9E3779B9 / 0xBB67AE85.
@@ -299,14 +324,15 @@ __device__ __forceinline__ void fill_to(uint16_t *h, int &fl, int e, int Hcap, u
 // may resume: one past the last slot lacking headroom (the jump its own first step would
 // make), or t when the op spans more than one step.  Only lanes whose four slots start
 // below t + p load and store.  The caller ensures t + p <= Hcap.
-__device__ __forceinline__ int place_first(uint16_t *h, int t, int p, uint32_t q2, int lane, bool &placed) {
+__device__ __forceinline__ int place_first(uint16_t *h, int t, int p, uint32_t q2, int lane, bool &placed,
+                                           int Hcap) {
     placed = false;
     const int c = t & ~3, e = t + p;
     if (e - c > 128) return t;
     const int b = c + 4 * lane;
     const bool mine = b < e;
     uint2 w = make_uint2(0u, 0u);  // lanes past the window: no slot in it
-    if (mine) w = *reinterpret_cast<const uint2 *>(h + b);
+    if (mine) w = *reinterpret_cast<const uint2 *>(h + FFS_IX(b, Hcap - 3));
     const uint2 m = slot_mask(b, t, e);
     // bit 15 of (h | 0x8000) - q is clear exactly where h < q (no borrow between halfwords)
     const uint32_t vx = ~((w.x | 0x80008000u) - q2) & m.x & 0x80008000u;
@@ -320,7 +346,7 @@ __device__ __forceinline__ int place_first(uint16_t *h, int t, int p, uint32_t q
     if (mine) {
         w.x -= q2 & m.x;
         w.y -= q2 & m.y;
-        *reinterpret_cast<uint2 *>(h + b) = w;
+        *reinterpret_cast<uint2 *>(h + FFS_IX(b, Hcap - 3)) = w;
     }
     placed = true;
     return t;
@@ -428,7 +454,7 @@ __device__ __forceinline__ int place_single(uint16_t *h, int &hw, int Hcap, int 
     const uint32_t q0 = __shfl_sync(kFull, q2, m0);
     bool placed = false;
     int from = t0;
-    if (t0 + p <= Hcap) from = place_first(h, t0, p, q0, lane, placed);
+    if (t0 + p <= Hcap) from = place_first(h, t0, p, q0, lane, placed, Hcap);
     if (!placed) return place_general(h, hw, Hcap, est, mf, q2, os, p, lane, m0, t0, q0, from, bt, bm);
     bt = t0;
     bm = m0;
@@ -530,7 +556,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
     for (int k = lane; k < K; k += 32) {
         const int v = y[k];
         if (v < 1 || v > K) bad = true;
-        else inv[K - v] = (int16_t)k;
+        else inv[FFS_IX(K - v, K)] = (int16_t)k;
         if (mach_gene(MACH)) {
             const int xm = x[k];
             if (xm < 0 || xm >= T.o[T.gstg[k]]) bad = true;
@@ -563,8 +589,8 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
             if (k >= 0) at = next[s] + __popc(grp & ((1u << lane) - 1u));
             __syncwarp();  // every lane has read next[s] before the group's last lane moves it
             if (k >= 0) {
-                order[at] = (int16_t)k;
-                if (lane == 31 - __clz(grp)) next[s] = at + 1;
+                order[FFS_IX(at, K)] = (int16_t)k;
+                if (lane == 31 - __clz(grp)) next[FFS_IX(s, g)] = at + 1;
             }
             __syncwarp();
         }
@@ -600,8 +626,8 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 int cj[G + 1];
 #pragma unroll
                 for (int u = 0; u <= G; ++u) {
-                    gr[u] = T.grec[order[min(lo + u, hi - 1)]];
-                    cj[u] = C[gr[u].x & 0xFFFFu];
+                    gr[u] = T.grec[FFS_IX(order[FFS_IX(min(lo + u, hi - 1), K)], K)];
+                    cj[u] = C[FFS_IX((int)(gr[u].x & 0xFFFFu), N)];
                 }
                 int est0 = max(cj[0], 0);
                 const unsigned k0 = __reduce_min_sync(kFull, ((unsigned)max(est0, mf) << 5) | (unsigned)lane);
@@ -629,18 +655,18 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                         one[u] = e[u] <= Hcap && e[u] - cc[u] <= 128;
                         mine[u] = one[u] && b[u] < e[u];
                         w[u] = make_uint2(0u, 0u);
-                        if (mine[u]) w[u] = *reinterpret_cast<const uint2 *>(h + b[u]);
+                        if (mine[u]) w[u] = *reinterpret_cast<const uint2 *>(h + FFS_IX(b[u], Hcap - 3));
                         mfc = lane == cm[u] ? e[u] : mfc;
                         est[u + 1] = max(cj[u + 1], 0);
                         const unsigned k = __reduce_min_sync(kFull, ((unsigned)max(est[u + 1], mfc) << 5) | (unsigned)lane);
-                        gn[u] = T.grec[order[min(n + G + 1 + u, hi - 1)]];
+                        gn[u] = T.grec[FFS_IX(order[FFS_IX(min(n + G + 1 + u, hi - 1), K)], K)];
                         ct[u + 1] = (int)(k >> 5);
                         cm[u + 1] = (int)(k & 31u);
                         cq[u + 1] = __shfl_sync(kFull, q2, cm[u + 1]);
                     }
                     int cjn[G];
 #pragma unroll
-                    for (int u = 0; u < G; ++u) cjn[u] = C[gn[u].x & 0xFFFFu];
+                    for (int u = 0; u < G; ++u) cjn[u] = C[FFS_IX((int)(gn[u].x & 0xFFFFu), N)];
                     uint2 m[G];
                     uint32_t vx[G], vy[G];
                     unsigned vm[G];
@@ -666,7 +692,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                             if (mine[u]) {
                                 w[u].x -= cq[u] & m[u].x;
                                 w[u].y -= cq[u] & m[u].y;
-                                *reinterpret_cast<uint2 *>(h + b[u]) = w[u];
+                                *reinterpret_cast<uint2 *>(h + FFS_IX(b[u], Hcap - 3)) = w[u];
                             }
                             tt[u] = ct[u];
                             mm[u] = cm[u];
@@ -685,7 +711,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                                 if (mine[u]) {
                                     w[u].x -= cq[u] & m[u].x;
                                     w[u].y -= cq[u] & m[u].y;
-                                    *reinterpret_cast<uint2 *>(h + b[u]) = w[u];
+                                    *reinterpret_cast<uint2 *>(h + FFS_IX(b[u], Hcap - 3)) = w[u];
                                 }
                                 if (lane == cm[u]) mf = e[u];
                                 hw = max(hw, e[u]);
@@ -714,7 +740,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                         cq[G] = __shfl_sync(kFull, q2, cm[G]);
                     }
 #pragma unroll
-                    for (int u = 0; u < G; ++u) C[jj[u]] = ee[u];  // every lane stores the same values
+                    for (int u = 0; u < G; ++u) C[FFS_IX(jj[u], N)] = ee[u];  // every lane stores the same values
                     if (S_out && lane == 0) {
 #pragma unroll
                         for (int u = 0; u < G; ++u) {
@@ -738,7 +764,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
 #pragma unroll
                 for (int u = 0; u + 1 < G; ++u) {
                     if (n + u < hi) {
-                        const int ju = (int)(gr[u].x & 0xFFFFu);
+                        const int ju = FFS_IX((int)(gr[u].x & 0xFFFFu), N);
                         int tu, mu;
                         const int e1 = place_single(h, hw, Hcap, u ? max(cj[u], 0) : est0, mf, q2, os,
                                                     (int)(gr[u].y & 0xFFFFu), lane, tu, mu);
@@ -904,7 +930,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                     int from = t0;
                     if (kFast && t0 + p <= Hcap) {
                         if (!FULL) fill_to(h, fl, t0 + p, Hcap, Q2, lane);
-                        from = place_first(h, t0, p, bq2, lane, placed);
+                        from = place_first(h, t0, p, bq2, lane, placed, Hcap);
                     }
                     if (placed)
                         best_t = t0;
@@ -923,7 +949,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                         bq2 = __shfl_sync(kFull, qo2, best_m);
                         if (t0 + pb <= Hcap) {
                             if (!FULL) fill_to(h, fl, t0 + pb, Hcap, Q2, lane);
-                            place_first(h, t0, pb, bq2, lane, placed);
+                            place_first(h, t0, pb, bq2, lane, placed, Hcap);
                         }
                         if (placed) {
                             best_t = t0;
@@ -945,7 +971,7 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                         bq2 = __shfl_sync(kFull, q2, best_m);
                         if (t0 + p <= Hcap) {
                             if (!FULL) fill_to(h, fl, t0 + p, Hcap, Q2, lane);
-                            from = place_first(h, t0, p, bq2, lane, placed);
+                            from = place_first(h, t0, p, bq2, lane, placed, Hcap);
                         }
                         if (placed) best_t = t0;
                     }

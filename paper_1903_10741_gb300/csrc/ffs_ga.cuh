@@ -171,7 +171,7 @@ __device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, con
             for (int u = 0; u < kRowU; ++u)
                 if (k0 + 32 * u < cy) {
                     w.y[k0 + 32 * u] = (int16_t)v[u];
-                    atomicOr(&w.bits[v[u] >> 5], 1u << (v[u] & 31));
+                    atomicOr(&w.bits[FFS_IX(v[u] >> 5, nw)], 1u << (v[u] & 31));
                 }
         }
         __syncwarp();
@@ -182,14 +182,14 @@ __device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, con
 #pragma unroll
             for (int u = 0; u < kRowU; ++u)
                 if (k0 + 32 * u < K) {
-                    const bool dup = (w.bits[v[u] >> 5] >> (v[u] & 31)) & 1u;
+                    const bool dup = (w.bits[FFS_IX(v[u] >> 5, nw)] >> (v[u] & 31)) & 1u;
                     w.y[k0 + 32 * u] = dup ? (int16_t)0 : (int16_t)v[u];
                 }
         }
         __syncwarp();
         for (int k = cy + lane; k < K; k += 32) {
             const int v = w.y[k];
-            if (v) atomicOr(&w.bits[v >> 5], 1u << (v & 31));
+            if (v) atomicOr(&w.bits[FFS_IX(v >> 5, nw)], 1u << (v & 31));
         }
         __syncwarp();
         // Missing values, ascending, into `miss`.
@@ -215,7 +215,7 @@ __device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, con
             while (m) {
                 const int b = __ffs(m) - 1;
                 m &= m - 1;
-                miss[o++] = (int16_t)(q * 32 + b);
+                miss[FFS_IX(o++, K)] = (int16_t)(q * 32 + b);
             }
             base += __shfl_sync(kFull, incl, 31);
         }
@@ -225,7 +225,7 @@ __device__ __forceinline__ bool make_child(const Tabs &T, const WarpPtrs &w, con
             const int k = k0 + lane;
             const bool dup = k < K && w.y[k] == 0;
             const unsigned bm = __ballot_sync(kFull, dup);
-            if (dup) w.y[k] = miss[rank + __popc(bm & ((1u << lane) - 1u))];
+            if (dup) w.y[k] = miss[FFS_IX(rank + __popc(bm & ((1u << lane) - 1u)), K)];
             rank += __popc(bm);
         }
         if (mach_gene(MACH))

@@ -540,6 +540,10 @@ cudaError_t prepare(KernelT kernel, int smem) {
 
 }  // namespace
 
+#ifdef FFS_CHECKED
+unsigned int bounds_faults_kernels() { return bounds_faults_take(); }
+#endif
+
 int cta_smem_bytes(const TabHeader &h, int Hcap, bool ga, bool global_profile, bool insert) {
     const WarpLayout L = warp_layout(h.N, h.M, h.K, global_profile ? 0 : Hcap, ga, insert && !global_profile ? h.maxo : 0);
     return 128 + ((h.bytes + 127) & ~127) + kWarpsPerBlock * L.bytes;

@@ -148,6 +148,13 @@ struct BatchArgs {
     volatile int32_t *stop;
 };
 
+#ifdef FFS_CHECKED
+// Bounds-checked builds: index faults counted since the last call in the decode and GA
+// kernels' and in the batched kernel's translation units (read and cleared).
+unsigned int bounds_faults_kernels();
+unsigned int bounds_faults_batch();
+#endif
+
 cudaError_t prepare_batch(int order, int mach, int smem_bytes);
 // Clusters of `cluster` CTAs of the given shape that can be resident at once.
 cudaError_t batch_max_clusters(int order, int mach, int cluster, int warps, int smem_bytes, int *clusters);

@@ -1172,6 +1172,19 @@ int ffs_debug_inject(int32_t mode) {
     return FFS_OK;
 }
 
+int ffs_debug_bounds_faults(uint32_t *count) {
+    if (!count) return FFS_E_ARG;
+#ifdef FFS_CHECKED
+    const unsigned int a = bounds_faults_kernels(), b = bounds_faults_batch();
+    if (a == ~0u || b == ~0u) return FFS_E_CUDA;
+    *count = a + b;
+    return FFS_OK;
+#else
+    *count = 0;
+    return FFS_E_STATE;  // an ordinary build does not check
+#endif
+}
+
 int ffs_kernel_launches(uint64_t *count) {
     if (!count) return FFS_E_ARG;
     *count = g_launches.load();

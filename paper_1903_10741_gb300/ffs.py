@@ -145,6 +145,7 @@ _SIGS = {
     "ffs_surrogate_gradients": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "ffs_surrogate_train": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p]),
     "ffs_debug_inject": (C.c_int, [C.c_int32]),
+    "ffs_debug_bounds_faults": (C.c_int, [C.POINTER(C.c_uint32)]),
     "ga_population_surrogate_keep": (C.c_int, [C.c_void_p, C.c_int32]),
     "ffs_surrogate_score_exactly": (C.c_int, [C.c_void_p, C.c_int32]),
     "ga_profile_read_phases": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -180,6 +181,13 @@ def kernel_launches() -> int:
     return int(n.value)
 
 
+def bounds_faults() -> int:
+    """Device indices found out of range since the last call (bounds-checked builds only)."""
+    n = C.c_uint32()
+    _check(lib().ffs_debug_bounds_faults(C.byref(n)), "ffs_debug_bounds_faults")
+    return int(n.value)
+
+
 def header_functions():
     """Names of the functions declared in include/ffs.h."""
     with open(os.path.join(_build.INCLUDE, "ffs.h")) as f:
@@ -188,10 +196,11 @@ def header_functions():
 
 
 def lib():
-    """Loads libffs.so (building it first if it is missing or stale)."""
+    """Loads libffs.so (building it first if it is missing or stale); with the environment
+    variable FFS_CHECKED=1, the bounds-checked build instead."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = _build.build(checked=os.environ.get("FFS_CHECKED") == "1")
         L = C.CDLL(path)
         for name, (res, args) in _SIGS.items():
             fn = getattr(L, name)
