@@ -173,8 +173,9 @@ __device__ void island_finish(const Args &a, int isl, int nx, int gen, int lane)
 // Selection -> paired crossover + correction -> mutation -> decode, one child per warp.
 // Each warp recomputes both parents of its pair from the counter-based stream, so the
 // children of a pair are built independently by two warps.  An explicit cap of 168
-// registers keeps every variant free of spills; shared memory sets 2 CTAs of 128 threads
-// per SM anyway, which the register file holds at that cap.
+// registers keeps every variant free of spills.  At that cap the register file holds 3
+// CTAs of 128 threads per SM; profile slices of the usual size (112 KB of shared memory per
+// CTA) allow 2 anyway.
 template <int ORDER, int MACH>
 __global__ void __maxnreg__(168) k_ga_generation(GenArgs a) {
     extern __shared__ __align__(128) char smem[];
