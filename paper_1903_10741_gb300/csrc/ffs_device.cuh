@@ -463,14 +463,51 @@ __device__ __forceinline__ int place_single(uint16_t *h, int &hw, int Hcap, int 
     return t0 + p;
 }
 
+// Unrelated machines, after the one-step check failed: the general search over the stage's
+// machines (lane m: availability mf, this op's time pl and power ql on machine m), and the
+// draw.  Returns the op's end (-1 when it would outgrow the slice); bp: its time there.
+template <bool INS = false>
+__device__ __forceinline__ void earliest_machine_u(const uint16_t *h, int hw, int t0, uint32_t q2, int p, int os,
+                                                   int lane, int &best_t, int &best_m, int &best_p,
+                                                   const uint32_t *busy = nullptr, int words = 0);
+__device__ __forceinline__ int place_general_u(uint16_t *h, int &hw, int Hcap, int est, int &mf, int pl,
+                                               uint32_t ql, int os, int lane, int &bt, int &bm, int &bp) {
+    earliest_machine_u<false>(h, hw, max(est, mf), ql, pl, os, lane, bt, bm, bp);
+    const int e = bt + bp;
+    if (e > Hcap) return -1;
+    commit_power_full(h, bt, e, __shfl_sync(kFull, ql, bm), lane);
+    if (lane == bm) mf = e;
+    hw = max(hw, e);
+    return e;
+}
+
+// Unrelated machines, from the true machine state: the machine whose completion bound is
+// lowest (lowest index on ties), its one-step check and draw, else the general search.
+__device__ __forceinline__ int place_single_u(uint16_t *h, int &hw, int Hcap, int est, int &mf, int pl, uint32_t ql,
+                                              int os, int lane, int &bt, int &bm, int &bp) {
+    const int tl = max(est, mf);
+    const unsigned k = __reduce_min_sync(kFull, lane < os ? ((unsigned)(tl + pl) << 5) | (unsigned)lane : 0xFFFFFFFFu);
+    const int m0 = (int)(k & 31u), p0 = __shfl_sync(kFull, pl, m0), t0 = (int)(k >> 5) - p0;
+    const uint32_t q0 = __shfl_sync(kFull, ql, m0);
+    bool placed = false;
+    if (t0 + p0 <= Hcap) place_first(h, t0, p0, q0, lane, placed, Hcap);
+    if (!placed) return place_general_u(h, hw, Hcap, est, mf, pl, ql, os, lane, bt, bm, bp);
+    bt = t0;
+    bm = m0;
+    bp = p0;
+    if (lane == m0) mf = t0 + p0;
+    hw = max(hw, t0 + p0);
+    return t0 + p0;
+}
+
 // Unrelated machines: lane m < os holds its machine's availability t0, power q2 and the
 // op's processing time p on it.  Returns the lexicographic minimum of (earliest completion
 // of a power-feasible start, machine) and that machine's p.  The machine whose completion
 // bound t0 + p is lowest is scanned first; another only if its bound could still win.
-template <bool INS = false>
+template <bool INS>
 __device__ __forceinline__ void earliest_machine_u(const uint16_t *h, int hw, int t0, uint32_t q2, int p, int os,
                                                    int lane, int &best_t, int &best_m, int &best_p,
-                                                   const uint32_t *busy = nullptr, int words = 0) {
+                                                   const uint32_t *busy, int words) {
     const int c0 = lane < os ? t0 + p : INT_MAX;
     const unsigned key = lane < os ? ((unsigned)c0 << 5) | (unsigned)lane : 0xFFFFFFFFu;
     const unsigned kmin = __reduce_min_sync(kFull, key);
@@ -768,6 +805,196 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                         int tu, mu;
                         const int e1 = place_single(h, hw, Hcap, u ? max(cj[u], 0) : est0, mf, q2, os,
                                                     (int)(gr[u].y & 0xFFFFu), lane, tu, mu);
+                        if (e1 < 0) return {0, 0, 1};
+                        C[ju] = e1;
+                        if (S_out && lane == 0) {
+                            S_out[ju * g + s] = tu + RS;
+                            M_out[ju * g + s] = mu;
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+        } else
+        // Unrelated machines, earliest completion, prefilled shared-memory profile: the same
+        // grouped placement, where each op's time and power differ per machine (lane m
+        // holds its machine's word p | q << 16 of the op) and the machine whose completion
+        // bound is lowest is checked first.
+        if (MACH == kMachEarliestU && PIPE && FULL) {
+            constexpr int G = kPlaceGroup;
+            for (int s = 0; s < g; ++s) {
+                const int lo = T.soff[s], hi = T.soff[s + 1];
+                if (lo == hi) continue;
+                const int mo = T.moff[s], os = T.o[s];
+                constexpr int kNever = 0x07FFFFFF;  // lanes past the stage's machines never win
+                int mf = kNever;
+                if (lane < os) mf = T.mfree0[mo + lane] - RS;
+                // the machine an op would take next (the lowest completion bound, lowest index
+                // on ties) given the machines' availability mv and the op's words pqv: its
+                // start, machine, power and time there
+                auto choose = [&](int est, int mv, uint32_t pqv, int &ct, int &cm, uint32_t &cq, int &pc) {
+                    const int pl = (int)(pqv & 0xFFFFu);
+                    const unsigned k = __reduce_min_sync(
+                        kFull, lane < os ? ((unsigned)(max(est, mv) + pl) << 5) | (unsigned)lane : 0xFFFFFFFFu);
+                    cm = (int)(k & 31u);
+                    pc = __shfl_sync(kFull, pl, cm);
+                    ct = (int)(k >> 5) - pc;
+                    cq = __shfl_sync(kFull, (pqv >> 16) * 0x10001u, cm);
+                };
+                // this lane's machine word of gene k
+                auto mword = [&](int k) -> uint32_t {
+                    return lane < os ? T.gm[(size_t)FFS_IX(k, K) * T.maxo + lane] : 0u;
+                };
+                // records of ops n .. n+G (this group and the next group's first op), and the
+                // job completions before them
+                uint2 gr[G + 1];
+                int cj[G + 1];
+                uint32_t pq[G + 1];
+#pragma unroll
+                for (int u = 0; u <= G; ++u) {
+                    const int ku = order[FFS_IX(min(lo + u, hi - 1), K)];
+                    gr[u] = T.grec[FFS_IX(ku, K)];
+                    pq[u] = mword(ku);
+                    cj[u] = C[FFS_IX((int)(gr[u].x & 0xFFFFu), N)];
+                }
+                int est0 = max(cj[0], 0);
+                int ct0, cm0, pc0 = 0;
+                uint32_t cq0;
+                choose(est0, mf, pq[0], ct0, cm0, cq0, pc0);
+                int n = lo;
+#pragma unroll 2
+                for (; n + G - 1 < hi; n += G) {
+                    int ct[G + 1], cm[G + 1], est[G + 1], pc[G + 1], e[G], cc[G], b[G], p[G], jj[G];
+                    uint32_t cq[G + 1], pqn[G];
+                    bool one[G], mine[G];
+                    uint2 w[G], gn[G];
+                    ct[0] = ct0;
+                    cm[0] = cm0;
+                    cq[0] = cq0;
+                    pc[0] = pc0;
+                    est[0] = est0;
+                    int mfc = mf;  // the machines as if ops 0 .. u of the group are placed
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+                        jj[u] = (int)(gr[u].x & 0xFFFFu);
+                        p[u] = pc[u];
+                        e[u] = ct[u] + p[u];
+                        cc[u] = ct[u] & ~3;
+                        b[u] = cc[u] + 4 * lane;
+                        one[u] = e[u] <= Hcap && e[u] - cc[u] <= 128;
+                        mine[u] = one[u] && b[u] < e[u];
+                        w[u] = make_uint2(0u, 0u);
+                        if (mine[u]) w[u] = *reinterpret_cast<const uint2 *>(h + FFS_IX(b[u], Hcap - 3));
+                        mfc = lane == cm[u] ? e[u] : mfc;
+                        est[u + 1] = max(cj[u + 1], 0);
+                        choose(est[u + 1], mfc, pq[u + 1], ct[u + 1], cm[u + 1], cq[u + 1], pc[u + 1]);
+                        const int kn = order[FFS_IX(min(n + G + 1 + u, hi - 1), K)];
+                        gn[u] = T.grec[FFS_IX(kn, K)];
+                        pqn[u] = mword(kn);
+                    }
+                    int cjn[G];
+#pragma unroll
+                    for (int u = 0; u < G; ++u) cjn[u] = C[FFS_IX((int)(gn[u].x & 0xFFFFu), N)];
+                    uint2 m[G];
+                    uint32_t vx[G], vy[G];
+                    unsigned vm[G];
+                    bool all = true;
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+#pragma unroll
+                        for (int v = 0; v < u; ++v) {  // earlier ops' draws where they overlap
+                            const uint2 o = slot_mask(b[u], ct[v], e[v]);
+                            w[u].x -= cq[v] & o.x;
+                            w[u].y -= cq[v] & o.y;
+                        }
+                        m[u] = slot_mask(b[u], ct[u], e[u]);
+                        vx[u] = ~((w[u].x | 0x80008000u) - cq[u]) & m[u].x & 0x80008000u;
+                        vy[u] = ~((w[u].y | 0x80008000u) - cq[u]) & m[u].y & 0x80008000u;
+                        vm[u] = __ballot_sync(kFull, (vx[u] | vy[u]) != 0u);
+                        all = all && one[u] && vm[u] == 0u;
+                    }
+                    int tt[G], mm[G], ee[G];
+                    if (all) {  // every op placed: their words in order (later ones include earlier draws)
+#pragma unroll
+                        for (int u = 0; u < G; ++u) {
+                            if (mine[u]) {
+                                w[u].x -= cq[u] & m[u].x;
+                                w[u].y -= cq[u] & m[u].y;
+                                *reinterpret_cast<uint2 *>(h + FFS_IX(b[u], Hcap - 3)) = w[u];
+                            }
+                            tt[u] = ct[u];
+                            mm[u] = cm[u];
+                            ee[u] = e[u];
+                            hw = max(hw, e[u]);
+                        }
+                        mf = mfc;
+                    } else {
+                        // ops before the first failure placed as checked; the first failure
+                        // searched from its machine, past its last slot short of headroom;
+                        // the rest one at a time from the true machine state
+                        bool placed = true;
+#pragma unroll
+                        for (int u = 0; u < G; ++u) {
+                            if (placed && one[u] && vm[u] == 0u) {
+                                if (mine[u]) {
+                                    w[u].x -= cq[u] & m[u].x;
+                                    w[u].y -= cq[u] & m[u].y;
+                                    *reinterpret_cast<uint2 *>(h + FFS_IX(b[u], Hcap - 3)) = w[u];
+                                }
+                                if (lane == cm[u]) mf = e[u];
+                                hw = max(hw, e[u]);
+                                tt[u] = ct[u];
+                                mm[u] = cm[u];
+                                ee[u] = e[u];
+                            } else if (placed) {
+                                // (the search over every machine starts afresh)
+                                int pu;
+                                ee[u] = place_general_u(h, hw, Hcap, est[u], mf, (int)(pq[u] & 0xFFFFu),
+                                                        (pq[u] >> 16) * 0x10001u, os, lane, tt[u], mm[u], pu);
+                                if (ee[u] < 0) return {0, 0, 1};
+                                placed = false;
+                            } else {
+                                int pu;
+                                ee[u] = place_single_u(h, hw, Hcap, est[u], mf, (int)(pq[u] & 0xFFFFu),
+                                                       (pq[u] >> 16) * 0x10001u, os, lane, tt[u], mm[u], pu);
+                                if (ee[u] < 0) return {0, 0, 1};
+                            }
+                        }
+                        choose(est[G], mf, pq[G], ct[G], cm[G], cq[G], pc[G]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < G; ++u) C[FFS_IX(jj[u], N)] = ee[u];  // every lane stores the same values
+                    if (S_out && lane == 0) {
+#pragma unroll
+                        for (int u = 0; u < G; ++u) {
+                            S_out[jj[u] * g + s] = tt[u] + RS;
+                            M_out[jj[u] * g + s] = mm[u];
+                        }
+                    }
+                    __syncwarp();
+                    gr[0] = gr[G];
+                    pq[0] = pq[G];
+                    est0 = est[G];
+                    ct0 = ct[G];
+                    cm0 = cm[G];
+                    cq0 = cq[G];
+                    pc0 = pc[G];
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+                        gr[u + 1] = gn[u];
+                        pq[u + 1] = pqn[u];
+                        cj[u + 1] = cjn[u];
+                    }
+                }
+                // the stage's last ops when its count is not a multiple of G
+#pragma unroll
+                for (int u = 0; u + 1 < G; ++u) {
+                    if (n + u < hi) {
+                        const int ju = FFS_IX((int)(gr[u].x & 0xFFFFu), N);
+                        int tu, mu, pu;
+                        const int eu = u ? max(cj[u], 0) : est0;
+                        const int e1 = place_single_u(h, hw, Hcap, eu, mf, (int)(pq[u] & 0xFFFFu),
+                                                      (pq[u] >> 16) * 0x10001u, os, lane, tu, mu, pu);
                         if (e1 < 0) return {0, 0, 1};
                         C[ju] = e1;
                         if (S_out && lane == 0) {
