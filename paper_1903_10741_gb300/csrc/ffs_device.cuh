@@ -352,6 +352,49 @@ __device__ __forceinline__ int place_first(uint16_t *h, int t, int p, uint32_t q
     return t;
 }
 
+// Insertion placement in one step, for identical machines and the earliest machine: the
+// machines that become available first (lanes m with tl == t0) are checked at t0 together.
+// Machine m fits if its occupancy bitmap is clear on [t0, t0+p) and every slot there has
+// headroom for its power q_m (the window's least headroom, one reduction).  Since no
+// machine can start before t0, the lowest machine that fits is the earliest-start choice;
+// its power is drawn from the words already loaded.  Returns that machine, or -1 with
+// nothing changed when none fits or the check does not fit one step (more than four
+// machines, a window past one 128-slot step or past Hcap).  The profile must be initialised
+// up to t0 + p.
+__device__ __forceinline__ int place_first_ins(uint16_t *h, int Hcap, const uint32_t *busy, int words, int t0, int p,
+                                               int tl, uint32_t q2, int os, int lane) {
+    const int c = t0 & ~3, e = t0 + p;
+    if (os > 4 || e > Hcap || e - c > 128) return -1;
+    const int b = c + 4 * lane;
+    const bool mine = b < e;
+    uint2 w = make_uint2(0u, 0u);
+    if (mine) w = *reinterpret_cast<const uint2 *>(h + FFS_IX(b, Hcap - 3));
+    const uint2 m = slot_mask(b, t0, e);
+    // least headroom over the window; slots outside it count as full
+    const uint32_t mn = __vminu2(w.x | ~m.x, w.y | ~m.y);
+    const unsigned least = __reduce_min_sync(kFull, min(mn & 0xFFFFu, mn >> 16));
+    // occupancy: lane l reads word (t0 >> 5) + (l & 7) of machine l >> 3 (5 words cover 128 slots)
+    const int bmach = lane >> 3, wd = (t0 >> 5) + (lane & 7);
+    uint32_t bz = 0u;
+    if (bmach < os && wd <= ((e - 1) >> 5)) {
+        const int lo = max(t0 - 32 * wd, 0), hi = min(e - 32 * wd, 32);
+        const uint32_t hm = hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u);
+        bz = busy[(size_t)bmach * words + FFS_IX(wd, words)] & hm & ~((1u << lo) - 1u);
+    }
+    const unsigned occ = __ballot_sync(kFull, bz != 0u);
+    const bool fits = lane < os && tl == t0 && ((occ >> (8 * lane)) & 0xFFu) == 0u && (q2 & 0xFFFFu) <= least;
+    const unsigned fm = __ballot_sync(kFull, fits);
+    if (!fm) return -1;
+    const int bm = __ffs(fm) - 1;
+    const uint32_t bq2 = __shfl_sync(kFull, q2, bm);
+    if (mine) {
+        w.x -= bq2 & m.x;
+        w.y -= bq2 & m.y;
+        *reinterpret_cast<uint2 *>(h + FFS_IX(b, Hcap - 3)) = w;
+    }
+    return bm;
+}
+
 // Marks slots [t, e) busy in a machine's occupancy bitmap; lane l takes word (t >> 5) + l
 // (+ 32 i), so no word has two writers.
 __device__ __forceinline__ void commit_busy(uint32_t *bm, int t, int e, int lane) {
@@ -1190,6 +1233,20 @@ __device__ DecodeOut decode_warp(const Tabs &T, uint16_t *h, int Hcap, int32_t *
                 } else {
                     const int tl = lane < os ? max(est, mf) : INT_MAX;
                     int from = 0;
+                    if (INS && !mach_unrel(MACH)) {  // every machine available first, checked at once
+                        const unsigned kmin = __reduce_min_sync(kFull, ((unsigned)max(est, mf) << 5) | (unsigned)lane);
+                        const int t0 = (int)(kmin >> 5);
+                        if (t0 + p <= Hcap) {
+                            if (!FULL) fill_to(h, fl, t0 + p, Hcap, Q2, lane);
+                            const int bm = place_first_ins(h, Hcap, busy, words, t0, p, tl, q2, os, lane);
+                            if (bm >= 0) {
+                                placed = true;
+                                best_t = t0;
+                                best_m = bm;
+                                bq2 = __shfl_sync(kFull, q2, bm);
+                            }
+                        }
+                    }
                     if (kFast) {  // the machine that frees first (lowest index on ties)
                         const unsigned key = ((unsigned)max(est, mf) << 5) | (unsigned)lane;
                         const unsigned kmin = __reduce_min_sync(kFull, key);
