@@ -251,10 +251,75 @@ __device__ __forceinline__ int earliest_start_win(const uint16_t *h, int hw, int
 // With INS, `bm` is the machine's occupancy bitmap (nw words; bit t: busy at slot t) and a
 // slot also violates when the machine is busy there; a candidate start that falls in a
 // busy stretch moves to the stretch's end directly.  Bits are only set below hw.
+// Insertion placement: the earliest start r >= t0 at which the machine is idle (occupancy
+// bitmap bm of nw words) and every slot of [r, r+p) has headroom q, slots at or beyond hw
+// being idle with full headroom.  Each step looks at the 1024 slots of 32 whole bitmap
+// words from the word that holds the candidate: lane l builds the violation bits of its
+// word (busy, short of headroom, or before the candidate).  The first clean run of p slots
+// is found from each word's clean slots at its start and end, the clean slots ending at
+// the previous word's end (a ballot and two shuffles), and, for p <= 32, the runs inside
+// one word; a clean run that reaches the step's end becomes the next step's candidate.
+// For p <= 512 (each step then advances at least 512 slots).  Returns `limit` as soon as
+// the answer cannot be below it.  Loads stay below hw <= Hcap (Hcap a multiple of 8).
+__device__ __forceinline__ int earliest_start_ins(const uint16_t *h, int hw, int t0, int p, uint32_t q2, int limit,
+                                                  int lane, const uint32_t *bm, int nw) {
+    int cur = t0;
+    for (;;) {
+        if (cur >= limit) return limit;
+        if (cur >= hw) return cur;  // idle with full headroom from there on
+        const int base = cur & ~31, s0 = base + 32 * lane;
+        uint32_t v = 0u;  // bit i: slot s0 + i violates
+        if (s0 < hw) {
+            v = bm[FFS_IX(s0 >> 5, nw)];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {  // four slots per load
+                const int sc = s0 + 4 * c;
+                if (sc < hw) {
+                    const uint2 w = *reinterpret_cast<const uint2 *>(h + sc);
+                    const uint32_t vx = ~((w.x | 0x80008000u) - q2), vy = ~((w.y | 0x80008000u) - q2);
+                    v |= (((vx >> 15) & 1u) | ((vx >> 30) & 2u) | ((vy >> 13) & 4u) | ((vy >> 28) & 8u)) << (4 * c);
+                }
+            }
+            if (cur > s0) v |= cur - s0 >= 32 ? 0xFFFFFFFFu : ((1u << (cur - s0)) - 1u);
+            if (hw - s0 < 32) v &= (1u << (hw - s0)) - 1u;
+        }
+        const int pre = v ? __ffs(v) - 1 : 32;  // clean slots at the word's start
+        const int suf = __clz(v);               // clean slots at its end (32 if v == 0)
+        // clean slots ending at this word's end: from the last word up to here with a violation
+        const unsigned upto = __ballot_sync(kFull, v != 0u) & (0xFFFFFFFFu >> (31 - lane));
+        const int j = upto ? 31 - __clz(upto) : 0;
+        const int sufj = __shfl_sync(kFull, suf, j);
+        const int E = upto ? sufj + 32 * (lane - j) : 32 * (lane + 1);
+        int Eprev = __shfl_up_sync(kFull, E, 1);
+        if (lane == 0) Eprev = 0;
+        int cand = INT_MAX;  // the first clean run of p slots this lane sees, in step coordinates
+        if (v != 0u) {
+            if (Eprev + pre >= p) cand = 32 * lane - Eprev;  // the run across the word's start
+            if (p <= 32) {                                  // runs inside the word
+                uint32_t r = ~v;
+                for (int have = 1; have < p;) {
+                    const int sft = min(have, p - have);
+                    r &= r >> sft;
+                    have += sft;
+                }
+                if (r) cand = min(cand, 32 * lane + __ffs(r) - 1);
+            }
+        }
+        if (lane == 31 && E >= p) cand = min(cand, 1024 - E);  // a run reaching the step's end
+        const unsigned best = __reduce_min_sync(kFull, (unsigned)cand);
+        if (best != (unsigned)INT_MAX) {
+            const int r = base + (int)best;
+            return r < limit ? r : limit;
+        }
+        cur = base + 1024 - __shfl_sync(kFull, E, 31);  // the clean run reaching the end, if any
+    }
+}
+
 template <bool INS = false, bool WIN = true>
 __device__ __forceinline__ int earliest_start(const uint16_t *h, int hw, int t0, int p, uint32_t q2,
                                               int limit, int lane, const uint32_t *bm = nullptr, int nw = 0) {
     if (!INS && WIN) return earliest_start_win(h, hw, t0, p, q2, limit, lane);
+    if (INS && p <= 512) return earliest_start_ins(h, hw, t0, p, q2, limit, lane, bm, nw);
     int run = t0;
     if (INS && run < limit) run = next_idle(bm, nw, run, lane);
     if (run >= limit) return limit;
