@@ -18,8 +18,20 @@ def test_library_exports_every_declared_function():
 
 
 def test_strerror_names_every_code():
-    for code in range(0, -9, -1):
+    for code in range(0, -10, -1):
         assert ffs.lib().ffs_strerror(code).decode() != "unknown status"
+
+
+def test_stop_requests_and_bounds_reader_validate_arguments():
+    """The early-stop calls reject a missing handle without touching a device, and an
+    ordinary build says that it does not check device indices."""
+    import ctypes as C
+    L = ffs.lib()
+    assert L.ga_batch_stop(None) == -1
+    assert L.ffs_service_stop_request(None, 1) == -1
+    assert L.ffs_debug_bounds_faults(None) == -1
+    n = C.c_uint32(7)
+    assert L.ffs_debug_bounds_faults(C.byref(n)) == -7 and n.value == 0
 
 
 def test_create_rejects_infeasible_and_bad_input():
