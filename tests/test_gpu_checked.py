@@ -35,6 +35,24 @@ for N, g, P in ((12, 3, 64), (40, 5, 128), (90, 6, 64)):
     ga.step(7)
     st = pop.read()
     assert np.array_equal(st["Y"], ga.Y[:, :ga.K]) and np.array_equal(st["obj"], ga.obj), N
+# unrelated machines (earliest completion) and idle-gap insertion, the other grouped and
+# one-step paths
+up = wl.unrelated_instance(rng, 30, 4, 2, 4, 60, 5, 25, 55)
+li, oi = ffs.Instance(up), oracle.Instance(up)
+Y, X = wl.random_chromosomes(rng, 33, oi.K, oi.gene_machines())
+out = li.decode(torch.from_numpy(Y).cuda(), torch.from_numpy(X).cuda(), order_mode=ffs.ORDER_STAGE,
+                mach_mode=ffs.MACH_EARLIEST)
+ref = [oi.decode(y, x, order_mode=oracle.ORDER_STAGE, mach_mode=oracle.MACH_EARLIEST)["obj"] for y, x in zip(Y, X)]
+assert np.array_equal(out["obj"].cpu().numpy(), np.array(ref)), "unrelated"
+prob = wl.random_instance(rng, 40, 4, 2, 4, 60, 3, 25, 50)
+li, oi = ffs.Instance(prob), oracle.Instance(prob)
+Y, X = wl.random_chromosomes(rng, 33, oi.K, oi.gene_machines())
+out = li.decode(torch.from_numpy(Y).cuda(), torch.from_numpy(X).cuda(), order_mode=ffs.ORDER_STAGE,
+                mach_mode=ffs.MACH_EARLIEST | ffs.PLACE_INSERT)
+ref = [oi.decode(y, x, order_mode=oracle.ORDER_STAGE, mach_mode=oracle.MACH_EARLIEST | oracle.PLACE_INSERT)["obj"]
+       for y, x in zip(Y, X)]
+assert np.array_equal(out["obj"].cpu().numpy(), np.array(ref)), "insertion"
+checked += 66
 faults = ffs.bounds_faults()
 assert faults == 0, faults
 print("checked build ok:", checked, "decodes and 3 GA runs, no index out of range")
