@@ -352,33 +352,6 @@ __device__ __forceinline__ void warp_copy_ind(int16_t *yd, int8_t *xd, const int
     }
 }
 
-// Two independent copies (src -> dst, src2 -> dst2, rows that do not overlap) in the same
-// chunks: every lane loads its share of both before storing any.
-template <int U = 4>
-__device__ __forceinline__ void warp_copy_two(int16_t *yd, int8_t *xd, const int16_t *ys, const int8_t *xs,
-                                              int16_t *yd2, int8_t *xd2, const int16_t *ys2, const int8_t *xs2,
-                                              int K, int lane) {
-#pragma unroll 1
-    for (int k0 = lane; k0 < K; k0 += 32 * U) {
-        const int n = K - k0;
-        uint32_t v[U], w[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (32 * u < n) {
-                v[u] = (uint16_t)__ldcg(ys + k0 + 32 * u) | ((uint32_t)(uint8_t)__ldcg(xs + k0 + 32 * u) << 16);
-                w[u] = (uint16_t)__ldcg(ys2 + k0 + 32 * u) | ((uint32_t)(uint8_t)__ldcg(xs2 + k0 + 32 * u) << 16);
-            }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (32 * u < n) {
-                yd[k0 + 32 * u] = (int16_t)(v[u] & 0xFFFFu);
-                xd[k0 + 32 * u] = (int8_t)(v[u] >> 16);
-                yd2[k0 + 32 * u] = (int16_t)(w[u] & 0xFFFFu);
-                xd2[k0 + 32 * u] = (int8_t)(w[u] >> 16);
-            }
-    }
-}
-
 // Best (largest fitness, lowest index) and worst (smallest fitness, lowest index) of an
 // island of at most 64 held in registers: lane l has slots l (f0, o0) and l + 32 (f1, o1),
 // lanes past the island LLONG_MIN / LLONG_MAX-free placeholders excluded by `h0`, `h1`.
