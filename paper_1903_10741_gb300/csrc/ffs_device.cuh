@@ -270,16 +270,22 @@ __device__ __forceinline__ int earliest_start_ins(const uint16_t *h, int hw, int
         const int base = cur & ~31, s0 = base + 32 * lane;
         uint32_t v = 0u;  // bit i: slot s0 + i violates
         if (s0 < hw) {
-            v = bm[FFS_IX(s0 >> 5, nw)];
+            uint32_t ok = 0u;  // bit i: slot s0 + i has headroom q (or lies at or past hw)
 #pragma unroll
             for (int c = 0; c < 8; ++c) {  // four slots per load
                 const int sc = s0 + 4 * c;
+                uint32_t n = 0xFu;
                 if (sc < hw) {
                     const uint2 w = *reinterpret_cast<const uint2 *>(h + sc);
-                    const uint32_t vx = ~((w.x | 0x80008000u) - q2), vy = ~((w.y | 0x80008000u) - q2);
-                    v |= (((vx >> 15) & 1u) | ((vx >> 30) & 2u) | ((vy >> 13) & 4u) | ((vy >> 28) & 8u)) << (4 * c);
+                    // bit 15 of each halfword of (h | 0x8000) - q: the slot has headroom q.
+                    // The bytes holding those bits, in slot order (bits 7, 15, 23, 31), then
+                    // a multiply whose partial products never overlap moves them to bits 28..31.
+                    const uint32_t t = __byte_perm((w.x | 0x80008000u) - q2, (w.y | 0x80008000u) - q2, 0x7531);
+                    n = ((t & 0x80808080u) * 0x00204081u) >> 28;
                 }
+                ok |= n << (4 * c);
             }
+            v = bm[FFS_IX(s0 >> 5, nw)] | ~ok;
             if (cur > s0) v |= cur - s0 >= 32 ? 0xFFFFFFFFu : ((1u << (cur - s0)) - 1u);
             if (hw - s0 < 32) v &= (1u << (hw - s0)) - 1u;
         }
